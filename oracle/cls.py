@@ -1,0 +1,139 @@
+"""Whole-problem CLS oracle -- test-only (see package docstring).
+
+Assignments are arrays x[v, r] (variable-major, restart-minor), r indexing
+independent restarts (Sec. 3.3: all batch elements iterate together).
+
+* objective / gradient -- Sec. 2.3, Eq. 5: F(x) = sum_c w_c FE_c(s_c o x_c)
+  (the paper's sum is unweighted: w_c = 1), dF/dx_v = sum over literals e on
+  v of w_c s_e dFE_c/dy_e.  FP64.
+* projected gradient step -- Sec. 2.3 (PGD on the cube Q^n): the step is
+  x' = clamp(x - lr*g, -1, 1), computed in FP32 as two roundings
+  (t = fl(lr*g), x' = fl(x - t)) so that it is reproducible bit for bit;
+  the clamp is IEEE fmax/fmin (NaN -> the bound); pinned variables
+  (partial assignment, Sec. 3.2) never move.
+* rounding -- Sec. 2.3 sign(X): a variable is True (-1) iff x < 0; +0, -0
+  and NaN round to False (+1).
+* score -- Sec. 2.3: sign(X) satisfies the formula iff sum_c FE_c = -m;
+  each constraint is satisfied iff its predicate holds on t, the number of
+  true literals at the rounded point.  Integer counts.
+* init -- x ~ U[-1, 1) from Philox4x64-10 (Salmon, Moraes, Dror, Shaw,
+  "Parallel random numbers: as easy as 1, 2, 3", SC'11), keyed by the seed,
+  counter (restart id, v div 4, 0, 0), output word v mod 4; x = (u >> 40) *
+  2^-23 - 1.  (Random draws are an input convention, not paper arithmetic.)
+"""
+import numpy as np
+
+from . import fe as _fe
+from . import spectra as _sp
+
+
+def literal_values(inst, X):
+    """y_e = s_e * x[v_e, r] for every literal e: array (nnz, R), FP64."""
+    X = np.asarray(X, dtype=np.float64)
+    return inst.lit_sign.astype(np.float64)[:, None] * X[inst.lit_var]
+
+
+def objective_grad(inst, X, spectra=None):
+    """Returns (obj[R], grad[n, R], fe_con[m, R]) in FP64.
+    fe_con[c] = FE_c (unweighted); obj = sum_c w_c fe_con[c]."""
+    X = np.asarray(X, dtype=np.float64)
+    n, R = X.shape
+    sps = spectra if spectra is not None else _sp.instance_spectra(inst)
+    Y = literal_values(inst, X)
+    fe_con = np.zeros((inst.m, R))
+    grad = np.zeros((n, R))
+    for c in range(inst.m):
+        a, b = int(inst.offsets[c]), int(inst.offsets[c + 1])
+        fe, g = _fe.fe_grad_dp(sps[c], Y[a:b])
+        fe_con[c] = fe
+        w = float(inst.weight[c])
+        for j in range(a, b):
+            grad[inst.lit_var[j]] += w * float(inst.lit_sign[j]) * g[j - a]
+    obj = (inst.weight.astype(np.float64)[:, None] * fe_con).sum(axis=0)
+    return obj, grad, fe_con
+
+
+def pgd_step(X, G, lr, fixed=None):
+    """One projected gradient step in FP32 (see module docstring)."""
+    X = np.asarray(X, dtype=np.float32)
+    G = np.asarray(G, dtype=np.float32)
+    t = np.float32(lr) * G                      # fl(lr * g)
+    # IEEE fmax/fmin (a NaN operand yields the other operand)
+    Xn = np.fmin(np.fmax(X - t, np.float32(-1.0)), np.float32(1.0))
+    if fixed is not None:
+        keep = np.asarray(fixed).astype(bool)
+        Xn[keep] = X[keep]
+    return Xn.astype(np.float32)
+
+
+def round_true(X):
+    """Boolean array: variable is True (x < 0) at the rounded point."""
+    return np.asarray(X, dtype=np.float32) < np.float32(0.0)
+
+
+def true_counts(inst, X):
+    """t[c, r] = number of true literals of constraint c at sign(X[:, r])."""
+    vt = round_true(X)                                   # (n, R)
+    lit_true = vt[inst.lit_var] ^ (inst.lit_sign < 0)[:, None]
+    cs = np.concatenate([np.zeros((1, lit_true.shape[1]), np.int64),
+                         np.cumsum(lit_true, axis=0, dtype=np.int64)])
+    return cs[inst.offsets[1:]] - cs[inst.offsets[:-1]]
+
+
+def score(inst, X, spectra=None):
+    """Returns (nsat[R] int64, wsat[R] float64, sat[m, R] bool)."""
+    t = true_counts(inst, X)
+    sps = spectra if spectra is not None else _sp.instance_spectra(inst)
+    sat = np.zeros(t.shape, dtype=bool)
+    for c in range(inst.m):
+        sat[c] = np.asarray(sps[c])[t[c]] == -1
+    nsat = sat.sum(axis=0).astype(np.int64)
+    wsat = (inst.weight.astype(np.float64)[:, None] * sat).sum(axis=0)
+    return nsat, wsat, sat
+
+
+def pack_bits(B):
+    """Pack a boolean (n, R) array into words[n, ceil(R/32)] uint32, bit
+    (r mod 32) of word r div 32 -- the bitset format of the library."""
+    B = np.asarray(B, dtype=bool)
+    n, R = B.shape
+    RW = (R + 31) // 32
+    pad = np.zeros((n, RW * 32), dtype=np.uint64)
+    pad[:, :R] = B
+    w = pad.reshape(n, RW, 32) << np.arange(32, dtype=np.uint64)
+    return w.sum(axis=2).astype(np.uint32)
+
+
+# --- Philox4x64-10 (Salmon et al., SC'11) --------------------------------
+_M0, _M1 = 0xD2E7470EE14C6C93, 0xCA5A826395121157
+_W0, _W1 = 0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B
+_MASK = (1 << 64) - 1
+
+
+def philox4x64(ctr, key, rounds=10):
+    """One Philox4x64 block: 4 counter words, 2 key words -> 4 words."""
+    x0, x1, x2, x3 = (int(c) & _MASK for c in ctr)
+    k0, k1 = (int(k) & _MASK for k in key)
+    for _ in range(rounds):
+        p0, p1 = _M0 * x0, _M1 * x2
+        x0, x1, x2, x3 = ((p1 >> 64) ^ x1 ^ k0, p1 & _MASK,
+                          (p0 >> 64) ^ x3 ^ k1, p0 & _MASK)
+        k0, k1 = (k0 + _W0) & _MASK, (k1 + _W1) & _MASK
+    return x0, x1, x2, x3
+
+
+def init_uniform(n, R, seed, r_offset=0, fixed=None, fixed_val=None):
+    """x[v, r] ~ U[-1, 1) as described in the module docstring; pinned
+    variables take fixed_val."""
+    X = np.empty((n, R), dtype=np.float32)
+    for r in range(R):
+        for q in range((n + 3) // 4):
+            words = philox4x64((r + r_offset, q, 0, 0), (seed, 0))
+            for j in range(4):
+                v = 4 * q + j
+                if v < n:
+                    X[v, r] = np.float32((words[j] >> 40) * 2.0 ** -23 - 1.0)
+    if fixed is not None:
+        f = np.asarray(fixed).astype(bool)
+        X[f] = np.asarray(fixed_val, dtype=np.float32)[f][:, None]
+    return X
