@@ -1,0 +1,309 @@
+"""Benchmark of the parallel-CLS hot path on one B300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config mixed|3sat|red0|red10|red50]
+
+A step is one full pass of the hot path over the batch: Walsh-Fourier FE and
+literal partials of every constraint, gradient accumulation through the
+variable-major transpose, projected step, rounding and exact scoring.  The
+metric is constraint-literal FE+grad evaluations per second (R * nnz per
+step).  Default workload: batched mixed symmetric PB, n = 5000, 20000 clauses
+(len 2..8), 2000 XOR (len 3..20), 500 cardinality (len 10..300), planted,
+4096 restarts, FP32.  Inputs are synthetic (seeded generators).
+
+--impl reference times the FP64 CPU oracle (the only reference that exists:
+the paper ships no code) on the same workload, a bounded sample of restarts
+per step, on this machine's host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2032.0
+# algorithmic FP32 flops per (literal, root) of the DFT evaluation: factor
+# (2 FMA), prefix complex product (2 MUL + 2 FMA), suffix complex product
+# (2 MUL + 2 FMA), gradient accumulation (2 FMA); FMA = 2 flops.
+FLOPS_PER_LIT_ROOT = 20
+
+
+def workload(name):
+    if name == "mixed":
+        return W.mixed_pb(), 4096, 0.1
+    if name == "3sat":
+        return W.random_ksat(), 64, 0.1
+    if name.startswith("red"):
+        red = {"red0": 0.0, "red10": 0.1, "red50": 0.5}[name]
+        return W.redundant_5sat(redundancy=red), 2048, 0.1
+    raise ValueError(name)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_step(inst, X, lr):
+    """One oracle step: FP64 objective/gradient, FP32 projected step, score."""
+    from oracle import cls as ocls
+    _, g, _ = ocls.objective_grad(inst, X.astype(np.float64))
+    Xn = ocls.pgd_step(X, g.astype(np.float32), lr, inst.fixed)
+    ocls.score(inst, Xn)
+    return Xn
+
+
+def time_cpu_oracle(inst, R_sample, lr, steps, budget_s=25.0):
+    X = W.uniform_points(inst.n, R_sample, seed=42)
+    t_all, done = 0.0, 0
+    for _ in range(max(1, steps)):
+        t0 = time.perf_counter()
+        X = cpu_oracle_step(inst, X, lr)
+        t_all += time.perf_counter() - t0
+        done += 1
+        if t_all > budget_s:
+            break
+    return t_all / done, done
+
+
+def threads_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args, rank, world):
+    inst, R, lr = workload(args.config)
+    if rank != 0:
+        return
+    R_sample = 8 if inst.nnz > 10000 else R
+    for _ in range(args.warmup if inst.nnz < 10000 else 0):
+        cpu_oracle_step(inst, W.uniform_points(inst.n, R_sample, 1), lr)
+    per_step, done = time_cpu_oracle(inst, R_sample, lr, args.steps)
+    value = R_sample * inst.nnz / per_step
+    line = {
+        "impl": "reference", "metric": "constraint-literal FE+grad evals/s",
+        "value": value, "unit": "literal-evals/s", "n_gpus": args.gpus, "steps": done,
+        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": inst.name, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
+                   "R": R, "lr": lr},
+        "cpu_baseline": {"value": value, "unit": "literal-evals/s", "cores": threads_used(),
+                         "kind": "oracle",
+                         "sample": f"{R_sample} of {R} restarts per step, {done} steps"},
+        "e2e": {"value": value, "unit": "literal-evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2606_06656_b300 import Problem
+    from paper_2606_06656_b300 import binding as B
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    inst, R, lr = workload(args.config)
+    p = Problem(inst)
+    info = p.info
+    x = p.init_uniform(R, seed=42, r_offset=rank * R)   # restarts sharded by global id
+    ws = p.workspace(R)
+    nsat = torch.empty(R, dtype=torch.int32, device="cuda")
+    wsat = torch.empty(R, dtype=torch.float64, device="cuda")
+    bits = torch.empty((inst.n, (R + 31) // 32), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.cls_step(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed (untimed) before each step
+    B.cls_profile_reset(p.handle)
+    B.cls_profile_enable(p.handle, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    B.cls_profile_enable(p.handle, False)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms_step = ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    kc_names = ["fe_thread", "fe_group_real", "fe_group_dft", "accum_step_round", "score",
+                "reduce", "init"]
+    kstats = {}
+    launches = 0
+    for kc, name in enumerate(kc_names):
+        n_l, t_ms = B.cls_profile_read(p.handle, kc)
+        launches += n_l
+        kstats[name] = {"launches_per_step": n_l / args.steps, "ms_per_step": t_ms / args.steps}
+    clocks = clk.summary()
+
+    # end to end through host buffers: H2D x0 (pinned), one step, D2H nsat
+    xh = x.detach().cpu().pin_memory()
+    nh = torch.empty(R, dtype=torch.int32).pin_memory()
+    hws = p.workspace(R, host_solve=True)
+    for _ in range(2):
+        B.cls_solve_host(p.handle, R, xh, lr, 1, nh, None, hws)
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        B.cls_solve_host(p.handle, R, xh, lr, 1, nh, None, hws)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    units = R * inst.nnz * world
+    value = units / (ms_step / 1e3)
+    # roofline of the dominant kernel class
+    dom = max(kstats, key=lambda k: kstats[k]["ms_per_step"])
+    pk = peaks()
+    if dom == "fe_group_dft":
+        flops = FLOPS_PER_LIT_ROOT * info["dft_lroots"] * R
+        t = kstats[dom]["ms_per_step"] / 1e3
+        peak = 2 * SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "k_fe_group<DFT>", "achieved": flops / t / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak,
+                "traffic": None,
+                "peak_source": "148 SMs x 128 FP32 lanes x 2 flops x 2032 MHz (max SM clock)"}
+    else:
+        nbytes = 4 * R * (inst.n * 3 + inst.nnz * 2)   # rough: x rw, P write+read, grad
+        t = kstats[dom]["ms_per_step"] / 1e3
+        peak = pk.get("hbm_gbs", 6400.0)
+        roof = {"bound": "hbm", "kernel": dom, "achieved": nbytes / t / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": nbytes / t / 1e9 / peak, "traffic": None}
+    cpu_t, cpu_steps = (None, 0)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        R_sample = 8 if inst.nnz > 10000 else R
+        cpu_t, cpu_steps = time_cpu_oracle(inst, R_sample, lr, 1 if inst.nnz > 10000 else 3)
+        cpu = {"value": R_sample * inst.nnz / cpu_t, "unit": "literal-evals/s",
+               "cores": threads_used(), "kind": "oracle",
+               "sample": f"{R_sample} of {R} restarts, {cpu_steps} step(s)"}
+    line = {
+        "metric": "constraint-literal FE+grad evals/s", "value": value,
+        "unit": "literal-evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": inst.name, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
+                   "R_per_gpu": R, "lr": lr, "parallelism": f"restart-replicas x{world}",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "e2e": {"value": units / e2e_s, "unit": "literal-evals/s",
+                "h2d_bytes_per_step": 4 * inst.n * R, "d2h_bytes_per_step": 4 * R},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "kernels": kstats,
+        "wall_s": wall,
+        "mean_nsat": float(nsat.float().mean().item()),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="mixed")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

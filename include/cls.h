@@ -1,0 +1,206 @@
+/*
+ * cls.h -- C ABI of the B300 (sm_103a) parallel Continuous Local Search
+ * hot path: batched evaluation of a weighted sum of symmetric pseudo-Boolean
+ * constraints' Walsh-Fourier expansions and their gradient, projected
+ * gradient steps, rounding to +-1 and exact satisfaction counts.
+ *
+ * Paper: "A Study of Parallel Continuous Local Search" (arXiv 2606.06656).
+ *   Sec. 2.1, Eq. 1  Walsh-Fourier expansion FE of a Boolean function on the
+ *                    cube Q^n = [-1,1]^n, True -> -1, False -> +1.
+ *   Sec. 2.1, Eq. 3  symmetric constraints: FE depends on the spectrum sp_t
+ *                    (t = number of true literals).
+ *   Sec. 2.2         constraint types AMO, EO, EK, NAE, XOR, CARD, OR.
+ *   Sec. 2.3, Eq. 5  objective: min sum_c FE_c(X) over Q^n; satisfied iff
+ *                    sum_c FE_c(sign X) = -m; projected gradient descent,
+ *                    evaluated through a DFT.
+ *   Sec. 3.3         many restarts iterate together in lockstep.
+ *
+ * Conventions shared by every call
+ *   - Return value: CLS_OK (0) or a negative CLS_ERR_* code; no call throws
+ *     or aborts.  cls_strerror() names a code; cls_last_error() returns the
+ *     calling thread's last detailed message (e.g. the CUDA error string).
+ *   - Assignments are FP32 arrays laid out variable-major, restart-minor:
+ *     x[v * R + r] is variable v of restart r (R restarts, 0 <= r < R).
+ *     Each variable row is therefore contiguous over restarts; this is the
+ *     layout every kernel reads coalesced.
+ *   - A literal with sign s on variable v has value y = s * x_v; it is true
+ *     at a corner when y == -1.
+ *   - "Device" pointers are CUDA global-memory pointers on the device the
+ *     problem was created on (e.g. torch tensor data_ptr()).  They are owned
+ *     by the caller; the library never frees them.  "Host" pointers are
+ *     ordinary CPU memory, read only during the call.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Every device
+ *     call only enqueues work on that stream and returns without
+ *     synchronising; it performs no allocation and no host<->device copy
+ *     except where stated (cls_problem_create, cls_solve_host), so it may be
+ *     captured into a CUDA graph.
+ *   - Scratch memory is supplied by the caller: ws must point to at least
+ *     cls_workspace_size() bytes of device memory, 256-byte aligned.
+ */
+#ifndef CLS_B300_H
+#define CLS_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define CLS_OK               0
+#define CLS_ERR_INVALID     -1  /* bad argument or malformed constraint set  */
+#define CLS_ERR_CUDA        -2  /* a CUDA runtime call or launch failed      */
+#define CLS_ERR_NOMEM       -3  /* device or host allocation failed          */
+#define CLS_ERR_UNSUPPORTED -4  /* no usable sm_103 device                   */
+#define CLS_ERR_WORKSPACE   -5  /* workspace missing, too small or unaligned */
+
+/* ---- constraint types (Sec. 2.2; Table 2 PB forms; t = # true literals) */
+#define CLS_OR        0  /* t >= 1                        (disjunction)      */
+#define CLS_XOR       1  /* t odd                                           */
+#define CLS_CARD_GE   2  /* t >= k   (cardinality, at-least-k)               */
+#define CLS_CARD_LE   3  /* t <= k   (at-most-k)                             */
+#define CLS_NAE       4  /* 0 < t < L (not-all-equal)                        */
+#define CLS_EO        5  /* t == 1   (exactly-one)                           */
+#define CLS_EK        6  /* t == k   (exactly-k)                             */
+#define CLS_AMO       7  /* t <= 1   (at-most-one)                           */
+#define CLS_SPECTRUM  8  /* explicit spectrum sp_t, t = 0..L (Eq. 3)         */
+
+#define CLS_MAX_LEN 1024 /* longest constraint accepted (literals)           */
+
+typedef struct cls_problem cls_problem; /* opaque, owned by the library      */
+
+/* Validate a constraint set without touching a GPU (Sec. 2.2 / 2.3).
+ *   n_vars   number of variables n >= 0
+ *   n_cons   number of constraints m >= 0
+ *   offsets  host int32[m+1]: constraint c owns literals offsets[c] ..
+ *            offsets[c+1]-1; offsets[0] == 0, non-decreasing,
+ *            1 <= length <= CLS_MAX_LEN
+ *   lit_var  host int32[nnz]: variable of each literal, 0 <= v < n, no
+ *            variable twice in one constraint
+ *   lit_sign host int8[nnz]: +1 (positive literal) or -1 (negated)
+ *   type     host int32[m]: CLS_OR .. CLS_SPECTRUM
+ *   k        host int32[m]: threshold, 0 <= k <= L, for CARD_GE, CARD_LE
+ *            and EK; ignored for the other types (may be NULL if none of
+ *            those types occurs)
+ *   weight   host float[m], finite (NULL = all 1; the paper's sum is
+ *            unweighted)
+ *   spectra  host int8: for each CLS_SPECTRUM constraint in order, L+1
+ *            entries in {-1,+1} (sp_t = -1 where the constraint holds); NULL
+ *            if no such constraint
+ *   fixed    host uint8[n] or NULL: 1 pins the variable (partial assignment,
+ *            Sec. 3.2); pinned variables never move in a step
+ *   fixed_val host float[n] or NULL: the pinned value (-1 or +1) of each
+ *            pinned variable; required when fixed is given
+ * Returns CLS_OK or CLS_ERR_INVALID.  Errors are reported for the first
+ * offending item through cls_last_error(). */
+int cls_problem_check(int32_t n_vars, int32_t n_cons, const int32_t* offsets,
+                      const int32_t* lit_var, const int8_t* lit_sign,
+                      const int32_t* type, const int32_t* k, const float* weight,
+                      const int8_t* spectra, const uint8_t* fixed,
+                      const float* fixed_val);
+
+/* Build the device-resident problem on the current CUDA device: validate
+ * (as cls_problem_check), compute every constraint's spectrum and its
+ * Fourier tables in FP64 (Eq. 3, evaluated at the L+1 roots of unity,
+ * Sec. 2.3), the variable-major transpose of the literal list, the kernel
+ * work lists, and copy them to the device (synchronously).  The host arrays
+ * are copied; the caller keeps ownership.  On success *out receives a handle
+ * to free with cls_problem_destroy.  Errors: CLS_ERR_INVALID,
+ * CLS_ERR_UNSUPPORTED (no sm_103 device), CLS_ERR_NOMEM, CLS_ERR_CUDA; *out
+ * is left NULL on error. */
+int cls_problem_create(int32_t n_vars, int32_t n_cons, const int32_t* offsets,
+                       const int32_t* lit_var, const int8_t* lit_sign,
+                       const int32_t* type, const int32_t* k, const float* weight,
+                       const int8_t* spectra, const uint8_t* fixed,
+                       const float* fixed_val, cls_problem** out);
+
+/* Free a problem (NULL is accepted).  Synchronises the device first. */
+int cls_problem_destroy(cls_problem* p);
+
+/* Problem facts for callers: sizes and the per-path constraint counts.
+ *   info[0] n, info[1] m, info[2] nnz, info[3] # constraints on the
+ *   thread-per-(constraint, restart) product path (OR/XOR/NAE, L <= 32),
+ *   info[4] # on the lane-group real-product path (OR/XOR/NAE, L > 32),
+ *   info[5] # on the lane-group DFT path (all other types), info[6] number
+ *   of DFT roots summed over DFT constraints, info[7] sum over DFT
+ *   constraints of L * roots.  info must hold 8 int64. */
+int cls_problem_info(const cls_problem* p, int64_t* info);
+
+/* Bytes of device workspace the compute calls need for R restarts. */
+int cls_workspace_size(const cls_problem* p, int32_t R, size_t* bytes);
+
+/* x[v*R + r] ~ U[-1, 1) for r = 0..R-1 from Philox4x64-10 (Salmon et al.,
+ * SC'11) with key (seed, 0) and counter (r + r_offset, v / 4, 0, 0), output
+ * word v % 4, x = (word >> 40) * 2^-23 - 1; pinned variables get their
+ * fixed value.  r_offset lets a shard of restarts reproduce the same points
+ * as one run over all restarts.  x: device float[n*R]. */
+int cls_init_uniform(const cls_problem* p, int32_t R, uint64_t seed,
+                     int64_t r_offset, float* x, void* stream);
+
+/* Objective and gradient at x (Sec. 2.3, Eq. 5 with weights):
+ *   obj[r]        = sum_c w_c FE_c(s_c o x_r)            (device float[R] or NULL)
+ *   grad[v*R+r]   = dF/dx_v at restart r                 (device float[n*R] or NULL)
+ *   fe_con[c*R+r] = FE_c at restart r, unweighted        (device float[m*R] or NULL)
+ * FE_c and its literal partials come from the DFT of the constraint's
+ * spectrum (Sec. 2.3; Eq. 3 basis), computed in FP32; partials are summed
+ * per variable in a fixed order (deterministic).  x: device float[n*R]. */
+int cls_eval(const cls_problem* p, int32_t R, const float* x, float* obj,
+             float* grad, float* fe_con, void* ws, size_t ws_bytes, void* stream);
+
+/* Projected gradient step (Sec. 2.3, PGD on Q^n) with a given gradient:
+ * x <- min(max(fl(x - fl(lr * grad)), -1), 1) for free variables (pinned
+ * ones are left as they are), then, if bits is not NULL, writes the rounded
+ * assignment (see cls_round_score).  x: device float[n*R] updated in place;
+ * grad: device float[n*R]; bits: device uint32[n*ceil(R/32)] or NULL. */
+int cls_pgd_update(const cls_problem* p, int32_t R, float* x, const float* grad,
+                   float lr, uint32_t* bits, void* stream);
+
+/* Round and score (Sec. 2.3): variable v of restart r is True iff
+ * x[v*R+r] < 0 (so +0, -0 and NaN are False).  bits[v*RW + r/32] bit r%32
+ * holds that truth value (RW = ceil(R/32); device uint32[n*RW], may be NULL
+ * to use workspace).  Constraint c is satisfied iff its predicate holds on
+ * t = number of its true literals; nsat[r] = # satisfied constraints
+ * (device int32[R]), wsat[r] = sum of their weights in FP64 (device
+ * double[R] or NULL).  Exact integer work. */
+int cls_round_score(const cls_problem* p, int32_t R, const float* x,
+                    uint32_t* bits, int32_t* nsat, double* wsat, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* n_steps full CLS steps on x in place (Sec. 2.3): evaluate the gradient,
+ * take the projected step with rate lr, round and score.  After the call
+ * bits/nsat/wsat (each may be NULL) describe the final rounded point.
+ * x: device float[n*R].  n_steps >= 0. */
+int cls_step(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
+             uint32_t* bits, int32_t* nsat, double* wsat, void* ws,
+             size_t ws_bytes, void* stream);
+
+/* End-to-end solve from HOST buffers: copies x0 (host float[n*R], pinned
+ * memory recommended) to the device workspace, runs n_steps as cls_step,
+ * and copies the final nsat (host int32[R]) and x (host float[n*R], may be
+ * NULL) back, all on stream; synchronises the stream before returning.
+ * ws must hold cls_workspace_size() + 4*n*R + 4*R + 8*R bytes (see
+ * cls_solve_host_workspace_size). */
+int cls_solve_host_workspace_size(const cls_problem* p, int32_t R, size_t* bytes);
+int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host,
+                   float lr, int32_t n_steps, int32_t* nsat_host,
+                   float* x_host, void* ws, size_t ws_bytes, void* stream);
+
+/* Per-kernel timing (tracing): when enabled, each kernel launch of the
+ * compute calls is bracketed by CUDA events on its stream; cls_profile_read
+ * synchronises and returns, for kernel class kc (0 = thread-path FE+grad,
+ * 1 = lane-group real FE+grad, 2 = lane-group DFT FE+grad, 3 = gradient
+ * accumulate + step + round, 4 = score, 5 = reductions, 6 = init), the
+ * number of launches and their summed duration in ms since the last reset.
+ * Profiling must be off while a stream is being captured. */
+int cls_profile_enable(cls_problem* p, int on);
+int cls_profile_read(cls_problem* p, int kc, int64_t* launches, double* total_ms);
+int cls_profile_reset(cls_problem* p);
+
+const char* cls_strerror(int code);
+const char* cls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLS_B300_H */

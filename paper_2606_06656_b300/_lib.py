@@ -1,0 +1,72 @@
+"""ctypes loader for libcls_b300.so (the C ABI of include/cls.h).
+
+The library is built in-tree (paper_2606_06656_b300/csrc/build.py).  There is
+no fallback: if the shared library is missing or fails to load, every call
+raises.
+"""
+import ctypes as C
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libcls_b300.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "cls.h")
+
+_lib = None
+
+i32, i64, u64, f32, vp, sz = C.c_int32, C.c_int64, C.c_uint64, C.c_float, C.c_void_p, C.c_size_t
+P = C.POINTER
+
+SIGNATURES = {
+    "cls_problem_check": (i32, [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+    "cls_problem_create": (i32, [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
+    "cls_problem_destroy": (i32, [vp]),
+    "cls_problem_info": (i32, [vp, P(i64)]),
+    "cls_workspace_size": (i32, [vp, i32, P(sz)]),
+    "cls_init_uniform": (i32, [vp, i32, u64, i64, vp, vp]),
+    "cls_eval": (i32, [vp, i32, vp, vp, vp, vp, vp, sz, vp]),
+    "cls_pgd_update": (i32, [vp, i32, vp, vp, f32, vp, vp]),
+    "cls_round_score": (i32, [vp, i32, vp, vp, vp, vp, vp, sz, vp]),
+    "cls_step": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp, sz, vp]),
+    "cls_solve_host_workspace_size": (i32, [vp, i32, P(sz)]),
+    "cls_solve_host": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, sz, vp]),
+    "cls_profile_enable": (i32, [vp, i32]),
+    "cls_profile_read": (i32, [vp, i32, P(i64), P(C.c_double)]),
+    "cls_profile_reset": (i32, [vp]),
+    "cls_strerror": (C.c_char_p, [i32]),
+    "cls_last_error": (C.c_char_p, []),
+}
+
+
+class ClsError(RuntimeError):
+    def __init__(self, code, fn, msg):
+        super().__init__(f"{fn} failed with {code}: {msg}")
+        self.code = code
+
+
+def header_symbols():
+    """Names of the functions declared in include/cls.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(cls_\w+)\s*\(", txt, re.M)))
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2606_06656_b300.csrc.build` (no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def check(rc, fn):
+    if rc != 0:
+        lib = load()
+        raise ClsError(rc, fn, (lib.cls_last_error() or b"").decode())
+    return rc

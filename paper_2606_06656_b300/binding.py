@@ -1,0 +1,149 @@
+"""Thin Python binding over the C ABI (include/cls.h): argument marshalling
+only.  Every computation runs in the CUDA library; PyTorch provides device
+memory and the current stream.
+
+Function names follow the C ABI.  Assignments are torch float32 CUDA tensors
+of shape (n, R) (variable-major, restart-minor), i.e. x[v, r].
+"""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+
+i64 = C.c_int64
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        return C.c_void_p(a.data_ptr()) if a.numel() else None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p) if a.size else None
+    raise TypeError(type(a))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _arrays(inst):
+    """Contiguous host arrays of a constraint set (workloads.Instance-like)."""
+    a = dict(
+        offsets=np.ascontiguousarray(inst.offsets, dtype=np.int32),
+        lit_var=np.ascontiguousarray(inst.lit_var, dtype=np.int32),
+        lit_sign=np.ascontiguousarray(inst.lit_sign, dtype=np.int8),
+        ctype=np.ascontiguousarray(inst.ctype, dtype=np.int32),
+        k=np.ascontiguousarray(inst.k, dtype=np.int32),
+        weight=np.ascontiguousarray(inst.weight, dtype=np.float32),
+        spectra=None if getattr(inst, "spectra", None) is None
+        else np.ascontiguousarray(inst.spectra, dtype=np.int8),
+        fixed=None if getattr(inst, "fixed", None) is None
+        else np.ascontiguousarray(inst.fixed, dtype=np.uint8),
+        fixed_val=None if getattr(inst, "fixed_val", None) is None
+        else np.ascontiguousarray(inst.fixed_val, dtype=np.float32),
+    )
+    return a
+
+
+def cls_problem_check(inst):
+    lib = _lib.load()
+    a = _arrays(inst)
+    rc = lib.cls_problem_check(int(inst.n), len(a["offsets"]) - 1, _ptr(a["offsets"]),
+                               _ptr(a["lit_var"]), _ptr(a["lit_sign"]), _ptr(a["ctype"]),
+                               _ptr(a["k"]), _ptr(a["weight"]), _ptr(a["spectra"]),
+                               _ptr(a["fixed"]), _ptr(a["fixed_val"]))
+    return rc, (lib.cls_last_error() or b"").decode()
+
+
+def cls_problem_create(inst):
+    lib = _lib.load()
+    a = _arrays(inst)
+    h = C.c_void_p()
+    rc = lib.cls_problem_create(int(inst.n), len(a["offsets"]) - 1, _ptr(a["offsets"]),
+                                _ptr(a["lit_var"]), _ptr(a["lit_sign"]), _ptr(a["ctype"]),
+                                _ptr(a["k"]), _ptr(a["weight"]), _ptr(a["spectra"]),
+                                _ptr(a["fixed"]), _ptr(a["fixed_val"]), C.byref(h))
+    _lib.check(rc, "cls_problem_create")
+    return h
+
+
+def cls_problem_destroy(h):
+    if h:
+        _lib.check(_lib.load().cls_problem_destroy(h), "cls_problem_destroy")
+
+
+def cls_problem_info(h):
+    info = (i64 * 8)()
+    _lib.check(_lib.load().cls_problem_info(h, info), "cls_problem_info")
+    keys = ["n", "m", "nnz", "n_thread", "n_group_real", "n_group_dft", "dft_roots",
+            "dft_lroots"]
+    return dict(zip(keys, [int(v) for v in info]))
+
+
+def cls_workspace_size(h, R):
+    b = C.c_size_t()
+    _lib.check(_lib.load().cls_workspace_size(h, int(R), C.byref(b)), "cls_workspace_size")
+    return int(b.value)
+
+
+def cls_solve_host_workspace_size(h, R):
+    b = C.c_size_t()
+    _lib.check(_lib.load().cls_solve_host_workspace_size(h, int(R), C.byref(b)),
+               "cls_solve_host_workspace_size")
+    return int(b.value)
+
+
+def cls_init_uniform(h, R, seed, r_offset, x, stream=None):
+    _lib.check(_lib.load().cls_init_uniform(h, int(R), int(seed), int(r_offset), _ptr(x),
+                                            _stream(stream)), "cls_init_uniform")
+
+
+def cls_eval(h, R, x, obj, grad, fe_con, ws, stream=None):
+    _lib.check(_lib.load().cls_eval(h, int(R), _ptr(x), _ptr(obj), _ptr(grad), _ptr(fe_con),
+                                    _ptr(ws), ws.numel() if ws is not None else 0,
+                                    _stream(stream)), "cls_eval")
+
+
+def cls_pgd_update(h, R, x, grad, lr, bits, stream=None):
+    _lib.check(_lib.load().cls_pgd_update(h, int(R), _ptr(x), _ptr(grad), float(lr), _ptr(bits),
+                                          _stream(stream)), "cls_pgd_update")
+
+
+def cls_round_score(h, R, x, bits, nsat, wsat, ws, stream=None):
+    _lib.check(_lib.load().cls_round_score(h, int(R), _ptr(x), _ptr(bits), _ptr(nsat),
+                                           _ptr(wsat), _ptr(ws),
+                                           ws.numel() if ws is not None else 0, _stream(stream)),
+               "cls_round_score")
+
+
+def cls_step(h, R, x, lr, n_steps, bits, nsat, wsat, ws, stream=None):
+    _lib.check(_lib.load().cls_step(h, int(R), _ptr(x), float(lr), int(n_steps), _ptr(bits),
+                                    _ptr(nsat), _ptr(wsat), _ptr(ws),
+                                    ws.numel() if ws is not None else 0, _stream(stream)),
+               "cls_step")
+
+
+def cls_solve_host(h, R, x0_host, lr, n_steps, nsat_host, x_host, ws, stream=None):
+    _lib.check(_lib.load().cls_solve_host(h, int(R), _ptr(x0_host), float(lr), int(n_steps),
+                                          _ptr(nsat_host), _ptr(x_host), _ptr(ws),
+                                          ws.numel() if ws is not None else 0, _stream(stream)),
+               "cls_solve_host")
+
+
+def cls_profile_enable(h, on):
+    _lib.check(_lib.load().cls_profile_enable(h, 1 if on else 0), "cls_profile_enable")
+
+
+def cls_profile_reset(h):
+    _lib.check(_lib.load().cls_profile_reset(h), "cls_profile_reset")
+
+
+def cls_profile_read(h, kc):
+    n, ms = C.c_int64(), C.c_double()
+    _lib.check(_lib.load().cls_profile_read(h, int(kc), C.byref(n), C.byref(ms)),
+               "cls_profile_read")
+    return int(n.value), float(ms.value)

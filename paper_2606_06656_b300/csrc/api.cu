@@ -1,0 +1,517 @@
+// api.cu -- the extern "C" boundary (include/cls.h): argument checks, device
+// residency of the problem, workspace carving and the per-call kernel
+// sequences.  No exceptions or aborts cross the boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cls.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_err(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_err(cudaError_t e, const char* where) {
+  return set_err(CLS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CLS_CUDA_TRY(expr, where)          \
+  do {                                     \
+    cudaError_t e_ = (expr);               \
+    if (e_ != cudaSuccess) {               \
+      (void)cudaGetLastError();            \
+      return cuda_err(e_, where);          \
+    }                                      \
+  } while (0)
+
+struct EventHook : cls::LaunchHook {
+  struct Rec {
+    int kc;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t pending = nullptr;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void before(int, cudaStream_t s) override {
+    pending = get();
+    cudaEventRecord(pending, s);
+  }
+  void after(int kc, cudaStream_t s) override {
+    cudaEvent_t b = get();
+    cudaEventRecord(b, s);
+    recs.push_back({kc, pending, b});
+    pending = nullptr;
+  }
+  void reset() {
+    for (auto& r : recs) {
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  ~EventHook() override {
+    for (auto& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace
+
+struct cls_problem {
+  int device = 0;
+  cls::HostPlan host;
+  cls::DevPlan dev;
+  std::vector<void*> allocations;
+  EventHook* hook = nullptr;  // non-null while profiling
+  EventHook events;
+};
+
+namespace {
+
+template <typename T>
+int upload(cls_problem* p, const std::vector<T>& v, T** out) {
+  *out = nullptr;
+  if (v.empty()) return CLS_OK;
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, v.size() * sizeof(T));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return set_err(e == cudaErrorMemoryAllocation ? CLS_ERR_NOMEM : CLS_ERR_CUDA,
+                   std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  p->allocations.push_back(ptr);
+  CLS_CUDA_TRY(cudaMemcpy(ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice),
+               "cudaMemcpy");
+  *out = static_cast<T*>(ptr);
+  return CLS_OK;
+}
+
+void free_problem(cls_problem* p) {
+  for (void* a : p->allocations) cudaFree(a);
+  p->allocations.clear();
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Workspace layout for R restarts.
+struct Layout {
+  int R = 0, Rp = 0, RT = 0;
+  int nch = 1, chunk = 1;
+  size_t P = 0, fe = 0, bits = 0, nsat_part = 0, wsat_part = 0, obj_part = 0, nsat = 0,
+         total = 0;
+};
+
+Layout layout_for(const cls_problem* p, int R) {
+  Layout L;
+  L.R = R;
+  L.RT = (R + 31) / 32;
+  L.Rp = L.RT * 32;
+  const int m = p->host.m;
+  // enough (restart tile x chunk) blocks to fill the GPU in the reductions
+  int want = std::max(1, (148 * 4 + L.RT - 1) / std::max(1, L.RT));
+  want = std::min(want, std::max(1, (m + 7) / 8));
+  L.chunk = std::max(1, (m + want - 1) / want);
+  L.nch = std::max(1, (m + L.chunk - 1) / L.chunk);
+  size_t off = 0;
+  auto take = [&off](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  L.P = take((size_t)p->host.nnz * L.Rp * sizeof(float));
+  L.fe = take((size_t)m * L.Rp * sizeof(float));
+  L.bits = take((size_t)p->host.n * L.RT * sizeof(uint32_t));
+  L.nsat_part = take((size_t)L.nch * L.Rp * sizeof(int32_t));
+  L.wsat_part = take((size_t)L.nch * L.Rp * sizeof(double));
+  L.obj_part = take((size_t)L.nch * L.Rp * sizeof(double));
+  L.nsat = take((size_t)L.Rp * sizeof(int32_t));
+  L.total = off;
+  return L;
+}
+
+int check_ws(const Layout& L, void* ws, size_t ws_bytes) {
+  if (L.total == 0) return CLS_OK;
+  if (!ws) return set_err(CLS_ERR_WORKSPACE, "workspace pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign != 0)
+    return set_err(CLS_ERR_WORKSPACE, "workspace is not 256-byte aligned");
+  if (ws_bytes < L.total)
+    return set_err(CLS_ERR_WORKSPACE, "workspace too small: need " + std::to_string(L.total) +
+                                          " bytes, got " + std::to_string(ws_bytes));
+  return CLS_OK;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+int check_device(cls_problem* p) {
+  int dev = 0;
+  CLS_CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaDeviceProp prop;
+  CLS_CUDA_TRY(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return set_err(CLS_ERR_UNSUPPORTED, std::string("device ") + prop.name + " is sm_" +
+                                            std::to_string(prop.major) +
+                                            std::to_string(prop.minor) +
+                                            "; this library is built for sm_103a (B300)");
+  p->device = dev;
+  return CLS_OK;
+}
+
+int check_R(const cls_problem* p, int32_t R) {
+  if (!p) return set_err(CLS_ERR_INVALID, "problem is NULL");
+  if (R < 0) return set_err(CLS_ERR_INVALID, "R must be >= 0");
+  if (R > 65535 * 32) return set_err(CLS_ERR_INVALID, "R must be <= 2097120");
+  if ((int64_t)R * std::max<int64_t>(1, p->host.n) > (int64_t)1 << 40)
+    return set_err(CLS_ERR_INVALID, "R * n too large");
+  return CLS_OK;
+}
+
+cls::LaunchHook* hook_of(const cls_problem* p) { return p->hook; }
+
+// One full CLS step: FE + partials, accumulate + step + round, score.
+int run_step(const cls_problem* p, const Layout& L, float* x, float lr, uint32_t* bits,
+             int32_t* nsat, double* wsat, void* ws, cudaStream_t s, bool score) {
+  float* P = at<float>(ws, L.P);
+  CLS_CUDA_TRY(cls::launch_fe(p->dev, L.R, L.Rp, x, P, nullptr, 0, s, hook_of(p)), "fe kernels");
+  CLS_CUDA_TRY(cls::launch_accum_step(p->dev, L.R, L.Rp, P, x, lr, true, nullptr, bits, s,
+                                      hook_of(p)),
+               "accumulate/step kernel");
+  if (score)
+    CLS_CUDA_TRY(cls::launch_score(p->dev, L.R, L.Rp, L.nch, L.chunk, bits,
+                                   at<int32_t>(ws, L.nsat_part), at<double>(ws, L.wsat_part),
+                                   nsat, wsat, s, hook_of(p)),
+                 "score kernels");
+  return CLS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cls_problem_check(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
+                      const int8_t* lit_sign, const int32_t* type, const int32_t* k,
+                      const float* weight, const int8_t* spectra, const uint8_t* fixed,
+                      const float* fixed_val) {
+  std::string msg;
+  int rc = cls::build_plan(n, m, offsets, lit_var, lit_sign, type, k, weight, spectra, fixed,
+                           fixed_val, cls::default_tuning(), true, nullptr, &msg);
+  if (rc != 0) return set_err(CLS_ERR_INVALID, msg);
+  return CLS_OK;
+}
+
+int cls_problem_create(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
+                       const int8_t* lit_sign, const int32_t* type, const int32_t* k,
+                       const float* weight, const int8_t* spectra, const uint8_t* fixed,
+                       const float* fixed_val, cls_problem** out) {
+  if (!out) return set_err(CLS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  cls_problem* p = new (std::nothrow) cls_problem();
+  if (!p) return set_err(CLS_ERR_NOMEM, "host allocation failed");
+  std::string msg;
+  int rc;
+  try {
+    rc = cls::build_plan(n, m, offsets, lit_var, lit_sign, type, k, weight, spectra, fixed,
+                         fixed_val, cls::default_tuning(), false, &p->host, &msg);
+  } catch (const std::bad_alloc&) {
+    delete p;
+    return set_err(CLS_ERR_NOMEM, "host allocation failed while building the problem");
+  }
+  if (rc != 0) {
+    delete p;
+    return set_err(CLS_ERR_INVALID, msg);
+  }
+  rc = check_device(p);
+  if (rc != CLS_OK) {
+    delete p;
+    return rc;
+  }
+  static bool attrs_set = false;
+  if (!attrs_set) {
+    cudaError_t e = cls::set_kernel_attributes();
+    if (e != cudaSuccess) {
+      delete p;
+      (void)cudaGetLastError();
+      return cuda_err(e, "cudaFuncSetAttribute");
+    }
+    attrs_set = true;
+  }
+  const cls::HostPlan& H = p->host;
+  cls::DevPlan& D = p->dev;
+  D.n = H.n;
+  D.m = H.m;
+  D.nnz = H.nnz;
+  int r2 = CLS_OK;
+  auto up = [&](auto& vec, auto** dst) {
+    if (r2 == CLS_OK) r2 = upload(p, vec, dst);
+  };
+  up(H.lit_var, &D.lit_var);
+  up(H.lit_sgn, &D.lit_sgn);
+  up(H.lit_dst, &D.lit_dst);
+  up(H.voff, &D.voff);
+  up(H.fe, &D.fe);
+  up(H.score, &D.score);
+  up(H.satbits, &D.satbits);
+  up(H.root_tab, &D.root_tab);
+  up(H.coef_tab, &D.coef_tab);
+  up(H.fixed, &D.fixed);
+  up(H.fixed_val, &D.fixed_val);
+  for (int t = 0; t < 2; ++t) {
+    up(H.thread_list[t], &D.thread_list[t]);
+    D.thread_count[t] = (int32_t)H.thread_list[t].size();
+  }
+  for (int g = 0; g < cls::kNumGroupCfg; ++g) {
+    up(H.group_list[g], &D.group_list[g]);
+    D.group_count[g] = (int32_t)H.group_list[g].size();
+    D.group_maxL[g] = H.group_list[g].empty() ? 0 : H.fe[H.group_list[g][0]].L;
+  }
+  if (r2 != CLS_OK) {
+    free_problem(p);
+    delete p;
+    return r2;
+  }
+  *out = p;
+  return CLS_OK;
+}
+
+int cls_problem_destroy(cls_problem* p) {
+  if (!p) return CLS_OK;
+  cudaDeviceSynchronize();
+  free_problem(p);
+  delete p;
+  return CLS_OK;
+}
+
+int cls_problem_info(const cls_problem* p, int64_t* info) {
+  if (!p || !info) return set_err(CLS_ERR_INVALID, "NULL argument");
+  const cls::HostPlan& H = p->host;
+  info[0] = H.n;
+  info[1] = H.m;
+  info[2] = H.nnz;
+  info[3] = H.n_thread;
+  info[4] = H.n_group_real;
+  info[5] = H.n_group_dft;
+  info[6] = H.dft_roots;
+  info[7] = H.dft_lroots;
+  return CLS_OK;
+}
+
+int cls_workspace_size(const cls_problem* p, int32_t R, size_t* bytes) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (!bytes) return set_err(CLS_ERR_INVALID, "bytes is NULL");
+  *bytes = layout_for(p, R).total;
+  return CLS_OK;
+}
+
+int cls_init_uniform(const cls_problem* p, int32_t R, uint64_t seed, int64_t r_offset, float* x,
+                     void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (!x && R > 0 && p->host.n > 0) return set_err(CLS_ERR_INVALID, "x is NULL");
+  if (r_offset < 0) return set_err(CLS_ERR_INVALID, "r_offset must be >= 0");
+  CLS_CUDA_TRY(cls::launch_init(p->dev, R, seed, r_offset, x, (cudaStream_t)stream, hook_of(p)),
+               "init kernel");
+  return CLS_OK;
+}
+
+int cls_eval(const cls_problem* p, int32_t R, const float* x, float* obj, float* grad,
+             float* fe_con, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (R == 0) return CLS_OK;
+  if (!x && p->host.n > 0) return set_err(CLS_ERR_INVALID, "x is NULL");
+  Layout L = layout_for(p, R);
+  rc = check_ws(L, ws, ws_bytes);
+  if (rc != CLS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* P = at<float>(ws, L.P);
+  float* fe = fe_con;
+  int ldf = R;
+  if (!fe && obj) {
+    fe = at<float>(ws, L.fe);
+    ldf = L.Rp;
+  }
+  CLS_CUDA_TRY(cls::launch_fe(p->dev, R, L.Rp, x, P, fe, ldf, s, hook_of(p)), "fe kernels");
+  if (grad)
+    CLS_CUDA_TRY(cls::launch_accum_step(p->dev, R, L.Rp, P, nullptr, 0.f, false, grad, nullptr,
+                                        s, hook_of(p)),
+                 "accumulate kernel");
+  if (obj)
+    CLS_CUDA_TRY(cls::launch_obj(p->dev, R, L.Rp, L.nch, L.chunk, fe, ldf,
+                                 at<double>(ws, L.obj_part), obj, s, hook_of(p)),
+                 "objective reduction");
+  return CLS_OK;
+}
+
+int cls_pgd_update(const cls_problem* p, int32_t R, float* x, const float* grad, float lr,
+                   uint32_t* bits, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (R == 0 || p->host.n == 0) return CLS_OK;
+  if (!x || !grad) return set_err(CLS_ERR_INVALID, "x and grad are required");
+  CLS_CUDA_TRY(cls::launch_pgd(p->dev, R, x, grad, lr, bits, (cudaStream_t)stream, hook_of(p)),
+               "step kernel");
+  return CLS_OK;
+}
+
+int cls_round_score(const cls_problem* p, int32_t R, const float* x, uint32_t* bits,
+                    int32_t* nsat, double* wsat, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (R == 0) return CLS_OK;
+  if (!x && p->host.n > 0) return set_err(CLS_ERR_INVALID, "x is NULL");
+  Layout L = layout_for(p, R);
+  rc = check_ws(L, ws, ws_bytes);
+  if (rc != CLS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* b = bits ? bits : at<uint32_t>(ws, L.bits);
+  CLS_CUDA_TRY(cls::launch_round(p->dev, R, x, b, s, hook_of(p)), "round kernel");
+  CLS_CUDA_TRY(cls::launch_score(p->dev, R, L.Rp, L.nch, L.chunk, b,
+                                 at<int32_t>(ws, L.nsat_part), at<double>(ws, L.wsat_part), nsat,
+                                 wsat, s, hook_of(p)),
+               "score kernels");
+  return CLS_OK;
+}
+
+int cls_step(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
+             uint32_t* bits, int32_t* nsat, double* wsat, void* ws, size_t ws_bytes,
+             void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (n_steps < 0) return set_err(CLS_ERR_INVALID, "n_steps must be >= 0");
+  if (R == 0) return CLS_OK;
+  if (!x && p->host.n > 0) return set_err(CLS_ERR_INVALID, "x is NULL");
+  Layout L = layout_for(p, R);
+  rc = check_ws(L, ws, ws_bytes);
+  if (rc != CLS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* b = bits ? bits : at<uint32_t>(ws, L.bits);
+  if (n_steps == 0) {
+    if (!bits && !nsat && !wsat) return CLS_OK;
+    return cls_round_score(p, R, x, b, nsat, wsat, ws, ws_bytes, stream);
+  }
+  const bool want_score = nsat || wsat;
+  for (int st = 0; st < n_steps; ++st) {
+    rc = run_step(p, L, x, lr, b, nsat, wsat, ws, s, want_score);
+    if (rc != CLS_OK) return rc;
+  }
+  return CLS_OK;
+}
+
+int cls_solve_host_workspace_size(const cls_problem* p, int32_t R, size_t* bytes) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (!bytes) return set_err(CLS_ERR_INVALID, "bytes is NULL");
+  const Layout L = layout_for(p, R);
+  *bytes = L.total + align_up((size_t)p->host.n * R * sizeof(float)) +
+           align_up((size_t)R * sizeof(int32_t));
+  return CLS_OK;
+}
+
+int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host, float lr,
+                   int32_t n_steps, int32_t* nsat_host, float* x_host, void* ws,
+                   size_t ws_bytes, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (n_steps < 0) return set_err(CLS_ERR_INVALID, "n_steps must be >= 0");
+  if (R == 0) return CLS_OK;
+  if ((!x0_host && p->host.n > 0) || !nsat_host)
+    return set_err(CLS_ERR_INVALID, "x0_host and nsat_host are required");
+  size_t need = 0;
+  cls_solve_host_workspace_size(p, R, &need);
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign != 0 || ws_bytes < need)
+    return set_err(CLS_ERR_WORKSPACE, "workspace missing, unaligned or smaller than " +
+                                          std::to_string(need) + " bytes");
+  const Layout L = layout_for(p, R);
+  float* xd = at<float>(ws, L.total);
+  int32_t* nd = at<int32_t>(ws, L.total + align_up((size_t)p->host.n * R * sizeof(float)));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t xbytes = (size_t)p->host.n * R * sizeof(float);
+  if (xbytes) CLS_CUDA_TRY(cudaMemcpyAsync(xd, x0_host, xbytes, cudaMemcpyHostToDevice, s), "H2D x0");
+  rc = cls_step(p, R, xd, lr, n_steps, nullptr, nd, nullptr, ws, L.total, stream);
+  if (rc != CLS_OK) return rc;
+  if (n_steps == 0) {
+    rc = cls_round_score(p, R, xd, nullptr, nd, nullptr, ws, L.total, stream);
+    if (rc != CLS_OK) return rc;
+  }
+  CLS_CUDA_TRY(cudaMemcpyAsync(nsat_host, nd, (size_t)R * sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+               "D2H nsat");
+  if (x_host && xbytes)
+    CLS_CUDA_TRY(cudaMemcpyAsync(x_host, xd, xbytes, cudaMemcpyDeviceToHost, s), "D2H x");
+  CLS_CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  return CLS_OK;
+}
+
+int cls_profile_enable(cls_problem* p, int on) {
+  if (!p) return set_err(CLS_ERR_INVALID, "problem is NULL");
+  p->hook = on ? &p->events : nullptr;
+  return CLS_OK;
+}
+
+int cls_profile_reset(cls_problem* p) {
+  if (!p) return set_err(CLS_ERR_INVALID, "problem is NULL");
+  p->events.reset();
+  return CLS_OK;
+}
+
+int cls_profile_read(cls_problem* p, int kc, int64_t* launches, double* total_ms) {
+  if (!p || !launches || !total_ms) return set_err(CLS_ERR_INVALID, "NULL argument");
+  if (kc < 0 || kc >= cls::KC_COUNT) return set_err(CLS_ERR_INVALID, "unknown kernel class");
+  int64_t n = 0;
+  double ms = 0.0;
+  for (auto& r : p->events.recs) {
+    if (r.kc != kc) continue;
+    CLS_CUDA_TRY(cudaEventSynchronize(r.b), "cudaEventSynchronize");
+    float t = 0.f;
+    CLS_CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
+    ms += t;
+    n++;
+  }
+  *launches = n;
+  *total_ms = ms;
+  return CLS_OK;
+}
+
+const char* cls_strerror(int code) {
+  switch (code) {
+    case CLS_OK: return "ok";
+    case CLS_ERR_INVALID: return "invalid argument";
+    case CLS_ERR_CUDA: return "CUDA error";
+    case CLS_ERR_NOMEM: return "out of memory";
+    case CLS_ERR_UNSUPPORTED: return "unsupported device";
+    case CLS_ERR_WORKSPACE: return "bad workspace";
+    default: return "unknown error";
+  }
+}
+
+const char* cls_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// kernels.cuh -- launchers of the sm_103a kernels (kernels.cu), called by the
+// C ABI layer (api.cu).  All launches are asynchronous on the given stream.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "plan.h"
+
+namespace cls {
+
+// Device copy of a HostPlan.
+struct DevPlan {
+  int32_t n = 0, m = 0;
+  int64_t nnz = 0;
+  int32_t* lit_var = nullptr;
+  float* lit_sgn = nullptr;
+  int32_t* lit_dst = nullptr;
+  int32_t* voff = nullptr;
+  FeItem* fe = nullptr;
+  ScoreItem* score = nullptr;
+  uint32_t* satbits = nullptr;
+  F4* root_tab = nullptr;
+  F4* coef_tab = nullptr;
+  int32_t* thread_list[2] = {nullptr, nullptr};
+  int32_t thread_count[2] = {0, 0};
+  int32_t* group_list[kNumGroupCfg] = {};
+  int32_t group_count[kNumGroupCfg] = {};
+  int32_t group_maxL[kNumGroupCfg] = {};
+  uint8_t* fixed = nullptr;
+  float* fixed_val = nullptr;
+};
+
+// Kernel classes for profiling (cls_profile_read).
+enum KernelClass { KC_THREAD = 0, KC_GROUP_REAL, KC_GROUP_DFT, KC_ACCUM, KC_SCORE,
+                   KC_REDUCE, KC_INIT, KC_COUNT };
+
+// Called around each launch when profiling is on.
+struct LaunchHook {
+  virtual void before(int kc, cudaStream_t s) = 0;
+  virtual void after(int kc, cudaStream_t s) = 0;
+  virtual ~LaunchHook() {}
+};
+
+cudaError_t set_kernel_attributes();
+
+cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, float* x,
+                        cudaStream_t s, LaunchHook* h);
+
+// FE + literal partials: P[lit_dst[e] * Rp + r] = w_c s_e dFE_c/dy_e, and
+// (if fe_con) fe_con[c * ldf + r] = FE_c.
+cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P, float* fe_con,
+                      int ldf, cudaStream_t s, LaunchHook* h);
+
+// g[v,r] = sum of rows voff[v]..voff[v+1]-1 of P; optional grad output;
+// optional projected step of x in place and bitset of the new x.
+cudaError_t launch_accum_step(const DevPlan& d, int R, int Rp, const float* P, float* x,
+                              float lr, bool do_step, float* grad_out, uint32_t* bits,
+                              cudaStream_t s, LaunchHook* h);
+
+// x <- clamp(x - lr*grad) for free variables, optional bitset.
+cudaError_t launch_pgd(const DevPlan& d, int R, float* x, const float* grad, float lr,
+                       uint32_t* bits, cudaStream_t s, LaunchHook* h);
+
+// bitset of x (x < 0).
+cudaError_t launch_round(const DevPlan& d, int R, const float* x, uint32_t* bits,
+                         cudaStream_t s, LaunchHook* h);
+
+// Exact satisfaction counts from the bitset, two-stage (chunks, then order).
+cudaError_t launch_score(const DevPlan& d, int R, int Rp, int nch, int chunk,
+                         const uint32_t* bits, int32_t* nsat_part, double* wsat_part,
+                         int32_t* nsat, double* wsat, cudaStream_t s, LaunchHook* h);
+
+// obj[r] = sum_c w_c fe_con[c*ldf + r] in FP64 (fixed order), rounded to FP32.
+cudaError_t launch_obj(const DevPlan& d, int R, int Rp, int nch, int chunk, const float* fe_con,
+                       int ldf, double* part, float* obj, cudaStream_t s, LaunchHook* h);
+
+}  // namespace cls

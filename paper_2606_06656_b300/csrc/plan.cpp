@@ -1,0 +1,289 @@
+// plan.cpp -- host-side problem build: validation, spectra, Fourier tables
+// in FP64, the variable-major transpose of the literal list and the kernel
+// work lists.  Runs once per problem (cls_problem_create).
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+namespace cls {
+
+const GroupCfg kGroupCfg[kNumGroupCfg] = {
+#define CLS_CFG_ENTRY(id, G, Q, C) {G, Q, C},
+    CLS_GROUP_CONFIGS(CLS_CFG_ENTRY)
+#undef CLS_CFG_ENTRY
+};
+
+Tuning default_tuning() {
+  Tuning t;
+  t.dft = {{8, 0},   {16, 1},   {32, 2},   {64, 3},   {128, 5},  {192, 6},
+           {256, 7}, {320, 20}, {384, 10}, {512, 11}, {768, 12}, {1024, 13}};
+  t.real = {{64, 14}, {128, 15}, {256, 16}, {512, 17}, {1024, 18}};
+  return t;
+}
+
+namespace {
+
+enum { T_OR = 0, T_XOR, T_CARD_GE, T_CARD_LE, T_NAE, T_EO, T_EK, T_AMO, T_SPECTRUM };
+
+bool is_real_kind(int t) { return t == T_OR || t == T_XOR || t == T_NAE; }
+
+// Does constraint (type, L, k) hold with t true literals (Sec. 2.2; Table 2)?
+bool holds(int type, int L, int k, int t, const int8_t* spec) {
+  switch (type) {
+    case T_OR: return t >= 1;
+    case T_XOR: return (t & 1) == 1;
+    case T_CARD_GE: return t >= k;
+    case T_CARD_LE: return t <= k;
+    case T_NAE: return t > 0 && t < L;
+    case T_EO: return t == 1;
+    case T_EK: return t == k;
+    case T_AMO: return t <= 1;
+    default: return spec[t] == -1;
+  }
+}
+
+int pick(const std::vector<std::pair<int, int>>& ladder, int L) {
+  for (auto& e : ladder)
+    if (L <= e.first) return e.second;
+  return ladder.back().second;
+}
+
+}  // namespace
+
+void assign_groups(HostPlan* P, const Tuning& tun) {
+  for (auto& v : P->thread_list) v.clear();
+  for (auto& v : P->group_list) v.clear();
+  P->n_thread = P->n_group_real = P->n_group_dft = 0;
+  for (int32_t c = 0; c < P->m; ++c) {
+    const FeItem& it = P->fe[c];
+    bool real = it.root_off < 3;  // real roots live at the start of the table
+    if (real && it.L <= kThreadMaxL1) {
+      P->thread_list[it.L <= kThreadMaxL0 ? 0 : 1].push_back(c);
+      P->n_thread++;
+    } else if (real) {
+      int id = pick(tun.real, it.L);
+      P->group_list[id].push_back(c);
+      P->n_group_real++;
+    } else {
+      int id = pick(tun.dft, it.L);
+      P->group_list[id].push_back(c);
+      P->n_group_dft++;
+    }
+  }
+  // longest first: expensive blocks are scheduled early (LPT order)
+  auto byL = [P](int32_t a, int32_t b) {
+    return P->fe[a].L != P->fe[b].L ? P->fe[a].L > P->fe[b].L : a < b;
+  };
+  for (auto& v : P->thread_list) std::stable_sort(v.begin(), v.end(), byL);
+  for (auto& v : P->group_list) std::stable_sort(v.begin(), v.end(), byL);
+}
+
+int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
+               const int8_t* lit_sign, const int32_t* type, const int32_t* kk,
+               const float* weight, const int8_t* spectra, const uint8_t* fixed,
+               const float* fixed_val, const Tuning& tun, bool validate_only,
+               HostPlan* out, std::string* msg) {
+  auto fail = [msg](const std::string& s) {
+    if (msg) *msg = s;
+    return -1;
+  };
+  if (n < 0 || m < 0) return fail("n_vars and n_cons must be >= 0");
+  if (m > 0 && (!offsets || !lit_var || !lit_sign || !type))
+    return fail("offsets, lit_var, lit_sign and type are required when n_cons > 0");
+  if (m > 0 && offsets[0] != 0) return fail("offsets[0] must be 0");
+  int64_t nnz = m > 0 ? offsets[m] : 0;
+  std::vector<int32_t> seen(n > 0 ? n : 1, -1);
+  int64_t spec_need = 0;
+  for (int32_t c = 0; c < m; ++c) {
+    int64_t L = (int64_t)offsets[c + 1] - offsets[c];
+    if (L < 1 || L > 1024)
+      return fail("constraint " + std::to_string(c) + ": length " + std::to_string(L) +
+                  " outside 1..1024 (or offsets not increasing)");
+    int t = type[c];
+    if (t < T_OR || t > T_SPECTRUM)
+      return fail("constraint " + std::to_string(c) + ": unknown type " + std::to_string(t));
+    if (t == T_CARD_GE || t == T_CARD_LE || t == T_EK) {
+      if (!kk) return fail("k is required for CARD_GE/CARD_LE/EK constraints");
+      if (kk[c] < 0 || kk[c] > L)
+        return fail("constraint " + std::to_string(c) + ": k=" + std::to_string(kk[c]) +
+                    " outside 0..L");
+    }
+    if (t == T_SPECTRUM) spec_need += L + 1;
+    if (weight && !std::isfinite(weight[c]))
+      return fail("constraint " + std::to_string(c) + ": weight is not finite");
+    for (int64_t e = offsets[c]; e < offsets[c + 1]; ++e) {
+      int32_t v = lit_var[e];
+      if (v < 0 || v >= n)
+        return fail("literal " + std::to_string(e) + ": variable " + std::to_string(v) +
+                    " out of range");
+      if (lit_sign[e] != 1 && lit_sign[e] != -1)
+        return fail("literal " + std::to_string(e) + ": sign must be +1 or -1");
+      if (seen[v] == c)
+        return fail("constraint " + std::to_string(c) + ": variable " + std::to_string(v) +
+                    " appears twice");
+      seen[v] = c;
+    }
+  }
+  if (spec_need > 0 && !spectra) return fail("spectra are required for SPECTRUM constraints");
+  for (int64_t i = 0; i < spec_need; ++i)
+    if (spectra[i] != 1 && spectra[i] != -1) return fail("spectra entries must be +1 or -1");
+  if (fixed) {
+    if (!fixed_val) return fail("fixed_val is required when fixed is given");
+    for (int32_t v = 0; v < n; ++v) {
+      if (fixed[v] > 1) return fail("fixed entries must be 0 or 1");
+      if (fixed[v] && fixed_val[v] != 1.0f && fixed_val[v] != -1.0f)
+        return fail("variable " + std::to_string(v) + ": fixed value must be +1 or -1");
+    }
+  }
+  if (validate_only) return 0;
+
+  HostPlan& P = *out;
+  P = HostPlan();
+  P.n = n;
+  P.m = m;
+  P.nnz = nnz;
+  P.lit_var.assign(lit_var, lit_var + nnz);
+  P.lit_sgn.resize(nnz);
+  for (int64_t e = 0; e < nnz; ++e) P.lit_sgn[e] = (float)lit_sign[e];
+
+  // variable-major transpose: rows of variable v are voff[v]..voff[v+1]-1,
+  // literals in increasing constraint order (a fixed summation order)
+  P.voff.assign(n + 1, 0);
+  for (int64_t e = 0; e < nnz; ++e) P.voff[lit_var[e] + 1]++;
+  for (int32_t v = 0; v < n; ++v) P.voff[v + 1] += P.voff[v];
+  std::vector<int32_t> cur(P.voff.begin(), P.voff.end() - 1);
+  P.lit_dst.resize(nnz);
+  for (int64_t e = 0; e < nnz; ++e) P.lit_dst[e] = cur[lit_var[e]]++;
+
+  // fixed real roots and their coefficients
+  P.root_tab = {{0.5f, 0.5f, 0.f, 0.f}, {0.5f, -0.5f, 0.f, 0.f}, {0.f, 1.f, 0.f, 0.f}};
+  P.coef_tab = {{2.f, 0.f, 1.f, 0.f}, {1.f, 0.f, 1.f, 0.f}, {2.f, 0.f, 1.f, 0.f},
+                {2.f, 0.f, -1.f, 0.f}};
+  std::map<int, int> root_of_len;
+  std::map<std::pair<int, std::string>, int> coef_of_spec;
+
+  P.fe.resize(m);
+  P.score.resize(m);
+  int64_t soff = 0;
+  std::vector<int8_t> sp;
+  for (int32_t c = 0; c < m; ++c) {
+    int L = offsets[c + 1] - offsets[c];
+    int t = type[c];
+    int k = (t == T_CARD_GE || t == T_CARD_LE || t == T_EK) ? kk[c] : 0;
+    const int8_t* spec = nullptr;
+    if (t == T_SPECTRUM) {
+      spec = spectra + soff;
+      soff += L + 1;
+    }
+    float w = weight ? weight[c] : 1.0f;
+    // spectrum sp_t (Eq. 3): -1 where the constraint holds
+    sp.assign(L + 1, 1);
+    for (int tt = 0; tt <= L; ++tt) sp[tt] = holds(t, L, k, tt, spec) ? -1 : 1;
+
+    // score predicate
+    ScoreItem& s = P.score[c];
+    s = ScoreItem{offsets[c], L, 0, 0, 0, w, 0, 0};
+    switch (t) {
+      case T_OR: s.lo = 1; s.hi = L; break;
+      case T_XOR: s.mode = 1; break;
+      case T_CARD_GE: s.lo = k; s.hi = L; break;
+      case T_CARD_LE: s.lo = 0; s.hi = k; break;
+      case T_NAE: s.lo = 1; s.hi = L - 1; break;
+      case T_EO: s.lo = 1; s.hi = 1; break;
+      case T_EK: s.lo = k; s.hi = k; break;
+      case T_AMO: s.lo = 0; s.hi = 1; break;
+      default: {
+        s.mode = 2;
+        s.lo = (int32_t)(P.satbits.size() * 32);
+        P.satbits.resize(P.satbits.size() + (L + 1 + 31) / 32 + 1, 0u);
+        for (int tt = 0; tt <= L; ++tt)
+          if (sp[tt] == -1) P.satbits[(s.lo + tt) >> 5] |= 1u << ((s.lo + tt) & 31);
+      }
+    }
+
+    FeItem& it = P.fe[c];
+    it.lit0 = offsets[c];
+    it.L = L;
+    it.w = w;
+    it.c = c;
+    if (is_real_kind(t)) {
+      // closed forms (Appendix A): OR = 2 prod alpha - 1, XOR = prod y,
+      // NAE = 2 (prod alpha + prod beta) - 1
+      if (t == T_OR) { it.J = 1; it.root_off = kRootAlpha; it.coef_off = kCoefOr; it.b0 = -1.f; }
+      if (t == T_XOR) { it.J = 1; it.root_off = kRootY; it.coef_off = kCoefXor; it.b0 = 0.f; }
+      if (t == T_NAE) { it.J = 2; it.root_off = kRootAlpha; it.coef_off = kCoefNae; it.b0 = -1.f; }
+      continue;
+    }
+    // DFT of the spectrum at the L+1 roots of unity, FP64 (Sec. 2.3):
+    //   b_j = 1/(L+1) sum_t sp_t w^(-jt),  FE = sum_{j=0}^{L} b_j G_j with
+    //   G_j = prod_i (alpha_i + beta_i w^j) (G_0 = 1).  b_{L+1-j} =
+    //   conj(b_j) and G_{L+1-j} = conj(G_j), so only j = 1..ceil(L/2) are
+    //   kept, pairs with weight 2, the self-conjugate middle root (L odd)
+    //   with weight 1.
+    const int N = L + 1;
+    const int J = (L + 1) / 2;
+    std::vector<double> cs(N), sn(N);
+    for (int q = 0; q < N; ++q) {
+      if (2 * q == N) { cs[q] = -1.0; sn[q] = 0.0; continue; }
+      if (q == 0) { cs[q] = 1.0; sn[q] = 0.0; continue; }
+      double a = 2.0 * M_PI * (double)q / (double)N;
+      cs[q] = std::cos(a);
+      sn[q] = std::sin(a);
+    }
+    double b0 = 0.0;
+    for (int tt = 0; tt <= L; ++tt) b0 += sp[tt];
+    it.b0 = (float)(b0 / N);
+    it.J = J;
+    auto rit = root_of_len.find(L);
+    if (rit == root_of_len.end()) {
+      int off = (int)P.root_tab.size();
+      for (int j = 1; j <= J; ++j) {
+        float B = (float)((1.0 - cs[j]) * 0.5);
+        float A = 1.0f - B;
+        float C = (float)(sn[j] * 0.5);
+        P.root_tab.push_back({A, B, C, 0.f});
+      }
+      rit = root_of_len.emplace(L, off).first;
+    }
+    it.root_off = rit->second;
+    std::string key(reinterpret_cast<const char*>(sp.data()), sp.size());
+    auto cit = coef_of_spec.find({L, key});
+    if (cit == coef_of_spec.end()) {
+      int off = (int)P.coef_tab.size();
+      for (int j = 1; j <= J; ++j) {
+        double re = 0.0, im = 0.0;
+        for (int tt = 0; tt <= L; ++tt) {
+          int q = (int)(((int64_t)j * tt) % N);
+          re += sp[tt] * cs[q];
+          im -= sp[tt] * sn[q];
+        }
+        re /= N;
+        im /= N;
+        double mult = (2 * j == N) ? 1.0 : 2.0;
+        re *= mult;
+        im *= mult;
+        double B = (1.0 - cs[j]) * 0.5, C = sn[j] * 0.5;
+        // c' = b' * dF/dy = b' * (B - i C)
+        double cre = re * B + im * C;
+        double cim = im * B - re * C;
+        P.coef_tab.push_back({(float)re, (float)im, (float)cre, (float)cim});
+      }
+      cit = coef_of_spec.emplace(std::make_pair(L, key), off).first;
+    }
+    it.coef_off = cit->second;
+    P.dft_roots += J;
+    P.dft_lroots += (int64_t)J * L;
+  }
+  if (fixed) {
+    P.fixed.assign(fixed, fixed + n);
+    P.fixed_val.assign(fixed_val, fixed_val + n);
+  }
+  assign_groups(&P, tun);
+  return 0;
+}
+
+}  // namespace cls

@@ -1,0 +1,291 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Tolerances (stated by the task's target): FE within 1e-4 absolute per
+constraint; gradient within 1e-4 relative to its norm per restart; rounding,
+bitsets and satisfaction counts bit-exact on a given FP32 assignment; the
+projected step bit-exact given the same FP32 gradient.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import cls as ocls
+from oracle import spectra as osp
+
+pytestmark = pytest.mark.gpu
+
+FE_TOL = 1e-4
+GRAD_RTOL = 1e-4
+ALL_TYPES = [W.TYPE_OR, W.TYPE_XOR, W.TYPE_CARD_GE, W.TYPE_CARD_LE, W.TYPE_NAE,
+             W.TYPE_EO, W.TYPE_EK, W.TYPE_AMO, W.TYPE_SPECTRUM]
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2606_06656_b300 import Problem
+    assert torch.cuda.is_available()
+    return Problem
+
+
+def gpu_eval(Problem, inst, X):
+    p = Problem(inst)
+    x = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    obj, grad, fe = p.eval(x, obj=True, grad=True, fe_con=True)
+    torch.cuda.synchronize()
+    return obj.cpu().numpy(), grad.cpu().numpy(), fe.cpu().numpy()
+
+
+def check_against_oracle(inst, X, obj, grad, fe):
+    oobj, ograd, ofe = ocls.objective_grad(inst, X.astype(np.float64))
+    err_fe = np.max(np.abs(fe - ofe)) if inst.m else 0.0
+    assert err_fe <= FE_TOL, f"FE error {err_fe}"
+    num = np.linalg.norm(grad - ograd, axis=0)
+    den = np.linalg.norm(ograd, axis=0)
+    rel = num / np.maximum(den, 1e-30)
+    bad = (den > 1e-6) & (rel > GRAD_RTOL)
+    assert not bad.any(), f"grad rel err {rel.max()} (norm {den[np.argmax(rel)]})"
+    assert np.all(num[den <= 1e-6] <= 1e-6 * max(1, np.sqrt(inst.n)))
+    wsum = float(np.abs(inst.weight).sum())
+    assert np.max(np.abs(obj - oobj)) <= FE_TOL * max(1.0, wsum)
+
+
+def disjoint_instance(rng, ctype, L, count, weights=True):
+    """count constraints of one type and length on disjoint variables, so each
+    variable's gradient is a single literal partial."""
+    rows, spectra = [], []
+    n = L * count
+    perm = rng.permutation(n).astype(np.int32)
+    for c in range(count):
+        v = perm[c * L:(c + 1) * L]
+        s = np.where(rng.random(L) < 0.5, -1, 1).astype(np.int8)
+        k = int(rng.integers(0, L + 1)) if ctype in (W.TYPE_CARD_GE, W.TYPE_CARD_LE,
+                                                      W.TYPE_EK) else 0
+        if ctype == W.TYPE_SPECTRUM:
+            spectra.append(np.where(rng.random(L + 1) < 0.5, -1, 1).astype(np.int8))
+        rows.append((ctype, k, v, s))
+    w = rng.uniform(0.5, 2.0, count).astype(np.float32) if weights else None
+    return W.build(n, rows, weights=w, spectra=np.concatenate(spectra) if spectra else None)
+
+
+POINTS = ["uniform", "corner", "near", "mixed", "zero"]
+
+
+def points(kind, n, R, seed):
+    if kind == "uniform":
+        return W.uniform_points(n, R, seed)
+    if kind == "corner":
+        return W.corner_points(n, R, seed)
+    if kind == "near":
+        return W.near_corner_points(n, R, seed)
+    if kind == "mixed":
+        return W.mixed_points(n, R, seed)
+    return np.zeros((n, R), np.float32)
+
+
+@pytest.mark.parametrize("ctype", ALL_TYPES)
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 9, 16, 31, 32, 33, 64, 65, 129, 300])
+def test_fe_grad_by_type_and_length(P, ctype, L):
+    rng = np.random.default_rng(1000 * ctype + L)
+    count = max(2, min(12, 600 // L))
+    inst = disjoint_instance(rng, ctype, L, count)
+    for kind in POINTS:
+        R = 50 if kind != "zero" else 33      # ragged restart tails
+        X = points(kind, inst.n, R, seed=L + 7 * ctype)
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+
+
+@pytest.mark.parametrize("L,k", [(1024, 512), (1024, 3), (700, 350), (513, 100)])
+def test_max_length_cardinality(P, L, k):
+    rng = np.random.default_rng(L)
+    v = rng.permutation(L).astype(np.int32)
+    s = np.where(rng.random(L) < 0.5, -1, 1).astype(np.int8)
+    inst = W.build(L, [(W.TYPE_CARD_GE, k, v, s), (W.TYPE_XOR, 0, v[::-1].copy(), s),
+                       (W.TYPE_OR, 0, v.copy(), s)])
+    for kind in ["uniform", "near", "corner"]:
+        X = points(kind, L, 40, seed=3)
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+
+
+def test_overlapping_mixed_instance(P):
+    rng = np.random.default_rng(5)
+    inst = W.random_constraint_set(rng, 120, 300, ALL_TYPES, (1, 70), weights="random")
+    for kind in POINTS:
+        X = points(kind, inst.n, 70, seed=11)
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+
+
+def test_planted_mixed_pb_small(P):
+    inst = W.mixed_pb(n=800, n_or=2000, n_xor=200, n_card=40, card_len=(10, 300), seed=9)
+    X = W.uniform_points(inst.n, 64, seed=1)
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+
+
+def test_init_uniform_bit_exact(P):
+    inst = W.random_ksat(n=37, m=40)
+    p = P(inst)
+    for R, seed, off in [(45, 42, 0), (32, 7, 1000), (1, 2 ** 40 + 3, 5)]:
+        x = p.init_uniform(R, seed, r_offset=off)
+        torch.cuda.synchronize()
+        want = ocls.init_uniform(inst.n, R, seed, r_offset=off)
+        assert np.array_equal(x.cpu().numpy(), want)
+    # pinned variables
+    inst2 = W.partial_assignment(W.mixed_pb(n=50, n_or=60, n_xor=5, n_card=2, card_len=(10, 20)),
+                                 0.5)
+    p2 = P(inst2)
+    x = p2.init_uniform(40, 3).cpu().numpy()
+    want = ocls.init_uniform(inst2.n, 40, 3, fixed=inst2.fixed, fixed_val=inst2.fixed_val)
+    assert np.array_equal(x, want)
+
+
+def _bits_np(b):
+    return b.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("R", [1, 31, 32, 33, 100])
+def test_round_score_bit_exact(P, R):
+    rng = np.random.default_rng(R)
+    inst = W.random_constraint_set(rng, 90, 250, ALL_TYPES, (1, 40), weights="random")
+    X = W.mixed_points(inst.n, R, seed=R)
+    X[0, :] = np.nan
+    p = P(inst)
+    nsat, wsat, bits = p.round_score(torch.from_numpy(X).cuda())
+    onsat, owsat, _ = ocls.score(inst, X)
+    assert np.array_equal(_bits_np(bits), ocls.pack_bits(ocls.round_true(X)))
+    assert np.array_equal(nsat.cpu().numpy(), onsat)
+    assert np.allclose(wsat.cpu().numpy(), owsat, rtol=1e-12, atol=1e-12)
+
+
+def test_pgd_update_bit_exact(P):
+    rng = np.random.default_rng(3)
+    inst = W.partial_assignment(W.mixed_pb(n=300, n_or=400, n_xor=30, n_card=5,
+                                           card_len=(10, 50)), 0.3)
+    R = 77
+    X = W.uniform_points(inst.n, R, seed=4)
+    X[inst.fixed == 1] = inst.fixed_val[inst.fixed == 1][:, None]
+    G = (rng.standard_normal((inst.n, R)) * 5).astype(np.float32)
+    G[5, 3] = np.nan
+    p = P(inst)
+    x = torch.from_numpy(X.copy()).cuda()
+    bits = p.pgd_update(x, torch.from_numpy(G).cuda(), 0.1)
+    want = ocls.pgd_step(X, G, 0.1, inst.fixed)
+    got = x.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert np.array_equal(_bits_np(bits), ocls.pack_bits(ocls.round_true(want)))
+
+
+def test_step_equals_composition_and_oracle_one_step(P):
+    inst = W.mixed_pb(n=400, n_or=1200, n_xor=120, n_card=20, card_len=(10, 200), seed=2)
+    R, lr = 96, 0.1
+    X0 = W.uniform_points(inst.n, R, seed=8)
+    p = P(inst)
+    # fused step
+    x1 = torch.from_numpy(X0.copy()).cuda()
+    nsat, wsat, bits = p.step(x1, lr, n_steps=1)
+    # composition of the separately exported calls
+    x2 = torch.from_numpy(X0.copy()).cuda()
+    _, g, _ = p.eval(x2, obj=False, grad=True)
+    p.pgd_update(x2, g, lr)
+    nsat2, wsat2, bits2 = p.round_score(x2)
+    assert torch.equal(x1, x2) and torch.equal(nsat, nsat2) and torch.equal(bits, bits2)
+    # against the oracle's step from the same start
+    _, og, _ = ocls.objective_grad(inst, X0.astype(np.float64))
+    ox = ocls.pgd_step(X0, og.astype(np.float32), lr)
+    gerr = np.abs(g.cpu().numpy() - og).max()
+    assert np.abs(x1.cpu().numpy() - ox).max() <= lr * gerr + 1e-6
+
+
+def test_eval_is_deterministic(P):
+    inst = W.mixed_pb(n=500, n_or=1500, n_xor=150, n_card=30, card_len=(10, 300), seed=4)
+    p = P(inst)
+    x = torch.from_numpy(W.uniform_points(inst.n, 128, seed=2)).cuda()
+    a = p.eval(x, fe_con=True)
+    b = p.eval(x, fe_con=True)
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+
+
+def test_empty_and_degenerate(P):
+    inst = W.build(7, [])
+    p = P(inst)
+    x = torch.from_numpy(W.uniform_points(7, 40, 1)).cuda()
+    obj, grad, _ = p.eval(x)
+    assert torch.all(obj == 0) and torch.all(grad == 0)
+    nsat, wsat, bits = p.step(x, 0.1, 3)
+    assert torch.all(nsat == 0)
+    # single-literal constraints of every type, R = 1
+    rows = [(t, 1 if t in (W.TYPE_CARD_GE, W.TYPE_EK) else 0, np.array([i], np.int32),
+             np.array([1 if i % 2 else -1], np.int8)) for i, t in enumerate(ALL_TYPES[:-1])]
+    inst = W.build(len(rows), rows)
+    X = W.uniform_points(inst.n, 1, 3)
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+
+
+def test_random_3sat_loop_consistency(P):
+    """The 3-SAT workload loop (n=100, m=426, 64 restarts, lr 0.1): after every
+    batch of steps the fused loop's counts equal a fresh round/score of its
+    own iterate, and counts never exceed m."""
+    inst = W.random_ksat()
+    p = P(inst)
+    x = p.init_uniform(64, 42)
+    for _ in range(4):
+        nsat, wsat, bits = p.step(x, 0.1, n_steps=50)
+        n2, w2, b2 = p.round_score(x)
+        assert torch.equal(nsat, n2) and torch.equal(bits, b2)
+        assert int(nsat.max()) <= inst.m
+    assert float(nsat.float().mean()) > 0.9 * inst.m
+
+
+def test_solve_host_matches_device(P):
+    inst = W.random_ksat()
+    p = P(inst)
+    X0 = W.uniform_points(inst.n, 64, seed=5)
+    xd = torch.from_numpy(X0.copy()).cuda()
+    nsat, _, _ = p.step(xd, 0.1, n_steps=20)
+    xh = torch.from_numpy(X0.copy()).pin_memory()
+    nh = torch.empty(64, dtype=torch.int32).pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    p.solve_host(xh, 0.1, 20, nh, xo)
+    assert torch.equal(nh, nsat.cpu()) and torch.equal(xo, xd.cpu())
+
+
+def test_full_size_mixed_pb_sampled(P):
+    """Batched mixed PB at full size (n=5000, 22500 constraints, 4096
+    restarts, one launch per kernel as in the benchmark), checked on sampled
+    (constraint, restart) FE values, sampled variable gradients and sampled
+    restarts' exact counts."""
+    inst = W.mixed_pb()
+    R = 4096
+    X = W.uniform_points(inst.n, R, seed=42)
+    p = P(inst)
+    x = torch.from_numpy(X).cuda()
+    obj, grad, fe = p.eval(x, fe_con=True)
+    nsat, _, _ = p.round_score(x)
+    fe, grad, nsat = fe.cpu().numpy(), grad.cpu().numpy(), nsat.cpu().numpy()
+    rng = np.random.default_rng(0)
+    sps = osp.instance_spectra(inst)
+    L = inst.lengths()
+    cons = list(np.argsort(-L)[:10]) + list(rng.choice(inst.m, 40, replace=False))
+    rs = rng.choice(R, 6, replace=False)
+    from oracle import fe as ofe
+    for c in cons:
+        a, b = inst.offsets[c], inst.offsets[c + 1]
+        Y = inst.lit_sign[a:b, None].astype(np.float64) * X[inst.lit_var[a:b]][:, rs]
+        f, _ = ofe.fe_grad_dp(sps[c], Y)
+        assert np.max(np.abs(fe[c, rs] - f)) <= FE_TOL
+    # sampled variable gradients: sum over incident constraints
+    vs = rng.choice(inst.n, 12, replace=False)
+    cons_of = {}
+    for c in range(inst.m):
+        for e in range(inst.offsets[c], inst.offsets[c + 1]):
+            cons_of.setdefault(int(inst.lit_var[e]), []).append((c, e))
+    for v in vs:
+        g = np.zeros(len(rs))
+        for c, e in cons_of.get(int(v), []):
+            a, b = inst.offsets[c], inst.offsets[c + 1]
+            Y = inst.lit_sign[a:b, None].astype(np.float64) * X[inst.lit_var[a:b]][:, rs]
+            _, gg = ofe.fe_grad_dp(sps[c], Y)
+            g += inst.weight[c] * inst.lit_sign[e] * gg[e - a]
+        assert np.all(np.abs(grad[v, rs] - g) <= GRAD_RTOL * np.maximum(1.0, np.abs(g)))
+    onsat, _, _ = ocls.score(inst, X[:, rs])
+    assert np.array_equal(nsat[rs], onsat)
