@@ -17,10 +17,16 @@ Two routes to the same polynomial:
   alpha_i = (1 + y_i)/2 = P[literal i false] and
   beta_i  = (1 - y_i)/2 = P[literal i true],
   FE(y) = sum_t sp_t P(T = t), T = number of true literals, a
-  Poisson-binomial count.  Forward DP over literals gives P(T = t); a reverse
-  adjoint A_{i-1}(t) = alpha_i A_i(t) + beta_i A_i(t+1), A_L = sp, gives
-  dFE/dy_i = 1/2 sum_t P_{i-1}(t) (A_i(t) - A_i(t+1)).
-  All quantities are convex combinations, so FP64 is accurate to ~L*1e-16.
+  Poisson-binomial count.  Forward DP over literals gives P(T = t).
+  The gradient is the paper's discrete derivative (Sec. 2.1, text under
+  Eq. 3: d_t = (sp_t - sp_{t+1})/2) averaged over the other literals:
+  dFE/dy_i = sum_t d_t P(T_{-i} = t), T_{-i} = # true literals other than i.
+  With prefix distributions P_{i-1} (literals 1..i-1) and the reverse
+  recurrence D_L(a) = d_a, D_{i-1}(a) = alpha_i D_i(a) + beta_i D_i(a+1)
+  (D_i(a) = E[d_{a + # true among literals i+1..L}]) it is
+  dFE/dy_i = sum_a P_{i-1}(a) D_i(a).
+  Every step is a convex combination, so for spectra whose d has one sign
+  (OR, CARD) the partials carry relative FP64 accuracy even when tiny.
 """
 import itertools
 import numpy as np
@@ -90,15 +96,15 @@ def fe_grad_dp(sp, Y):
         P[i] = alpha[i - 1] * P[i - 1]
         P[i, 1:] += beta[i - 1] * P[i - 1, :-1]
     fe = (sp[:, None] * P[L]).sum(axis=0)
-    # reverse adjoint: A_i(t) = E[sp_{t + #true among literals i+1..L}]
-    A = np.repeat(sp[:, None], R, axis=1).astype(np.float64)  # A_L
-    A_ext = np.zeros((L + 2, R))
+    # reverse recurrence on the discrete derivative d_t, t = 0..L-1
+    d = 0.5 * (sp[:-1] - sp[1:])
+    D = np.zeros((L + 1, R))
+    D[:L] = d[:, None]                    # D_L(a) = d_a
     grad = np.zeros((L, R))
     for i in range(L, 0, -1):
-        A_ext[:L + 1] = A
-        A_ext[L + 1] = 0.0
-        # dFE/dy_i = 1/2 sum_t P_{i-1}(t) (A_i(t) - A_i(t+1)), t = 0..i-1
-        grad[i - 1] = 0.5 * (P[i - 1, :i] * (A_ext[:i] - A_ext[1:i + 1])).sum(axis=0)
-        # A_{i-1}(t) = alpha_i A_i(t) + beta_i A_i(t+1)
-        A = alpha[i - 1] * A_ext[:L + 1] + beta[i - 1] * A_ext[1:L + 2]
+        # dFE/dy_i = sum_{a=0}^{i-1} P_{i-1}(a) D_i(a)
+        grad[i - 1] = (P[i - 1, :i] * D[:i]).sum(axis=0)
+        # D_{i-1}(a) = alpha_i D_i(a) + beta_i D_i(a+1), a = 0..i-2
+        D[:i - 1] = alpha[i - 1] * D[:i - 1] + beta[i - 1] * D[1:i]
+        D[i - 1:] = 0.0
     return fe, grad

@@ -17,6 +17,35 @@ pytestmark = pytest.mark.gpu
 
 FE_TOL = 1e-4
 GRAD_RTOL = 1e-4
+U32 = 2.0 ** -24   # FP32 unit roundoff
+U64 = 2.0 ** -53   # FP64 unit roundoff
+
+
+REAL_TYPES = (W.TYPE_OR, W.TYPE_XOR, W.TYPE_NAE)
+
+
+def fp32_floor(inst):
+    """Per-variable absolute error floor of the FP32 gradient, for the
+    isolated single-type stress tests whose exact gradient can be arbitrarily
+    small (far-tail probabilities such as 1e-115, or near-corner points).
+    A DFT literal partial is Re sum_j c'_j T_ij with |c'_j| summing to O(1)
+    and each T_ij a product of L-1 factors of modulus <= 1 carried with two
+    roundings per complex multiply: its absolute error is a few L*u however
+    small the exact value is.  We allow 4*L*u per DFT literal (times the
+    weight); closed-form real products keep relative accuracy and get only
+    the FP32 underflow floor (1e-30).  The FP64 oracle's own floor is added:
+    its partial sum_a P_{i-1}(a) D_i(a) cancels for alternating spectra (XOR:
+    prefix terms of both signs summing to a tiny product), a few L*2^-53."""
+    L = inst.lengths().astype(np.float64)
+    dft = ~np.isin(inst.ctype, REAL_TYPES)
+    w = np.abs(inst.weight.astype(np.float64))
+    per_con = np.where(dft, 4.0 * L * U32 * w, 0.0) + 4.0 * L * U64 * w
+    per_lit = np.repeat(per_con, inst.lengths())
+    out = np.full(inst.n, 1e-30)
+    np.add.at(out, inst.lit_var, per_lit)
+    return out
+
+
 ALL_TYPES = [W.TYPE_OR, W.TYPE_XOR, W.TYPE_CARD_GE, W.TYPE_CARD_LE, W.TYPE_NAE,
              W.TYPE_EO, W.TYPE_EK, W.TYPE_AMO, W.TYPE_SPECTRUM]
 
@@ -36,16 +65,17 @@ def gpu_eval(Problem, inst, X):
     return obj.cpu().numpy(), grad.cpu().numpy(), fe.cpu().numpy()
 
 
-def check_against_oracle(inst, X, obj, grad, fe):
+def check_against_oracle(inst, X, obj, grad, fe, floored=False):
     oobj, ograd, ofe = ocls.objective_grad(inst, X.astype(np.float64))
     err_fe = np.max(np.abs(fe - ofe)) if inst.m else 0.0
     assert err_fe <= FE_TOL, f"FE error {err_fe}"
     num = np.linalg.norm(grad - ograd, axis=0)
     den = np.linalg.norm(ograd, axis=0)
-    rel = num / np.maximum(den, 1e-30)
-    bad = (den > 1e-6) & (rel > GRAD_RTOL)
-    assert not bad.any(), f"grad rel err {rel.max()} (norm {den[np.argmax(rel)]})"
-    assert np.all(num[den <= 1e-6] <= 1e-6 * max(1, np.sqrt(inst.n)))
+    floor = np.linalg.norm(fp32_floor(inst)) if floored else 0.0
+    ok = num <= GRAD_RTOL * den + floor + 1e-30
+    r = int(np.argmax(num - GRAD_RTOL * den - floor))
+    assert ok.all(), (f"grad error {num[r]:.3e} vs norm {den[r]:.3e} (rel {num[r]/max(den[r],1e-30):.2e},"
+                      f" floor {floor:.2e})")
     wsum = float(np.abs(inst.weight).sum())
     assert np.max(np.abs(obj - oobj)) <= FE_TOL * max(1.0, wsum)
 
@@ -92,7 +122,7 @@ def test_fe_grad_by_type_and_length(P, ctype, L):
     for kind in POINTS:
         R = 50 if kind != "zero" else 33      # ragged restart tails
         X = points(kind, inst.n, R, seed=L + 7 * ctype)
-        check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X), floored=True)
 
 
 @pytest.mark.parametrize("L,k", [(1024, 512), (1024, 3), (700, 350), (513, 100)])
@@ -104,7 +134,7 @@ def test_max_length_cardinality(P, L, k):
                        (W.TYPE_OR, 0, v.copy(), s)])
     for kind in ["uniform", "near", "corner"]:
         X = points(kind, L, 40, seed=3)
-        check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X), floored=True)
 
 
 def test_overlapping_mixed_instance(P):
@@ -112,7 +142,10 @@ def test_overlapping_mixed_instance(P):
     inst = W.random_constraint_set(rng, 120, 300, ALL_TYPES, (1, 70), weights="random")
     for kind in POINTS:
         X = points(kind, inst.n, 70, seed=11)
-        check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+        # realistic overlapping instance: strict relative criterion at
+        # interior points, FP32 floor only where the gradient is tiny
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X),
+                             floored=kind in ("corner", "near", "mixed"))
 
 
 def test_planted_mixed_pb_small(P):
