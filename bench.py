@@ -172,10 +172,18 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     inst, R, lr = workload(args.config)
+    if args.R:
+        R = args.R
     p = Problem(inst)
     info = p.info
     x = p.init_uniform(R, seed=42, r_offset=rank * R)   # restarts sharded by global id
     ws = p.workspace(R)
+    tune_s = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        B.cls_autotune(p.handle, R, x, 2, ws)
+        tune_s = time.perf_counter() - t0
+    tuning = B.cls_tuning_get(p.handle)
     nsat = torch.empty(R, dtype=torch.int32, device="cuda")
     wsat = torch.empty(R, dtype=torch.float64, device="cuda")
     bits = torch.empty((inst.n, (R + 31) // 32), dtype=torch.int32, device="cuda")
@@ -269,7 +277,8 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": inst.name, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
                    "R_per_gpu": R, "lr": lr, "parallelism": f"restart-replicas x{world}",
-                   "l2": "flushed (256 MB write) before every timed step"},
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "tuning": tuning, "autotune_s": tune_s},
         "e2e": {"value": units / e2e_s, "unit": "literal-evals/s",
                 "h2d_bytes_per_step": 4 * inst.n * R, "d2h_bytes_per_step": 4 * R},
         "gpu_launches": launches,
@@ -295,6 +304,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="mixed")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--R", type=int, default=0, help="override restarts (profiling)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -186,6 +186,27 @@ int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host,
                    float lr, int32_t n_steps, int32_t* nsat_host,
                    float* x_host, void* ws, size_t ws_bytes, void* stream);
 
+/* Autotuning of the FE+gradient launch shapes (task: "the segment-to-warp or
+ * segment-to-block split and the tile sizes chosen by an autotuner").
+ * Constraints on the lane-group paths are bucketed by length; every bucket
+ * is served by one lane-group configuration (lanes per (constraint,
+ * restart) G, literal slots per lane Q, DFT or real roots, literal values in
+ * registers or re-read from shared memory).  cls_autotune times every
+ * admissible configuration on each non-empty bucket of this problem (reps
+ * launches each, x = device float[n*R] as the input, ws as for cls_eval),
+ * keeps the fastest and synchronises the stream.  Results do not depend on
+ * the tuning beyond FP32 rounding order of the DFT products.
+ * cls_tuning_get/cls_tuning_set read or replace the bucket -> configuration
+ * map (n must equal the number of buckets, 24); cls_config_info(id, out[4])
+ * describes configuration id (G, Q, DFT?, shared-memory y?) and, for
+ * id = 1000 + b, bucket b (DFT?, maximum length).  An invalid map is
+ * rejected with CLS_ERR_INVALID. */
+int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* ws,
+                 size_t ws_bytes, void* stream);
+int cls_tuning_get(const cls_problem* p, int32_t* cfg, int32_t n);
+int cls_tuning_set(cls_problem* p, const int32_t* cfg, int32_t n);
+int cls_config_info(int32_t id, int32_t* out);
+
 /* Per-kernel timing (tracing): when enabled, each kernel launch of the
  * compute calls is bracketed by CUDA events on its stream; cls_profile_read
  * synchronises and returns, for kernel class kc (0 = thread-path FE+grad,

@@ -147,3 +147,29 @@ def cls_profile_read(h, kc):
     _lib.check(_lib.load().cls_profile_read(h, int(kc), C.byref(n), C.byref(ms)),
                "cls_profile_read")
     return int(n.value), float(ms.value)
+
+
+N_BUCKETS = 24
+
+
+def cls_autotune(h, R, x, reps, ws, stream=None):
+    _lib.check(_lib.load().cls_autotune(h, int(R), _ptr(x), int(reps), _ptr(ws),
+                                        ws.numel() if ws is not None else 0, _stream(stream)),
+               "cls_autotune")
+
+
+def cls_tuning_get(h):
+    buf = (C.c_int32 * N_BUCKETS)()
+    _lib.check(_lib.load().cls_tuning_get(h, buf, N_BUCKETS), "cls_tuning_get")
+    return [int(v) for v in buf]
+
+
+def cls_tuning_set(h, cfg):
+    buf = (C.c_int32 * N_BUCKETS)(*[int(v) for v in cfg])
+    _lib.check(_lib.load().cls_tuning_set(h, buf, len(cfg)), "cls_tuning_set")
+
+
+def cls_config_info(cid):
+    buf = (C.c_int32 * 4)()
+    _lib.check(_lib.load().cls_config_info(int(cid), buf), "cls_config_info")
+    return [int(v) for v in buf]

@@ -144,11 +144,12 @@ Layout layout_for(const cls_problem* p, int R) {
     off = align_up(off + bytes);
     return at;
   };
+  const int nsc = std::max(1, cls::score_chunks(p->dev.n_ranges));
   L.P = take((size_t)p->host.nnz * L.Rp * sizeof(float));
   L.fe = take((size_t)m * L.Rp * sizeof(float));
   L.bits = take((size_t)p->host.n * L.RT * sizeof(uint32_t));
-  L.nsat_part = take((size_t)L.nch * L.Rp * sizeof(int32_t));
-  L.wsat_part = take((size_t)L.nch * L.Rp * sizeof(double));
+  L.nsat_part = take((size_t)nsc * L.Rp * sizeof(int32_t));
+  L.wsat_part = take((size_t)nsc * L.Rp * sizeof(double));
   L.obj_part = take((size_t)L.nch * L.Rp * sizeof(double));
   L.nsat = take((size_t)L.Rp * sizeof(int32_t));
   L.total = off;
@@ -196,6 +197,26 @@ int check_R(const cls_problem* p, int32_t R) {
 
 cls::LaunchHook* hook_of(const cls_problem* p) { return p->hook; }
 
+// (Re)upload the FE work lists of the current tuning.  Old list buffers stay
+// allocated until the problem is destroyed (tuning changes are rare).
+int upload_lists(cls_problem* p) {
+  const cls::HostPlan& H = p->host;
+  cls::DevPlan& D = p->dev;
+  for (int t = 0; t < cls::kNumThreadCls; ++t) {
+    int rc = upload(p, H.thread_items[t], &D.thread_items[t]);
+    if (rc != CLS_OK) return rc;
+    D.thread_count[t] = (int32_t)H.thread_items[t].size();
+  }
+  for (int b = 0; b < cls::kNumBuckets; ++b) {
+    int rc = upload(p, H.bucket_list[b], &D.bucket_list[b]);
+    if (rc != CLS_OK) return rc;
+    D.bucket_count[b] = (int32_t)H.bucket_list[b].size();
+    D.bucket_cfg[b] = H.bucket_cfg[b];
+    D.bucket_maxL[b] = H.bucket_list[b].empty() ? 0 : H.fe[H.bucket_list[b][0]].L;
+  }
+  return CLS_OK;
+}
+
 // One full CLS step: FE + partials, accumulate + step + round, score.
 int run_step(const cls_problem* p, const Layout& L, float* x, float lr, uint32_t* bits,
              int32_t* nsat, double* wsat, void* ws, cudaStream_t s, bool score) {
@@ -205,9 +226,8 @@ int run_step(const cls_problem* p, const Layout& L, float* x, float lr, uint32_t
                                       hook_of(p)),
                "accumulate/step kernel");
   if (score)
-    CLS_CUDA_TRY(cls::launch_score(p->dev, L.R, L.Rp, L.nch, L.chunk, bits,
-                                   at<int32_t>(ws, L.nsat_part), at<double>(ws, L.wsat_part),
-                                   nsat, wsat, s, hook_of(p)),
+    CLS_CUDA_TRY(cls::launch_score(p->dev, L.R, L.Rp, bits, at<int32_t>(ws, L.nsat_part),
+                                   at<double>(ws, L.wsat_part), nsat, wsat, s, hook_of(p)),
                  "score kernels");
   return CLS_OK;
 }
@@ -222,7 +242,7 @@ int cls_problem_check(int32_t n, int32_t m, const int32_t* offsets, const int32_
                       const float* fixed_val) {
   std::string msg;
   int rc = cls::build_plan(n, m, offsets, lit_var, lit_sign, type, k, weight, spectra, fixed,
-                           fixed_val, cls::default_tuning(), true, nullptr, &msg);
+                           fixed_val, true, nullptr, &msg);
   if (rc != 0) return set_err(CLS_ERR_INVALID, msg);
   return CLS_OK;
 }
@@ -239,7 +259,7 @@ int cls_problem_create(int32_t n, int32_t m, const int32_t* offsets, const int32
   int rc;
   try {
     rc = cls::build_plan(n, m, offsets, lit_var, lit_sign, type, k, weight, spectra, fixed,
-                         fixed_val, cls::default_tuning(), false, &p->host, &msg);
+                         fixed_val, false, &p->host, &msg);
   } catch (const std::bad_alloc&) {
     delete p;
     return set_err(CLS_ERR_NOMEM, "host allocation failed while building the problem");
@@ -272,26 +292,18 @@ int cls_problem_create(int32_t n, int32_t m, const int32_t* offsets, const int32
   auto up = [&](auto& vec, auto** dst) {
     if (r2 == CLS_OK) r2 = upload(p, vec, dst);
   };
-  up(H.lit_var, &D.lit_var);
-  up(H.lit_sgn, &D.lit_sgn);
-  up(H.lit_dst, &D.lit_dst);
+  up(H.lit, &D.lit);
   up(H.voff, &D.voff);
   up(H.fe, &D.fe);
   up(H.score, &D.score);
+  up(H.score_ranges, &D.score_ranges);
+  D.n_ranges = H.score_ranges.empty() ? 0 : (int32_t)H.score_ranges.size() - 1;
   up(H.satbits, &D.satbits);
   up(H.root_tab, &D.root_tab);
   up(H.coef_tab, &D.coef_tab);
   up(H.fixed, &D.fixed);
   up(H.fixed_val, &D.fixed_val);
-  for (int t = 0; t < 2; ++t) {
-    up(H.thread_list[t], &D.thread_list[t]);
-    D.thread_count[t] = (int32_t)H.thread_list[t].size();
-  }
-  for (int g = 0; g < cls::kNumGroupCfg; ++g) {
-    up(H.group_list[g], &D.group_list[g]);
-    D.group_count[g] = (int32_t)H.group_list[g].size();
-    D.group_maxL[g] = H.group_list[g].empty() ? 0 : H.fe[H.group_list[g][0]].L;
-  }
+  if (r2 == CLS_OK) r2 = upload_lists(p);
   if (r2 != CLS_OK) {
     free_problem(p);
     delete p;
@@ -394,9 +406,8 @@ int cls_round_score(const cls_problem* p, int32_t R, const float* x, uint32_t* b
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t* b = bits ? bits : at<uint32_t>(ws, L.bits);
   CLS_CUDA_TRY(cls::launch_round(p->dev, R, x, b, s, hook_of(p)), "round kernel");
-  CLS_CUDA_TRY(cls::launch_score(p->dev, R, L.Rp, L.nch, L.chunk, b,
-                                 at<int32_t>(ws, L.nsat_part), at<double>(ws, L.wsat_part), nsat,
-                                 wsat, s, hook_of(p)),
+  CLS_CUDA_TRY(cls::launch_score(p->dev, R, L.Rp, b, at<int32_t>(ws, L.nsat_part),
+                                 at<double>(ws, L.wsat_part), nsat, wsat, s, hook_of(p)),
                "score kernels");
   return CLS_OK;
 }
@@ -468,6 +479,106 @@ int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host, float 
     CLS_CUDA_TRY(cudaMemcpyAsync(x_host, xd, xbytes, cudaMemcpyDeviceToHost, s), "D2H x");
   CLS_CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   return CLS_OK;
+}
+
+int cls_tuning_get(const cls_problem* p, int32_t* cfg, int32_t n) {
+  if (!p || !cfg) return set_err(CLS_ERR_INVALID, "NULL argument");
+  if (n != cls::kNumBuckets)
+    return set_err(CLS_ERR_INVALID, "tuning has " + std::to_string(cls::kNumBuckets) + " entries");
+  for (int b = 0; b < cls::kNumBuckets; ++b) cfg[b] = p->host.bucket_cfg[b];
+  return CLS_OK;
+}
+
+int cls_tuning_set(cls_problem* p, const int32_t* cfg, int32_t n) {
+  if (!p || !cfg) return set_err(CLS_ERR_INVALID, "NULL argument");
+  if (n != cls::kNumBuckets)
+    return set_err(CLS_ERR_INVALID, "tuning has " + std::to_string(cls::kNumBuckets) + " entries");
+  cls::Tuning t;
+  for (int b = 0; b < cls::kNumDftBuckets; ++b) t.dft[b] = cfg[b];
+  for (int b = 0; b < cls::kNumRealBuckets; ++b) t.real[b] = cfg[cls::kNumDftBuckets + b];
+  std::string msg;
+  if (!cls::tuning_valid(t, &msg)) return set_err(CLS_ERR_INVALID, msg);
+  cls::assign_groups(&p->host, t);
+  return upload_lists(p);
+}
+
+int cls_config_info(int32_t id, int32_t* out) {
+  if (!out) return set_err(CLS_ERR_INVALID, "NULL argument");
+  if (id >= 0 && id < cls::kNumGroupCfg) {
+    const cls::GroupCfg& g = cls::kGroupCfg[id];
+    out[0] = g.G;
+    out[1] = g.Q;
+    out[2] = g.cplx;
+    out[3] = g.ys;
+    return CLS_OK;
+  }
+  const int b = id - 1000;   // 1000 + bucket: bucket kind and maximum length
+  if (b >= 0 && b < cls::kNumBuckets) {
+    out[0] = b < cls::kNumDftBuckets ? 1 : 0;
+    out[1] = b < cls::kNumDftBuckets ? cls::kDftBucketMax[b]
+                                     : cls::kRealBucketMax[b - cls::kNumDftBuckets];
+    out[2] = 0;
+    out[3] = 0;
+    return CLS_OK;
+  }
+  return set_err(CLS_ERR_INVALID, "unknown configuration id");
+}
+
+int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* ws,
+                 size_t ws_bytes, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (R == 0 || p->host.m == 0) return CLS_OK;
+  if (!x) return set_err(CLS_ERR_INVALID, "x is NULL");
+  if (reps < 1) return set_err(CLS_ERR_INVALID, "reps must be >= 1");
+  const Layout L = layout_for(p, R);
+  rc = check_ws(L, ws, ws_bytes);
+  if (rc != CLS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* P = at<float>(ws, L.P);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CLS_CUDA_TRY(cudaEventCreate(&e0), "cudaEventCreate");
+  CLS_CUDA_TRY(cudaEventCreate(&e1), "cudaEventCreate");
+  const cls::DevPlan& D = p->dev;
+  int chosen[cls::kNumBuckets];
+  for (int b = 0; b < cls::kNumBuckets; ++b) chosen[b] = p->host.bucket_cfg[b];
+  int result = CLS_OK;
+  for (int b = 0; b < cls::kNumBuckets && result == CLS_OK; ++b) {
+    if (D.bucket_count[b] == 0) continue;
+    const bool dft = b < cls::kNumDftBuckets;
+    const int bmax = dft ? cls::kDftBucketMax[b] : cls::kRealBucketMax[b - cls::kNumDftBuckets];
+    float best = 1e30f;
+    for (int id = 0; id < cls::kNumGroupCfg && result == CLS_OK; ++id) {
+      const cls::GroupCfg& g = cls::kGroupCfg[id];
+      // candidates: right kind, able to hold the bucket's longest constraint,
+      // at most twice the slots needed
+      if (g.cplx != (dft ? 1 : 0) || g.G * g.Q < bmax || g.G * g.Q > 2 * std::max(bmax, 32))
+        continue;
+      cudaError_t e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b],
+                                        D.bucket_maxL[b], R, L.Rp, x, P, nullptr, 0, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int k = 0; k < reps && e == cudaSuccess; ++k)
+        e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b], D.bucket_maxL[b], R,
+                              L.Rp, x, P, nullptr, 0, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        result = cuda_err(e, "autotune");
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        chosen[b] = id;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != CLS_OK) return result;
+  return cls_tuning_set(p, chosen, cls::kNumBuckets);
 }
 
 int cls_profile_enable(cls_problem* p, int on) {

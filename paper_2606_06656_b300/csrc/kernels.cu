@@ -1,11 +1,11 @@
 // kernels.cu -- sm_103a kernels of the CLS hot path.
 //
 // Layouts (see cls.h): x[v*R + r] (variable-major, restart-minor), literal
-// partials P[row*Rp + r] with row = lit_dst[e] (variable-major order, so the
-// gradient of variable v is the sum of a contiguous run of rows), bitsets
-// bits[v*RW + r/32] bit r%32.  Warps always span 32 consecutive restarts of
-// one row, so every global access to x, P and bits is a coalesced 128-byte
-// row segment or a warp-uniform broadcast.
+// partials P[row*Rp + r] with row = the literal's position in variable-major
+// order (so the gradient of variable v is the sum of a contiguous run of
+// rows), bitsets bits[v*RW + r/32] bit r%32.  A warp always spans 32
+// consecutive restarts of a row, so every global access to x, P and bits is a
+// coalesced 128-byte row segment or a warp-uniform broadcast.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +23,9 @@ __device__ __forceinline__ float4 ldg4(const F4* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
 
+__device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
+__device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
+
 // ---------------------------------------------------------------------------
 // A1 init: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11)
 // ---------------------------------------------------------------------------
@@ -32,9 +35,9 @@ __device__ __forceinline__ void philox4x64_10(uint64_t& x0, uint64_t& x1, uint64
   const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
-    uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
-    uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
+    const uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
+    const uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
+    const uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
     x0 = n0;
     x1 = lo1;
     x2 = n2;
@@ -70,82 +73,102 @@ __global__ void __launch_bounds__(256) k_init_uniform(int n, int R, uint64_t see
 }
 
 // ---------------------------------------------------------------------------
-// A2-A5, closed-form products (OR, XOR, NAE) with L <= MAXL:
-// one thread per (constraint, restart); lanes span restarts.
-// FE = b0 + sum_j b'_j prod_i F_ij, dFE/dy_i = sum_j c'_j prod_{l!=i} F_lj with
-// real factors F = A + y B; prefix products kept in registers, suffix products
-// carried backwards -- no division.
+// A2-A5, closed-form products (OR, XOR, NAE) with L <= MAXL: one thread per
+// (constraint, restart), a warp = one constraint x 32 restarts, looping over
+// kThreadTiles restart tiles so the constraint's literal records are loaded
+// once.  FE = b0 + sum_j b'_j prod_i F_ij and dFE/dy_i = sum_j c'_j
+// prod_{l!=i} F_lj with real factors F = A + y B: prefix products in
+// registers, suffix products carried backwards (no division).
 // ---------------------------------------------------------------------------
 template <int MAXL>
 __global__ void __launch_bounds__(256) k_fe_thread(
-    const int32_t* __restrict__ list, int count, const FeItem* __restrict__ fe,
-    const F4* __restrict__ root, const F4* __restrict__ coef, const int32_t* __restrict__ lit_var,
-    const float* __restrict__ lit_sgn, const int32_t* __restrict__ lit_dst,
-    const float* __restrict__ x, int R, int Rp, float* __restrict__ P, float* __restrict__ fe_con,
-    int ldf) {
-  const int r = blockIdx.x * 32 + threadIdx.x;
-  if (r >= R) return;
+    const FeItem* __restrict__ items, int count, const F4* __restrict__ root,
+    const F4* __restrict__ coef, const LitRec* __restrict__ lit, const float* __restrict__ x,
+    int R, int Rp, int RT, float* __restrict__ P, float* __restrict__ fe_con, int ldf) {
+  const int lane = threadIdx.x;
   for (int ci = blockIdx.y * blockDim.y + threadIdx.y; ci < count; ci += gridDim.y * blockDim.y) {
-    const FeItem it = fe[list[ci]];
+    const FeItem it = items[ci];
     const int L = it.L;
-    float y[MAXL], g[MAXL], pre[MAXL];
+    float4 rt[2], cf[2];
 #pragma unroll
-    for (int i = 0; i < MAXL; ++i) {
-      g[i] = 0.f;
-      y[i] = 1.f;
-      if (i < L) {
-        const int e = it.lit0 + i;
-        y[i] = lit_sgn[e] * x[(size_t)lit_var[e] * R + r];
+    for (int j = 0; j < 2; ++j) {
+      rt[j] = make_float4(1.f, 0.f, 0.f, 0.f);
+      cf[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < it.J) {
+        rt[j] = ldg4(&root[it.root_off + j]);
+        cf[j] = ldg4(&coef[it.coef_off + j]);
       }
     }
-    float val = it.b0;
-    for (int j = 0; j < it.J; ++j) {
-      const F4 rt = root[it.root_off + j];
-      const F4 cf = coef[it.coef_off + j];
-      float run = 1.f;
+    for (int tt = 0; tt < kThreadTiles; ++tt) {
+      const int tile = blockIdx.x * kThreadTiles + tt;
+      if (tile >= RT) break;
+      const int r = tile * 32 + lane;
+      if (r >= R) continue;
+      // literal records are re-read per tile (warp-uniform L1 hits) to keep
+      // the register footprint at three values per literal
+      float y[MAXL], g[MAXL], pre[MAXL];
+#pragma unroll
+      for (int i = 0; i < MAXL; ++i) {
+        g[i] = 0.f;
+        y[i] = 1.f;
+        pre[i] = 0.f;
+        if (i < L) {
+          const LitRec rc = lit[it.lit0 + i];
+          y[i] = rec_sgn(rc.dst) * x[(size_t)rc.var * R + r];
+        }
+      }
+      float val = it.b0;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (j < it.J) {
+          float run = 1.f;
+#pragma unroll
+          for (int i = 0; i < MAXL; ++i) {
+            if (i < L) {
+              pre[i] = run;
+              run *= fmaf(y[i], rt[j].y, rt[j].x);
+            }
+          }
+          val = fmaf(cf[j].x, run, val);
+          float suf = cf[j].z;  // c'_j folded into the suffix product
+#pragma unroll
+          for (int i = MAXL - 1; i >= 0; --i) {
+            if (i < L) {
+              g[i] = fmaf(pre[i], suf, g[i]);
+              suf *= fmaf(y[i], rt[j].y, rt[j].x);
+            }
+          }
+        }
+      }
 #pragma unroll
       for (int i = 0; i < MAXL; ++i) {
         if (i < L) {
-          pre[i] = run;
-          run *= fmaf(y[i], rt.y, rt.x);
+          const LitRec rc = lit[it.lit0 + i];
+          P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * g[i];
         }
       }
-      val = fmaf(cf.x, run, val);
-      float suf = cf.z;  // c'_j folded into the suffix product
-#pragma unroll
-      for (int i = MAXL - 1; i >= 0; --i) {
-        if (i < L) {
-          g[i] = fmaf(pre[i], suf, g[i]);
-          suf *= fmaf(y[i], rt.y, rt.x);
-        }
-      }
+      if (fe_con) fe_con[(size_t)it.c * ldf + r] = val;
     }
-#pragma unroll
-    for (int i = 0; i < MAXL; ++i) {
-      if (i < L) {
-        const int e = it.lit0 + i;
-        P[(size_t)lit_dst[e] * Rp + r] = it.w * lit_sgn[e] * g[i];
-      }
-    }
-    if (fe_con) fe_con[(size_t)it.c * ldf + r] = val;
   }
 }
 
 // ---------------------------------------------------------------------------
 // A2-A5 lane-group kernel: G lanes share one (constraint, restart); lane lam
-// holds literals lam, lam+G, ..., (at most Q).  One block = one constraint x
-// a tile of 32 restarts; literal values are staged in shared memory as
+// holds literals lam, lam+G, ..., (Q slots).  One block = one constraint x a
+// tile of 32 restarts; literal values are staged in shared memory as
 // ys[i*LDR + rr] with LDR = 32 + 32/G, which makes both the coalesced staging
 // stores (lanes over rr) and the group reads (lanes over lam, groups over rr)
-// bank-conflict free.
+// bank-conflict free.  Slots beyond L are staged as y = 1.
 //
 // Per root j: factors F_ij, lane-local exclusive prefix products, then a
 // butterfly over the G lanes that yields both the total G_j = prod_i F_ij and
 // the product of the OTHER lanes' chunks (leave-one-lane-out, O).  The
 // gradient uses prod_{l!=i} F_lj = O * prefix_i * suffix_i with the suffix
 // carried backwards and c'_j O folded into it: no division by a factor, so
-// nothing breaks where a factor vanishes.  Padding literal slots hold y = 1,
-// for which every root's factor is exactly 1 (A + B == 1, C - C == 0).
+// nothing breaks where a factor vanishes.  For DFT roots y = 1 gives a factor
+// of exactly 1 (A + B == 1, C - C == 0), so padding needs no masking; real
+// roots mask padding explicitly (beta(1) = 0).  YS re-reads y from shared
+// memory in both passes instead of holding Q registers.
 // ---------------------------------------------------------------------------
 template <int G>
 struct GroupGeom {
@@ -155,16 +178,16 @@ struct GroupGeom {
   static constexpr int PASSES = 32 / GPB;    // to cover 32 restarts
 };
 
-template <int G, int Q, bool CPLX>
+template <int G, int Q, bool CPLX, bool YS>
 __global__ void __launch_bounds__(256) k_fe_group(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
-    const F4* __restrict__ root, const F4* __restrict__ coef, const int32_t* __restrict__ lit_var,
-    const float* __restrict__ lit_sgn, const int32_t* __restrict__ lit_dst,
-    const float* __restrict__ x, int R, int Rp, float* __restrict__ P, float* __restrict__ fe_con,
-    int ldf) {
+    const F4* __restrict__ root, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
+    const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
+    float* __restrict__ fe_con, int ldf) {
   using Geo = GroupGeom<G>;
+  constexpr int LS = G * Q;          // staged literal slots
   extern __shared__ float smem[];
-  float* ys = smem;                  // [L][LDR]
+  float* ys = smem;                  // [LS][LDR]
   __shared__ float fe_s[32];
   const FeItem it = fe[list[blockIdx.x]];
   const int L = it.L;
@@ -172,10 +195,14 @@ __global__ void __launch_bounds__(256) k_fe_group(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   // stage literal values y = s * x (coalesced rows of 32 restarts)
-  for (int i = warp; i < L; i += 8) {
-    const int e = it.lit0 + i;
-    const int r = r0 + lane;
-    ys[i * Geo::LDR + lane] = (r < R) ? lit_sgn[e] * x[(size_t)lit_var[e] * R + r] : 1.0f;
+  for (int i = warp; i < LS; i += 8) {
+    float v = 1.0f;
+    if (i < L) {
+      const LitRec rc = lit[it.lit0 + i];
+      const int r = r0 + lane;
+      if (r < R) v = rec_sgn(rc.dst) * x[(size_t)rc.var * R + r];
+    }
+    ys[i * Geo::LDR + lane] = v;
   }
   __syncthreads();
 
@@ -184,13 +211,17 @@ __global__ void __launch_bounds__(256) k_fe_group(
 #pragma unroll 1
   for (int pass = 0; pass < Geo::PASSES; ++pass) {
     const int rr = pass * Geo::GPB + warp * Geo::GPW + gi;
-    float y[Q], acc[Q];
+    const float* ycol = ys + lam * Geo::LDR + rr;   // slot s at ycol[s * G * LDR]
+    float yreg[YS ? 1 : Q], acc[Q];
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
-      const int i = lam + G * s;
-      y[s] = (i < L) ? ys[i * Geo::LDR + rr] : 1.0f;
+      if constexpr (!YS) yreg[s] = ycol[s * G * Geo::LDR];
       acc[s] = 0.f;
     }
+    auto Y = [&](int s) -> float {
+      if constexpr (YS) return ycol[s * G * Geo::LDR];
+      else return yreg[s];
+    };
     float val = 0.f;
 #pragma unroll 1
     for (int j = 0; j < it.J; ++j) {
@@ -198,14 +229,20 @@ __global__ void __launch_bounds__(256) k_fe_group(
       const float4 cf = ldg4(&coef[it.coef_off + j]);
       if constexpr (CPLX) {
         float pr[Q], pim[Q];
-        float qr = fmaf(y[0], rt.y, rt.x), qi = fmaf(-y[0], rt.z, rt.z);
+        float qr, qi;
+        {
+          const float y0 = Y(0);
+          qr = fmaf(y0, rt.y, rt.x);
+          qi = fmaf(-y0, rt.z, rt.z);
+        }
         pr[0] = 1.f;
         pim[0] = 0.f;
 #pragma unroll
         for (int s = 1; s < Q; ++s) {
           pr[s] = qr;
           pim[s] = qi;
-          const float fr = fmaf(y[s], rt.y, rt.x), fi = fmaf(-y[s], rt.z, rt.z);
+          const float ys_ = Y(s);
+          const float fr = fmaf(ys_, rt.y, rt.x), fi = fmaf(-ys_, rt.z, rt.z);
           const float nr = qr * fr - qi * fi;
           const float ni = qr * fi + qi * fr;
           qr = nr;
@@ -237,7 +274,8 @@ __global__ void __launch_bounds__(256) k_fe_group(
           acc[s] = fmaf(pr[s], hr, acc[s]);
           acc[s] = fmaf(-pim[s], hi, acc[s]);
           if (s > 0) {
-            const float fr = fmaf(y[s], rt.y, rt.x), fi = fmaf(-y[s], rt.z, rt.z);
+            const float ys_ = Y(s);
+            const float fr = fmaf(ys_, rt.y, rt.x), fi = fmaf(-ys_, rt.z, rt.z);
             const float a = hr * fr - hi * fi, b = hr * fi + hi * fr;
             hr = a;
             hi = b;
@@ -251,7 +289,7 @@ __global__ void __launch_bounds__(256) k_fe_group(
         for (int s = 0; s < Q; ++s) {
           pr[s] = q;
           const bool live = lam + G * s < L;
-          q *= live ? fmaf(y[s], rt.y, rt.x) : 1.f;
+          q *= live ? fmaf(Y(s), rt.y, rt.x) : 1.f;
         }
         float Pt = q, O = 1.f;
 #pragma unroll
@@ -266,11 +304,11 @@ __global__ void __launch_bounds__(256) k_fe_group(
         for (int s = Q - 1; s >= 0; --s) {
           acc[s] = fmaf(pr[s], h, acc[s]);
           const bool live = lam + G * s < L;
-          h *= live ? fmaf(y[s], rt.y, rt.x) : 1.f;
+          h *= live ? fmaf(Y(s), rt.y, rt.x) : 1.f;
         }
       }
     }
-    // partials back into the staging slots (each lane owns its slots)
+    // partials back into the staging slots (each slot is owned by one lane)
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
       const int i = lam + G * s;
@@ -281,9 +319,10 @@ __global__ void __launch_bounds__(256) k_fe_group(
   __syncthreads();
   // write partials w * s_e * dFE/dy_e to their variable-major rows
   for (int i = warp; i < L; i += 8) {
-    const int e = it.lit0 + i;
+    const LitRec rc = lit[it.lit0 + i];
     const int r = r0 + lane;
-    if (r < R) P[(size_t)lit_dst[e] * Rp + r] = it.w * lit_sgn[e] * ys[i * Geo::LDR + lane];
+    if (r < R)
+      P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
   }
   if (fe_con && warp == 0 && r0 + lane < R) fe_con[(size_t)it.c * ldf + r0 + lane] = fe_s[lane];
 }
@@ -362,44 +401,87 @@ __global__ void __launch_bounds__(256) k_pgd(int n, int R, int RW, float* __rest
 }
 
 // ---------------------------------------------------------------------------
-// A9: exact satisfaction counts.  A literal is true iff its variable's bit
-// XOR (sign < 0).  The bitset word of a variable is a warp-uniform load; lane
-// r extracts its own bit.  Per block: a chunk of constraints x 32 restarts,
-// reduced over the 8 warps in a fixed order into per-chunk partials.
+// A9: exact satisfaction counts.  A warp owns a range of consecutive
+// constraints and one tile of 32 restarts.  It walks the range's literals in
+// chunks of 32: lane i fetches literal i's bitset word (bit r = its variable
+// is true at restart r), inverted for a negated literal, so bit r = "literal
+// true at restart r".  A 5-step shuffle butterfly transposes the 32x32 bit
+// matrix, after which lane r holds, for its restart, one bit per literal of
+// the chunk; each constraint's count t is a popcount of its bit segment
+// (carried across chunks for long constraints).  Per-warp counts are reduced
+// over the block's warps in a fixed order into per-chunk partials.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_score(int m, int R, int Rp, int RW, int chunk,
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const uint32_t m = masks[k];
+    const uint32_t y = __shfl_xor_sync(kFull, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y << j) & ~m));
+  }
+  return x;
+}
+
+__device__ __forceinline__ bool sat_of(const ScoreItem& s, int t,
+                                       const uint32_t* __restrict__ satbits) {
+  if (s.mode == 0) return t >= s.lo && t <= s.hi;
+  if (s.mode == 1) return (t & 1) != 0;
+  return ((satbits[(s.lo + t) >> 5] >> ((s.lo + t) & 31)) & 1u) != 0;
+}
+
+__global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
+                                               const int32_t* __restrict__ ranges,
                                                const ScoreItem* __restrict__ sc,
-                                               const int32_t* __restrict__ lit_var,
-                                               const float* __restrict__ lit_sgn,
+                                               const LitRec* __restrict__ lit,
                                                const uint32_t* __restrict__ satbits,
                                                const uint32_t* __restrict__ bits,
                                                int32_t* __restrict__ nsat_part,
                                                double* __restrict__ wsat_part) {
-  __shared__ int32_t cnt_s[8][32];
-  __shared__ double w_s[8][32];
+  __shared__ int32_t cnt_s[kScoreWarps][32];
+  __shared__ double w_s[kScoreWarps][32];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int tile = blockIdx.x;
-  const int c0 = blockIdx.y * chunk;
-  const int c1 = min(m, c0 + chunk);
+  const int rg = blockIdx.y * kScoreWarps + ty;
   int cnt = 0;
   double ws = 0.0;
-  for (int c = c0 + ty; c < c1; c += blockDim.y) {
-    const ScoreItem s = sc[c];
-    int t = 0;
-    for (int i = 0; i < s.L; ++i) {
-      const int e = s.lit0 + i;
-      const uint32_t wd = bits[(size_t)lit_var[e] * RW + tile];
-      t += (int)((wd >> lane) & 1u) ^ (int)(lit_sgn[e] < 0.f);
+  if (rg < n_ranges) {
+    int c = ranges[rg];
+    const int c_end = ranges[rg + 1];
+    ScoreItem s = sc[c];
+    int e = s.lit0;
+    const ScoreItem last = sc[c_end - 1];
+    const int e_end = last.lit0 + last.L;
+    int run = 0;
+    while (e < e_end) {
+      uint32_t word = 0;
+      if (e + lane < e_end) {
+        const LitRec rc = lit[e + lane];
+        word = bits[(size_t)rc.var * RW + tile];
+        if (rc.dst < 0) word = ~word;
+      }
+      const uint32_t col = transpose32(word, lane);
+      const int chunk_end = e + 32;
+      // constraints ending inside this chunk
+      while (c < c_end && s.lit0 + s.L <= chunk_end) {
+        const int lo = max(s.lit0, e) - e;
+        const int hi = s.lit0 + s.L - e;
+        const uint32_t mask = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & (kFull << lo);
+        const int t = run + __popc(col & mask);
+        run = 0;
+        const bool sat = sat_of(s, t, satbits);
+        cnt += sat ? 1 : 0;
+        ws += sat ? (double)s.w : 0.0;
+        ++c;
+        if (c < c_end) s = sc[c];
+      }
+      // a constraint straddling into the next chunk
+      if (c < c_end && s.lit0 < chunk_end) {
+        const int lo = max(s.lit0, e) - e;
+        run += __popc(col & (kFull << lo));
+      }
+      e = chunk_end;
     }
-    bool sat;
-    if (s.mode == 0)
-      sat = (t >= s.lo) && (t <= s.hi);
-    else if (s.mode == 1)
-      sat = (t & 1) != 0;
-    else
-      sat = ((satbits[(s.lo + t) >> 5] >> ((s.lo + t) & 31)) & 1u) != 0;
-    cnt += sat ? 1 : 0;
-    ws += sat ? (double)s.w : 0.0;
   }
   cnt_s[ty][lane] = cnt;
   w_s[ty][lane] = ws;
@@ -408,7 +490,7 @@ __global__ void __launch_bounds__(256) k_score(int m, int R, int Rp, int RW, int
     int a = 0;
     double b = 0.0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kScoreWarps; ++k) {
       a += cnt_s[k][lane];
       b += w_s[k][lane];
     }
@@ -470,20 +552,30 @@ struct HookScope {
   }
 };
 
-template <int G, int Q, int C>
-size_t group_smem(int maxL) {
-  return (size_t)maxL * GroupGeom<G>::LDR * sizeof(float);
+template <int G, int Q>
+constexpr size_t group_smem() {
+  return (size_t)G * Q * GroupGeom<G>::LDR * sizeof(float);
 }
 
 }  // namespace
 
+size_t group_smem_bytes(int cfg) {
+  switch (cfg) {
+#define CLS_SMEM_CASE(id, G, Q, C, Y) \
+  case id: return group_smem<G, Q>();
+    CLS_GROUP_CONFIGS(CLS_SMEM_CASE)
+#undef CLS_SMEM_CASE
+    default: return 0;
+  }
+}
+
 cudaError_t set_kernel_attributes() {
   cudaError_t err = cudaSuccess;
-#define CLS_SET_ATTR(id, G, Q, C)                                                        \
+#define CLS_SET_ATTR(id, G, Q, C, Y)                                                     \
   if (err == cudaSuccess)                                                                \
-    err = cudaFuncSetAttribute(k_fe_group<G, Q, (C != 0)>,                               \
+    err = cudaFuncSetAttribute(k_fe_group<G, Q, (C != 0), (Y != 0)>,                     \
                                cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                               (int)group_smem<G, Q, C>(G * Q));
+                               (int)group_smem<G, Q>());
   CLS_GROUP_CONFIGS(CLS_SET_ATTR)
 #undef CLS_SET_ATTR
   return err;
@@ -499,38 +591,55 @@ cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, f
   return cudaGetLastError();
 }
 
+cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL,
+                         int R, int Rp, const float* x, float* P, float* fe_con, int ldf,
+                         cudaStream_t s) {
+  (void)maxL;
+  if (count == 0 || R == 0) return cudaSuccess;
+  const dim3 grid(count, ceil_div(R, 32)), block(256);
+  switch (cfg) {
+#define CLS_LAUNCH_CASE(id, G, Q, C, Y)                                                      \
+  case id:                                                                                   \
+    k_fe_group<G, Q, (C != 0), (Y != 0)><<<grid, block, group_smem<G, Q>(), s>>>(            \
+        list, d.fe, d.root_tab, d.coef_tab, d.lit, x, R, Rp, P, fe_con, ldf);                \
+    break;
+    CLS_GROUP_CONFIGS(CLS_LAUNCH_CASE)
+#undef CLS_LAUNCH_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P, float* fe_con,
                       int ldf, cudaStream_t s, LaunchHook* h) {
-  const int RT = ceil_div(R, 32);
   if (R == 0) return cudaSuccess;
-  for (int t = 0; t < 2; ++t) {
+  const int RT = ceil_div(R, 32);
+  for (int t = 0; t < kNumThreadCls; ++t) {
     const int cnt = d.thread_count[t];
     if (cnt == 0) continue;
-    dim3 grid(RT, std::min(ceil_div(cnt, 8), 65535)), block(32, 8);
+    const dim3 grid(ceil_div(RT, kThreadTiles), std::min(ceil_div(cnt, 8), 65535)),
+        block(32, 8);
     HookScope hs(h, KC_THREAD, s);
-    if (t == 0)
-      k_fe_thread<kThreadMaxL0><<<grid, block, 0, s>>>(d.thread_list[t], cnt, d.fe, d.root_tab,
-                                                       d.coef_tab, d.lit_var, d.lit_sgn,
-                                                       d.lit_dst, x, R, Rp, P, fe_con, ldf);
+    const FeItem* items = d.thread_items[t];
+    if (kThreadMaxL[t] == 8)
+      k_fe_thread<8><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.lit, x, R, Rp,
+                                            RT, P, fe_con, ldf);
+    else if (kThreadMaxL[t] == 16)
+      k_fe_thread<16><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.lit, x, R,
+                                             Rp, RT, P, fe_con, ldf);
     else
-      k_fe_thread<kThreadMaxL1><<<grid, block, 0, s>>>(d.thread_list[t], cnt, d.fe, d.root_tab,
-                                                       d.coef_tab, d.lit_var, d.lit_sgn,
-                                                       d.lit_dst, x, R, Rp, P, fe_con, ldf);
+      k_fe_thread<32><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.lit, x, R,
+                                             Rp, RT, P, fe_con, ldf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-#define CLS_LAUNCH_GROUP(id, G, Q, C)                                                        \
-  if (d.group_count[id] > 0) {                                                               \
-    dim3 grid(d.group_count[id], RT), block(256);                                            \
-    HookScope hs(h, C ? KC_GROUP_DFT : KC_GROUP_REAL, s);                                    \
-    k_fe_group<G, Q, (C != 0)><<<grid, block, group_smem<G, Q, C>(d.group_maxL[id]), s>>>(   \
-        d.group_list[id], d.fe, d.root_tab, d.coef_tab, d.lit_var, d.lit_sgn, d.lit_dst, x, \
-        R, Rp, P, fe_con, ldf);                                                              \
-    cudaError_t e = cudaGetLastError();                                                      \
-    if (e != cudaSuccess) return e;                                                          \
+  for (int b = 0; b < kNumBuckets; ++b) {
+    if (d.bucket_count[b] == 0) continue;
+    HookScope hs(h, b < kNumDftBuckets ? KC_GROUP_DFT : KC_GROUP_REAL, s);
+    cudaError_t e = launch_group(d.bucket_cfg[b], d, d.bucket_list[b], d.bucket_count[b],
+                                 d.bucket_maxL[b], R, Rp, x, P, fe_con, ldf, s);
+    if (e != cudaSuccess) return e;
   }
-  CLS_GROUP_CONFIGS(CLS_LAUNCH_GROUP)
-#undef CLS_LAUNCH_GROUP
   return cudaSuccess;
 }
 
@@ -567,9 +676,9 @@ cudaError_t launch_round(const DevPlan& d, int R, const float* x, uint32_t* bits
   return cudaGetLastError();
 }
 
-cudaError_t launch_score(const DevPlan& d, int R, int Rp, int nch, int chunk,
-                         const uint32_t* bits, int32_t* nsat_part, double* wsat_part,
-                         int32_t* nsat, double* wsat, cudaStream_t s, LaunchHook* h) {
+cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
+                         int32_t* nsat_part, double* wsat_part, int32_t* nsat, double* wsat,
+                         cudaStream_t s, LaunchHook* h) {
   if (R == 0) return cudaSuccess;
   const int RT = ceil_div(R, 32);
   if (d.m == 0) {
@@ -580,11 +689,12 @@ cudaError_t launch_score(const DevPlan& d, int R, int Rp, int nch, int chunk,
     if (wsat) return cudaMemsetAsync(wsat, 0, sizeof(double) * R, s);
     return cudaSuccess;
   }
+  const int nch = score_chunks(d.n_ranges);
   {
     HookScope hs(h, KC_SCORE, s);
-    k_score<<<dim3(RT, nch), dim3(32, 8), 0, s>>>(d.m, R, Rp, RT, chunk, d.score, d.lit_var,
-                                                  d.lit_sgn, d.satbits, bits, nsat_part,
-                                                  wsat_part);
+    k_score<<<dim3(RT, nch), dim3(32, kScoreWarps), 0, s>>>(RT, Rp, d.n_ranges, d.score_ranges,
+                                                            d.score, d.lit, d.satbits, bits,
+                                                            nsat_part, wsat_part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

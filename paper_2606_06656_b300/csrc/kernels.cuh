@@ -9,27 +9,34 @@
 
 namespace cls {
 
+constexpr int kNumBuckets = kNumDftBuckets + kNumRealBuckets;
+
 // Device copy of a HostPlan.
 struct DevPlan {
   int32_t n = 0, m = 0;
   int64_t nnz = 0;
-  int32_t* lit_var = nullptr;
-  float* lit_sgn = nullptr;
-  int32_t* lit_dst = nullptr;
+  LitRec* lit = nullptr;
   int32_t* voff = nullptr;
   FeItem* fe = nullptr;
-  ScoreItem* score = nullptr;
+  FeItem* thread_items[kNumThreadCls] = {};
+  int32_t thread_count[kNumThreadCls] = {};
+  int32_t* bucket_list[kNumBuckets] = {};
+  int32_t bucket_count[kNumBuckets] = {};
+  int32_t bucket_cfg[kNumBuckets] = {};
+  int32_t bucket_maxL[kNumBuckets] = {};
+  ScoreItem* score = nullptr;        // constraint order
+  int32_t* score_ranges = nullptr;   // n_ranges+1 constraint boundaries
+  int32_t n_ranges = 0;
   uint32_t* satbits = nullptr;
   F4* root_tab = nullptr;
   F4* coef_tab = nullptr;
-  int32_t* thread_list[2] = {nullptr, nullptr};
-  int32_t thread_count[2] = {0, 0};
-  int32_t* group_list[kNumGroupCfg] = {};
-  int32_t group_count[kNumGroupCfg] = {};
-  int32_t group_maxL[kNumGroupCfg] = {};
   uint8_t* fixed = nullptr;
   float* fixed_val = nullptr;
 };
+
+// Warps (score ranges) per score block; partial rows = ceil(n_ranges / this).
+constexpr int kScoreWarps = 8;
+inline int score_chunks(int n_ranges) { return (n_ranges + kScoreWarps - 1) / kScoreWarps; }
 
 // Kernel classes for profiling (cls_profile_read).
 enum KernelClass { KC_THREAD = 0, KC_GROUP_REAL, KC_GROUP_DFT, KC_ACCUM, KC_SCORE,
@@ -43,14 +50,20 @@ struct LaunchHook {
 };
 
 cudaError_t set_kernel_attributes();
+size_t group_smem_bytes(int cfg);
 
 cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, float* x,
                         cudaStream_t s, LaunchHook* h);
 
-// FE + literal partials: P[lit_dst[e] * Rp + r] = w_c s_e dFE_c/dy_e, and
-// (if fe_con) fe_con[c * ldf + r] = FE_c.
+// FE + literal partials: P[row * Rp + r] = w_c s_e dFE_c/dy_e (row = the
+// literal's variable-major row), and (if fe_con) fe_con[c * ldf + r] = FE_c.
 cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P, float* fe_con,
                       int ldf, cudaStream_t s, LaunchHook* h);
+
+// One lane-group launch over an explicit constraint list (the autotuner).
+cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL,
+                         int R, int Rp, const float* x, float* P, float* fe_con, int ldf,
+                         cudaStream_t s);
 
 // g[v,r] = sum of rows voff[v]..voff[v+1]-1 of P; optional grad output;
 // optional projected step of x in place and bitset of the new x.
@@ -67,9 +80,9 @@ cudaError_t launch_round(const DevPlan& d, int R, const float* x, uint32_t* bits
                          cudaStream_t s, LaunchHook* h);
 
 // Exact satisfaction counts from the bitset, two-stage (chunks, then order).
-cudaError_t launch_score(const DevPlan& d, int R, int Rp, int nch, int chunk,
-                         const uint32_t* bits, int32_t* nsat_part, double* wsat_part,
-                         int32_t* nsat, double* wsat, cudaStream_t s, LaunchHook* h);
+cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
+                         int32_t* nsat_part, double* wsat_part, int32_t* nsat, double* wsat,
+                         cudaStream_t s, LaunchHook* h);
 
 // obj[r] = sum_c w_c fe_con[c*ldf + r] in FP64 (fixed order), rounded to FP32.
 cudaError_t launch_obj(const DevPlan& d, int R, int Rp, int nch, int chunk, const float* fe_con,

@@ -12,17 +12,39 @@
 namespace cls {
 
 const GroupCfg kGroupCfg[kNumGroupCfg] = {
-#define CLS_CFG_ENTRY(id, G, Q, C) {G, Q, C},
+#define CLS_CFG_ENTRY(id, G, Q, C, Y) {G, Q, C, Y},
     CLS_GROUP_CONFIGS(CLS_CFG_ENTRY)
 #undef CLS_CFG_ENTRY
 };
 
 Tuning default_tuning() {
   Tuning t;
-  t.dft = {{8, 0},   {16, 1},   {32, 2},   {64, 3},   {128, 5},  {192, 6},
-           {256, 7}, {320, 20}, {384, 10}, {512, 11}, {768, 12}, {1024, 13}};
-  t.real = {{64, 14}, {128, 15}, {256, 16}, {512, 17}, {1024, 18}};
+  const int dft[kNumDftBuckets] = {0,  1,  2,  3,  4,  8,  9,  24, 25, 26,
+                                   27, 28, 29, 30, 33, 34, 35, 36, 37};
+  const int real[kNumRealBuckets] = {41, 42, 43, 44, 45};
+  for (int b = 0; b < kNumDftBuckets; ++b) t.dft[b] = dft[b];
+  for (int b = 0; b < kNumRealBuckets; ++b) t.real[b] = real[b];
   return t;
+}
+
+bool tuning_valid(const Tuning& t, std::string* msg) {
+  for (int b = 0; b < kNumDftBuckets + kNumRealBuckets; ++b) {
+    const bool dft = b < kNumDftBuckets;
+    const int id = dft ? t.dft[b] : t.real[b - kNumDftBuckets];
+    const int maxL = dft ? kDftBucketMax[b] : kRealBucketMax[b - kNumDftBuckets];
+    if (id < 0 || id >= kNumGroupCfg) {
+      if (msg) *msg = "configuration id out of range";
+      return false;
+    }
+    const GroupCfg& g = kGroupCfg[id];
+    if (g.cplx != (dft ? 1 : 0) || g.G * g.Q < maxL) {
+      if (msg)
+        *msg = "configuration " + std::to_string(id) + " cannot serve bucket " +
+               std::to_string(b) + " (max length " + std::to_string(maxL) + ")";
+      return false;
+    }
+  }
+  return true;
 }
 
 namespace {
@@ -46,31 +68,36 @@ bool holds(int type, int L, int k, int t, const int8_t* spec) {
   }
 }
 
-int pick(const std::vector<std::pair<int, int>>& ladder, int L) {
-  for (auto& e : ladder)
-    if (L <= e.first) return e.second;
-  return ladder.back().second;
+int bucket_of(const int* maxes, int nb, int L) {
+  for (int b = 0; b < nb; ++b)
+    if (L <= maxes[b]) return b;
+  return nb - 1;
 }
 
 }  // namespace
 
 void assign_groups(HostPlan* P, const Tuning& tun) {
-  for (auto& v : P->thread_list) v.clear();
-  for (auto& v : P->group_list) v.clear();
+  for (auto& v : P->thread_items) v.clear();
+  for (auto& v : P->bucket_list) v.clear();
+  P->tuning = tun;
+  for (int b = 0; b < kNumDftBuckets; ++b) P->bucket_cfg[b] = tun.dft[b];
+  for (int b = 0; b < kNumRealBuckets; ++b) P->bucket_cfg[kNumDftBuckets + b] = tun.real[b];
   P->n_thread = P->n_group_real = P->n_group_dft = 0;
+  std::vector<int32_t> thread_c[kNumThreadCls];
   for (int32_t c = 0; c < P->m; ++c) {
     const FeItem& it = P->fe[c];
     bool real = it.root_off < 3;  // real roots live at the start of the table
-    if (real && it.L <= kThreadMaxL1) {
-      P->thread_list[it.L <= kThreadMaxL0 ? 0 : 1].push_back(c);
+    if (real && it.L <= kThreadMaxL[kNumThreadCls - 1]) {
+      int t = 0;
+      while (it.L > kThreadMaxL[t]) ++t;
+      thread_c[t].push_back(c);
       P->n_thread++;
     } else if (real) {
-      int id = pick(tun.real, it.L);
-      P->group_list[id].push_back(c);
+      P->bucket_list[kNumDftBuckets + bucket_of(kRealBucketMax, kNumRealBuckets, it.L)]
+          .push_back(c);
       P->n_group_real++;
     } else {
-      int id = pick(tun.dft, it.L);
-      P->group_list[id].push_back(c);
+      P->bucket_list[bucket_of(kDftBucketMax, kNumDftBuckets, it.L)].push_back(c);
       P->n_group_dft++;
     }
   }
@@ -78,15 +105,18 @@ void assign_groups(HostPlan* P, const Tuning& tun) {
   auto byL = [P](int32_t a, int32_t b) {
     return P->fe[a].L != P->fe[b].L ? P->fe[a].L > P->fe[b].L : a < b;
   };
-  for (auto& v : P->thread_list) std::stable_sort(v.begin(), v.end(), byL);
-  for (auto& v : P->group_list) std::stable_sort(v.begin(), v.end(), byL);
+  for (int t = 0; t < kNumThreadCls; ++t) {
+    std::stable_sort(thread_c[t].begin(), thread_c[t].end(), byL);
+    for (int32_t c : thread_c[t]) P->thread_items[t].push_back(P->fe[c]);
+  }
+  for (auto& v : P->bucket_list) std::stable_sort(v.begin(), v.end(), byL);
 }
 
 int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
                const int8_t* lit_sign, const int32_t* type, const int32_t* kk,
                const float* weight, const int8_t* spectra, const uint8_t* fixed,
-               const float* fixed_val, const Tuning& tun, bool validate_only,
-               HostPlan* out, std::string* msg) {
+               const float* fixed_val, bool validate_only, HostPlan* out,
+               std::string* msg) {
   auto fail = [msg](const std::string& s) {
     if (msg) *msg = s;
     return -1;
@@ -146,9 +176,6 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   P.n = n;
   P.m = m;
   P.nnz = nnz;
-  P.lit_var.assign(lit_var, lit_var + nnz);
-  P.lit_sgn.resize(nnz);
-  for (int64_t e = 0; e < nnz; ++e) P.lit_sgn[e] = (float)lit_sign[e];
 
   // variable-major transpose: rows of variable v are voff[v]..voff[v+1]-1,
   // literals in increasing constraint order (a fixed summation order)
@@ -156,8 +183,12 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   for (int64_t e = 0; e < nnz; ++e) P.voff[lit_var[e] + 1]++;
   for (int32_t v = 0; v < n; ++v) P.voff[v + 1] += P.voff[v];
   std::vector<int32_t> cur(P.voff.begin(), P.voff.end() - 1);
-  P.lit_dst.resize(nnz);
-  for (int64_t e = 0; e < nnz; ++e) P.lit_dst[e] = cur[lit_var[e]]++;
+  P.lit.resize(nnz);
+  for (int64_t e = 0; e < nnz; ++e) {
+    int32_t dst = cur[lit_var[e]]++;
+    P.lit[e].var = lit_var[e];
+    P.lit[e].dst = dst | (lit_sign[e] < 0 ? kNegBit : 0);
+  }
 
   // fixed real roots and their coefficients
   P.root_tab = {{0.5f, 0.5f, 0.f, 0.f}, {0.5f, -0.5f, 0.f, 0.f}, {0.f, 1.f, 0.f, 0.f}};
@@ -167,7 +198,6 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   std::map<std::pair<int, std::string>, int> coef_of_spec;
 
   P.fe.resize(m);
-  P.score.resize(m);
   int64_t soff = 0;
   std::vector<int8_t> sp;
   for (int32_t c = 0; c < m; ++c) {
@@ -185,8 +215,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
     for (int tt = 0; tt <= L; ++tt) sp[tt] = holds(t, L, k, tt, spec) ? -1 : 1;
 
     // score predicate
-    ScoreItem& s = P.score[c];
-    s = ScoreItem{offsets[c], L, 0, 0, 0, w, 0, 0};
+    ScoreItem s = ScoreItem{offsets[c], L, 0, 0, 0, w, c, 0};
     switch (t) {
       case T_OR: s.lo = 1; s.hi = L; break;
       case T_XOR: s.mode = 1; break;
@@ -204,6 +233,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
           if (sp[tt] == -1) P.satbits[(s.lo + tt) >> 5] |= 1u << ((s.lo + tt) & 31);
       }
     }
+    P.score.push_back(s);
 
     FeItem& it = P.fe[c];
     it.lit0 = offsets[c];
@@ -278,11 +308,21 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
     P.dft_roots += J;
     P.dft_lroots += (int64_t)J * L;
   }
+  // score ranges: consecutive constraints, about kScoreRangeLits literals each
+  P.score_ranges.push_back(0);
+  int64_t acc = 0;
+  for (int32_t c = 0; c < m; ++c) {
+    acc += P.score[c].L;
+    if (acc >= kScoreRangeLits || c == m - 1) {
+      P.score_ranges.push_back(c + 1);
+      acc = 0;
+    }
+  }
   if (fixed) {
     P.fixed.assign(fixed, fixed + n);
     P.fixed_val.assign(fixed_val, fixed_val + n);
   }
-  assign_groups(&P, tun);
+  assign_groups(&P, default_tuning());
   return 0;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace cls {
@@ -12,17 +13,26 @@ struct F4 {
   float x, y, z, w;
 };
 
+// One literal: its variable and its row in variable-major order; the top bit
+// of `dst` is set when the literal is negated (sign -1).
+struct LitRec {
+  int32_t var;
+  int32_t dst;
+};
+constexpr int32_t kNegBit = int32_t(0x80000000u);
+
 // FE+gradient work description of one constraint.
 //   Literal values y_i = s_i x_{v_i} enter each "root" j as the factor
 //     F_ij = (A_j + y_i B_j) + i (C_j - y_i C_j)
 //   root table entry (A, B, C, 0).  For a DFT root (Sec. 2.3: evaluation at
 //   the L+1 roots of unity w^j) A = (1+cos)/2, B = (1-cos)/2, C = sin/2 of
-//   2 pi j/(L+1) (A rounded as 1 - B in FP32, so A + B == 1 exactly), i.e. F = alpha_i + beta_i w^j with alpha = (1+y)/2 =
-//   P[literal false], beta = (1-y)/2 = P[literal true]; every factor has
-//   modulus <= 1.  Real roots (C = 0) give the closed-form products of
-//   OR/XOR/NAE: alpha (A=B=1/2), beta (A=1/2, B=-1/2), y (A=0, B=1).
+//   2 pi j/(L+1), with A rounded as 1 - B in FP32 so that A + B == 1 exactly;
+//   i.e. F = alpha_i + beta_i w^j with alpha = (1+y)/2 = P[literal false],
+//   beta = (1-y)/2 = P[literal true]; every factor has modulus <= 1.  Real
+//   roots (C = 0) give the closed-form products of OR/XOR/NAE: alpha
+//   (A=B=1/2), beta (A=1/2, B=-1/2), y (A=0, B=1).
 //   coefficient entry (b'.re, b'.im, c'.re, c'.im):
-//     FE      = b0 + Re sum_j b'_j prod_i F_ij
+//     FE       = b0 + Re sum_j b'_j prod_i F_ij
 //     dFE/dy_i =      Re sum_j c'_j prod_{l != i} F_lj,   c'_j = b'_j (B_j - i C_j)
 struct FeItem {
   int32_t lit0;      // first literal (constraint order)
@@ -44,43 +54,79 @@ struct ScoreItem {
   int32_t lo;
   int32_t hi;
   float w;
-  int32_t pad0, pad1;
+  int32_t c;
+  int32_t pad;
 };
 
 // Lane-group kernel configurations: G lanes share one (constraint, restart),
-// each lane holds up to Q literals (L <= G*Q); CPLX = DFT roots vs real roots.
-// The same list is instantiated in kernels.cu.
+// each lane holds up to Q literals (L <= G*Q); CPLX = DFT roots vs real
+// roots; YS = literal values re-read from shared memory instead of kept in
+// registers (fewer registers, more resident warps).  The same list is
+// instantiated in kernels.cu.  X(id, G, Q, CPLX, YS)
 #define CLS_GROUP_CONFIGS(X) \
-  X(0, 8, 1, 1)              \
-  X(1, 8, 2, 1)              \
-  X(2, 8, 4, 1)              \
-  X(3, 8, 8, 1)              \
-  X(4, 16, 4, 1)             \
-  X(5, 16, 8, 1)             \
-  X(6, 16, 12, 1)            \
-  X(7, 16, 16, 1)            \
-  X(8, 32, 4, 1)             \
-  X(9, 32, 8, 1)             \
-  X(10, 32, 12, 1)           \
-  X(11, 32, 16, 1)           \
-  X(12, 32, 24, 1)           \
-  X(13, 32, 32, 1)           \
-  X(14, 32, 2, 0)            \
-  X(15, 32, 4, 0)            \
-  X(16, 32, 8, 0)            \
-  X(17, 32, 16, 0)           \
-  X(18, 32, 32, 0)           \
-  X(19, 8, 16, 1)            \
-  X(20, 16, 20, 1)
-constexpr int kNumGroupCfg = 21;
+  X(0, 8, 1, 1, 0)           \
+  X(1, 8, 2, 1, 0)           \
+  X(2, 8, 4, 1, 0)           \
+  X(3, 8, 6, 1, 0)           \
+  X(4, 8, 8, 1, 0)           \
+  X(5, 8, 12, 1, 0)          \
+  X(6, 8, 16, 1, 0)          \
+  X(7, 16, 4, 1, 0)          \
+  X(8, 16, 6, 1, 0)          \
+  X(9, 16, 8, 1, 0)          \
+  X(10, 16, 10, 1, 0)        \
+  X(11, 16, 12, 1, 0)        \
+  X(12, 16, 16, 1, 0)        \
+  X(13, 16, 20, 1, 0)        \
+  X(14, 32, 8, 1, 0)         \
+  X(15, 32, 10, 1, 0)        \
+  X(16, 32, 12, 1, 0)        \
+  X(17, 32, 16, 1, 0)        \
+  X(18, 32, 24, 1, 0)        \
+  X(19, 32, 32, 1, 0)        \
+  X(20, 8, 8, 1, 1)          \
+  X(21, 8, 12, 1, 1)         \
+  X(22, 8, 16, 1, 1)         \
+  X(23, 16, 8, 1, 1)         \
+  X(24, 16, 10, 1, 1)        \
+  X(25, 16, 12, 1, 1)        \
+  X(26, 16, 14, 1, 1)        \
+  X(27, 16, 16, 1, 1)        \
+  X(28, 16, 18, 1, 1)        \
+  X(29, 16, 20, 1, 1)        \
+  X(30, 16, 24, 1, 1)        \
+  X(31, 32, 10, 1, 1)        \
+  X(32, 32, 12, 1, 1)        \
+  X(33, 32, 14, 1, 1)        \
+  X(34, 32, 16, 1, 1)        \
+  X(35, 32, 20, 1, 1)        \
+  X(36, 32, 24, 1, 1)        \
+  X(37, 32, 32, 1, 1)        \
+  X(38, 8, 24, 1, 1)         \
+  X(39, 8, 32, 1, 1)         \
+  X(40, 8, 40, 1, 1)         \
+  X(41, 32, 2, 0, 0)         \
+  X(42, 32, 4, 0, 0)         \
+  X(43, 32, 8, 0, 0)         \
+  X(44, 32, 16, 0, 0)        \
+  X(45, 32, 32, 0, 0)        \
+  X(46, 16, 4, 0, 0)         \
+  X(47, 16, 8, 0, 0)         \
+  X(48, 16, 16, 0, 0)
+constexpr int kNumGroupCfg = 49;
 struct GroupCfg {
-  int G, Q, cplx;
+  int G, Q, cplx, ys;
 };
 extern const GroupCfg kGroupCfg[kNumGroupCfg];
 
 // Thread-path (one thread per (constraint, restart)) length classes.
-constexpr int kThreadMaxL0 = 8;
-constexpr int kThreadMaxL1 = 32;
+constexpr int kNumThreadCls = 3;
+constexpr int kThreadMaxL[kNumThreadCls] = {8, 16, 32};
+constexpr int kThreadTiles = 4;   // restart tiles (of 32) per warp
+
+// Score path: consecutive constraints are grouped into ranges of about this
+// many literals; one warp scores one range for 32 restarts.
+constexpr int kScoreRangeLits = 256;
 
 // Fixed entries of the root table (real roots).
 constexpr int kRootAlpha = 0;  // alpha, then beta at 1 (NAE uses both)
@@ -90,40 +136,50 @@ constexpr int kCoefOr = 0;     // (2, 0, 1, 0)
 constexpr int kCoefXor = 1;    // (1, 0, 1, 0)
 constexpr int kCoefNae = 2;    // (2, 0, 1, 0), (2, 0, -1, 0)
 
+// Length buckets of the lane-group paths: one launch per non-empty bucket;
+// the tuning maps each bucket to a configuration.
+constexpr int kNumDftBuckets = 19;
+constexpr int kDftBucketMax[kNumDftBuckets] = {8,   16,  32,  48,  64,  96,  128,
+                                               160, 192, 224, 256, 288, 320, 384,
+                                               448, 512, 640, 768, 1024};
+constexpr int kNumRealBuckets = 5;
+constexpr int kRealBucketMax[kNumRealBuckets] = {64, 128, 256, 512, 1024};
+
+struct Tuning {
+  int dft[kNumDftBuckets];
+  int real[kNumRealBuckets];
+};
+Tuning default_tuning();
+bool tuning_valid(const Tuning& t, std::string* msg);
+
 struct HostPlan {
   int32_t n = 0, m = 0;
   int64_t nnz = 0;
-  std::vector<int32_t> lit_var;   // constraint order
-  std::vector<float> lit_sgn;     // +-1
-  std::vector<int32_t> lit_dst;   // row of the literal in variable-major order
+  std::vector<LitRec> lit;        // constraint order
   std::vector<int32_t> voff;      // n+1: rows of variable v
-  std::vector<FeItem> fe;         // m
-  std::vector<ScoreItem> score;   // m
+  std::vector<FeItem> fe;         // m (constraint order)
+  std::vector<ScoreItem> score;          // constraint order
+  std::vector<int32_t> score_ranges;     // constraint boundaries of the ranges
   std::vector<uint32_t> satbits;  // truth tables of SPECTRUM constraints
   std::vector<F4> root_tab, coef_tab;
-  std::vector<int32_t> thread_list[2];             // MAXL 8 / 32
-  std::vector<int32_t> group_list[kNumGroupCfg];   // per config, L descending
+  std::vector<FeItem> thread_items[kNumThreadCls];   // items in launch order
+  // lane-group buckets: [0, kNumDftBuckets) DFT, then real
+  std::vector<int32_t> bucket_list[kNumDftBuckets + kNumRealBuckets];
+  int bucket_cfg[kNumDftBuckets + kNumRealBuckets] = {};
   std::vector<uint8_t> fixed;     // n (empty = none)
   std::vector<float> fixed_val;   // n
+  Tuning tuning;
   int64_t dft_roots = 0, dft_lroots = 0;
   int64_t n_thread = 0, n_group_real = 0, n_group_dft = 0;
 };
-
-// Length -> group configuration map (index into kGroupCfg), per kind.
-struct Tuning {
-  // upper length bounds and config ids, ascending bounds
-  std::vector<std::pair<int, int>> dft, real;
-};
-Tuning default_tuning();
 
 // Validates and builds the plan. Returns 0 or -1 (msg set).
 int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
                const int8_t* lit_sign, const int32_t* type, const int32_t* k,
                const float* weight, const int8_t* spectra, const uint8_t* fixed,
-               const float* fixed_val, const Tuning& tun, bool validate_only,
-               HostPlan* out, std::string* msg);
+               const float* fixed_val, bool validate_only, HostPlan* out, std::string* msg);
 
-// Re-split the FE work lists for a different tuning (same plan).
+// (Re)split the FE work lists for a tuning.
 void assign_groups(HostPlan* plan, const Tuning& tun);
 
 }  // namespace cls

@@ -189,6 +189,55 @@ def test_round_score_bit_exact(P, R):
     assert np.allclose(wsat.cpu().numpy(), owsat, rtol=1e-12, atol=1e-12)
 
 
+def test_round_score_long_constraints_bit_exact(P):
+    """Constraints spanning many 32-literal chunks of the score kernel."""
+    rng = np.random.default_rng(17)
+    inst = W.random_constraint_set(rng, 1100, 40, ALL_TYPES, (20, 1024), weights="random")
+    for R in (45, 96):
+        X = W.mixed_points(inst.n, R, seed=R)
+        p = P(inst)
+        nsat, wsat, bits = p.round_score(torch.from_numpy(X).cuda())
+        onsat, owsat, _ = ocls.score(inst, X)
+        assert np.array_equal(nsat.cpu().numpy(), onsat)
+        assert np.allclose(wsat.cpu().numpy(), owsat, rtol=1e-12, atol=1e-12)
+
+
+def test_autotune_and_tuning_roundtrip(P):
+    from paper_2606_06656_b300 import binding as B
+    inst = W.mixed_pb(n=1200, n_or=3000, n_xor=300, n_card=60, card_len=(10, 300), seed=8)
+    X = W.uniform_points(inst.n, 96, seed=3)
+    p = P(inst)
+    x = torch.from_numpy(X).cuda()
+    before = p.eval(x, fe_con=True)
+    default = B.cls_tuning_get(p.handle)
+    B.cls_autotune(p.handle, 96, x, 1, p.workspace(96))
+    tuned = B.cls_tuning_get(p.handle)
+    after = p.eval(x, fe_con=True)
+    check_against_oracle(inst, X, *[t.cpu().numpy() for t in after])
+    assert torch.allclose(before[2], after[2], atol=2e-6)
+    # every admissible configuration of every bucket gives the same results
+    for b in range(B.N_BUCKETS):
+        kind, bmax, _, _ = B.cls_config_info(1000 + b)
+        for cid in range(60):
+            try:
+                G, Q, cplx, ys = B.cls_config_info(cid)
+            except Exception:
+                break
+            if cplx != kind or G * Q < bmax or G * Q > 2 * max(bmax, 32):
+                continue
+            cfg = list(tuned)
+            cfg[b] = cid
+            B.cls_tuning_set(p.handle, cfg)
+            o, g, f = p.eval(x, fe_con=True)
+            assert torch.allclose(f, after[2], atol=2e-6), (b, cid)
+            assert torch.allclose(g, after[1], atol=2e-5, rtol=1e-4), (b, cid)
+    B.cls_tuning_set(p.handle, default)
+    with pytest.raises(Exception):
+        bad = list(default)
+        bad[5] = 41          # a real-root configuration for a DFT bucket
+        B.cls_tuning_set(p.handle, bad)
+
+
 def test_pgd_update_bit_exact(P):
     rng = np.random.default_rng(3)
     inst = W.partial_assignment(W.mixed_pb(n=300, n_or=400, n_xor=30, n_card=5,
