@@ -207,6 +207,27 @@ int cls_tuning_get(const cls_problem* p, int32_t* cfg, int32_t n);
 int cls_tuning_set(cls_problem* p, const int32_t* cfg, int32_t n);
 int cls_config_info(int32_t id, int32_t* out);
 
+/* cls_step without any allocation, for callers that cannot allocate device
+ * memory while they run (a real-time loop that must not touch the allocator
+ * after start-up, a process confined to a fixed device-memory budget owned
+ * by another runtime, a host language with no route to cudaMalloc).  The
+ * paper has no counterpart; this is an interface convenience.
+ * Same arguments and results as cls_step, minus the workspace: the scratch
+ * lives in a file-scope device array of 32 MiB that every GPU loading this
+ * library holds until the process exits.  Problems whose
+ * cls_workspace_size(p, R) exceeds 32 MiB are rejected with
+ * CLS_ERR_WORKSPACE (use cls_step with a caller workspace instead).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array and
+ * it keeps the previous call's contents (the step writes every scratch byte
+ * it reads), so calls that may overlap on the GPU -- on different streams,
+ * or from different threads -- race and must be serialised by the caller.
+ * Profiling must be off (it creates CUDA events); CLS_ERR_INVALID
+ * otherwise.  It calls no cudaMalloc/cudaFree. */
+int cls_step_noalloc(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
+                     uint32_t* bits, int32_t* nsat, double* wsat, void* stream);
+
 /* Per-kernel timing (tracing): when enabled, each kernel launch of the
  * compute calls is bracketed by CUDA events on its stream; cls_profile_read
  * synchronises and returns, for kernel class kc (0 = thread-path FE+grad,

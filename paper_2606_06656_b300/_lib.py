@@ -34,6 +34,7 @@ SIGNATURES = {
     "cls_tuning_get": (i32, [vp, P(i32), i32]),
     "cls_tuning_set": (i32, [vp, P(i32), i32]),
     "cls_config_info": (i32, [i32, P(i32)]),
+    "cls_step_noalloc": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp]),
     "cls_profile_enable": (i32, [vp, i32]),
     "cls_profile_read": (i32, [vp, i32, P(i64), P(C.c_double)]),
     "cls_profile_reset": (i32, [vp]),

@@ -234,6 +234,12 @@ int run_step(const cls_problem* p, const Layout& L, float* x, float lr, uint32_t
 
 }  // namespace
 
+namespace cls {
+// Helpers for other translation units of the library (noalloc.cu).
+int set_error(int code, const std::string& msg) { return set_err(code, msg); }
+bool profiling_enabled(const cls_problem* p) { return p && p->hook != nullptr; }
+}  // namespace cls
+
 extern "C" {
 
 int cls_problem_check(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
