@@ -190,37 +190,51 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
     stream = torch.cuda.current_stream()
 
-    def step():
+    def step_eager():
         B.cls_step(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
+
+    graph = None if args.eager else B.cls_graph_create(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
+
+    def step():
+        if graph is not None:
+            B.cls_graph_launch(graph)
+        else:
+            step_eager()
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
 
-    # timed region: K steps, L2 flushed (untimed) before each step
-    B.cls_profile_reset(p.handle)
-    B.cls_profile_enable(p.handle, True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
+    def timed(fn, k_steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k_steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(k_steps):
+            flush.fill_(k & 0xFF)            # untimed: evict L2 before each step
             evs[k][0].record(stream)
-            step()
+            fn()
             evs[k][1].record(stream)
         torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / k_steps
+
+    # timed region: K steps (graph launches unless --eager); then the same
+    # steps run eagerly with a CUDA event pair around every launch on its
+    # stream, for the per-kernel durations (clocks sampled over both)
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        ms_step = timed(step, args.steps)
         wall = time.perf_counter() - t0
-    B.cls_profile_enable(p.handle, False)
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    ms_step = ms / args.steps
+        B.cls_profile_reset(p.handle)
+        B.cls_profile_enable(p.handle, True)
+        ms_eager = timed(step_eager, args.steps)
+        B.cls_profile_enable(p.handle, False)
     if dist:
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
+    graph_launches = B.cls_graph_kernel_count(graph) if graph is not None else None
     kc_names = ["fe_thread", "fe_group_real", "fe_group_dft", "accum_step_round", "score",
                 "reduce", "init"]
     kstats = {}
@@ -229,6 +243,7 @@ def run_ours(args, rank, world, local_rank):
         n_l, t_ms = B.cls_profile_read(p.handle, kc)
         launches += n_l
         kstats[name] = {"launches_per_step": n_l / args.steps, "ms_per_step": t_ms / args.steps}
+    launches_timed = graph_launches * args.steps if graph_launches is not None else launches
     clocks = clk.summary()
 
     # end to end through host buffers: H2D x0 (pinned), one step, D2H nsat
@@ -281,7 +296,9 @@ def run_ours(args, rank, world, local_rank):
                    "tuning": tuning, "autotune_s": tune_s},
         "e2e": {"value": units / e2e_s, "unit": "literal-evals/s",
                 "h2d_bytes_per_step": 4 * inst.n * R, "d2h_bytes_per_step": 4 * R},
-        "gpu_launches": launches,
+        "gpu_launches": launches_timed,
+        "mode": "cuda-graph (1 step per launch)" if graph is not None else "eager",
+        "ms_per_step_eager": ms_eager,
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -291,6 +308,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if graph is not None:
+        B.cls_graph_destroy(graph)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -305,6 +324,7 @@ def main():
     ap.add_argument("--config", default="mixed")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="time eager launches, not the graph")
     ap.add_argument("--R", type=int, default=0, help="override restarts (profiling)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -148,6 +148,14 @@ int cls_init_uniform(const cls_problem* p, int32_t R, uint64_t seed,
 int cls_eval(const cls_problem* p, int32_t R, const float* x, float* obj,
              float* grad, float* fe_con, void* ws, size_t ws_bytes, void* stream);
 
+/* Vector-Jacobian product of the per-restart objective for reverse-mode
+ * differentiation (the adjoint of cls_eval's obj output):
+ * out[v*R + r] = scale[r] * g[v*R + r], where g is cls_eval's gradient and
+ * scale[r] = dLoss/dobj[r].  g, out: device float[n*R] (may alias);
+ * scale: device float[R]. */
+int cls_restart_scale(const cls_problem* p, int32_t R, const float* g, const float* scale,
+                      float* out, void* stream);
+
 /* Projected gradient step (Sec. 2.3, PGD on Q^n) with a given gradient:
  * x <- min(max(fl(x - fl(lr * grad)), -1), 1) for free variables (pinned
  * ones are left as they are), then, if bits is not NULL, writes the rounded
@@ -185,6 +193,27 @@ int cls_solve_host_workspace_size(const cls_problem* p, int32_t R, size_t* bytes
 int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host,
                    float lr, int32_t n_steps, int32_t* nsat_host,
                    float* x_host, void* ws, size_t ws_bytes, void* stream);
+
+/* The step loop as one CUDA graph (task: the step loop captured in a CUDA
+ * graph; Sec. 3.3: all restarts iterate in lockstep).  cls_graph_create
+ * records n_steps steps exactly as cls_step would run them (same kernels,
+ * same arguments, same results) on private streams and instantiates the
+ * graph.  Inside a step the FE+gradient launches of the different length
+ * classes run concurrently (they write disjoint partial rows); step k's
+ * score runs concurrently with step k+1's FE launches, and step k+1's
+ * accumulate waits for it.  The pointers (x, bits, nsat, wsat, ws) are
+ * baked into the graph and must stay valid; each cls_graph_launch then
+ * performs the n_steps steps on `stream`.  Profiling must be off while
+ * creating.  cls_graph_kernel_count returns the number of kernel launches
+ * one graph launch performs.  Errors as cls_step; CLS_ERR_CUDA if capture
+ * or instantiation fails. */
+typedef struct cls_graph cls_graph;
+int cls_graph_create(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
+                     uint32_t* bits, int32_t* nsat, double* wsat, void* ws, size_t ws_bytes,
+                     cls_graph** out);
+int cls_graph_launch(cls_graph* g, void* stream);
+int cls_graph_kernel_count(const cls_graph* g, int64_t* n);
+int cls_graph_destroy(cls_graph* g);
 
 /* Autotuning of the FE+gradient launch shapes (task: "the segment-to-warp or
  * segment-to-block split and the tile sizes chosen by an autotuner").

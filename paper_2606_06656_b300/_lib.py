@@ -26,6 +26,7 @@ SIGNATURES = {
     "cls_init_uniform": (i32, [vp, i32, u64, i64, vp, vp]),
     "cls_eval": (i32, [vp, i32, vp, vp, vp, vp, vp, sz, vp]),
     "cls_pgd_update": (i32, [vp, i32, vp, vp, f32, vp, vp]),
+    "cls_restart_scale": (i32, [vp, i32, vp, vp, vp, vp]),
     "cls_round_score": (i32, [vp, i32, vp, vp, vp, vp, vp, sz, vp]),
     "cls_step": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp, sz, vp]),
     "cls_solve_host_workspace_size": (i32, [vp, i32, P(sz)]),
@@ -34,6 +35,10 @@ SIGNATURES = {
     "cls_tuning_get": (i32, [vp, P(i32), i32]),
     "cls_tuning_set": (i32, [vp, P(i32), i32]),
     "cls_config_info": (i32, [i32, P(i32)]),
+    "cls_graph_create": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp, sz, P(vp)]),
+    "cls_graph_launch": (i32, [vp, vp]),
+    "cls_graph_kernel_count": (i32, [vp, P(i64)]),
+    "cls_graph_destroy": (i32, [vp]),
     "cls_step_noalloc": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp]),
     "cls_profile_enable": (i32, [vp, i32]),
     "cls_profile_read": (i32, [vp, i32, P(i64), P(C.c_double)]),

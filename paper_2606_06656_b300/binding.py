@@ -108,6 +108,11 @@ def cls_eval(h, R, x, obj, grad, fe_con, ws, stream=None):
                                     _stream(stream)), "cls_eval")
 
 
+def cls_restart_scale(h, R, g, scale, out, stream=None):
+    _lib.check(_lib.load().cls_restart_scale(h, int(R), _ptr(g), _ptr(scale), _ptr(out),
+                                             _stream(stream)), "cls_restart_scale")
+
+
 def cls_pgd_update(h, R, x, grad, lr, bits, stream=None):
     _lib.check(_lib.load().cls_pgd_update(h, int(R), _ptr(x), _ptr(grad), float(lr), _ptr(bits),
                                           _stream(stream)), "cls_pgd_update")
@@ -173,3 +178,27 @@ def cls_config_info(cid):
     buf = (C.c_int32 * 4)()
     _lib.check(_lib.load().cls_config_info(int(cid), buf), "cls_config_info")
     return [int(v) for v in buf]
+
+
+def cls_graph_create(h, R, x, lr, n_steps, bits, nsat, wsat, ws):
+    g = C.c_void_p()
+    _lib.check(_lib.load().cls_graph_create(h, int(R), _ptr(x), float(lr), int(n_steps),
+                                            _ptr(bits), _ptr(nsat), _ptr(wsat), _ptr(ws),
+                                            ws.numel() if ws is not None else 0, C.byref(g)),
+               "cls_graph_create")
+    return g
+
+
+def cls_graph_launch(g, stream=None):
+    _lib.check(_lib.load().cls_graph_launch(g, _stream(stream)), "cls_graph_launch")
+
+
+def cls_graph_kernel_count(g):
+    n = C.c_int64()
+    _lib.check(_lib.load().cls_graph_kernel_count(g, C.byref(n)), "cls_graph_kernel_count")
+    return int(n.value)
+
+
+def cls_graph_destroy(g):
+    if g:
+        _lib.check(_lib.load().cls_graph_destroy(g), "cls_graph_destroy")

@@ -389,6 +389,18 @@ int cls_eval(const cls_problem* p, int32_t R, const float* x, float* obj, float*
   return CLS_OK;
 }
 
+int cls_restart_scale(const cls_problem* p, int32_t R, const float* g, const float* scale,
+                      float* out, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (R == 0 || p->host.n == 0) return CLS_OK;
+  if (!g || !scale || !out) return set_err(CLS_ERR_INVALID, "g, scale and out are required");
+  CLS_CUDA_TRY(cls::launch_restart_scale(p->host.n, R, g, scale, out, (cudaStream_t)stream,
+                                         hook_of(p)),
+               "scale kernel");
+  return CLS_OK;
+}
+
 int cls_pgd_update(const cls_problem* p, int32_t R, float* x, const float* grad, float lr,
                    uint32_t* bits, void* stream) {
   int rc = check_R(p, R);
@@ -585,6 +597,156 @@ int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* 
   cudaEventDestroy(e1);
   if (result != CLS_OK) return result;
   return cls_tuning_set(p, chosen, cls::kNumBuckets);
+}
+
+}  // extern "C"
+
+struct cls_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> events;
+  int64_t launches = 0;
+};
+
+namespace {
+
+void graph_release(cls_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (auto e : g->events) cudaEventDestroy(e);
+  for (auto s : g->side) cudaStreamDestroy(s);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  delete g;
+}
+
+// Records the n-step loop into the capturing stream g->cap.  FE units fork
+// onto side streams (they write disjoint partial rows); step k's score runs
+// on its own stream, concurrently with step k+1's FE, and step k+1's
+// accumulate (which rewrites the bitset) waits for it.
+int record_steps(const cls_problem* p, const Layout& L, cls_graph* g, float* x, float lr,
+                 int n_steps, uint32_t* bits, int32_t* nsat, double* wsat, void* ws, bool score) {
+  const cls::DevPlan& D = p->dev;
+  float* P = at<float>(ws, L.P);
+  std::vector<int> units;
+  for (int u = 0; u < cls::kNumFeUnits; ++u)
+    if (cls::fe_unit_active(D, u)) units.push_back(u);
+  const int nside = (int)g->side.size();
+  cudaEvent_t ev_fork = g->events[0], ev_score = g->events[1];
+  cudaStream_t s_score = g->side[nside - 1];
+  bool have_score = false;
+  for (int st = 0; st < n_steps; ++st) {
+    CLS_CUDA_TRY(cudaEventRecord(ev_fork, g->cap), "fork");
+    for (size_t i = 0; i < units.size(); ++i) {
+      cudaStream_t s = (i == 0) ? g->cap : g->side[(i - 1) % (nside - 1)];
+      if (s != g->cap) CLS_CUDA_TRY(cudaStreamWaitEvent(s, ev_fork, 0), "fork wait");
+      CLS_CUDA_TRY(cls::launch_fe_unit(D, units[i], L.R, L.Rp, x, P, nullptr, 0, s, nullptr),
+                   "fe unit");
+      g->launches++;
+    }
+    for (int k = 0; k + 1 < nside && k + 1 < (int)units.size(); ++k) {
+      CLS_CUDA_TRY(cudaEventRecord(g->events[2 + k], g->side[k]), "join");
+      CLS_CUDA_TRY(cudaStreamWaitEvent(g->cap, g->events[2 + k], 0), "join wait");
+    }
+    if (have_score) CLS_CUDA_TRY(cudaStreamWaitEvent(g->cap, ev_score, 0), "score wait");
+    CLS_CUDA_TRY(cls::launch_accum_step(D, L.R, L.Rp, P, x, lr, true, nullptr, bits, g->cap,
+                                        nullptr),
+                 "accumulate/step kernel");
+    g->launches++;
+    if (score) {
+      CLS_CUDA_TRY(cudaEventRecord(ev_fork, g->cap), "score fork");
+      CLS_CUDA_TRY(cudaStreamWaitEvent(s_score, ev_fork, 0), "score fork wait");
+      CLS_CUDA_TRY(cls::launch_score(D, L.R, L.Rp, bits, at<int32_t>(ws, L.nsat_part),
+                                     at<double>(ws, L.wsat_part), nsat, wsat, s_score, nullptr),
+                   "score kernels");
+      g->launches += D.m > 0 ? 2 : 0;
+      CLS_CUDA_TRY(cudaEventRecord(ev_score, s_score), "score done");
+      have_score = true;
+    }
+  }
+  if (have_score) CLS_CUDA_TRY(cudaStreamWaitEvent(g->cap, ev_score, 0), "final join");
+  return CLS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cls_graph_create(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
+                     uint32_t* bits, int32_t* nsat, double* wsat, void* ws, size_t ws_bytes,
+                     cls_graph** out) {
+  if (!out) return set_err(CLS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (n_steps < 1) return set_err(CLS_ERR_INVALID, "n_steps must be >= 1");
+  if (R == 0 || (!x && p->host.n > 0)) return set_err(CLS_ERR_INVALID, "x is NULL or R == 0");
+  if (p->hook) return set_err(CLS_ERR_INVALID, "disable profiling before capturing a graph");
+  const Layout L = layout_for(p, R);
+  rc = check_ws(L, ws, ws_bytes);
+  if (rc != CLS_OK) return rc;
+  cls_graph* g = new (std::nothrow) cls_graph();
+  if (!g) return set_err(CLS_ERR_NOMEM, "host allocation failed");
+  const int nside = 7;   // 6 FE side streams + 1 score stream
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+  for (int i = 0; i < nside && e == cudaSuccess; ++i) {
+    cudaStream_t s = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) g->side.push_back(s);
+  }
+  for (int i = 0; i < nside + 2 && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) g->events.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    graph_release(g);
+    (void)cudaGetLastError();
+    return cuda_err(e, "graph resources");
+  }
+  uint32_t* b = bits ? bits : at<uint32_t>(ws, L.bits);
+  e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    graph_release(g);
+    (void)cudaGetLastError();
+    return cuda_err(e, "cudaStreamBeginCapture");
+  }
+  rc = record_steps(p, L, g, x, lr, n_steps, b, nsat, wsat, ws, nsat || wsat);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(g->cap, &graph);
+  g->graph = graph;
+  if (rc != CLS_OK || e != cudaSuccess) {
+    graph_release(g);
+    (void)cudaGetLastError();
+    return rc != CLS_OK ? rc : cuda_err(e, "cudaStreamEndCapture");
+  }
+  e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) {
+    graph_release(g);
+    (void)cudaGetLastError();
+    return cuda_err(e, "cudaGraphInstantiate");
+  }
+  *out = g;
+  return CLS_OK;
+}
+
+int cls_graph_launch(cls_graph* g, void* stream) {
+  if (!g || !g->exec) return set_err(CLS_ERR_INVALID, "graph is NULL");
+  CLS_CUDA_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "cudaGraphLaunch");
+  return CLS_OK;
+}
+
+int cls_graph_kernel_count(const cls_graph* g, int64_t* n) {
+  if (!g || !n) return set_err(CLS_ERR_INVALID, "NULL argument");
+  *n = g->launches;
+  return CLS_OK;
+}
+
+int cls_graph_destroy(cls_graph* g) {
+  graph_release(g);
+  return CLS_OK;
 }
 
 int cls_profile_enable(cls_problem* p, int on) {

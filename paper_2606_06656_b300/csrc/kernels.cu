@@ -538,6 +538,16 @@ __global__ void k_obj_final(int R, int Rp, int nch, const double* __restrict__ p
   obj[r] = (float)a;
 }
 
+// vector-Jacobian product of the per-restart objective: out[v,r] = s[r] g[v,r]
+__global__ void __launch_bounds__(256) k_restart_scale(int64_t total, int R,
+                                                       const float* __restrict__ g,
+                                                       const float* __restrict__ sc,
+                                                       float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = sc[i % R] * g[i];
+}
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 struct HookScope {
@@ -610,13 +620,14 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
   return cudaGetLastError();
 }
 
-cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P, float* fe_con,
-                      int ldf, cudaStream_t s, LaunchHook* h) {
+cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const float* x, float* P,
+                           float* fe_con, int ldf, cudaStream_t s, LaunchHook* h) {
   if (R == 0) return cudaSuccess;
   const int RT = ceil_div(R, 32);
-  for (int t = 0; t < kNumThreadCls; ++t) {
+  if (unit < kNumThreadCls) {
+    const int t = unit;
     const int cnt = d.thread_count[t];
-    if (cnt == 0) continue;
+    if (cnt == 0) return cudaSuccess;
     const dim3 grid(ceil_div(RT, kThreadTiles), std::min(ceil_div(cnt, 8), 65535)),
         block(32, 8);
     HookScope hs(h, KC_THREAD, s);
@@ -630,14 +641,25 @@ cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P,
     else
       k_fe_thread<32><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.lit, x, R,
                                              Rp, RT, P, fe_con, ldf);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
   }
-  for (int b = 0; b < kNumBuckets; ++b) {
-    if (d.bucket_count[b] == 0) continue;
-    HookScope hs(h, b < kNumDftBuckets ? KC_GROUP_DFT : KC_GROUP_REAL, s);
-    cudaError_t e = launch_group(d.bucket_cfg[b], d, d.bucket_list[b], d.bucket_count[b],
-                                 d.bucket_maxL[b], R, Rp, x, P, fe_con, ldf, s);
+  const int b = unit - kNumThreadCls;
+  if (b >= kNumBuckets || d.bucket_count[b] == 0) return cudaSuccess;
+  HookScope hs(h, b < kNumDftBuckets ? KC_GROUP_DFT : KC_GROUP_REAL, s);
+  return launch_group(d.bucket_cfg[b], d, d.bucket_list[b], d.bucket_count[b], d.bucket_maxL[b],
+                      R, Rp, x, P, fe_con, ldf, s);
+}
+
+bool fe_unit_active(const DevPlan& d, int unit) {
+  if (unit < kNumThreadCls) return d.thread_count[unit] > 0;
+  const int b = unit - kNumThreadCls;
+  return b < kNumBuckets && d.bucket_count[b] > 0;
+}
+
+cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P, float* fe_con,
+                      int ldf, cudaStream_t s, LaunchHook* h) {
+  for (int u = 0; u < kNumFeUnits; ++u) {
+    cudaError_t e = launch_fe_unit(d, u, R, Rp, x, P, fe_con, ldf, s, h);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -700,6 +722,16 @@ cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
   }
   HookScope hs(h, KC_REDUCE, s);
   k_score_final<<<ceil_div(R, 256), 256, 0, s>>>(R, Rp, nch, nsat_part, wsat_part, nsat, wsat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restart_scale(int n, int R, const float* g, const float* sc, float* out,
+                                 cudaStream_t s, LaunchHook* h) {
+  const int64_t total = (int64_t)n * R;
+  if (total == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
+  HookScope hs(h, KC_REDUCE, s);
+  k_restart_scale<<<blocks, 256, 0, s>>>(total, R, g, sc, out);
   return cudaGetLastError();
 }
 

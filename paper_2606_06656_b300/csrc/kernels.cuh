@@ -60,6 +60,13 @@ cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, f
 cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P, float* fe_con,
                       int ldf, cudaStream_t s, LaunchHook* h);
 
+// The FE stage as independent units (thread-path classes, then lane-group
+// buckets); units write disjoint partial rows and may run concurrently.
+constexpr int kNumFeUnits = kNumThreadCls + kNumBuckets;
+bool fe_unit_active(const DevPlan& d, int unit);
+cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const float* x, float* P,
+                           float* fe_con, int ldf, cudaStream_t s, LaunchHook* h);
+
 // One lane-group launch over an explicit constraint list (the autotuner).
 cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL,
                          int R, int Rp, const float* x, float* P, float* fe_con, int ldf,
@@ -83,6 +90,10 @@ cudaError_t launch_round(const DevPlan& d, int R, const float* x, uint32_t* bits
 cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
                          int32_t* nsat_part, double* wsat_part, int32_t* nsat, double* wsat,
                          cudaStream_t s, LaunchHook* h);
+
+// out[v*R + r] = sc[r] * g[v*R + r] (vector-Jacobian product of obj[r]).
+cudaError_t launch_restart_scale(int n, int R, const float* g, const float* sc, float* out,
+                                 cudaStream_t s, LaunchHook* h);
 
 // obj[r] = sum_c w_c fe_con[c*ldf + r] in FP64 (fixed order), rounded to FP32.
 cudaError_t launch_obj(const DevPlan& d, int R, int Rp, int nch, int chunk, const float* fe_con,

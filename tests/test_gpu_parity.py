@@ -318,6 +318,36 @@ def test_random_3sat_loop_consistency(P):
     assert float(nsat.float().mean()) > 0.9 * inst.m
 
 
+@pytest.mark.parametrize("steps", [1, 7])
+def test_graph_equals_eager_steps(P, steps):
+    """The captured step loop (concurrent FE branches, score overlapped with
+    the next step) gives bit-identical iterates and counts to cls_step."""
+    from paper_2606_06656_b300 import binding as B
+    inst = W.mixed_pb(n=700, n_or=2000, n_xor=200, n_card=40, card_len=(10, 300), seed=12)
+    p = P(inst)
+    R = 96
+    X0 = W.uniform_points(inst.n, R, seed=4)
+    xa = torch.from_numpy(X0.copy()).cuda()
+    nsat_a, wsat_a, bits_a = p.step(xa, 0.1, n_steps=steps)
+    xb = torch.from_numpy(X0.copy()).cuda()
+    bits_b = torch.empty_like(bits_a)
+    nsat_b = torch.empty_like(nsat_a)
+    wsat_b = torch.empty_like(wsat_a)
+    ws = p.workspace(R)
+    g = B.cls_graph_create(p.handle, R, xb, 0.1, steps, bits_b, nsat_b, wsat_b, ws)
+    assert B.cls_graph_kernel_count(g) >= 3 * steps
+    B.cls_graph_launch(g)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb) and torch.equal(nsat_a, nsat_b) and torch.equal(bits_a, bits_b)
+    assert torch.equal(wsat_a, wsat_b)
+    # relaunching continues from the updated iterate, like further cls_step calls
+    B.cls_graph_launch(g)
+    p.step(xa, 0.1, n_steps=steps)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb)
+    B.cls_graph_destroy(g)
+
+
 def test_solve_host_matches_device(P):
     inst = W.random_ksat()
     p = P(inst)
@@ -371,3 +401,33 @@ def test_full_size_mixed_pb_sampled(P):
         assert np.all(np.abs(grad[v, rs] - g) <= GRAD_RTOL * np.maximum(1.0, np.abs(g)))
     onsat, _, _ = ocls.score(inst, X[:, rs])
     assert np.array_equal(nsat[rs], onsat)
+
+
+def test_autograd_objective_matches_oracle_and_finite_differences(P):
+    """CLSObjective's backward (the hand-written adjoint) against the FP64
+    oracle gradient and against exact multilinear finite differences
+    dF/dx_v = (F(x_v = 1) - F(x_v = -1)) / 2 taken with the forward."""
+    from paper_2606_06656_b300.autograd import CLSObjective
+    inst = W.mixed_pb(n=120, n_or=300, n_xor=30, n_card=8, card_len=(10, 60), seed=21)
+    p = P(inst)
+    R = 40
+    X = W.uniform_points(inst.n, R, seed=9)
+    x = torch.from_numpy(X.copy()).cuda().requires_grad_(True)
+    c = torch.linspace(-1.0, 2.0, R, device="cuda")
+    obj = CLSObjective.apply(p, x)
+    (obj * c).sum().backward()
+    g = x.grad.cpu().numpy()
+    oobj, ograd, _ = ocls.objective_grad(inst, X.astype(np.float64))
+    assert np.abs(obj.detach().cpu().numpy() - oobj).max() <= FE_TOL * inst.m
+    want = ograd * c.cpu().numpy()[None, :]
+    rel = np.linalg.norm(g - want) / np.linalg.norm(want)
+    assert rel <= GRAD_RTOL, rel
+    # exact finite differences of the forward, a few variables
+    for v in [0, 17, 63, 119]:
+        xp = torch.from_numpy(X.copy()).cuda()
+        xm = xp.clone()
+        xp[v] = 1.0
+        xm[v] = -1.0
+        with torch.no_grad():
+            fd = 0.5 * (CLSObjective.apply(p, xp) - CLSObjective.apply(p, xm)) * c
+        assert torch.allclose(torch.from_numpy(g[v]).cuda(), fd, atol=5e-5 * inst.m ** 0.5)
