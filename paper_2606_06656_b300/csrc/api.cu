@@ -522,6 +522,13 @@ int cls_tuning_set(cls_problem* p, const int32_t* cfg, int32_t n) {
 
 int cls_config_info(int32_t id, int32_t* out) {
   if (!out) return set_err(CLS_ERR_INVALID, "NULL argument");
+  if (id == cls::kCkptCfg) {   // checkpointed restart-parallel kernel, real roots
+    out[0] = 1;
+    out[1] = 1024;
+    out[2] = 0;
+    out[3] = 0;
+    return CLS_OK;
+  }
   if (id >= 0 && id < cls::kNumGroupCfg) {
     const cls::GroupCfg& g = cls::kGroupCfg[id];
     out[0] = g.G;
@@ -566,12 +573,17 @@ int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* 
     const bool dft = b < cls::kNumDftBuckets;
     const int bmax = dft ? cls::kDftBucketMax[b] : cls::kRealBucketMax[b - cls::kNumDftBuckets];
     float best = 1e30f;
-    for (int id = 0; id < cls::kNumGroupCfg && result == CLS_OK; ++id) {
-      const cls::GroupCfg& g = cls::kGroupCfg[id];
-      // candidates: right kind, able to hold the bucket's longest constraint,
-      // at most twice the slots needed
-      if (g.cplx != (dft ? 1 : 0) || g.G * g.Q < bmax || g.G * g.Q > 2 * std::max(bmax, 32))
-        continue;
+    for (int id = 0; id <= cls::kNumGroupCfg && result == CLS_OK; ++id) {
+      if (id == cls::kNumGroupCfg) {
+        if (dft) break;
+        id = cls::kCkptCfg;          // the checkpointed thread kernel (real buckets)
+      } else {
+        const cls::GroupCfg& g = cls::kGroupCfg[id];
+        // candidates: right kind, able to hold the bucket's longest
+        // constraint, at most twice the slots needed
+        if (g.cplx != (dft ? 1 : 0) || g.G * g.Q < bmax || g.G * g.Q > 2 * std::max(bmax, 32))
+          continue;
+      }
       cudaError_t e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b],
                                         D.bucket_maxL[b], R, L.Rp, x, P, nullptr, 0, s);
       if (e == cudaSuccess) e = cudaEventRecord(e0, s);
@@ -591,6 +603,7 @@ int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* 
         best = ms;
         chosen[b] = id;
       }
+      if (id == cls::kCkptCfg) break;
     }
   }
   cudaEventDestroy(e0);

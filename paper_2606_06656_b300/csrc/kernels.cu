@@ -153,6 +153,117 @@ __global__ void __launch_bounds__(256) k_fe_thread(
 }
 
 // ---------------------------------------------------------------------------
+// A2-A5, closed-form products (OR, XOR, NAE) of any length: one thread per
+// (constraint, restart), a warp = one constraint x 32 restarts (kThreadTiles
+// tiles).  The forward pass keeps only every kCkptInterval-th prefix product
+// (in shared memory, lane-minor); the backward pass walks the literal blocks
+// from the end, recomputes a block's prefixes from its checkpoint in
+// registers and combines them with the running suffix product.  Literal
+// values are gathered twice (coalesced rows, L1/L2 hits the second time).
+// Dynamic shared memory: 8 warps x NJ x ceil(maxL / kCkptInterval) x 32.
+// ---------------------------------------------------------------------------
+template <int NJ>
+__device__ __forceinline__ void ckpt_tile(const FeItem& it, const F4* __restrict__ root,
+                                          const F4* __restrict__ coef,
+                                          const LitRec* __restrict__ lit,
+                                          const float* __restrict__ x, int R, int Rp, int r,
+                                          int lane, int nck, float* ck, float* __restrict__ P,
+                                          float* __restrict__ fe_con, int ldf) {
+  constexpr int CI = kCkptInterval;
+  const int L = it.L;
+  const int nb = (L + CI - 1) / CI;
+  const bool act = r < R;
+  float4 rt[NJ], cf[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    rt[j] = ldg4(&root[it.root_off + j]);
+    cf[j] = ldg4(&coef[it.coef_off + j]);
+  }
+  // forward: running products, checkpoint at each block start
+  float run[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) run[j] = 1.f;
+  for (int b = 0; b < nb; ++b) {
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) ck[(j * nck + b) * 32 + lane] = run[j];
+#pragma unroll
+    for (int t = 0; t < CI; ++t) {
+      const int i = b * CI + t;
+      if (i < L) {
+        const LitRec rc = lit[it.lit0 + i];
+        const float y = act ? rec_sgn(rc.dst) * x[(size_t)rc.var * R + r] : 1.f;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) run[j] *= fmaf(y, rt[j].y, rt[j].x);
+      }
+    }
+  }
+  float val = it.b0;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) val = fmaf(cf[j].x, run[j], val);
+  // backward: suffix products with c'_j folded in
+  float suf[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) suf[j] = cf[j].z;
+  for (int b = nb - 1; b >= 0; --b) {
+    float yb[CI], pre[NJ][CI];
+    float p[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) p[j] = ck[(j * nck + b) * 32 + lane];
+#pragma unroll
+    for (int t = 0; t < CI; ++t) {
+      const int i = b * CI + t;
+      yb[t] = 1.f;
+      if (i < L) {
+        const LitRec rc = lit[it.lit0 + i];
+        yb[t] = act ? rec_sgn(rc.dst) * x[(size_t)rc.var * R + r] : 1.f;
+      }
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        pre[j][t] = p[j];
+        p[j] *= fmaf(yb[t], rt[j].y, rt[j].x);
+      }
+    }
+#pragma unroll
+    for (int t = CI - 1; t >= 0; --t) {
+      const int i = b * CI + t;
+      if (i < L) {
+        float g = 0.f;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+          g = fmaf(pre[j][t], suf[j], g);
+          suf[j] *= fmaf(yb[t], rt[j].y, rt[j].x);
+        }
+        const LitRec rc = lit[it.lit0 + i];
+        if (act) P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * g;
+      }
+    }
+  }
+  if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = val;
+}
+
+__global__ void __launch_bounds__(256) k_fe_thread_ckpt(
+    const int32_t* __restrict__ list, int count, const FeItem* __restrict__ fe,
+    const F4* __restrict__ root, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
+    const float* __restrict__ x, int R, int Rp, int RT, int nck, float* __restrict__ P,
+    float* __restrict__ fe_con, int ldf) {
+  extern __shared__ float ck_s[];                  // [warp][root][block][lane]
+  const int lane = threadIdx.x, w = threadIdx.y;
+  float* ck = ck_s + (size_t)w * 2 * nck * 32;
+  for (int ci = blockIdx.y * blockDim.y + w; ci < count; ci += gridDim.y * blockDim.y) {
+    const FeItem it = fe[list[ci]];
+    for (int tt = 0; tt < kThreadTiles; ++tt) {
+      const int tile = blockIdx.x * kThreadTiles + tt;
+      if (tile >= RT) break;
+      const int r = tile * 32 + lane;
+      if (it.J == 1)
+        ckpt_tile<1>(it, root, coef, lit, x, R, Rp, r, lane, nck, ck, P, fe_con, ldf);
+      else
+        ckpt_tile<2>(it, root, coef, lit, x, R, Rp, r, lane, nck, ck, P, fe_con, ldf);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // A2-A5 lane-group kernel: G lanes share one (constraint, restart); lane lam
 // holds literals lam, lam+G, ..., (Q slots).  One block = one constraint x a
 // tile of 32 restarts; literal values are staged in shared memory as
@@ -588,6 +699,9 @@ cudaError_t set_kernel_attributes() {
                                (int)group_smem<G, Q>());
   CLS_GROUP_CONFIGS(CLS_SET_ATTR)
 #undef CLS_SET_ATTR
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_fe_thread_ckpt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               8 * 2 * ((1024 + kCkptInterval - 1) / kCkptInterval) * 32 * 4);
   return err;
 }
 
@@ -604,8 +718,17 @@ cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, f
 cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL,
                          int R, int Rp, const float* x, float* P, float* fe_con, int ldf,
                          cudaStream_t s) {
-  (void)maxL;
   if (count == 0 || R == 0) return cudaSuccess;
+  if (cfg == kCkptCfg) {
+    const int RT = ceil_div(R, 32);
+    const int nck = std::max(1, ceil_div(maxL, kCkptInterval));
+    const dim3 g2(ceil_div(RT, kThreadTiles), std::min(ceil_div(count, 8), 65535)), b2(32, 8);
+    // NJ = 2 covers NAE; OR and XOR use one root (the second is never read)
+    const size_t smem = (size_t)8 * 2 * nck * 32 * sizeof(float);
+    k_fe_thread_ckpt<<<g2, b2, smem, s>>>(list, count, d.fe, d.root_tab, d.coef_tab, d.lit, x, R,
+                                          Rp, RT, nck, P, fe_con, ldf);
+    return cudaGetLastError();
+  }
   const dim3 grid(count, ceil_div(R, 32)), block(256);
   switch (cfg) {
 #define CLS_LAUNCH_CASE(id, G, Q, C, Y)                                                      \

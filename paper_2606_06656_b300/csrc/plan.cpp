@@ -21,7 +21,7 @@ Tuning default_tuning() {
   Tuning t;
   const int dft[kNumDftBuckets] = {0,  1,  2,  3,  4,  8,  9,  24, 25, 26,
                                    27, 28, 29, 30, 33, 34, 35, 36, 37};
-  const int real[kNumRealBuckets] = {41, 42, 43, 44, 45};
+  const int real[kNumRealBuckets] = {kCkptCfg, kCkptCfg, kCkptCfg, kCkptCfg, kCkptCfg};
   for (int b = 0; b < kNumDftBuckets; ++b) t.dft[b] = dft[b];
   for (int b = 0; b < kNumRealBuckets; ++b) t.real[b] = real[b];
   return t;
@@ -32,6 +32,7 @@ bool tuning_valid(const Tuning& t, std::string* msg) {
     const bool dft = b < kNumDftBuckets;
     const int id = dft ? t.dft[b] : t.real[b - kNumDftBuckets];
     const int maxL = dft ? kDftBucketMax[b] : kRealBucketMax[b - kNumDftBuckets];
+    if (!dft && id == kCkptCfg) continue;
     if (id < 0 || id >= kNumGroupCfg) {
       if (msg) *msg = "configuration id out of range";
       return false;
@@ -309,11 +310,15 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
     P.dft_lroots += (int64_t)J * L;
   }
   // score ranges: consecutive constraints, about kScoreRangeLits literals each
+  // (fewer for small problems, so that their scoring still spreads over
+  // many warps)
+  const int64_t range_lits =
+      std::min<int64_t>(kScoreRangeLits, std::max<int64_t>(32, nnz / 1024));
   P.score_ranges.push_back(0);
   int64_t acc = 0;
   for (int32_t c = 0; c < m; ++c) {
     acc += P.score[c].L;
-    if (acc >= kScoreRangeLits || c == m - 1) {
+    if (acc >= range_lits || c == m - 1) {
       P.score_ranges.push_back(c + 1);
       acc = 0;
     }

@@ -114,6 +114,10 @@ struct ScoreItem {
   X(47, 16, 8, 0, 0)         \
   X(48, 16, 16, 0, 0)
 constexpr int kNumGroupCfg = 49;
+// Configuration id of the restart-parallel checkpointed kernel for real-root
+// (closed-form) constraints of any length; valid only for real buckets.
+constexpr int kCkptCfg = 100;
+constexpr int kCkptInterval = 16;   // literals between stored prefix products
 struct GroupCfg {
   int G, Q, cplx, ys;
 };
