@@ -257,6 +257,54 @@ int cls_config_info(int32_t id, int32_t* out);
 int cls_step_noalloc(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
                      uint32_t* bits, int32_t* nsat, double* wsat, void* stream);
 
+/* Learned initial points (task: a small message-passing network over the
+ * constraint-variable incidence graph proposes initial points; the paper
+ * has no learned component).  Model, per node, hidden width 64:
+ *   embed   h_v = relu(W_vin f_v + b_vin),  h_c = relu(W_cin f_c + b_cin),
+ *           f_v = [1, deg/16, pos/deg, neg/deg],
+ *           f_c = [onehot(type, 9), L/64, k/L, w]
+ *   layers  a_c = L^-1/2 sum_{e in c} s_e h_v[v_e];   h_c = relu(W_cl [h_c, a_c] + b_cl)
+ *   (x2)    a_v = deg^-1/2 sum_{e on v} s_e h_c[c_e]; h_v = relu(W_vl [h_v, a_v] + b_vl)
+ *   head    z_v = w_out . h_v + b_out
+ *   points  x0[v*R + r] = tanh(z_v + tau u[v,r]) with u the draws of
+ *           cls_init_uniform (same seed / counter convention); pinned
+ *           variables keep their fixed value.
+ * The four 128-wide dense layers run on tensor cores with bf16 operands
+ * and fp32 accumulation (forward and both backward products); everything
+ * else is fp32.  Parameters are one flat fp32 vector (cls_mpnn_sizes gives
+ * its length and the activation workspace size); the layout is
+ * W_vin(64x4) b_vin W_cin(64x12) b_cin, then per layer W_c(64x128) b_c
+ * W_v(64x128) b_v, then w_out(64) b_out(1).  All reductions are blocked and
+ * summed in a fixed order: results are deterministic.
+ *   cls_mpnn_create     build the graph view of a problem (allocates, sync)
+ *   cls_mpnn_param_init weights U(-a, a), a = fan_in^-1/2 (Philox), ReLU
+ *                       biases 0.01, head bias 0
+ *   cls_mpnn_forward    z[n]; keeps activations in act for the backward
+ *   cls_mpnn_points     x0 from z (device float[n*R])
+ *   cls_mpnn_head_grad  dz_v = sum_r gx0[v,r](1 - x0^2) +
+ *                       lam/n_free * d/dz softplus(-2 t_v z_v) (target may
+ *                       be NULL: no target term); pinned variables get 0
+ *   cls_mpnn_backward   dparams = d(sum_v dz_v z_v)/dparams, using the act
+ *                       of the immediately preceding forward with the same
+ *                       params
+ *   cls_adam_step       one bias-corrected Adam update (Kingma & Ba), step
+ *                       t >= 1, all arrays device float[n] */
+typedef struct cls_mpnn cls_mpnn;
+int cls_mpnn_create(const cls_problem* p, cls_mpnn** out);
+int cls_mpnn_destroy(cls_mpnn* g);
+int cls_mpnn_sizes(const cls_mpnn* g, int64_t* n_params, size_t* act_bytes);
+int cls_mpnn_param_init(const cls_mpnn* g, uint64_t seed, float* params, void* stream);
+int cls_mpnn_forward(const cls_mpnn* g, const float* params, float* z, void* act,
+                     size_t act_bytes, void* stream);
+int cls_mpnn_points(const cls_mpnn* g, const float* z, int32_t R, uint64_t seed,
+                    int64_t r_offset, float tau, float* x0, void* stream);
+int cls_mpnn_head_grad(const cls_mpnn* g, const float* z, const float* x0, const float* gx0,
+                       int32_t R, const int8_t* target, float lam, float* dz, void* stream);
+int cls_mpnn_backward(const cls_mpnn* g, const float* params, const float* dz, float* dparams,
+                      void* act, size_t act_bytes, void* stream);
+int cls_adam_step(int64_t n, float* params, const float* grads, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, int32_t t, void* stream);
+
 /* Per-kernel timing (tracing): when enabled, each kernel launch of the
  * compute calls is bracketed by CUDA events on its stream; cls_profile_read
  * synchronises and returns, for kernel class kc (0 = thread-path FE+grad,

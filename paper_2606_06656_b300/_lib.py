@@ -40,6 +40,15 @@ SIGNATURES = {
     "cls_graph_kernel_count": (i32, [vp, P(i64)]),
     "cls_graph_destroy": (i32, [vp]),
     "cls_step_noalloc": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp]),
+    "cls_mpnn_create": (i32, [vp, P(vp)]),
+    "cls_mpnn_destroy": (i32, [vp]),
+    "cls_mpnn_sizes": (i32, [vp, P(i64), P(sz)]),
+    "cls_mpnn_param_init": (i32, [vp, u64, vp, vp]),
+    "cls_mpnn_forward": (i32, [vp, vp, vp, vp, sz, vp]),
+    "cls_mpnn_points": (i32, [vp, vp, i32, u64, i64, f32, vp, vp]),
+    "cls_mpnn_head_grad": (i32, [vp, vp, vp, vp, i32, vp, f32, vp, vp]),
+    "cls_mpnn_backward": (i32, [vp, vp, vp, vp, vp, sz, vp]),
+    "cls_adam_step": (i32, [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp]),
     "cls_profile_enable": (i32, [vp, i32]),
     "cls_profile_read": (i32, [vp, i32, P(i64), P(C.c_double)]),
     "cls_profile_reset": (i32, [vp]),

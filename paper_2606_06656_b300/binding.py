@@ -202,3 +202,53 @@ def cls_graph_kernel_count(g):
 def cls_graph_destroy(g):
     if g:
         _lib.check(_lib.load().cls_graph_destroy(g), "cls_graph_destroy")
+
+
+def cls_mpnn_create(h):
+    g = C.c_void_p()
+    _lib.check(_lib.load().cls_mpnn_create(h, C.byref(g)), "cls_mpnn_create")
+    return g
+
+
+def cls_mpnn_destroy(g):
+    if g:
+        _lib.check(_lib.load().cls_mpnn_destroy(g), "cls_mpnn_destroy")
+
+
+def cls_mpnn_sizes(g):
+    n, b = C.c_int64(), C.c_size_t()
+    _lib.check(_lib.load().cls_mpnn_sizes(g, C.byref(n), C.byref(b)), "cls_mpnn_sizes")
+    return int(n.value), int(b.value)
+
+
+def cls_mpnn_param_init(g, seed, params, stream=None):
+    _lib.check(_lib.load().cls_mpnn_param_init(g, int(seed), _ptr(params), _stream(stream)),
+               "cls_mpnn_param_init")
+
+
+def cls_mpnn_forward(g, params, z, act, stream=None):
+    _lib.check(_lib.load().cls_mpnn_forward(g, _ptr(params), _ptr(z), _ptr(act), act.numel(),
+                                            _stream(stream)), "cls_mpnn_forward")
+
+
+def cls_mpnn_points(g, z, R, seed, r_offset, tau, x0, stream=None):
+    _lib.check(_lib.load().cls_mpnn_points(g, _ptr(z), int(R), int(seed), int(r_offset),
+                                           float(tau), _ptr(x0), _stream(stream)),
+               "cls_mpnn_points")
+
+
+def cls_mpnn_head_grad(g, z, x0, gx0, R, target, lam, dz, stream=None):
+    _lib.check(_lib.load().cls_mpnn_head_grad(g, _ptr(z), _ptr(x0), _ptr(gx0), int(R),
+                                              _ptr(target), float(lam), _ptr(dz),
+                                              _stream(stream)), "cls_mpnn_head_grad")
+
+
+def cls_mpnn_backward(g, params, dz, dparams, act, stream=None):
+    _lib.check(_lib.load().cls_mpnn_backward(g, _ptr(params), _ptr(dz), _ptr(dparams), _ptr(act),
+                                             act.numel(), _stream(stream)), "cls_mpnn_backward")
+
+
+def cls_adam_step(params, grads, m, v, lr, b1, b2, eps, t, stream=None):
+    _lib.check(_lib.load().cls_adam_step(params.numel(), _ptr(params), _ptr(grads), _ptr(m),
+                                         _ptr(v), float(lr), float(b1), float(b2), float(eps),
+                                         int(t), _stream(stream)), "cls_adam_step")

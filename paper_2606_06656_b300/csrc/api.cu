@@ -12,6 +12,7 @@
 
 #include "../../include/cls.h"
 #include "kernels.cuh"
+#include "mpnn.cuh"
 #include "plan.h"
 
 namespace {
@@ -759,6 +760,209 @@ int cls_graph_kernel_count(const cls_graph* g, int64_t* n) {
 
 int cls_graph_destroy(cls_graph* g) {
   graph_release(g);
+  return CLS_OK;
+}
+
+}  // extern "C"
+
+struct cls_mpnn {
+  const cls_problem* p = nullptr;
+  cls::mp::Graph G;
+  std::vector<void*> allocations;
+  int32_t* fan_in = nullptr;
+  int64_t n_params = 0;
+  size_t act_bytes = 0;
+};
+
+namespace {
+template <typename T>
+int upload_to(std::vector<void*>& allocs, const std::vector<T>& v, const T** out) {
+  *out = nullptr;
+  if (v.empty()) return CLS_OK;
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, v.size() * sizeof(T));
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return set_err(e == cudaErrorMemoryAllocation ? CLS_ERR_NOMEM : CLS_ERR_CUDA,
+                   std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  allocs.push_back(ptr);
+  CLS_CUDA_TRY(cudaMemcpy(ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice),
+               "cudaMemcpy");
+  *out = static_cast<const T*>(ptr);
+  return CLS_OK;
+}
+
+void mpnn_free(cls_mpnn* g) {
+  if (!g) return;
+  for (void* a : g->allocations) cudaFree(a);
+  delete g;
+}
+
+int check_act(const cls_mpnn* g, void* act, size_t act_bytes) {
+  if (!act) return set_err(CLS_ERR_WORKSPACE, "activation workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(act) % kAlign != 0)
+    return set_err(CLS_ERR_WORKSPACE, "activation workspace is not 256-byte aligned");
+  if (act_bytes < g->act_bytes)
+    return set_err(CLS_ERR_WORKSPACE, "activation workspace too small: need " +
+                                          std::to_string(g->act_bytes) + " bytes");
+  return CLS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int cls_mpnn_create(const cls_problem* p, cls_mpnn** out) {
+  if (!p || !out) return set_err(CLS_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  const cls::HostPlan& H = p->host;
+  const int n = H.n, m = H.m;
+  std::vector<int32_t> con_off(m + 1, 0), con_var(H.nnz), var_con(H.nnz);
+  std::vector<float> con_sgn(H.nnz), var_sgn(H.nnz), isL(m), isd(n);
+  std::vector<float> fv((size_t)n * cls::mp::kFv), fc((size_t)m * cls::mp::kFc, 0.f);
+  std::vector<int32_t> deg(n, 0), pos(n, 0);
+  for (int c = 0; c < m; ++c) {
+    con_off[c + 1] = H.fe[c].lit0 + H.fe[c].L;
+    isL[c] = 1.0f / std::sqrt((float)H.fe[c].L);
+    for (int e = H.fe[c].lit0; e < H.fe[c].lit0 + H.fe[c].L; ++e) {
+      const cls::LitRec& rc = H.lit[e];
+      const float sg = rc.dst < 0 ? -1.f : 1.f;
+      con_var[e] = rc.var;
+      con_sgn[e] = sg;
+      const int row = rc.dst & 0x7fffffff;
+      var_con[row] = c;
+      var_sgn[row] = sg;
+      deg[rc.var]++;
+      if (sg > 0) pos[rc.var]++;
+    }
+    // f_c = [onehot(type, 9), L/64, k/L, w]
+    float* f = &fc[(size_t)c * cls::mp::kFc];
+    f[H.ctype[c]] = 1.f;
+    f[9] = (float)H.fe[c].L / 64.f;
+    f[10] = (float)H.kthr[c] / (float)H.fe[c].L;
+    f[11] = H.weight[c];
+  }
+  int n_free = n;
+  for (int v = 0; v < n; ++v) {
+    const float d1 = (float)std::max(deg[v], 1);
+    isd[v] = 1.0f / std::sqrt(d1);
+    float* f = &fv[(size_t)v * cls::mp::kFv];
+    f[0] = 1.f;
+    f[1] = (float)deg[v] / 16.f;
+    f[2] = (float)pos[v] / d1;
+    f[3] = (float)(deg[v] - pos[v]) / d1;
+    if (!H.fixed.empty() && H.fixed[v]) n_free--;
+  }
+  cls_mpnn* g = new (std::nothrow) cls_mpnn();
+  if (!g) return set_err(CLS_ERR_NOMEM, "host allocation failed");
+  g->p = p;
+  cls::mp::Graph& G = g->G;
+  G.n = n;
+  G.m = m;
+  G.n_free = n_free;
+  int rc = CLS_OK;
+  auto up = [&](auto& vec, auto** dst) {
+    if (rc == CLS_OK) rc = upload_to(g->allocations, vec, dst);
+  };
+  up(con_off, &G.con_off);
+  up(con_var, &G.con_var);
+  up(con_sgn, &G.con_sgn);
+  up(H.voff, &G.var_off);
+  up(var_con, &G.var_con);
+  up(var_sgn, &G.var_sgn);
+  up(isL, &G.isL);
+  up(isd, &G.isd);
+  up(fv, &G.fv);
+  up(fc, &G.fc);
+  std::vector<int32_t> fan = cls::mp::fan_in_table();
+  const int32_t* fan_dev = nullptr;
+  up(fan, &fan_dev);
+  if (rc != CLS_OK) {
+    mpnn_free(g);
+    return rc;
+  }
+  g->fan_in = const_cast<int32_t*>(fan_dev);
+  G.fixed = p->dev.fixed;
+  G.fixed_val = p->dev.fixed_val;
+  g->n_params = cls::mp::param_layout().total;
+  g->act_bytes = cls::mp::act_layout(n, m).total_floats * sizeof(float);
+  *out = g;
+  return CLS_OK;
+}
+
+int cls_mpnn_destroy(cls_mpnn* g) {
+  mpnn_free(g);
+  return CLS_OK;
+}
+
+int cls_mpnn_sizes(const cls_mpnn* g, int64_t* n_params, size_t* act_bytes) {
+  if (!g || !n_params || !act_bytes) return set_err(CLS_ERR_INVALID, "NULL argument");
+  *n_params = g->n_params;
+  *act_bytes = g->act_bytes;
+  return CLS_OK;
+}
+
+int cls_mpnn_param_init(const cls_mpnn* g, uint64_t seed, float* params, void* stream) {
+  if (!g || !params) return set_err(CLS_ERR_INVALID, "NULL argument");
+  CLS_CUDA_TRY(cls::mp::param_init(g->fan_in, g->n_params, seed, params, (cudaStream_t)stream),
+               "param init kernel");
+  return CLS_OK;
+}
+
+int cls_mpnn_forward(const cls_mpnn* g, const float* params, float* z, void* act,
+                     size_t act_bytes, void* stream) {
+  if (!g || !params || (!z && g->G.n > 0)) return set_err(CLS_ERR_INVALID, "NULL argument");
+  int rc = check_act(g, act, act_bytes);
+  if (rc != CLS_OK) return rc;
+  CLS_CUDA_TRY(cls::mp::forward(g->G, params, z, static_cast<float*>(act), (cudaStream_t)stream),
+               "mpnn forward");
+  return CLS_OK;
+}
+
+int cls_mpnn_points(const cls_mpnn* g, const float* z, int32_t R, uint64_t seed, int64_t r_offset,
+                    float tau, float* x0, void* stream) {
+  if (!g) return set_err(CLS_ERR_INVALID, "NULL argument");
+  int rc = check_R(g->p, R);
+  if (rc != CLS_OK) return rc;
+  if (R == 0 || g->G.n == 0) return CLS_OK;
+  if (!z || !x0) return set_err(CLS_ERR_INVALID, "z and x0 are required");
+  if (r_offset < 0) return set_err(CLS_ERR_INVALID, "r_offset must be >= 0");
+  CLS_CUDA_TRY(cls::mp::points(g->G, z, R, seed, r_offset, tau, x0, (cudaStream_t)stream),
+               "points kernel");
+  return CLS_OK;
+}
+
+int cls_mpnn_head_grad(const cls_mpnn* g, const float* z, const float* x0, const float* gx0,
+                       int32_t R, const int8_t* target, float lam, float* dz, void* stream) {
+  if (!g) return set_err(CLS_ERR_INVALID, "NULL argument");
+  int rc = check_R(g->p, R);
+  if (rc != CLS_OK) return rc;
+  if (g->G.n == 0) return CLS_OK;
+  if (!z || !dz || (gx0 && !x0)) return set_err(CLS_ERR_INVALID, "z, dz (and x0 with gx0) required");
+  CLS_CUDA_TRY(cls::mp::head_grad(g->G, z, x0, gx0, R, target, lam, dz, (cudaStream_t)stream),
+               "head gradient kernel");
+  return CLS_OK;
+}
+
+int cls_mpnn_backward(const cls_mpnn* g, const float* params, const float* dz, float* dparams,
+                      void* act, size_t act_bytes, void* stream) {
+  if (!g || !params || !dparams || (!dz && g->G.n > 0))
+    return set_err(CLS_ERR_INVALID, "NULL argument");
+  int rc = check_act(g, act, act_bytes);
+  if (rc != CLS_OK) return rc;
+  CLS_CUDA_TRY(cls::mp::backward(g->G, params, dz, dparams, static_cast<float*>(act),
+                                 (cudaStream_t)stream),
+               "mpnn backward");
+  return CLS_OK;
+}
+
+int cls_adam_step(int64_t n, float* params, const float* grads, float* m, float* v, float lr,
+                  float beta1, float beta2, float eps, int32_t t, void* stream) {
+  if (n < 0 || (n > 0 && (!params || !grads || !m || !v)) || t < 1)
+    return set_err(CLS_ERR_INVALID, "bad Adam arguments");
+  CLS_CUDA_TRY(cls::mp::adam(n, params, grads, m, v, lr, beta1, beta2, eps, t,
+                             (cudaStream_t)stream),
+               "adam kernel");
   return CLS_OK;
 }
 

@@ -199,6 +199,9 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   std::map<std::pair<int, std::string>, int> coef_of_spec;
 
   P.fe.resize(m);
+  P.ctype.assign(type, type + m);
+  P.kthr.assign(m, 0);
+  P.weight.assign(m, 1.0f);
   int64_t soff = 0;
   std::vector<int8_t> sp;
   for (int32_t c = 0; c < m; ++c) {
@@ -211,6 +214,8 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
       soff += L + 1;
     }
     float w = weight ? weight[c] : 1.0f;
+    P.kthr[c] = k;
+    P.weight[c] = w;
     // spectrum sp_t (Eq. 3): -1 where the constraint holds
     sp.assign(L + 1, 1);
     for (int tt = 0; tt <= L; ++tt) sp[tt] = holds(t, L, k, tt, spec) ? -1 : 1;

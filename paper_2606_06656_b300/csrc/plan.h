@@ -170,6 +170,8 @@ struct HostPlan {
   // lane-group buckets: [0, kNumDftBuckets) DFT, then real
   std::vector<int32_t> bucket_list[kNumDftBuckets + kNumRealBuckets];
   int bucket_cfg[kNumDftBuckets + kNumRealBuckets] = {};
+  std::vector<int32_t> ctype, kthr;   // per constraint: type and threshold (0 if none)
+  std::vector<float> weight;          // per constraint
   std::vector<uint8_t> fixed;     // n (empty = none)
   std::vector<float> fixed_val;   // n
   Tuning tuning;
