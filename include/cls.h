@@ -115,16 +115,35 @@ int cls_problem_create(int32_t n_vars, int32_t n_cons, const int32_t* offsets,
                        const int8_t* spectra, const uint8_t* fixed,
                        const float* fixed_val, cls_problem** out);
 
+/* As cls_problem_create, with flags:
+ *   CLS_SIMPLIFY_FIXED  fold pinned variables into the spectra (Sec. 3.2's
+ *     partial assignment): a pinned literal's factor is exactly 1 (false) or
+ *     w^j (true), so a constraint with f pinned-true literals and L' free ones
+ *     has the expansion of the spectrum sp'_t = sp_{t+f}, t = 0..L', over its
+ *     free literals -- the same FE for every assignment of the free
+ *     variables.  Pinned literals are then skipped by the FE+gradient
+ *     kernels (pinned variables get a zero gradient; they never move), while
+ *     scoring still counts every literal.  Ignored when fixed is NULL. */
+#define CLS_SIMPLIFY_FIXED 1u
+int cls_problem_create_ex(int32_t n_vars, int32_t n_cons, const int32_t* offsets,
+                          const int32_t* lit_var, const int8_t* lit_sign,
+                          const int32_t* type, const int32_t* k, const float* weight,
+                          const int8_t* spectra, const uint8_t* fixed,
+                          const float* fixed_val, uint32_t flags, cls_problem** out);
+
 /* Free a problem (NULL is accepted).  Synchronises the device first. */
 int cls_problem_destroy(cls_problem* p);
 
 /* Problem facts for callers: sizes and the per-path constraint counts.
- *   info[0] n, info[1] m, info[2] nnz, info[3] # constraints on the
- *   thread-per-(constraint, restart) product path (OR/XOR/NAE, L <= 32),
- *   info[4] # on the lane-group real-product path (OR/XOR/NAE, L > 32),
- *   info[5] # on the lane-group DFT path (all other types), info[6] number
- *   of DFT roots summed over DFT constraints, info[7] sum over DFT
- *   constraints of L * roots.  info must hold 8 int64. */
+ *   info[0] n, info[1] m, info[2] nnz, info[3] # constraints whose spectrum
+ *   is a closed-form product of real roots (OR, XOR, NAE and their
+ *   complements, Appendix A) with L <= 32 (one thread per (constraint,
+ *   restart)), info[4] # such constraints with L > 32, info[5] # on the
+ *   DFT path (every other spectrum), info[6] number of DFT roots summed
+ *   over DFT constraints, info[7] sum over DFT constraints of L * roots,
+ *   info[8] literals entering FE (nnz minus folded pinned literals),
+ *   info[9] constraints whose expansion is constant.  info must hold 10
+ *   int64. */
 int cls_problem_info(const cls_problem* p, int64_t* info);
 
 /* Bytes of device workspace the compute calls need for R restarts. */
@@ -208,6 +227,15 @@ int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host,
  * one graph launch performs.  Errors as cls_step; CLS_ERR_CUDA if capture
  * or instantiation fails. */
 typedef struct cls_graph cls_graph;
+/* cls_batch_graph_create: the same for `count` independent problems (e.g.
+ * several instances, each with its own restarts, as in Sec. 3.2's
+ * partial-assignment study), captured as concurrent branches of ONE graph;
+ * per-problem arrays of restarts, iterates, outputs (bits/nsats/wsats may
+ * be NULL or hold NULL entries) and workspaces. */
+int cls_batch_graph_create(int32_t count, const cls_problem* const* ps, const int32_t* Rs,
+                           float* const* xs, float lr, int32_t n_steps, uint32_t* const* bits,
+                           int32_t* const* nsats, double* const* wsats, void* const* wss,
+                           const size_t* ws_bytes, cls_graph** out);
 int cls_graph_create(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
                      uint32_t* bits, int32_t* nsat, double* wsat, void* ws, size_t ws_bytes,
                      cls_graph** out);

@@ -20,6 +20,8 @@ P = C.POINTER
 SIGNATURES = {
     "cls_problem_check": (i32, [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     "cls_problem_create": (i32, [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]),
+    "cls_problem_create_ex": (i32, [i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_uint32,
+                                    P(vp)]),
     "cls_problem_destroy": (i32, [vp]),
     "cls_problem_info": (i32, [vp, P(i64)]),
     "cls_workspace_size": (i32, [vp, i32, P(sz)]),
@@ -36,6 +38,7 @@ SIGNATURES = {
     "cls_tuning_set": (i32, [vp, P(i32), i32]),
     "cls_config_info": (i32, [i32, P(i32)]),
     "cls_graph_create": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp, sz, P(vp)]),
+    "cls_batch_graph_create": (i32, [i32, vp, vp, vp, f32, i32, vp, vp, vp, vp, vp, P(vp)]),
     "cls_graph_launch": (i32, [vp, vp]),
     "cls_graph_kernel_count": (i32, [vp, P(i64)]),
     "cls_graph_destroy": (i32, [vp]),

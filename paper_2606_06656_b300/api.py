@@ -14,10 +14,11 @@ from . import binding as B
 
 
 class Problem:
-    def __init__(self, inst, device=None):
+    def __init__(self, inst, device=None, simplify_fixed=False):
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
-            self.handle = B.cls_problem_create(inst)
+            self.handle = B.cls_problem_create(
+                inst, B.CLS_SIMPLIFY_FIXED if simplify_fixed else 0)
         info = B.cls_problem_info(self.handle)
         self.info = info
         self.n, self.m, self.nnz = info["n"], info["m"], info["nnz"]

@@ -59,15 +59,19 @@ def cls_problem_check(inst):
     return rc, (lib.cls_last_error() or b"").decode()
 
 
-def cls_problem_create(inst):
+CLS_SIMPLIFY_FIXED = 1
+
+
+def cls_problem_create(inst, flags=0):
     lib = _lib.load()
     a = _arrays(inst)
     h = C.c_void_p()
-    rc = lib.cls_problem_create(int(inst.n), len(a["offsets"]) - 1, _ptr(a["offsets"]),
-                                _ptr(a["lit_var"]), _ptr(a["lit_sign"]), _ptr(a["ctype"]),
-                                _ptr(a["k"]), _ptr(a["weight"]), _ptr(a["spectra"]),
-                                _ptr(a["fixed"]), _ptr(a["fixed_val"]), C.byref(h))
-    _lib.check(rc, "cls_problem_create")
+    rc = lib.cls_problem_create_ex(int(inst.n), len(a["offsets"]) - 1, _ptr(a["offsets"]),
+                                   _ptr(a["lit_var"]), _ptr(a["lit_sign"]), _ptr(a["ctype"]),
+                                   _ptr(a["k"]), _ptr(a["weight"]), _ptr(a["spectra"]),
+                                   _ptr(a["fixed"]), _ptr(a["fixed_val"]), int(flags),
+                                   C.byref(h))
+    _lib.check(rc, "cls_problem_create_ex")
     return h
 
 
@@ -77,10 +81,10 @@ def cls_problem_destroy(h):
 
 
 def cls_problem_info(h):
-    info = (i64 * 8)()
+    info = (i64 * 10)()
     _lib.check(_lib.load().cls_problem_info(h, info), "cls_problem_info")
     keys = ["n", "m", "nnz", "n_thread", "n_group_real", "n_group_dft", "dft_roots",
-            "dft_lroots"]
+            "dft_lroots", "nnz_fe", "n_const"]
     return dict(zip(keys, [int(v) for v in info]))
 
 
@@ -252,3 +256,20 @@ def cls_adam_step(params, grads, m, v, lr, b1, b2, eps, t, stream=None):
     _lib.check(_lib.load().cls_adam_step(params.numel(), _ptr(params), _ptr(grads), _ptr(m),
                                          _ptr(v), float(lr), float(b1), float(b2), float(eps),
                                          int(t), _stream(stream)), "cls_adam_step")
+
+
+def cls_batch_graph_create(handles, Rs, xs, lr, n_steps, nsats, wss):
+    """One graph over several problems (each with its own restarts)."""
+    n = len(handles)
+    VP = C.c_void_p * n
+    hs = VP(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    rs = (C.c_int32 * n)(*[int(r) for r in Rs])
+    xp = VP(*[t.data_ptr() for t in xs])
+    npp = VP(*[t.data_ptr() if t is not None else None for t in nsats])
+    wp = VP(*[t.data_ptr() for t in wss])
+    wb = (C.c_size_t * n)(*[t.numel() for t in wss])
+    g = C.c_void_p()
+    _lib.check(_lib.load().cls_batch_graph_create(n, hs, rs, xp, float(lr), int(n_steps), None,
+                                                  npp, None, wp, wb, C.byref(g)),
+               "cls_batch_graph_create")
+    return g

@@ -146,7 +146,7 @@ Layout layout_for(const cls_problem* p, int R) {
     return at;
   };
   const int nsc = std::max(1, cls::score_chunks(p->dev.n_ranges));
-  L.P = take((size_t)p->host.nnz * L.Rp * sizeof(float));
+  L.P = take((size_t)p->host.nnz_fe * L.Rp * sizeof(float));
   L.fe = take((size_t)m * L.Rp * sizeof(float));
   L.bits = take((size_t)p->host.n * L.RT * sizeof(uint32_t));
   L.nsat_part = take((size_t)nsc * L.Rp * sizeof(int32_t));
@@ -208,6 +208,11 @@ int upload_lists(cls_problem* p) {
     if (rc != CLS_OK) return rc;
     D.thread_count[t] = (int32_t)H.thread_items[t].size();
   }
+  {
+    int rc = upload(p, H.const_list, &D.const_list);
+    if (rc != CLS_OK) return rc;
+    D.const_count = (int32_t)H.const_list.size();
+  }
   for (int b = 0; b < cls::kNumBuckets; ++b) {
     int rc = upload(p, H.bucket_list[b], &D.bucket_list[b]);
     if (rc != CLS_OK) return rc;
@@ -249,7 +254,7 @@ int cls_problem_check(int32_t n, int32_t m, const int32_t* offsets, const int32_
                       const float* fixed_val) {
   std::string msg;
   int rc = cls::build_plan(n, m, offsets, lit_var, lit_sign, type, k, weight, spectra, fixed,
-                           fixed_val, true, nullptr, &msg);
+                           fixed_val, 0u, true, nullptr, &msg);
   if (rc != 0) return set_err(CLS_ERR_INVALID, msg);
   return CLS_OK;
 }
@@ -258,7 +263,16 @@ int cls_problem_create(int32_t n, int32_t m, const int32_t* offsets, const int32
                        const int8_t* lit_sign, const int32_t* type, const int32_t* k,
                        const float* weight, const int8_t* spectra, const uint8_t* fixed,
                        const float* fixed_val, cls_problem** out) {
+  return cls_problem_create_ex(n, m, offsets, lit_var, lit_sign, type, k, weight, spectra, fixed,
+                               fixed_val, 0u, out);
+}
+
+int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
+                          const int8_t* lit_sign, const int32_t* type, const int32_t* k,
+                          const float* weight, const int8_t* spectra, const uint8_t* fixed,
+                          const float* fixed_val, uint32_t flags, cls_problem** out) {
   if (!out) return set_err(CLS_ERR_INVALID, "out is NULL");
+  if (flags & ~(uint32_t)CLS_SIMPLIFY_FIXED) return set_err(CLS_ERR_INVALID, "unknown flags");
   *out = nullptr;
   cls_problem* p = new (std::nothrow) cls_problem();
   if (!p) return set_err(CLS_ERR_NOMEM, "host allocation failed");
@@ -266,7 +280,7 @@ int cls_problem_create(int32_t n, int32_t m, const int32_t* offsets, const int32
   int rc;
   try {
     rc = cls::build_plan(n, m, offsets, lit_var, lit_sign, type, k, weight, spectra, fixed,
-                         fixed_val, false, &p->host, &msg);
+                         fixed_val, flags, false, &p->host, &msg);
   } catch (const std::bad_alloc&) {
     delete p;
     return set_err(CLS_ERR_NOMEM, "host allocation failed while building the problem");
@@ -301,6 +315,8 @@ int cls_problem_create(int32_t n, int32_t m, const int32_t* offsets, const int32
   };
   up(H.lit, &D.lit);
   up(H.voff, &D.voff);
+  up(H.fe_lit, &D.fe_lit);
+  up(H.fe_voff, &D.fe_voff);
   up(H.fe, &D.fe);
   up(H.score, &D.score);
   up(H.score_ranges, &D.score_ranges);
@@ -339,6 +355,8 @@ int cls_problem_info(const cls_problem* p, int64_t* info) {
   info[5] = H.n_group_dft;
   info[6] = H.dft_roots;
   info[7] = H.dft_lroots;
+  info[8] = H.nnz_fe;
+  info[9] = (int64_t)H.const_list.size();
   return CLS_OK;
 }
 
@@ -379,6 +397,7 @@ int cls_eval(const cls_problem* p, int32_t R, const float* x, float* obj, float*
     ldf = L.Rp;
   }
   CLS_CUDA_TRY(cls::launch_fe(p->dev, R, L.Rp, x, P, fe, ldf, s, hook_of(p)), "fe kernels");
+  CLS_CUDA_TRY(cls::launch_fe_const(p->dev, R, fe, ldf, s), "constant expansions");
   if (grad)
     CLS_CUDA_TRY(cls::launch_accum_step(p->dev, R, L.Rp, P, nullptr, 0.f, false, grad, nullptr,
                                         s, hook_of(p)),
@@ -619,8 +638,8 @@ struct cls_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
-  std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> events;
+  std::vector<cudaStream_t> streams;   // every stream created for the capture
+  std::vector<cudaEvent_t> events;     // every event created for the capture
   int64_t launches = 0;
 };
 
@@ -631,57 +650,91 @@ void graph_release(cls_graph* g) {
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   for (auto e : g->events) cudaEventDestroy(e);
-  for (auto s : g->side) cudaStreamDestroy(s);
+  for (auto s : g->streams) cudaStreamDestroy(s);
   if (g->cap) cudaStreamDestroy(g->cap);
   delete g;
 }
 
-// Records the n-step loop into the capturing stream g->cap.  FE units fork
-// onto side streams (they write disjoint partial rows); step k's score runs
-// on its own stream, concurrently with step k+1's FE, and step k+1's
-// accumulate (which rewrites the bitset) waits for it.
-int record_steps(const cls_problem* p, const Layout& L, cls_graph* g, float* x, float lr,
-                 int n_steps, uint32_t* bits, int32_t* nsat, double* wsat, void* ws, bool score) {
+
+// Streams and events of one problem's branch of a captured graph.
+struct Branch {
+  cudaStream_t main = nullptr;
+  std::vector<cudaStream_t> side;   // FE side streams, then the score stream last
+  std::vector<cudaEvent_t> ev;      // fork, score-done, then one join event per side
+};
+
+// Records the n-step loop of one problem into br.main (which must already be
+// part of the capture).  FE units fork onto side streams (they write disjoint
+// partial rows); step k's score runs on its own stream, concurrently with
+// step k+1's FE, and step k+1's accumulate (which rewrites the bitset) waits
+// for it.
+int record_steps(const cls_problem* p, const Layout& L, const Branch& br, int64_t* launches,
+                 float* x, float lr, int n_steps, uint32_t* bits, int32_t* nsat, double* wsat,
+                 void* ws, bool score) {
   const cls::DevPlan& D = p->dev;
   float* P = at<float>(ws, L.P);
   std::vector<int> units;
   for (int u = 0; u < cls::kNumFeUnits; ++u)
     if (cls::fe_unit_active(D, u)) units.push_back(u);
-  const int nside = (int)g->side.size();
-  cudaEvent_t ev_fork = g->events[0], ev_score = g->events[1];
-  cudaStream_t s_score = g->side[nside - 1];
+  const int nside = (int)br.side.size();
+  cudaEvent_t ev_fork = br.ev[0], ev_score = br.ev[1];
+  cudaStream_t s_score = br.side[nside - 1];
   bool have_score = false;
   for (int st = 0; st < n_steps; ++st) {
-    CLS_CUDA_TRY(cudaEventRecord(ev_fork, g->cap), "fork");
+    CLS_CUDA_TRY(cudaEventRecord(ev_fork, br.main), "fork");
     for (size_t i = 0; i < units.size(); ++i) {
-      cudaStream_t s = (i == 0) ? g->cap : g->side[(i - 1) % (nside - 1)];
-      if (s != g->cap) CLS_CUDA_TRY(cudaStreamWaitEvent(s, ev_fork, 0), "fork wait");
+      cudaStream_t s = (i == 0) ? br.main : br.side[(i - 1) % (nside - 1)];
+      if (s != br.main) CLS_CUDA_TRY(cudaStreamWaitEvent(s, ev_fork, 0), "fork wait");
       CLS_CUDA_TRY(cls::launch_fe_unit(D, units[i], L.R, L.Rp, x, P, nullptr, 0, s, nullptr),
                    "fe unit");
-      g->launches++;
+      (*launches)++;
     }
     for (int k = 0; k + 1 < nside && k + 1 < (int)units.size(); ++k) {
-      CLS_CUDA_TRY(cudaEventRecord(g->events[2 + k], g->side[k]), "join");
-      CLS_CUDA_TRY(cudaStreamWaitEvent(g->cap, g->events[2 + k], 0), "join wait");
+      CLS_CUDA_TRY(cudaEventRecord(br.ev[2 + k], br.side[k]), "join");
+      CLS_CUDA_TRY(cudaStreamWaitEvent(br.main, br.ev[2 + k], 0), "join wait");
     }
-    if (have_score) CLS_CUDA_TRY(cudaStreamWaitEvent(g->cap, ev_score, 0), "score wait");
-    CLS_CUDA_TRY(cls::launch_accum_step(D, L.R, L.Rp, P, x, lr, true, nullptr, bits, g->cap,
+    if (have_score) CLS_CUDA_TRY(cudaStreamWaitEvent(br.main, ev_score, 0), "score wait");
+    CLS_CUDA_TRY(cls::launch_accum_step(D, L.R, L.Rp, P, x, lr, true, nullptr, bits, br.main,
                                         nullptr),
                  "accumulate/step kernel");
-    g->launches++;
+    (*launches)++;
     if (score) {
-      CLS_CUDA_TRY(cudaEventRecord(ev_fork, g->cap), "score fork");
+      CLS_CUDA_TRY(cudaEventRecord(ev_fork, br.main), "score fork");
       CLS_CUDA_TRY(cudaStreamWaitEvent(s_score, ev_fork, 0), "score fork wait");
       CLS_CUDA_TRY(cls::launch_score(D, L.R, L.Rp, bits, at<int32_t>(ws, L.nsat_part),
                                      at<double>(ws, L.wsat_part), nsat, wsat, s_score, nullptr),
                    "score kernels");
-      g->launches += D.m > 0 ? 2 : 0;
+      *launches += D.m > 0 ? 2 : 0;
       CLS_CUDA_TRY(cudaEventRecord(ev_score, s_score), "score done");
       have_score = true;
     }
   }
-  if (have_score) CLS_CUDA_TRY(cudaStreamWaitEvent(g->cap, ev_score, 0), "final join");
+  if (have_score) CLS_CUDA_TRY(cudaStreamWaitEvent(br.main, ev_score, 0), "final join");
   return CLS_OK;
+}
+
+constexpr int kSideStreams = 7;   // 6 FE side streams + 1 score stream
+
+cudaError_t make_branch(Branch* br, bool own_main) {
+  cudaError_t e = cudaSuccess;
+  if (own_main) e = cudaStreamCreateWithFlags(&br->main, cudaStreamNonBlocking);
+  for (int i = 0; i < kSideStreams && e == cudaSuccess; ++i) {
+    cudaStream_t s = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) br->side.push_back(s);
+  }
+  for (int i = 0; i < kSideStreams + 2 && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) br->ev.push_back(ev);
+  }
+  return e;
+}
+
+void adopt(cls_graph* g, const Branch& br) {
+  if (br.main) g->streams.push_back(br.main);
+  for (auto s : br.side) g->streams.push_back(s);
+  for (auto e : br.ev) g->events.push_back(e);
 }
 
 }  // namespace
@@ -695,39 +748,79 @@ int cls_graph_create(const cls_problem* p, int32_t R, float* x, float lr, int32_
   *out = nullptr;
   int rc = check_R(p, R);
   if (rc != CLS_OK) return rc;
-  if (n_steps < 1) return set_err(CLS_ERR_INVALID, "n_steps must be >= 1");
   if (R == 0 || (!x && p->host.n > 0)) return set_err(CLS_ERR_INVALID, "x is NULL or R == 0");
-  if (p->hook) return set_err(CLS_ERR_INVALID, "disable profiling before capturing a graph");
-  const Layout L = layout_for(p, R);
-  rc = check_ws(L, ws, ws_bytes);
-  if (rc != CLS_OK) return rc;
+  return cls_batch_graph_create(1, &p, &R, &x, lr, n_steps, &bits, &nsat, &wsat, &ws, &ws_bytes,
+                                out);
+}
+
+int cls_batch_graph_create(int32_t count, const cls_problem* const* ps, const int32_t* Rs,
+                           float* const* xs, float lr, int32_t n_steps, uint32_t* const* bits,
+                           int32_t* const* nsats, double* const* wsats, void* const* wss,
+                           const size_t* ws_bytes, cls_graph** out) {
+  if (!out) return set_err(CLS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !ps || !Rs || !xs || !wss || !ws_bytes)
+    return set_err(CLS_ERR_INVALID, "count >= 1 and the per-problem arrays are required");
+  if (n_steps < 1) return set_err(CLS_ERR_INVALID, "n_steps must be >= 1");
+  std::vector<Layout> lays;
+  for (int i = 0; i < count; ++i) {
+    int rc = check_R(ps[i], Rs[i]);
+    if (rc != CLS_OK) return rc;
+    if (Rs[i] == 0 || (!xs[i] && ps[i]->host.n > 0))
+      return set_err(CLS_ERR_INVALID, "x is NULL or R == 0 for problem " + std::to_string(i));
+    if (ps[i]->hook) return set_err(CLS_ERR_INVALID, "disable profiling before capturing a graph");
+    lays.push_back(layout_for(ps[i], Rs[i]));
+    rc = check_ws(lays.back(), wss[i], ws_bytes[i]);
+    if (rc != CLS_OK) return rc;
+  }
   cls_graph* g = new (std::nothrow) cls_graph();
   if (!g) return set_err(CLS_ERR_NOMEM, "host allocation failed");
-  const int nside = 7;   // 6 FE side streams + 1 score stream
   cudaError_t e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
-  for (int i = 0; i < nside && e == cudaSuccess; ++i) {
-    cudaStream_t s = nullptr;
-    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e == cudaSuccess) g->side.push_back(s);
-  }
-  for (int i = 0; i < nside + 2 && e == cudaSuccess; ++i) {
-    cudaEvent_t ev = nullptr;
-    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) g->events.push_back(ev);
+  std::vector<Branch> branches(count);
+  cudaEvent_t ev_start = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+  if (ev_start) g->events.push_back(ev_start);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    // one problem alone records straight into the capture stream
+    Branch& br = branches[i];
+    if (count == 1) br.main = g->cap;
+    e = make_branch(&br, count > 1);
+    if (count == 1) br.main = nullptr, adopt(g, br), br.main = g->cap;
+    else adopt(g, br);
   }
   if (e != cudaSuccess) {
     graph_release(g);
     (void)cudaGetLastError();
     return cuda_err(e, "graph resources");
   }
-  uint32_t* b = bits ? bits : at<uint32_t>(ws, L.bits);
   e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
     graph_release(g);
     (void)cudaGetLastError();
     return cuda_err(e, "cudaStreamBeginCapture");
   }
-  rc = record_steps(p, L, g, x, lr, n_steps, b, nsat, wsat, ws, nsat || wsat);
+  int rc = CLS_OK;
+  if (count > 1) {
+    e = cudaEventRecord(ev_start, g->cap);
+    for (int i = 0; i < count && e == cudaSuccess; ++i)
+      e = cudaStreamWaitEvent(branches[i].main, ev_start, 0);
+    if (e != cudaSuccess) rc = cuda_err(e, "batch fork");
+  }
+  for (int i = 0; i < count && rc == CLS_OK; ++i) {
+    const cls_problem* p = ps[i];
+    uint32_t* b = (bits && bits[i]) ? bits[i] : at<uint32_t>(wss[i], lays[i].bits);
+    int32_t* ns = nsats ? nsats[i] : nullptr;
+    double* wsv = wsats ? wsats[i] : nullptr;
+    rc = record_steps(p, lays[i], branches[i], &g->launches, xs[i], lr, n_steps, b, ns, wsv,
+                      wss[i], ns || wsv);
+  }
+  if (rc == CLS_OK && count > 1) {
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(branches[i].ev[1], branches[i].main);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cap, branches[i].ev[1], 0);
+    }
+    if (e != cudaSuccess) rc = cuda_err(e, "batch join");
+  }
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(g->cap, &graph);
   g->graph = graph;
@@ -822,9 +915,10 @@ int cls_mpnn_create(const cls_problem* p, cls_mpnn** out) {
   std::vector<float> fv((size_t)n * cls::mp::kFv), fc((size_t)m * cls::mp::kFc, 0.f);
   std::vector<int32_t> deg(n, 0), pos(n, 0);
   for (int c = 0; c < m; ++c) {
-    con_off[c + 1] = H.fe[c].lit0 + H.fe[c].L;
-    isL[c] = 1.0f / std::sqrt((float)H.fe[c].L);
-    for (int e = H.fe[c].lit0; e < H.fe[c].lit0 + H.fe[c].L; ++e) {
+    const int lit0 = H.score[c].lit0, Lc = H.score[c].L;
+    con_off[c + 1] = lit0 + Lc;
+    isL[c] = 1.0f / std::sqrt((float)Lc);
+    for (int e = lit0; e < lit0 + Lc; ++e) {
       const cls::LitRec& rc = H.lit[e];
       const float sg = rc.dst < 0 ? -1.f : 1.f;
       con_var[e] = rc.var;
@@ -838,8 +932,8 @@ int cls_mpnn_create(const cls_problem* p, cls_mpnn** out) {
     // f_c = [onehot(type, 9), L/64, k/L, w]
     float* f = &fc[(size_t)c * cls::mp::kFc];
     f[H.ctype[c]] = 1.f;
-    f[9] = (float)H.fe[c].L / 64.f;
-    f[10] = (float)H.kthr[c] / (float)H.fe[c].L;
+    f[9] = (float)Lc / 64.f;
+    f[10] = (float)H.kthr[c] / (float)Lc;
     f[11] = H.weight[c];
   }
   int n_free = n;

@@ -649,6 +649,18 @@ __global__ void k_obj_final(int R, int Rp, int nch, const double* __restrict__ p
   obj[r] = (float)a;
 }
 
+// constant expansions (no literals enter FE): fe_con[c, r] = b0
+__global__ void __launch_bounds__(256) k_fe_const(const int32_t* __restrict__ list, int count,
+                                                  const FeItem* __restrict__ fe, int R,
+                                                  float* __restrict__ fe_con, int ldf) {
+  const int64_t total = (int64_t)count * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const FeItem it = fe[list[i / R]];
+    fe_con[(size_t)it.c * ldf + (i % R)] = it.b0;
+  }
+}
+
 // vector-Jacobian product of the per-restart objective: out[v,r] = s[r] g[v,r]
 __global__ void __launch_bounds__(256) k_restart_scale(int64_t total, int R,
                                                        const float* __restrict__ g,
@@ -725,7 +737,7 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
     const dim3 g2(ceil_div(RT, kThreadTiles), std::min(ceil_div(count, 8), 65535)), b2(32, 8);
     // NJ = 2 covers NAE; OR and XOR use one root (the second is never read)
     const size_t smem = (size_t)8 * 2 * nck * 32 * sizeof(float);
-    k_fe_thread_ckpt<<<g2, b2, smem, s>>>(list, count, d.fe, d.root_tab, d.coef_tab, d.lit, x, R,
+    k_fe_thread_ckpt<<<g2, b2, smem, s>>>(list, count, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R,
                                           Rp, RT, nck, P, fe_con, ldf);
     return cudaGetLastError();
   }
@@ -734,7 +746,7 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
 #define CLS_LAUNCH_CASE(id, G, Q, C, Y)                                                      \
   case id:                                                                                   \
     k_fe_group<G, Q, (C != 0), (Y != 0)><<<grid, block, group_smem<G, Q>(), s>>>(            \
-        list, d.fe, d.root_tab, d.coef_tab, d.lit, x, R, Rp, P, fe_con, ldf);                \
+        list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf);             \
     break;
     CLS_GROUP_CONFIGS(CLS_LAUNCH_CASE)
 #undef CLS_LAUNCH_CASE
@@ -756,13 +768,13 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
     HookScope hs(h, KC_THREAD, s);
     const FeItem* items = d.thread_items[t];
     if (kThreadMaxL[t] == 8)
-      k_fe_thread<8><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.lit, x, R, Rp,
+      k_fe_thread<8><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp,
                                             RT, P, fe_con, ldf);
     else if (kThreadMaxL[t] == 16)
-      k_fe_thread<16><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.lit, x, R,
+      k_fe_thread<16><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R,
                                              Rp, RT, P, fe_con, ldf);
     else
-      k_fe_thread<32><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.lit, x, R,
+      k_fe_thread<32><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R,
                                              Rp, RT, P, fe_con, ldf);
     return cudaGetLastError();
   }
@@ -795,7 +807,7 @@ cudaError_t launch_accum_step(const DevPlan& d, int R, int Rp, const float* P, f
   const int RT = ceil_div(R, 32);
   dim3 grid(RT, std::min(ceil_div(d.n, 8), 65535)), block(32, 8);
   HookScope hs(h, KC_ACCUM, s);
-  k_accum_step<<<grid, block, 0, s>>>(d.n, R, Rp, RT, d.voff, P, x, lr, do_step ? 1 : 0,
+  k_accum_step<<<grid, block, 0, s>>>(d.n, R, Rp, RT, d.fe_voff, P, x, lr, do_step ? 1 : 0,
                                       d.fixed, grad_out, bits);
   return cudaGetLastError();
 }
@@ -845,6 +857,14 @@ cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
   }
   HookScope hs(h, KC_REDUCE, s);
   k_score_final<<<ceil_div(R, 256), 256, 0, s>>>(R, Rp, nch, nsat_part, wsat_part, nsat, wsat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fe_const(const DevPlan& d, int R, float* fe_con, int ldf, cudaStream_t s) {
+  const int64_t total = (int64_t)d.const_count * R;
+  if (total == 0 || !fe_con) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 8);
+  k_fe_const<<<blocks, 256, 0, s>>>(d.const_list, d.const_count, d.fe, R, fe_con, ldf);
   return cudaGetLastError();
 }
 

@@ -15,8 +15,12 @@ constexpr int kNumBuckets = kNumDftBuckets + kNumRealBuckets;
 struct DevPlan {
   int32_t n = 0, m = 0;
   int64_t nnz = 0;
-  LitRec* lit = nullptr;
+  LitRec* lit = nullptr;        // all literals (score, learned initialiser)
   int32_t* voff = nullptr;
+  LitRec* fe_lit = nullptr;     // literals entering FE; dst = partial-buffer row
+  int32_t* fe_voff = nullptr;   // n+1 partial-buffer rows per variable
+  int32_t* const_list = nullptr;
+  int32_t const_count = 0;
   FeItem* fe = nullptr;
   FeItem* thread_items[kNumThreadCls] = {};
   int32_t thread_count[kNumThreadCls] = {};
@@ -66,6 +70,9 @@ constexpr int kNumFeUnits = kNumThreadCls + kNumBuckets;
 bool fe_unit_active(const DevPlan& d, int unit);
 cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const float* x, float* P,
                            float* fe_con, int ldf, cudaStream_t s, LaunchHook* h);
+
+// fe_con[c * ldf + r] = b0 for constraints whose expansion is constant.
+cudaError_t launch_fe_const(const DevPlan& d, int R, float* fe_con, int ldf, cudaStream_t s);
 
 // One lane-group launch over an explicit constraint list (the autotuner).
 cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL,

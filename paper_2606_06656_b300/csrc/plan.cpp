@@ -52,8 +52,6 @@ namespace {
 
 enum { T_OR = 0, T_XOR, T_CARD_GE, T_CARD_LE, T_NAE, T_EO, T_EK, T_AMO, T_SPECTRUM };
 
-bool is_real_kind(int t) { return t == T_OR || t == T_XOR || t == T_NAE; }
-
 // Does constraint (type, L, k) hold with t true literals (Sec. 2.2; Table 2)?
 bool holds(int type, int L, int k, int t, const int8_t* spec) {
   switch (type) {
@@ -80,6 +78,7 @@ int bucket_of(const int* maxes, int nb, int L) {
 void assign_groups(HostPlan* P, const Tuning& tun) {
   for (auto& v : P->thread_items) v.clear();
   for (auto& v : P->bucket_list) v.clear();
+  P->const_list.clear();
   P->tuning = tun;
   for (int b = 0; b < kNumDftBuckets; ++b) P->bucket_cfg[b] = tun.dft[b];
   for (int b = 0; b < kNumRealBuckets; ++b) P->bucket_cfg[kNumDftBuckets + b] = tun.real[b];
@@ -87,6 +86,10 @@ void assign_groups(HostPlan* P, const Tuning& tun) {
   std::vector<int32_t> thread_c[kNumThreadCls];
   for (int32_t c = 0; c < P->m; ++c) {
     const FeItem& it = P->fe[c];
+    if (it.L == 0) {              // constant expansion: no FE work, no partials
+      P->const_list.push_back(c);
+      continue;
+    }
     bool real = it.root_off < 3;  // real roots live at the start of the table
     if (real && it.L <= kThreadMaxL[kNumThreadCls - 1]) {
       int t = 0;
@@ -116,7 +119,7 @@ void assign_groups(HostPlan* P, const Tuning& tun) {
 int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
                const int8_t* lit_sign, const int32_t* type, const int32_t* kk,
                const float* weight, const int8_t* spectra, const uint8_t* fixed,
-               const float* fixed_val, bool validate_only, HostPlan* out,
+               const float* fixed_val, uint32_t flags, bool validate_only, HostPlan* out,
                std::string* msg) {
   auto fail = [msg](const std::string& s) {
     if (msg) *msg = s;
@@ -180,6 +183,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
 
   // variable-major transpose: rows of variable v are voff[v]..voff[v+1]-1,
   // literals in increasing constraint order (a fixed summation order)
+  P.flags = flags;
   P.voff.assign(n + 1, 0);
   for (int64_t e = 0; e < nnz; ++e) P.voff[lit_var[e] + 1]++;
   for (int32_t v = 0; v < n; ++v) P.voff[v + 1] += P.voff[v];
@@ -193,8 +197,12 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
 
   // fixed real roots and their coefficients
   P.root_tab = {{0.5f, 0.5f, 0.f, 0.f}, {0.5f, -0.5f, 0.f, 0.f}, {0.f, 1.f, 0.f, 0.f}};
-  P.coef_tab = {{2.f, 0.f, 1.f, 0.f}, {1.f, 0.f, 1.f, 0.f}, {2.f, 0.f, 1.f, 0.f},
-                {2.f, 0.f, -1.f, 0.f}};
+  P.coef_tab = {{2.f, 0.f, 1.f, 0.f},  {1.f, 0.f, 1.f, 0.f},   {2.f, 0.f, 1.f, 0.f},
+                {2.f, 0.f, -1.f, 0.f}, {-1.f, 0.f, -1.f, 0.f}, {-2.f, 0.f, -1.f, 0.f},
+                {-2.f, 0.f, 1.f, 0.f}};
+  const bool simplify = (flags & kFlagSimplifyFixed) && fixed;
+  std::vector<LitRec> fe_lit_tmp;      // FE literals: var, sign bit (rows later)
+  fe_lit_tmp.reserve(nnz);
   std::map<int, int> root_of_len;
   std::map<std::pair<int, std::string>, int> coef_of_spec;
 
@@ -241,19 +249,79 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
     }
     P.score.push_back(s);
 
+    // literals that enter FE: all of them, or only the free ones when pinned
+    // variables are folded into a shifted spectrum sp'_t = sp_{t + f}, f =
+    // number of pinned literals that are true (a pinned literal's factor is
+    // exactly 1 or w^j, Sec. 3.2's partial assignment).
+    int f_true = 0, Lf = 0;
+    const size_t fe0 = fe_lit_tmp.size();
+    for (int e = offsets[c]; e < offsets[c + 1]; ++e) {
+      const int v = lit_var[e];
+      if (simplify && fixed[v]) {
+        if ((float)lit_sign[e] * fixed_val[v] == -1.0f) ++f_true;
+        continue;
+      }
+      fe_lit_tmp.push_back({v, lit_sign[e] < 0 ? kNegBit : 0});
+      ++Lf;
+    }
+    std::vector<int8_t> spf(sp.begin() + f_true, sp.begin() + f_true + Lf + 1);
     FeItem& it = P.fe[c];
-    it.lit0 = offsets[c];
-    it.L = L;
+    it.lit0 = (int32_t)fe0;
+    it.L = Lf;
     it.w = w;
     it.c = c;
-    if (is_real_kind(t)) {
-      // closed forms (Appendix A): OR = 2 prod alpha - 1, XOR = prod y,
-      // NAE = 2 (prod alpha + prod beta) - 1
-      if (t == T_OR) { it.J = 1; it.root_off = kRootAlpha; it.coef_off = kCoefOr; it.b0 = -1.f; }
-      if (t == T_XOR) { it.J = 1; it.root_off = kRootY; it.coef_off = kCoefXor; it.b0 = 0.f; }
-      if (t == T_NAE) { it.J = 2; it.root_off = kRootAlpha; it.coef_off = kCoefNae; it.b0 = -1.f; }
+    // classify the (shifted) spectrum: constant, a closed-form product of one
+    // or two real roots (Appendix A's OR, XOR, NAE and their complements),
+    // or the generic DFT
+    bool all_same = true;
+    for (int tt = 1; tt <= Lf; ++tt) all_same &= spf[tt] == spf[0];
+    auto is_pattern = [&](auto fn) {
+      for (int tt = 0; tt <= Lf; ++tt)
+        if (spf[tt] != fn(tt)) return false;
+      return true;
+    };
+    auto set_real = [&](int J, int root, int coef, float b0v) {
+      it.J = J;
+      it.root_off = root;
+      it.coef_off = coef;
+      it.b0 = b0v;
+    };
+    if (Lf == 0 || all_same) {           // FE constant, no gradient
+      fe_lit_tmp.resize(fe0);
+      it.L = 0;
+      set_real(0, kRootAlpha, kCoefOr, (float)spf[0]);
       continue;
     }
+    if (is_pattern([](int tt) { return tt == 0 ? 1 : -1; })) {            // OR
+      set_real(1, kRootAlpha, kCoefOr, -1.f);
+      continue;
+    }
+    if (is_pattern([](int tt) { return tt == 0 ? -1 : 1; })) {            // none true
+      set_real(1, kRootAlpha, kCoefNor, 1.f);
+      continue;
+    }
+    if (is_pattern([Lf](int tt) { return tt == Lf ? -1 : 1; })) {         // all true
+      set_real(1, kRootBeta, kCoefAllTrue, 1.f);
+      continue;
+    }
+    if (is_pattern([Lf](int tt) { return tt == Lf ? 1 : -1; })) {         // not all true
+      set_real(1, kRootBeta, kCoefNae + 1, -1.f);
+      continue;
+    }
+    if (is_pattern([](int tt) { return (tt & 1) ? -1 : 1; })) {           // XOR
+      set_real(1, kRootY, kCoefXor, 0.f);
+      continue;
+    }
+    if (is_pattern([](int tt) { return (tt & 1) ? 1 : -1; })) {           // XNOR
+      set_real(1, kRootY, kCoefXnor, 0.f);
+      continue;
+    }
+    if (Lf >= 2 && is_pattern([Lf](int tt) { return (tt == 0 || tt == Lf) ? 1 : -1; })) {
+      set_real(2, kRootAlpha, kCoefNae, -1.f);                             // NAE
+      continue;
+    }
+    sp.swap(spf);   // the DFT below works on sp with L = Lf
+    L = Lf;
     // DFT of the spectrum at the L+1 roots of unity, FP64 (Sec. 2.3):
     //   b_j = 1/(L+1) sum_t sp_t w^(-jt),  FE = sum_{j=0}^{L} b_j G_j with
     //   G_j = prod_i (alpha_i + beta_i w^j) (G_0 = 1).  b_{L+1-j} =
@@ -313,6 +381,17 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
     it.coef_off = cit->second;
     P.dft_roots += J;
     P.dft_lroots += (int64_t)J * L;
+  }
+  // variable-major rows of the FE literals (the partial buffer): rows of
+  // variable v are fe_voff[v]..fe_voff[v+1]-1, in constraint order
+  P.nnz_fe = (int64_t)fe_lit_tmp.size();
+  P.fe_voff.assign(n + 1, 0);
+  for (const LitRec& r : fe_lit_tmp) P.fe_voff[r.var + 1]++;
+  for (int32_t v = 0; v < n; ++v) P.fe_voff[v + 1] += P.fe_voff[v];
+  {
+    std::vector<int32_t> fcur(P.fe_voff.begin(), P.fe_voff.end() - 1);
+    P.fe_lit = fe_lit_tmp;
+    for (LitRec& r : P.fe_lit) r.dst |= fcur[r.var]++;
   }
   // score ranges: consecutive constraints, about kScoreRangeLits literals each
   // (fewer for small problems, so that their scoring still spreads over

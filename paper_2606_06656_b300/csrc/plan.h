@@ -138,7 +138,13 @@ constexpr int kRootBeta = 1;
 constexpr int kRootY = 2;
 constexpr int kCoefOr = 0;     // (2, 0, 1, 0)
 constexpr int kCoefXor = 1;    // (1, 0, 1, 0)
-constexpr int kCoefNae = 2;    // (2, 0, 1, 0), (2, 0, -1, 0)
+constexpr int kCoefNae = 2;    // (2, 0, 1, 0), (2, 0, -1, 0); the second alone: not all true
+constexpr int kCoefXnor = 4;   // (-1, 0, -1, 0): FE = -prod y
+constexpr int kCoefNor = 5;    // (-2, 0, -1, 0): FE = 1 - 2 prod alpha (no literal true)
+constexpr int kCoefAllTrue = 6;  // (-2, 0, 1, 0): FE = 1 - 2 prod beta (every literal true)
+
+// Problem build flags.
+constexpr uint32_t kFlagSimplifyFixed = 1;   // fold pinned variables into the spectra
 
 // Length buckets of the lane-group paths: one launch per non-empty bucket;
 // the tuning maps each bucket to a configuration.
@@ -159,8 +165,12 @@ bool tuning_valid(const Tuning& t, std::string* msg);
 struct HostPlan {
   int32_t n = 0, m = 0;
   int64_t nnz = 0;
-  std::vector<LitRec> lit;        // constraint order
-  std::vector<int32_t> voff;      // n+1: rows of variable v
+  uint32_t flags = 0;
+  std::vector<LitRec> lit;        // all literals, constraint order; dst = row among all
+  std::vector<int32_t> voff;      // n+1: rows of variable v among all literals
+  std::vector<LitRec> fe_lit;     // literals entering FE (all, or the free ones)
+  std::vector<int32_t> fe_voff;   // n+1: rows of variable v in the partial buffer
+  int64_t nnz_fe = 0;
   std::vector<FeItem> fe;         // m (constraint order)
   std::vector<ScoreItem> score;          // constraint order
   std::vector<int32_t> score_ranges;     // constraint boundaries of the ranges
@@ -172,6 +182,7 @@ struct HostPlan {
   int bucket_cfg[kNumDftBuckets + kNumRealBuckets] = {};
   std::vector<int32_t> ctype, kthr;   // per constraint: type and threshold (0 if none)
   std::vector<float> weight;          // per constraint
+  std::vector<int32_t> const_list;    // constraints whose expansion is a constant
   std::vector<uint8_t> fixed;     // n (empty = none)
   std::vector<float> fixed_val;   // n
   Tuning tuning;
@@ -183,7 +194,8 @@ struct HostPlan {
 int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
                const int8_t* lit_sign, const int32_t* type, const int32_t* k,
                const float* weight, const int8_t* spectra, const uint8_t* fixed,
-               const float* fixed_val, bool validate_only, HostPlan* out, std::string* msg);
+               const float* fixed_val, uint32_t flags, bool validate_only, HostPlan* out,
+               std::string* msg);
 
 // (Re)split the FE work lists for a tuning.
 void assign_groups(HostPlan* plan, const Tuning& tun);

@@ -144,3 +144,26 @@ def test_training_reduces_loss_and_objective():
     train(entries, params, steps=300, R=32, lam=0.5, tau=1.0, lr=3e-3)
     after = mean_obj(params)
     assert after < before - 0.02, (before, after)
+
+
+def test_learned_initialisation_gains_over_uniform():
+    """Trained on planted mixed instances through the CLS objective, the
+    network's initial points reach the satisfied fraction that uniform starts
+    reach after 100 steps in fewer steps, on held-out instances."""
+    from paper_2606_06656_b300 import learned as Lr
+    train = W.mixed_instances(20, n_range=(600, 900), seed=1400)
+    held = W.mixed_instances(3, n_range=(600, 900), seed=91400)
+    tr = Lr.build_entries(train, harvest_R=64, harvest_steps=150)
+    te = Lr.build_entries(held, harvest_R=8, harvest_steps=1)
+    params = tr[0][1].init_params(3)
+    Lr.train(tr, params, steps=800, R=32, lam=0.5, tau=1.0, lr=2e-3)
+    res = Lr.compare(te, params, R=256, S=100, tau=1.0)
+    gain = 0
+    for r in res:
+        assert r["steps_learned"] is not None
+        gain += r["steps_learned"] < r["steps_uniform"]
+    assert gain >= 2, res
+    f0u = np.median([Lr.median_fraction_after(p, p.init_uniform(256, 5), 1) for p, _, _ in te])
+    f0l = np.median([Lr.median_fraction_after(p, n.points(n.forward(params), 256, 5, 1.0), 1)
+                     for p, n, _ in te])
+    assert f0l > f0u, (f0l, f0u)

@@ -431,3 +431,80 @@ def test_autograd_objective_matches_oracle_and_finite_differences(P):
         with torch.no_grad():
             fd = 0.5 * (CLSObjective.apply(p, xp) - CLSObjective.apply(p, xm)) * c
         assert torch.allclose(torch.from_numpy(g[v]).cuda(), fd, atol=5e-5 * inst.m ** 0.5)
+
+
+@pytest.mark.parametrize("frac", [0.5, 0.9])
+def test_simplified_pinned_variables_match_masked_and_oracle(P, frac):
+    """Folding pinned variables into shifted spectra (sp'_t = sp_{t+f}) gives
+    the same expansions, the same gradient on free variables and the same
+    counts as evaluating every literal."""
+    from paper_2606_06656_b300 import Problem
+    base = W.mixed_pb(n=600, n_or=1500, n_xor=150, n_card=40, card_len=(10, 200), seed=31)
+    inst = W.partial_assignment(base, frac, seed=4)
+    R = 70
+    X = W.uniform_points(inst.n, R, seed=6)
+    piv = inst.fixed == 1
+    X[piv] = inst.fixed_val[piv][:, None]
+    pm = Problem(inst)
+    ps = Problem(inst, simplify_fixed=True)
+    assert ps.info["nnz_fe"] < pm.info["nnz_fe"] and ps.info["n_const"] > 0
+    om, gm, fm = [t.cpu().numpy() for t in pm.eval(torch.from_numpy(X).cuda(), fe_con=True)]
+    os_, gs, fs = [t.cpu().numpy() for t in ps.eval(torch.from_numpy(X).cuda(), fe_con=True)]
+    oobj, ograd, ofe = ocls.objective_grad(inst, X.astype(np.float64))
+    assert np.abs(fs - ofe).max() <= FE_TOL and np.abs(fm - ofe).max() <= FE_TOL
+    assert np.abs(os_ - oobj).max() <= FE_TOL * inst.m
+    free = ~piv
+    rel = np.linalg.norm(gs[free] - ograd[free]) / np.linalg.norm(ograd[free])
+    assert rel <= GRAD_RTOL, rel
+    assert np.all(gs[piv] == 0.0)
+    nm, _, bm = pm.round_score(torch.from_numpy(X).cuda())
+    ns, _, bs = ps.round_score(torch.from_numpy(X).cuda())
+    onsat, _, _ = ocls.score(inst, X)
+    assert np.array_equal(ns.cpu().numpy(), onsat) and torch.equal(nm, ns)
+    # steps move only free variables and agree between the two modes
+    xm = torch.from_numpy(X.copy()).cuda()
+    xs = torch.from_numpy(X.copy()).cuda()
+    pm.step(xm, 0.1, 5)
+    ps.step(xs, 0.1, 5)
+    assert torch.equal(xs[torch.from_numpy(piv).cuda()], torch.from_numpy(X[piv]).cuda())
+    assert torch.allclose(xm, xs, atol=1e-4)
+
+
+def test_spectrum_patterns_take_the_closed_form_paths(P):
+    """Thresholds that turn a cardinality or exactly-k constraint into a
+    clause or a product are routed to the real-root products; the results
+    still equal the oracle's."""
+    rng = np.random.default_rng(8)
+    n = 400
+    rows = []
+    for L in (3, 7, 40, 90):
+        v = rng.choice(n, L, replace=False).astype(np.int32)
+        s = np.where(rng.random(L) < 0.5, -1, 1).astype(np.int8)
+        rows += [(W.TYPE_CARD_GE, 1, v, s), (W.TYPE_CARD_GE, L, v, s), (W.TYPE_CARD_LE, L - 1, v, s),
+                 (W.TYPE_EK, 0, v, s), (W.TYPE_CARD_GE, 0, v, s), (W.TYPE_CARD_LE, L, v, s)]
+    inst = W.build(n, rows)
+    p = P(inst)
+    assert p.info["n_group_dft"] == 0 and p.info["n_const"] == 8
+    for kind in POINTS:
+        X = points(kind, n, 40, seed=2)
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X),
+                             floored=kind in ("corner", "near", "mixed"))
+
+
+def test_batch_graph_equals_separate_steps(P):
+    from paper_2606_06656_b300 import binding as B
+    insts = W.mixed_instances(3, n_range=(200, 400), seed=55)
+    probs = [P(i) for i in insts]
+    Rs = [32, 64, 96]
+    X0 = [W.uniform_points(i.n, R, seed=k) for k, (i, R) in enumerate(zip(insts, Rs))]
+    xa = [torch.from_numpy(x.copy()).cuda() for x in X0]
+    na = [p.step(x, 0.1, n_steps=4)[0] for p, x in zip(probs, xa)]
+    xb = [torch.from_numpy(x.copy()).cuda() for x in X0]
+    nb = [torch.empty(R, dtype=torch.int32, device="cuda") for R in Rs]
+    g = B.cls_batch_graph_create([p.handle for p in probs], Rs, xb, 0.1, 4, nb,
+                                 [p.workspace(R) for p, R in zip(probs, Rs)])
+    B.cls_graph_launch(g)
+    torch.cuda.synchronize()
+    for a, b, u, v in zip(xa, xb, na, nb):
+        assert torch.equal(a, b) and torch.equal(u, v)
+    B.cls_graph_destroy(g)
