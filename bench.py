@@ -1,7 +1,7 @@
 """Benchmark of the parallel-CLS hot path on one B300 (or N replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config mixed|3sat|red0|red10|red50]
+                    [--config mixed|3sat|red0|red10|red50|learned|partial]
 
 A step is one full pass of the hot path over the batch: Walsh-Fourier FE and
 literal partials of every constraint, gradient accumulation through the
@@ -315,6 +315,99 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_learned(args):
+    """Learned vs uniform initialisation: train the message-passing network
+    on planted mixed-PB instances (n ~ U{1000..4000}, m = 4.5 n) through the
+    CLS objective, then on held-out instances measure the device seconds to
+    reach the median satisfied fraction that uniform starts reach after S
+    steps (1024 restarts each)."""
+    import torch
+    from paper_2606_06656_b300 import learned as Lr
+    t0 = time.perf_counter()
+    train = W.mixed_instances(args.train_instances, n_range=(1000, 4000), seed=1400)
+    held = W.mixed_instances(args.held_out, n_range=(1000, 4000), seed=91400)
+    tr = Lr.build_entries(train, harvest_R=64, harvest_steps=200)
+    te = Lr.build_entries(held, harvest_R=8, harvest_steps=1)
+    t_build = time.perf_counter() - t0
+    params = tr[0][1].init_params(3)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    log = Lr.train(tr, params, steps=args.train_steps, R=32, lam=0.5, tau=1.0, lr=2e-3,
+                   log_every=max(1, args.train_steps // 8))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    res = Lr.compare(te, params, R=1024, S=500, tau=1.0)
+    su = [r["s_uniform"] for r in res]
+    sl = [r["s_learned"] if r["s_learned"] is not None else float("inf") for r in res]
+    line = {
+        "metric": "time-to-equal-sat, learned vs uniform init (median device s)",
+        "value": float(np.median(sl)), "unit": "s", "higher_is_better": False,
+        "uniform_s": float(np.median(su)), "speedup": float(np.median(su) / np.median(sl)),
+        "n_gpus": 1, "dtype": "f32 (network bf16 x bf16 -> f32)", "data": "synthetic",
+        "config": {"workload": "planted mixed PB, n~U{1000..4000}, m=4.5n",
+                   "train_instances": args.train_instances, "held_out": args.held_out,
+                   "train_steps": args.train_steps, "restarts": 1024, "S": 500,
+                   "build_s": t_build, "train_s": t_train},
+        "train_log": log, "per_instance": res,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_partial(args):
+    """Partial-assignment completion: 16 planted mixed-PB instances, n ~
+    U{10000..30000}, m = 4.5 n, 90% of the variables pinned to the plant,
+    512 restarts each, all instances in one CUDA graph; masked (every literal
+    evaluated) vs simplified (pinned variables folded into the spectra)."""
+    import torch
+    from paper_2606_06656_b300 import Problem
+    from paper_2606_06656_b300 import binding as B
+    insts = []
+    for i in range(16):
+        rng = np.random.default_rng(1500 + i)
+        n = int(rng.integers(10000, 30001))
+        m = int(round(4.5 * n))
+        base = W.mixed_pb(n=n, n_or=m - round(m * 2500 / 22500), n_xor=round(m * 2000 / 22500),
+                          n_card=round(m * 500 / 22500), card_len=(10, 300), seed=2500 + i)
+        insts.append(W.partial_assignment(base, 0.9, seed=3500 + i))
+    R = 512
+    units = R * sum(i.nnz for i in insts)
+    out = {}
+    for mode in ("masked", "simplified"):
+        probs = [Problem(i, simplify_fixed=(mode == "simplified")) for i in insts]
+        xs = [p.init_uniform(R, seed=42 + k) for k, p in enumerate(probs)]
+        ns = [torch.empty(R, dtype=torch.int32, device="cuda") for _ in probs]
+        g = B.cls_batch_graph_create([p.handle for p in probs], [R] * 16, xs, 0.1, 1, ns,
+                                     [p.workspace(R) for p in probs])
+        for _ in range(max(3, args.warmup)):
+            B.cls_graph_launch(g)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            B.cls_graph_launch(g)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        out[mode] = {"ms_per_step": ms, "value": units / (ms / 1e3),
+                     "nnz_fe": int(sum(p.info["nnz_fe"] for p in probs)),
+                     "kernels_per_step": B.cls_graph_kernel_count(g),
+                     "mean_nsat_frac": float(np.mean([n.float().mean().item() / p.m
+                                                      for n, p in zip(ns, probs)]))}
+        B.cls_graph_destroy(g)
+        del probs
+        torch.cuda.empty_cache()
+    line = {"metric": "constraint-literal FE+grad evals/s (all literals counted)",
+            "value": out["simplified"]["value"], "unit": "literal-evals/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "dtype": "f32",
+            "data": "synthetic", "speedup_simplified_vs_masked":
+                out["masked"]["ms_per_step"] / out["simplified"]["ms_per_step"],
+            "config": {"workload": "16 planted mixed-PB instances, n~U{10000..30000}, "
+                                   "m=4.5n, 90% pinned", "R_per_instance": R,
+                       "nnz_total": sum(i.nnz for i in insts), "one_graph": True},
+            "modes": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,12 +419,19 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time eager launches, not the graph")
     ap.add_argument("--R", type=int, default=0, help="override restarts (profiling)")
+    ap.add_argument("--train-instances", type=int, default=512)
+    ap.add_argument("--held-out", type=int, default=16)
+    ap.add_argument("--train-steps", type=int, default=3000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == "learned":
+        run_learned(args)
+    elif args.config == "partial":
+        run_partial(args)
     else:
         run_ours(args, rank, world, local_rank)
 

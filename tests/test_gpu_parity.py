@@ -477,11 +477,13 @@ def test_spectrum_patterns_take_the_closed_form_paths(P):
     rng = np.random.default_rng(8)
     n = 400
     rows = []
+    def lits(L):   # fresh variables per constraint: no exact cancellation between them
+        return (rng.choice(n, L, replace=False).astype(np.int32),
+                np.where(rng.random(L) < 0.5, -1, 1).astype(np.int8))
     for L in (3, 7, 40, 90):
-        v = rng.choice(n, L, replace=False).astype(np.int32)
-        s = np.where(rng.random(L) < 0.5, -1, 1).astype(np.int8)
-        rows += [(W.TYPE_CARD_GE, 1, v, s), (W.TYPE_CARD_GE, L, v, s), (W.TYPE_CARD_LE, L - 1, v, s),
-                 (W.TYPE_EK, 0, v, s), (W.TYPE_CARD_GE, 0, v, s), (W.TYPE_CARD_LE, L, v, s)]
+        rows += [(W.TYPE_CARD_GE, 1, *lits(L)), (W.TYPE_CARD_GE, L, *lits(L)),
+                 (W.TYPE_CARD_LE, L - 1, *lits(L)), (W.TYPE_EK, 0, *lits(L)),
+                 (W.TYPE_CARD_GE, 0, *lits(L)), (W.TYPE_CARD_LE, L, *lits(L))]
     inst = W.build(n, rows)
     p = P(inst)
     assert p.info["n_group_dft"] == 0 and p.info["n_const"] == 8
