@@ -601,7 +601,7 @@ int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* 
         const cls::GroupCfg& g = cls::kGroupCfg[id];
         // candidates: right kind, able to hold the bucket's longest
         // constraint, at most twice the slots needed
-        if (g.cplx != (dft ? 1 : 0) || g.G * g.Q < bmax || g.G * g.Q > 2 * std::max(bmax, 32))
+        if ((g.cplx != 0) != dft || g.G * g.Q < bmax || g.G * g.Q > 2 * std::max(bmax, 32))
           continue;
       }
       cudaError_t e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b],

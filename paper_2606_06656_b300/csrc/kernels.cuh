@@ -54,6 +54,10 @@ struct LaunchHook {
 };
 
 cudaError_t set_kernel_attributes();
+cudaError_t set_p2_attributes();   // kernels_p2.cu
+cudaError_t launch_group_p2(int cfg, const DevPlan& d, const int32_t* list, int count, int R,
+                            int Rp, const float* x, float* P, float* fe_con, int ldf,
+                            cudaStream_t s);
 size_t group_smem_bytes(int cfg);
 
 cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, float* x,

@@ -13,7 +13,7 @@ namespace cls {
 
 const GroupCfg kGroupCfg[kNumGroupCfg] = {
 #define CLS_CFG_ENTRY(id, G, Q, C, Y) {G, Q, C, Y},
-    CLS_GROUP_CONFIGS(CLS_CFG_ENTRY)
+    CLS_GROUP_CONFIGS(CLS_CFG_ENTRY) CLS_P2_CONFIGS(CLS_CFG_ENTRY)
 #undef CLS_CFG_ENTRY
 };
 
@@ -38,7 +38,7 @@ bool tuning_valid(const Tuning& t, std::string* msg) {
       return false;
     }
     const GroupCfg& g = kGroupCfg[id];
-    if (g.cplx != (dft ? 1 : 0) || g.G * g.Q < maxL) {
+    if ((g.cplx != 0) != dft || g.G * g.Q < maxL) {
       if (msg)
         *msg = "configuration " + std::to_string(id) + " cannot serve bucket " +
                std::to_string(b) + " (max length " + std::to_string(maxL) + ")";

@@ -113,7 +113,31 @@ struct ScoreItem {
   X(46, 16, 4, 0, 0)         \
   X(47, 16, 8, 0, 0)         \
   X(48, 16, 16, 0, 0)
-constexpr int kNumGroupCfg = 49;
+// DFT roots processed in pairs with packed FP32x2 arithmetic (CPLX = 2),
+// instantiated in kernels_p2.cu.
+#define CLS_P2_CONFIGS(X) \
+  X(49, 8, 4, 2, 0)   \
+  X(50, 8, 8, 2, 0)   \
+  X(51, 8, 8, 2, 1)   \
+  X(52, 8, 16, 2, 1)  \
+  X(53, 16, 4, 2, 0)  \
+  X(54, 16, 8, 2, 0)  \
+  X(55, 16, 8, 2, 1)  \
+  X(56, 16, 10, 2, 1) \
+  X(57, 16, 12, 2, 1) \
+  X(58, 16, 14, 2, 1) \
+  X(59, 16, 16, 2, 1) \
+  X(60, 16, 18, 2, 1) \
+  X(61, 16, 20, 2, 1) \
+  X(62, 32, 8, 2, 1)  \
+  X(63, 32, 10, 2, 1) \
+  X(64, 32, 12, 2, 1) \
+  X(65, 32, 14, 2, 1) \
+  X(66, 32, 16, 2, 1) \
+  X(67, 32, 20, 2, 1) \
+  X(68, 8, 2, 2, 0)   \
+  X(69, 8, 1, 2, 0)   
+constexpr int kNumGroupCfg = 70;
 // Configuration id of the restart-parallel checkpointed kernel for real-root
 // (closed-form) constraints of any length; valid only for real buckets.
 constexpr int kCkptCfg = 100;

@@ -218,12 +218,12 @@ def test_autotune_and_tuning_roundtrip(P):
     # every admissible configuration of every bucket gives the same results
     for b in range(B.N_BUCKETS):
         kind, bmax, _, _ = B.cls_config_info(1000 + b)
-        for cid in range(60):
+        for cid in range(80):
             try:
                 G, Q, cplx, ys = B.cls_config_info(cid)
             except Exception:
                 break
-            if cplx != kind or G * Q < bmax or G * Q > 2 * max(bmax, 32):
+            if (cplx > 0) != (kind > 0) or G * Q < bmax or G * Q > 2 * max(bmax, 32):
                 continue
             cfg = list(tuned)
             cfg[b] = cid
