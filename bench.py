@@ -179,7 +179,9 @@ def run_ours(args, rank, world, local_rank):
     x = p.init_uniform(R, seed=42, r_offset=rank * R)   # restarts sharded by global id
     ws = p.workspace(R)
     tune_s = None
-    if not args.no_tune:
+    if args.tuning:
+        B.cls_tuning_set(p.handle, [int(v) for v in args.tuning.split(",")])
+    elif not args.no_tune:
         t0 = time.perf_counter()
         B.cls_autotune(p.handle, R, x, 2, ws)
         tune_s = time.perf_counter() - t0
@@ -418,6 +420,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time eager launches, not the graph")
+    ap.add_argument("--tuning", default="", help="fixed bucket->configuration map (24 ids)")
     ap.add_argument("--R", type=int, default=0, help="override restarts (profiling)")
     ap.add_argument("--train-instances", type=int, default=512)
     ap.add_argument("--held-out", type=int, default=16)
