@@ -420,7 +420,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time eager launches, not the graph")
-    ap.add_argument("--tuning", default="", help="fixed bucket->configuration map (24 ids)")
+    ap.add_argument("--tuning", default="", help="fixed bucket->configuration map (25 ids)")
     ap.add_argument("--R", type=int, default=0, help="override restarts (profiling)")
     ap.add_argument("--train-instances", type=int, default=512)
     ap.add_argument("--held-out", type=int, default=16)

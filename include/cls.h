@@ -137,8 +137,8 @@ int cls_problem_destroy(cls_problem* p);
 /* Problem facts for callers: sizes and the per-path constraint counts.
  *   info[0] n, info[1] m, info[2] nnz, info[3] # constraints whose spectrum
  *   is a closed-form product of real roots (OR, XOR, NAE and their
- *   complements, Appendix A) with L <= 32 (one thread per (constraint,
- *   restart)), info[4] # such constraints with L > 32, info[5] # on the
+ *   complements, Appendix A) with L <= 16 (one thread per (constraint,
+ *   restart)), info[4] # such constraints with L > 16, info[5] # on the
  *   DFT path (every other spectrum), info[6] number of DFT roots summed
  *   over DFT constraints, info[7] sum over DFT constraints of L * roots,
  *   info[8] literals entering FE (nnz minus folded pinned literals),
@@ -254,7 +254,7 @@ int cls_graph_destroy(cls_graph* g);
  * keeps the fastest and synchronises the stream.  Results do not depend on
  * the tuning beyond FP32 rounding order of the DFT products.
  * cls_tuning_get/cls_tuning_set read or replace the bucket -> configuration
- * map (n must equal the number of buckets, 24); cls_config_info(id, out[4])
+ * map (n must equal the number of buckets, 25); cls_config_info(id, out[4])
  * describes configuration id (G, Q, DFT?, shared-memory y?) and, for
  * id = 1000 + b, bucket b (DFT?, maximum length).  An invalid map is
  * rejected with CLS_ERR_INVALID. */

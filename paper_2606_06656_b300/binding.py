@@ -158,7 +158,7 @@ def cls_profile_read(h, kc):
     return int(n.value), float(ms.value)
 
 
-N_BUCKETS = 24
+N_BUCKETS = 25
 
 
 def cls_autotune(h, R, x, reps, ws, stream=None):

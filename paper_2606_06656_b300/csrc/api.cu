@@ -309,6 +309,7 @@ int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const in
   D.n = H.n;
   D.m = H.m;
   D.nnz = H.nnz;
+  D.nnz_fe = H.nnz_fe;
   int r2 = CLS_OK;
   auto up = [&](auto& vec, auto** dst) {
     if (r2 == CLS_OK) r2 = upload(p, vec, dst);

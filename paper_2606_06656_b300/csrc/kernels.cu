@@ -73,14 +73,93 @@ __global__ void __launch_bounds__(256) k_init_uniform(int n, int R, uint64_t see
 }
 
 // ---------------------------------------------------------------------------
-// A2-A5, closed-form products (OR, XOR, NAE) with L <= MAXL: one thread per
-// (constraint, restart), a warp = one constraint x 32 restarts, looping over
-// kThreadTiles restart tiles so the constraint's literal records are loaded
-// once.  FE = b0 + sum_j b'_j prod_i F_ij and dFE/dy_i = sum_j c'_j
-// prod_{l!=i} F_lj with real factors F = A + y B: prefix products in
-// registers, suffix products carried backwards (no division).
+// A2-A5, closed-form products (clause, XOR, NAE and complements) of short
+// constraints: one thread per (constraint, restart), a warp = one constraint x
+// 32 restarts, looping over kThreadTiles restart tiles.  The body is
+// specialised on the exact length L (no guards in the unrolled loops); the
+// literals' x and partial-row offsets are computed once per constraint (IDX =
+// int when every offset fits in 31 bits).  FE = b0 + sum_j b'_j prod_i F_ij
+// and dFE/dy_i = sum_j c'_j prod_{l!=i} F_lj with real factors F = A + y B:
+// prefix products in registers, suffix products carried backwards (no
+// division).
 // ---------------------------------------------------------------------------
-template <int MAXL>
+template <int L, typename IDX>
+__device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restrict__ root,
+                                            const F4* __restrict__ coef,
+                                            const LitRec* __restrict__ lit,
+                                            const float* __restrict__ x, int R, int Rp, int RT,
+                                            int lane, float* __restrict__ P,
+                                            float* __restrict__ fe_con, int ldf) {
+  IDX xo[L], po[L];
+  float sg[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const LitRec rc = lit[it.lit0 + i];
+    xo[i] = (IDX)rc.var * (IDX)R;
+    po[i] = (IDX)rec_row(rc.dst) * (IDX)Rp;
+    sg[i] = rec_sgn(rc.dst);
+  }
+  const float4 rt0 = ldg4(&root[it.root_off]), cf0 = ldg4(&coef[it.coef_off]);
+  const bool two = it.J == 2;
+  const float4 rt1 = two ? ldg4(&root[it.root_off + 1]) : make_float4(1.f, 0.f, 0.f, 0.f);
+  const float4 cf1 = two ? ldg4(&coef[it.coef_off + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int tt = 0; tt < kThreadTiles; ++tt) {
+    const int tile = blockIdx.x * kThreadTiles + tt;
+    if (tile >= RT) break;
+    const int r = tile * 32 + lane;
+    if (r >= R) continue;
+    float y[L], g[L], pre[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) y[i] = sg[i] * x[xo[i] + r];
+    float run = 1.f;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      pre[i] = run;
+      run *= fmaf(y[i], rt0.y, rt0.x);
+    }
+    float val = fmaf(cf0.x, run, it.b0);
+    float suf = cf0.z;
+#pragma unroll
+    for (int i = L - 1; i >= 0; --i) {
+      g[i] = pre[i] * suf;
+      suf *= fmaf(y[i], rt0.y, rt0.x);
+    }
+    if (two) {
+      run = 1.f;
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        pre[i] = run;
+        run *= fmaf(y[i], rt1.y, rt1.x);
+      }
+      val = fmaf(cf1.x, run, val);
+      suf = cf1.z;
+#pragma unroll
+      for (int i = L - 1; i >= 0; --i) {
+        g[i] = fmaf(pre[i], suf, g[i]);
+        suf *= fmaf(y[i], rt1.y, rt1.x);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) P[po[i] + r] = it.w * sg[i] * g[i];
+    if (fe_con) fe_con[(size_t)it.c * ldf + r] = val;
+  }
+}
+
+template <int LO, int HI, typename IDX>
+__device__ __forceinline__ void thread_dispatch(int L, const FeItem& it, const F4* root,
+                                                const F4* coef, const LitRec* lit,
+                                                const float* x, int R, int Rp, int RT, int lane,
+                                                float* P, float* fe_con, int ldf) {
+  if constexpr (LO <= HI) {
+    if (L == LO)
+      thread_body<LO, IDX>(it, root, coef, lit, x, R, Rp, RT, lane, P, fe_con, ldf);
+    else
+      thread_dispatch<LO + 1, HI, IDX>(L, it, root, coef, lit, x, R, Rp, RT, lane, P, fe_con,
+                                       ldf);
+  }
+}
+
+template <int LO, int HI, typename IDX>
 __global__ void __launch_bounds__(256) k_fe_thread(
     const FeItem* __restrict__ items, int count, const F4* __restrict__ root,
     const F4* __restrict__ coef, const LitRec* __restrict__ lit, const float* __restrict__ x,
@@ -88,67 +167,7 @@ __global__ void __launch_bounds__(256) k_fe_thread(
   const int lane = threadIdx.x;
   for (int ci = blockIdx.y * blockDim.y + threadIdx.y; ci < count; ci += gridDim.y * blockDim.y) {
     const FeItem it = items[ci];
-    const int L = it.L;
-    float4 rt[2], cf[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      rt[j] = make_float4(1.f, 0.f, 0.f, 0.f);
-      cf[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j < it.J) {
-        rt[j] = ldg4(&root[it.root_off + j]);
-        cf[j] = ldg4(&coef[it.coef_off + j]);
-      }
-    }
-    for (int tt = 0; tt < kThreadTiles; ++tt) {
-      const int tile = blockIdx.x * kThreadTiles + tt;
-      if (tile >= RT) break;
-      const int r = tile * 32 + lane;
-      if (r >= R) continue;
-      // literal records are re-read per tile (warp-uniform L1 hits) to keep
-      // the register footprint at three values per literal
-      float y[MAXL], g[MAXL], pre[MAXL];
-#pragma unroll
-      for (int i = 0; i < MAXL; ++i) {
-        g[i] = 0.f;
-        y[i] = 1.f;
-        pre[i] = 0.f;
-        if (i < L) {
-          const LitRec rc = lit[it.lit0 + i];
-          y[i] = rec_sgn(rc.dst) * x[(size_t)rc.var * R + r];
-        }
-      }
-      float val = it.b0;
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (j < it.J) {
-          float run = 1.f;
-#pragma unroll
-          for (int i = 0; i < MAXL; ++i) {
-            if (i < L) {
-              pre[i] = run;
-              run *= fmaf(y[i], rt[j].y, rt[j].x);
-            }
-          }
-          val = fmaf(cf[j].x, run, val);
-          float suf = cf[j].z;  // c'_j folded into the suffix product
-#pragma unroll
-          for (int i = MAXL - 1; i >= 0; --i) {
-            if (i < L) {
-              g[i] = fmaf(pre[i], suf, g[i]);
-              suf *= fmaf(y[i], rt[j].y, rt[j].x);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < MAXL; ++i) {
-        if (i < L) {
-          const LitRec rc = lit[it.lit0 + i];
-          P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * g[i];
-        }
-      }
-      if (fe_con) fe_con[(size_t)it.c * ldf + r] = val;
-    }
+    thread_dispatch<LO, HI, IDX>(it.L, it, root, coef, lit, x, R, Rp, RT, lane, P, fe_con, ldf);
   }
 }
 
@@ -773,15 +792,21 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
         block(32, 8);
     HookScope hs(h, KC_THREAD, s);
     const FeItem* items = d.thread_items[t];
-    if (kThreadMaxL[t] == 8)
-      k_fe_thread<8><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp,
-                                            RT, P, fe_con, ldf);
-    else if (kThreadMaxL[t] == 16)
-      k_fe_thread<16><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R,
-                                             Rp, RT, P, fe_con, ldf);
-    else
-      k_fe_thread<32><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R,
-                                             Rp, RT, P, fe_con, ldf);
+    // 32-bit offsets when every x and partial index fits
+    const bool i32 = (int64_t)d.n * R < (int64_t)1 << 31 && d.nnz_fe * Rp < (int64_t)1 << 31;
+#define CLS_THREAD_LAUNCH(LO, HI)                                                            \
+  if (i32)                                                                                 \
+    k_fe_thread<LO, HI, int><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab,      \
+                                                    d.fe_lit, x, R, Rp, RT, P, fe_con, ldf);  \
+  else                                                                                     \
+    k_fe_thread<LO, HI, int64_t><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab,  \
+                                                        d.fe_lit, x, R, Rp, RT, P, fe_con, ldf);
+    if (t == 0) {
+      CLS_THREAD_LAUNCH(1, 8)
+    } else {
+      CLS_THREAD_LAUNCH(9, 16)
+    }
+#undef CLS_THREAD_LAUNCH
     return cudaGetLastError();
   }
   const int b = unit - kNumThreadCls;

@@ -14,7 +14,7 @@ constexpr int kNumBuckets = kNumDftBuckets + kNumRealBuckets;
 // Device copy of a HostPlan.
 struct DevPlan {
   int32_t n = 0, m = 0;
-  int64_t nnz = 0;
+  int64_t nnz = 0, nnz_fe = 0;
   LitRec* lit = nullptr;        // all literals (score, learned initialiser)
   int32_t* voff = nullptr;
   LitRec* fe_lit = nullptr;     // literals entering FE; dst = partial-buffer row

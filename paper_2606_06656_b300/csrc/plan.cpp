@@ -21,7 +21,7 @@ Tuning default_tuning() {
   Tuning t;
   const int dft[kNumDftBuckets] = {0,  1,  2,  3,  4,  8,  9,  24, 25, 26,
                                    27, 28, 29, 30, 33, 34, 35, 36, 37};
-  const int real[kNumRealBuckets] = {kCkptCfg, kCkptCfg, kCkptCfg, kCkptCfg, kCkptCfg};
+  const int real[kNumRealBuckets] = {41, kCkptCfg, 48, 43, kCkptCfg, kCkptCfg};
   for (int b = 0; b < kNumDftBuckets; ++b) t.dft[b] = dft[b];
   for (int b = 0; b < kNumRealBuckets; ++b) t.real[b] = real[b];
   return t;

@@ -148,8 +148,8 @@ struct GroupCfg {
 extern const GroupCfg kGroupCfg[kNumGroupCfg];
 
 // Thread-path (one thread per (constraint, restart)) length classes.
-constexpr int kNumThreadCls = 3;
-constexpr int kThreadMaxL[kNumThreadCls] = {8, 16, 32};
+constexpr int kNumThreadCls = 2;
+constexpr int kThreadMaxL[kNumThreadCls] = {8, 16};
 constexpr int kThreadTiles = 4;   // restart tiles (of 32) per warp
 
 // Score path: consecutive constraints are grouped into ranges of about this
@@ -176,8 +176,8 @@ constexpr int kNumDftBuckets = 19;
 constexpr int kDftBucketMax[kNumDftBuckets] = {8,   16,  32,  48,  64,  96,  128,
                                                160, 192, 224, 256, 288, 320, 384,
                                                448, 512, 640, 768, 1024};
-constexpr int kNumRealBuckets = 5;
-constexpr int kRealBucketMax[kNumRealBuckets] = {64, 128, 256, 512, 1024};
+constexpr int kNumRealBuckets = 6;
+constexpr int kRealBucketMax[kNumRealBuckets] = {32, 64, 128, 256, 512, 1024};
 
 struct Tuning {
   int dft[kNumDftBuckets];
