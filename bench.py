@@ -195,11 +195,17 @@ def run_ours(args, rank, world, local_rank):
     def step_eager():
         B.cls_step(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
 
-    graph = None if args.eager else B.cls_graph_create(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
+    def step_persistent():
+        B.cls_step_persistent(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
+
+    graph = None if (args.eager or args.persistent) else \
+        B.cls_graph_create(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
 
     def step():
         if graph is not None:
             B.cls_graph_launch(graph)
+        elif args.persistent:
+            step_persistent()
         else:
             step_eager()
 
@@ -232,6 +238,8 @@ def run_ours(args, rank, world, local_rank):
         B.cls_profile_enable(p.handle, True)
         ms_eager = timed(step_eager, args.steps)
         B.cls_profile_enable(p.handle, False)
+    if args.persistent and B.cls_persistent_status(p.handle, R, ws) != 0:
+        raise RuntimeError("persistent loop: a grid barrier timed out")
     if dist:
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -246,6 +254,8 @@ def run_ours(args, rank, world, local_rank):
         launches += n_l
         kstats[name] = {"launches_per_step": n_l / args.steps, "ms_per_step": t_ms / args.steps}
     launches_timed = graph_launches * args.steps if graph_launches is not None else launches
+    if args.persistent:
+        launches_timed = args.steps                 # one cooperative kernel per step
     clocks = clk.summary()
 
     # end to end through host buffers: H2D x0 (pinned), one step, D2H nsat
@@ -299,7 +309,9 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": units / e2e_s, "unit": "literal-evals/s",
                 "h2d_bytes_per_step": 4 * inst.n * R, "d2h_bytes_per_step": 4 * R},
         "gpu_launches": launches_timed,
-        "mode": "cuda-graph (1 step per launch)" if graph is not None else "eager",
+        "mode": ("cuda-graph (1 step per launch)" if graph is not None else
+                 "persistent cooperative kernel (1 step per launch)" if args.persistent
+                 else "eager"),
         "ms_per_step_eager": ms_eager,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -420,6 +432,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time eager launches, not the graph")
+    ap.add_argument("--persistent", action="store_true",
+                    help="time the one-launch persistent step (short closed-form problems)")
     ap.add_argument("--tuning", default="", help="fixed bucket->configuration map (25 ids)")
     ap.add_argument("--R", type=int, default=0, help="override restarts (profiling)")
     ap.add_argument("--train-instances", type=int, default=512)

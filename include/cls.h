@@ -202,6 +202,34 @@ int cls_step(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_step
              uint32_t* bits, int32_t* nsat, double* wsat, void* ws,
              size_t ws_bytes, void* stream);
 
+/* The n-step loop as ONE persistent launch (task: all restarts and all
+ * constraints in one persistent launch; Sec. 3.3's lockstep batch): a
+ * cooperative kernel whose warps take, in turn, the FE+gradient items, the
+ * accumulate/step/round items and the scoring items of every step, separated
+ * by grid barriers.  Same arguments and results as cls_step.  Supported when
+ * every constraint that needs FE work is a closed-form product of at most
+ * 16 literals (e.g. random k-SAT); otherwise CLS_ERR_UNSUPPORTED (use
+ * cls_step or a graph), likewise without cooperative launch.  The barriers
+ * never spin unboundedly: a barrier that waits too long (~2^22 polls) sets
+ * an error flag in the workspace and every block returns; read it with
+ * cls_persistent_status (synchronous; 0 = ok, 1 = a barrier timed out). */
+int cls_step_persistent(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
+                        uint32_t* bits, int32_t* nsat, double* wsat, void* ws, size_t ws_bytes,
+                        void* stream);
+int cls_persistent_status(const cls_problem* p, int32_t R, const void* ws, size_t ws_bytes,
+                          int32_t* status);
+
+/* Self-check of the persistent loop's grid barrier (no counterpart in the
+ * paper): a cooperative launch of one block per SM passes `rounds` barriers
+ * that release after (blocks + extra) arrivals.  With extra = 0 all rounds
+ * pass (*status = 0, *passed = rounds); with extra > 0 no barrier can
+ * release, every block gives up after spin_limit polls (0 < spin_limit <=
+ * 2^24; ~100 ns each) and returns, *status = 1 and *passed = 0: the bounded
+ * wait ends the kernel instead of hanging it.  scratch: >= 16 device bytes,
+ * overwritten.  Synchronous on the legacy default stream. */
+int cls_grid_barrier_check(int32_t rounds, int32_t extra, uint32_t spin_limit, void* scratch,
+                           size_t scratch_bytes, int32_t* status, int32_t* passed);
+
 /* End-to-end solve from HOST buffers: copies x0 (host float[n*R], pinned
  * memory recommended) to the device workspace, runs n_steps as cls_step,
  * and copies the final nsat (host int32[R]) and x (host float[n*R], may be

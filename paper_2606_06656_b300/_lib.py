@@ -15,6 +15,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "cls.h")
 _lib = None
 
 i32, i64, u64, f32, vp, sz = C.c_int32, C.c_int64, C.c_uint64, C.c_float, C.c_void_p, C.c_size_t
+u32 = C.c_uint32
 P = C.POINTER
 
 SIGNATURES = {
@@ -31,6 +32,9 @@ SIGNATURES = {
     "cls_restart_scale": (i32, [vp, i32, vp, vp, vp, vp]),
     "cls_round_score": (i32, [vp, i32, vp, vp, vp, vp, vp, sz, vp]),
     "cls_step": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp, sz, vp]),
+    "cls_step_persistent": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, vp, sz, vp]),
+    "cls_persistent_status": (i32, [vp, i32, vp, sz, P(i32)]),
+    "cls_grid_barrier_check": (i32, [i32, i32, u32, vp, sz, P(i32), P(i32)]),
     "cls_solve_host_workspace_size": (i32, [vp, i32, P(sz)]),
     "cls_solve_host": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, sz, vp]),
     "cls_autotune": (i32, [vp, i32, vp, i32, vp, sz, vp]),

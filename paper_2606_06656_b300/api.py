@@ -93,6 +93,21 @@ class Problem:
         B.cls_step(self.handle, R, x, lr, n_steps, b, nsat, wsat, self.workspace(R))
         return nsat, wsat, b
 
+    def step_persistent(self, x, lr, n_steps=1, bits=True, score=True):
+        """Same results as step(), the whole loop in one cooperative launch
+        (problems whose FE work is all short closed forms).  Raises if a
+        grid barrier timed out."""
+        R = self._x(x)
+        b = torch.empty((self.n, (R + 31) // 32), dtype=torch.int32, device=self.device) \
+            if bits else None
+        nsat = torch.empty(R, dtype=torch.int32, device=self.device) if score else None
+        wsat = torch.empty(R, dtype=torch.float64, device=self.device) if score else None
+        ws = self.workspace(R)
+        B.cls_step_persistent(self.handle, R, x, lr, n_steps, b, nsat, wsat, ws)
+        if n_steps > 0 and R > 0 and B.cls_persistent_status(self.handle, R, ws) != 0:
+            raise RuntimeError("cls_step_persistent: a grid barrier timed out")
+        return nsat, wsat, b
+
     def solve_host(self, x0_host, lr, n_steps, nsat_host, x_host=None):
         """x0_host: (n, R) float32 CPU tensor (pinned for async copies)."""
         R = x0_host.shape[1]

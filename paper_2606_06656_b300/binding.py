@@ -273,3 +273,25 @@ def cls_batch_graph_create(handles, Rs, xs, lr, n_steps, nsats, wss):
                                                   npp, None, wp, wb, C.byref(g)),
                "cls_batch_graph_create")
     return g
+
+
+def cls_step_persistent(h, R, x, lr, n_steps, bits, nsat, wsat, ws, stream=None):
+    _lib.check(_lib.load().cls_step_persistent(h, int(R), _ptr(x), float(lr), int(n_steps),
+                                               _ptr(bits), _ptr(nsat), _ptr(wsat), _ptr(ws),
+                                               ws.numel() if ws is not None else 0,
+                                               _stream(stream)), "cls_step_persistent")
+
+
+def cls_persistent_status(h, R, ws):
+    st = C.c_int32()
+    _lib.check(_lib.load().cls_persistent_status(h, int(R), _ptr(ws), ws.numel(), C.byref(st)),
+               "cls_persistent_status")
+    return int(st.value)
+
+
+def cls_grid_barrier_check(rounds, extra, spin_limit, scratch):
+    st, passed = C.c_int32(), C.c_int32()
+    _lib.check(_lib.load().cls_grid_barrier_check(int(rounds), int(extra), int(spin_limit),
+                                                  _ptr(scratch), scratch.numel(), C.byref(st),
+                                                  C.byref(passed)), "cls_grid_barrier_check")
+    return int(st.value), int(passed.value)

@@ -125,7 +125,7 @@ struct Layout {
   int R = 0, Rp = 0, RT = 0;
   int nch = 1, chunk = 1;
   size_t P = 0, fe = 0, bits = 0, nsat_part = 0, wsat_part = 0, obj_part = 0, nsat = 0,
-         total = 0;
+         rpart_n = 0, rpart_w = 0, bar = 0, total = 0;
 };
 
 Layout layout_for(const cls_problem* p, int R) {
@@ -153,6 +153,11 @@ Layout layout_for(const cls_problem* p, int R) {
   L.wsat_part = take((size_t)nsc * L.Rp * sizeof(double));
   L.obj_part = take((size_t)L.nch * L.Rp * sizeof(double));
   L.nsat = take((size_t)L.Rp * sizeof(int32_t));
+  // persistent loop: per-range score partials and the grid barrier words
+  const size_t nr = (size_t)std::max(1, p->dev.n_ranges);
+  L.rpart_n = take(nr * L.Rp * sizeof(int32_t));
+  L.rpart_w = take(nr * L.Rp * sizeof(double));
+  L.bar = take(4 * sizeof(int32_t));
   L.total = off;
   return L;
 }
@@ -473,6 +478,70 @@ int cls_step(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_step
     rc = run_step(p, L, x, lr, b, nsat, wsat, ws, s, want_score);
     if (rc != CLS_OK) return rc;
   }
+  return CLS_OK;
+}
+
+int cls_step_persistent(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
+                        uint32_t* bits, int32_t* nsat, double* wsat, void* ws, size_t ws_bytes,
+                        void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (n_steps < 0) return set_err(CLS_ERR_INVALID, "n_steps must be >= 0");
+  if (R == 0 || n_steps == 0) return CLS_OK;
+  if (!x) return set_err(CLS_ERR_INVALID, "x is NULL");
+  if (!cls::persistent_eligible(p->dev))
+    return set_err(CLS_ERR_UNSUPPORTED,
+                   "the persistent loop needs every FE constraint on the short closed-form path "
+                   "(<= 16 literals); use cls_step or a graph");
+  const Layout L = layout_for(p, R);
+  rc = check_ws(L, ws, ws_bytes);
+  if (rc != CLS_OK) return rc;
+  uint32_t* b = bits ? bits : at<uint32_t>(ws, L.bits);
+  unsigned* bar = at<unsigned>(ws, L.bar);
+  cudaError_t e = cls::launch_persistent(p->dev, R, L.Rp, x, lr, n_steps, at<float>(ws, L.P), b,
+                                         at<int32_t>(ws, L.rpart_n), at<double>(ws, L.rpart_w),
+                                         nsat, wsat, bar, reinterpret_cast<int*>(bar + 2),
+                                         (cudaStream_t)stream);
+  if (e == cudaErrorNotSupported)
+    return set_err(CLS_ERR_UNSUPPORTED, "cooperative launch not available on this device");
+  CLS_CUDA_TRY(e, "persistent kernel");
+  return CLS_OK;
+}
+
+int cls_persistent_status(const cls_problem* p, int32_t R, const void* ws, size_t ws_bytes,
+                          int32_t* status) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (!status) return set_err(CLS_ERR_INVALID, "status is NULL");
+  const Layout L = layout_for(p, R);
+  rc = check_ws(L, const_cast<void*>(ws), ws_bytes);
+  if (rc != CLS_OK) return rc;
+  int v = 0;
+  CLS_CUDA_TRY(cudaMemcpy(&v, static_cast<const char*>(ws) + L.bar + 2 * sizeof(unsigned),
+                          sizeof(int), cudaMemcpyDeviceToHost),
+               "status copy");
+  *status = v;
+  return CLS_OK;
+}
+
+int cls_grid_barrier_check(int32_t rounds, int32_t extra, uint32_t spin_limit, void* scratch,
+                           size_t scratch_bytes, int32_t* status, int32_t* passed) {
+  if (rounds < 0 || extra < 0 || spin_limit == 0 || spin_limit > (1u << 24))
+    return set_err(CLS_ERR_INVALID, "rounds/extra must be >= 0 and 0 < spin_limit <= 2^24");
+  if (!scratch || scratch_bytes < 16) return set_err(CLS_ERR_INVALID, "scratch < 16 bytes");
+  if (!status || !passed) return set_err(CLS_ERR_INVALID, "status/passed is NULL");
+  unsigned* bar = static_cast<unsigned*>(scratch);
+  cudaError_t e = cls::launch_barrier_check(rounds, (unsigned)extra, spin_limit, bar,
+                                            reinterpret_cast<int*>(bar + 2),
+                                            reinterpret_cast<int*>(bar + 3), nullptr);
+  if (e == cudaErrorNotSupported)
+    return set_err(CLS_ERR_UNSUPPORTED, "cooperative launch not available on this device");
+  CLS_CUDA_TRY(e, "barrier check");
+  CLS_CUDA_TRY(cudaStreamSynchronize(nullptr), "barrier check");
+  int32_t v[2] = {0, 0};
+  CLS_CUDA_TRY(cudaMemcpy(v, bar + 2, sizeof(v), cudaMemcpyDeviceToHost), "barrier check copy");
+  *status = v[0];
+  *passed = v[1];
   return CLS_OK;
 }
 

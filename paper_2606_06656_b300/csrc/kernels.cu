@@ -23,6 +23,14 @@ __device__ __forceinline__ float4 ldg4(const F4* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
 
+// Loads of data that an earlier stage of the SAME launch wrote (the
+// persistent kernel) must not take the read-only path; CG = true routes them
+// through L2 (ld.global.cg).
+template <bool CG, typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
 __device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
 __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
 
@@ -83,12 +91,12 @@ __global__ void __launch_bounds__(256) k_init_uniform(int n, int R, uint64_t see
 // prefix products in registers, suffix products carried backwards (no
 // division).
 // ---------------------------------------------------------------------------
-template <int L, typename IDX>
+template <int L, typename IDX, bool CG = false>
 __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restrict__ root,
                                             const F4* __restrict__ coef,
                                             const LitRec* __restrict__ lit,
                                             const float* __restrict__ x, int R, int Rp, int RT,
-                                            int lane, float* __restrict__ P,
+                                            int tile0, int lane, float* __restrict__ P,
                                             float* __restrict__ fe_con, int ldf) {
   IDX xo[L], po[L];
   float sg[L];
@@ -104,13 +112,13 @@ __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restri
   const float4 rt1 = two ? ldg4(&root[it.root_off + 1]) : make_float4(1.f, 0.f, 0.f, 0.f);
   const float4 cf1 = two ? ldg4(&coef[it.coef_off + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
   for (int tt = 0; tt < kThreadTiles; ++tt) {
-    const int tile = blockIdx.x * kThreadTiles + tt;
+    const int tile = tile0 + tt;
     if (tile >= RT) break;
     const int r = tile * 32 + lane;
     if (r >= R) continue;
     float y[L], g[L], pre[L];
 #pragma unroll
-    for (int i = 0; i < L; ++i) y[i] = sg[i] * x[xo[i] + r];
+    for (int i = 0; i < L; ++i) y[i] = sg[i] * ldx<CG>(&x[xo[i] + r]);
     float run = 1.f;
 #pragma unroll
     for (int i = 0; i < L; ++i) {
@@ -145,17 +153,17 @@ __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restri
   }
 }
 
-template <int LO, int HI, typename IDX>
+template <int LO, int HI, typename IDX, bool CG = false>
 __device__ __forceinline__ void thread_dispatch(int L, const FeItem& it, const F4* root,
                                                 const F4* coef, const LitRec* lit,
-                                                const float* x, int R, int Rp, int RT, int lane,
-                                                float* P, float* fe_con, int ldf) {
+                                                const float* x, int R, int Rp, int RT, int tile0,
+                                                int lane, float* P, float* fe_con, int ldf) {
   if constexpr (LO <= HI) {
     if (L == LO)
-      thread_body<LO, IDX>(it, root, coef, lit, x, R, Rp, RT, lane, P, fe_con, ldf);
+      thread_body<LO, IDX, CG>(it, root, coef, lit, x, R, Rp, RT, tile0, lane, P, fe_con, ldf);
     else
-      thread_dispatch<LO + 1, HI, IDX>(L, it, root, coef, lit, x, R, Rp, RT, lane, P, fe_con,
-                                       ldf);
+      thread_dispatch<LO + 1, HI, IDX, CG>(L, it, root, coef, lit, x, R, Rp, RT, tile0, lane, P,
+                                       fe_con, ldf);
   }
 }
 
@@ -167,7 +175,8 @@ __global__ void __launch_bounds__(256) k_fe_thread(
   const int lane = threadIdx.x;
   for (int ci = blockIdx.y * blockDim.y + threadIdx.y; ci < count; ci += gridDim.y * blockDim.y) {
     const FeItem it = items[ci];
-    thread_dispatch<LO, HI, IDX>(it.L, it, root, coef, lit, x, R, Rp, RT, lane, P, fe_con, ldf);
+    thread_dispatch<LO, HI, IDX>(it.L, it, root, coef, lit, x, R, Rp, RT,
+                                 blockIdx.x * kThreadTiles, lane, P, fe_con, ldf);
   }
 }
 
@@ -468,6 +477,48 @@ __device__ __forceinline__ float pgd_project(float xv, float g, float lr) {
   return fminf(fmaxf(__fsub_rn(xv, t), -1.0f), 1.0f);
 }
 
+// one (variable, 32-restart tile): called by whole warps
+template <bool CG = false>
+__device__ __forceinline__ void accum_one(int v, int tile, int lane, int R, int Rp, int RW,
+                                          const int32_t* __restrict__ voff,
+                                          const float* __restrict__ P, float* __restrict__ x,
+                                          float lr, int do_step, const uint8_t* __restrict__ fixed,
+                                          float* __restrict__ grad_out,
+                                          uint32_t* __restrict__ bits) {
+  const int r = tile * 32 + lane;
+  const bool act = r < R;
+  {
+    const int k0 = voff[v], k1 = voff[v + 1];
+    float g = 0.f;
+    if (act) {
+      const float* p = P + (size_t)k0 * Rp + r;
+      int k = k0;
+      for (; k + 4 <= k1; k += 4, p += 4 * (size_t)Rp) {
+        const float a0 = ldx<CG>(p), a1 = ldx<CG>(p + (size_t)Rp);
+        const float a2 = ldx<CG>(p + 2 * (size_t)Rp), a3 = ldx<CG>(p + 3 * (size_t)Rp);
+        g += a0;
+        g += a1;
+        g += a2;
+        g += a3;
+      }
+      for (; k < k1; ++k, p += Rp) g += ldx<CG>(p);
+    }
+    if (grad_out && act) grad_out[(size_t)v * R + r] = g;
+    if (do_step) {
+      float xv = 0.f;
+      if (act) {
+        xv = ldx<CG>(&x[(size_t)v * R + r]);
+        if (!(fixed && fixed[v])) {
+          xv = pgd_project(xv, g, lr);
+          x[(size_t)v * R + r] = xv;
+        }
+      }
+      const uint32_t b = __ballot_sync(kFull, act && xv < 0.0f);
+      if (bits && lane == 0) bits[(size_t)v * RW + tile] = b;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_accum_step(int n, int R, int Rp, int RW,
                                                     const int32_t* __restrict__ voff,
                                                     const float* __restrict__ P,
@@ -475,38 +526,9 @@ __global__ void __launch_bounds__(256) k_accum_step(int n, int R, int Rp, int RW
                                                     const uint8_t* __restrict__ fixed,
                                                     float* __restrict__ grad_out,
                                                     uint32_t* __restrict__ bits) {
-  const int lane = threadIdx.x;
-  const int r = blockIdx.x * 32 + lane;
-  const bool act = r < R;
-  for (int v = blockIdx.y * blockDim.y + threadIdx.y; v < n; v += gridDim.y * blockDim.y) {
-    const int k0 = voff[v], k1 = voff[v + 1];
-    float g = 0.f;
-    if (act) {
-      const float* p = P + (size_t)k0 * Rp + r;
-      int k = k0;
-      for (; k + 4 <= k1; k += 4, p += 4 * (size_t)Rp) {
-        const float a0 = p[0], a1 = p[(size_t)Rp], a2 = p[2 * (size_t)Rp], a3 = p[3 * (size_t)Rp];
-        g += a0;
-        g += a1;
-        g += a2;
-        g += a3;
-      }
-      for (; k < k1; ++k, p += Rp) g += p[0];
-    }
-    if (grad_out && act) grad_out[(size_t)v * R + r] = g;
-    if (do_step) {
-      float xv = 0.f;
-      if (act) {
-        xv = x[(size_t)v * R + r];
-        if (!(fixed && fixed[v])) {
-          xv = pgd_project(xv, g, lr);
-          x[(size_t)v * R + r] = xv;
-        }
-      }
-      const uint32_t b = __ballot_sync(kFull, act && xv < 0.0f);
-      if (bits && lane == 0) bits[(size_t)v * RW + blockIdx.x] = b;
-    }
-  }
+  for (int v = blockIdx.y * blockDim.y + threadIdx.y; v < n; v += gridDim.y * blockDim.y)
+    accum_one(v, blockIdx.x, threadIdx.x, R, Rp, RW, voff, P, x, lr, do_step, fixed, grad_out,
+              bits);
 }
 
 __global__ void __launch_bounds__(256) k_pgd(int n, int R, int RW, float* __restrict__ x,
@@ -560,6 +582,58 @@ __device__ __forceinline__ bool sat_of(const ScoreItem& s, int t,
   return ((satbits[(s.lo + t) >> 5] >> ((s.lo + t) & 31)) & 1u) != 0;
 }
 
+// one range of constraints for one tile of 32 restarts (whole warp); returns
+// the lane's satisfied count and satisfied weight
+template <bool CG = false>
+__device__ __forceinline__ void score_range(int rg, int tile, int lane, int RW,
+                                            const int32_t* __restrict__ ranges,
+                                            const ScoreItem* __restrict__ sc,
+                                            const LitRec* __restrict__ lit,
+                                            const uint32_t* __restrict__ satbits,
+                                            const uint32_t* __restrict__ bits, int* cnt_out,
+                                            double* ws_out) {
+  int cnt = 0;
+  double ws = 0.0;
+  int c = ranges[rg];
+  const int c_end = ranges[rg + 1];
+  ScoreItem s = sc[c];
+  int e = s.lit0;
+  const ScoreItem last = sc[c_end - 1];
+  const int e_end = last.lit0 + last.L;
+  int run = 0;
+  while (e < e_end) {
+    uint32_t word = 0;
+    if (e + lane < e_end) {
+      const LitRec rc = lit[e + lane];
+      word = ldx<CG>(&bits[(size_t)rc.var * RW + tile]);
+      if (rc.dst < 0) word = ~word;
+    }
+    const uint32_t col = transpose32(word, lane);
+    const int chunk_end = e + 32;
+    // constraints ending inside this chunk
+    while (c < c_end && s.lit0 + s.L <= chunk_end) {
+      const int lo = max(s.lit0, e) - e;
+      const int hi = s.lit0 + s.L - e;
+      const uint32_t mask = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & (kFull << lo);
+      const int t = run + __popc(col & mask);
+      run = 0;
+      const bool sat = sat_of(s, t, satbits);
+      cnt += sat ? 1 : 0;
+      ws += sat ? (double)s.w : 0.0;
+      ++c;
+      if (c < c_end) s = sc[c];
+    }
+    // a constraint straddling into the next chunk
+    if (c < c_end && s.lit0 < chunk_end) {
+      const int lo = max(s.lit0, e) - e;
+      run += __popc(col & (kFull << lo));
+    }
+    e = chunk_end;
+  }
+  *cnt_out = cnt;
+  *ws_out = ws;
+}
+
 __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
                                                const int32_t* __restrict__ ranges,
                                                const ScoreItem* __restrict__ sc,
@@ -575,44 +649,7 @@ __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
   const int rg = blockIdx.y * kScoreWarps + ty;
   int cnt = 0;
   double ws = 0.0;
-  if (rg < n_ranges) {
-    int c = ranges[rg];
-    const int c_end = ranges[rg + 1];
-    ScoreItem s = sc[c];
-    int e = s.lit0;
-    const ScoreItem last = sc[c_end - 1];
-    const int e_end = last.lit0 + last.L;
-    int run = 0;
-    while (e < e_end) {
-      uint32_t word = 0;
-      if (e + lane < e_end) {
-        const LitRec rc = lit[e + lane];
-        word = bits[(size_t)rc.var * RW + tile];
-        if (rc.dst < 0) word = ~word;
-      }
-      const uint32_t col = transpose32(word, lane);
-      const int chunk_end = e + 32;
-      // constraints ending inside this chunk
-      while (c < c_end && s.lit0 + s.L <= chunk_end) {
-        const int lo = max(s.lit0, e) - e;
-        const int hi = s.lit0 + s.L - e;
-        const uint32_t mask = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & (kFull << lo);
-        const int t = run + __popc(col & mask);
-        run = 0;
-        const bool sat = sat_of(s, t, satbits);
-        cnt += sat ? 1 : 0;
-        ws += sat ? (double)s.w : 0.0;
-        ++c;
-        if (c < c_end) s = sc[c];
-      }
-      // a constraint straddling into the next chunk
-      if (c < c_end && s.lit0 < chunk_end) {
-        const int lo = max(s.lit0, e) - e;
-        run += __popc(col & (kFull << lo));
-      }
-      e = chunk_end;
-    }
-  }
+  if (rg < n_ranges) score_range(rg, tile, lane, RW, ranges, sc, lit, satbits, bits, &cnt, &ws);
   cnt_s[ty][lane] = cnt;
   w_s[ty][lane] = ws;
   __syncthreads();
@@ -688,6 +725,151 @@ __global__ void __launch_bounds__(256) k_restart_scale(int64_t total, int R,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = sc[i % R] * g[i];
+}
+
+// ---------------------------------------------------------------------------
+// A10 as one persistent launch (problems whose FE work is all on the short
+// closed-form path, e.g. random k-SAT): a cooperative kernel runs the whole
+// step loop, its warps taking work items of each stage in turn, with a grid
+// barrier between stages.  The barrier spins at most ~2^22 polls; on time-out
+// it raises *err and every block returns (no hang).
+// ---------------------------------------------------------------------------
+struct PersistArgs {
+  int R, Rp, RT, n_steps;
+  float lr;
+  float* x;
+  float* P;
+  uint32_t* bits;
+  int32_t* rpart_n;     // [range][Rp]
+  double* rpart_w;
+  int32_t* nsat;
+  double* wsat;
+  unsigned* bar;        // [0] arrivals, [1] generation
+  int* err;
+  unsigned spin_limit;  // polls before a barrier gives up
+};
+
+constexpr unsigned kBarrierSpinLimit = 1u << 22;
+
+// Grid barrier for a cooperative launch: arrival counter + generation word.
+// Thread (0,0) of each block arrives and polls the generation with
+// __nanosleep between polls; after spin_limit polls (or when another block
+// already gave up) it raises *err and the call returns false; the caller then
+// returns from the kernel.  nblocks is the number of arrivals that releases
+// the barrier (gridDim.x in normal use).
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err, unsigned nblocks,
+                                          unsigned spin_limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*gen == g) {
+        if (++spins > spin_limit || *((volatile int*)err)) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*((volatile int*)err)) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256) k_persistent(DevPlan d, PersistArgs a) {
+  const int lane = threadIdx.x;
+  const int gw = blockIdx.x * blockDim.y + threadIdx.y;
+  const int nw = gridDim.x * blockDim.y;
+  const int tgroups = (a.RT + kThreadTiles - 1) / kThreadTiles;
+  const int n0 = d.thread_count[0], n1 = d.thread_count[1];
+  const bool i32 = (int64_t)d.n * a.R < (int64_t)1 << 31 && d.nnz_fe * a.Rp < (int64_t)1 << 31;
+  for (int step = 0; step < a.n_steps; ++step) {
+    // FE + literal partials (short closed forms): items (constraint, 4 tiles)
+    const int fe_items = (n0 + n1) * tgroups;
+    for (int item = gw; item < fe_items; item += nw) {
+      const int ci = item / tgroups, tg = item % tgroups;
+      if (ci < n0) {
+        const FeItem it = d.thread_items[0][ci];
+        if (i32)
+          thread_dispatch<1, 8, int, true>(it.L, it, d.root_tab, d.coef_tab, d.fe_lit, a.x, a.R, a.Rp,
+                                     a.RT, tg * kThreadTiles, lane, a.P, nullptr, 0);
+        else
+          thread_dispatch<1, 8, int64_t, true>(it.L, it, d.root_tab, d.coef_tab, d.fe_lit, a.x, a.R,
+                                         a.Rp, a.RT, tg * kThreadTiles, lane, a.P, nullptr, 0);
+      } else {
+        const FeItem it = d.thread_items[1][ci - n0];
+        if (i32)
+          thread_dispatch<9, 16, int, true>(it.L, it, d.root_tab, d.coef_tab, d.fe_lit, a.x, a.R,
+                                      a.Rp, a.RT, tg * kThreadTiles, lane, a.P, nullptr, 0);
+        else
+          thread_dispatch<9, 16, int64_t, true>(it.L, it, d.root_tab, d.coef_tab, d.fe_lit, a.x, a.R,
+                                          a.Rp, a.RT, tg * kThreadTiles, lane, a.P, nullptr, 0);
+      }
+    }
+    if (!grid_sync(a.bar, a.err, gridDim.x, a.spin_limit)) return;
+    // accumulate + projected step + rounding: items (variable, tile)
+    const int acc_items = d.n * a.RT;
+    for (int item = gw; item < acc_items; item += nw)
+      accum_one<true>(item / a.RT, item % a.RT, lane, a.R, a.Rp, a.RT, d.fe_voff, a.P, a.x, a.lr, 1,
+                d.fixed, nullptr, a.bits);
+    if (!grid_sync(a.bar, a.err, gridDim.x, a.spin_limit)) return;
+    // score: items (range, tile) -> per-range partials
+    const int sc_items = d.n_ranges * a.RT;
+    for (int item = gw; item < sc_items; item += nw) {
+      const int rg = item / a.RT, tile = item % a.RT;
+      int cnt;
+      double ws;
+      score_range<true>(rg, tile, lane, a.RT, d.score_ranges, d.score, d.lit, d.satbits, a.bits, &cnt,
+                  &ws);
+      a.rpart_n[(size_t)rg * a.Rp + tile * 32 + lane] = cnt;
+      a.rpart_w[(size_t)rg * a.Rp + tile * 32 + lane] = ws;
+    }
+    if (!grid_sync(a.bar, a.err, gridDim.x, a.spin_limit)) return;
+    // totals per restart, summed in the same order as k_score + k_score_final
+    // (groups of kScoreWarps ranges, then over groups), so both paths agree
+    // bit for bit
+    for (int r = blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + lane; r < a.R;
+         r += gridDim.x * blockDim.x * blockDim.y) {
+      int cnt = 0;
+      double ws = 0.0;
+      for (int rg0 = 0; rg0 < d.n_ranges; rg0 += kScoreWarps) {
+        int bc = 0;
+        double bw = 0.0;
+        for (int rg = rg0; rg < min(rg0 + kScoreWarps, d.n_ranges); ++rg) {
+          bc += __ldcg(&a.rpart_n[(size_t)rg * a.Rp + r]);
+          bw += __ldcg(&a.rpart_w[(size_t)rg * a.Rp + r]);
+        }
+        cnt += bc;
+        ws += bw;
+      }
+      if (a.nsat) a.nsat[r] = cnt;
+      if (a.wsat) a.wsat[r] = ws;
+    }
+  }
+}
+
+// Barrier check: `rounds` grid barriers that release after gridDim.x + extra
+// arrivals; with extra > 0 none can release, so every block must time out,
+// raise *err and return.  Block 0 records how many barriers it passed.
+__global__ void __launch_bounds__(32) k_barrier_check(unsigned* bar, int* err, int rounds,
+                                                      unsigned extra, unsigned spin_limit,
+                                                      int* passed) {
+  int k = 0;
+  for (; k < rounds; ++k)
+    if (!grid_sync(bar, err, gridDim.x + extra, spin_limit)) break;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *passed = k;
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -889,6 +1071,52 @@ cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
   HookScope hs(h, KC_REDUCE, s);
   k_score_final<<<ceil_div(R, 256), 256, 0, s>>>(R, Rp, nch, nsat_part, wsat_part, nsat, wsat);
   return cudaGetLastError();
+}
+
+bool persistent_eligible(const DevPlan& d) {
+  for (int b = 0; b < kNumBuckets; ++b)
+    if (d.bucket_count[b] > 0) return false;
+  return d.m > 0 && d.n > 0;
+}
+
+cudaError_t launch_persistent(const DevPlan& d, int R, int Rp, float* x, float lr, int n_steps,
+                              float* P, uint32_t* bits, int32_t* rpart_n, double* rpart_w,
+                              int32_t* nsat, double* wsat, unsigned* bar, int* err,
+                              cudaStream_t s) {
+  if (n_steps == 0 || R == 0) return cudaSuccess;
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (!coop || per_sm < 1) return cudaErrorNotSupported;
+  e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  PersistArgs a{R,       Rp,      ceil_div(R, 32), n_steps, lr,  x,   P,
+                bits,    rpart_n, rpart_w,         nsat,    wsat, bar, err, kBarrierSpinLimit};
+  DevPlan dd = d;
+  void* args[] = {&dd, &a};
+  return cudaLaunchCooperativeKernel((const void*)k_persistent, dim3(sms * per_sm),
+                                     dim3(32, 8), args, 0, s);
+}
+
+cudaError_t launch_barrier_check(int rounds, unsigned extra, unsigned spin_limit, unsigned* bar,
+                                 int* err, int* passed, cudaStream_t s) {
+  int dev = 0, sms = 0, coop = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e != cudaSuccess) return e;
+  if (!coop) return cudaErrorNotSupported;
+  e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&bar, &err, &rounds, &extra, &spin_limit, &passed};
+  return cudaLaunchCooperativeKernel((const void*)k_barrier_check, dim3(sms), dim3(32), args, 0,
+                                     s);
 }
 
 cudaError_t launch_fe_const(const DevPlan& d, int R, float* fe_con, int ldf, cudaStream_t s) {

@@ -75,6 +75,18 @@ bool fe_unit_active(const DevPlan& d, int unit);
 cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const float* x, float* P,
                            float* fe_con, int ldf, cudaStream_t s, LaunchHook* h);
 
+// The whole step loop as one cooperative persistent launch; only for
+// problems whose FE work is all on the short closed-form path.
+bool persistent_eligible(const DevPlan& d);
+cudaError_t launch_persistent(const DevPlan& d, int R, int Rp, float* x, float lr, int n_steps,
+                              float* P, uint32_t* bits, int32_t* rpart_n, double* rpart_w,
+                              int32_t* nsat, double* wsat, unsigned* bar, int* err,
+                              cudaStream_t s);
+
+// The grid barrier alone (see cls_grid_barrier_check).
+cudaError_t launch_barrier_check(int rounds, unsigned extra, unsigned spin_limit, unsigned* bar,
+                                 int* err, int* passed, cudaStream_t s);
+
 // fe_con[c * ldf + r] = b0 for constraints whose expansion is constant.
 cudaError_t launch_fe_const(const DevPlan& d, int R, float* fe_con, int ldf, cudaStream_t s);
 
