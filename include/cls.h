@@ -283,9 +283,12 @@ int cls_graph_destroy(cls_graph* g);
  * the tuning beyond FP32 rounding order of the DFT products.
  * cls_tuning_get/cls_tuning_set read or replace the bucket -> configuration
  * map (n must equal the number of buckets, 25); cls_config_info(id, out[4])
- * describes configuration id (G, Q, DFT?, shared-memory y?) and, for
- * id = 1000 + b, bucket b (DFT?, maximum length).  An invalid map is
- * rejected with CLS_ERR_INVALID. */
+ * describes configuration id (G, Q, kind, shared-memory y?) and, for
+ * id = 1000 + b, bucket b (DFT?, maximum length).  Configuration ids run
+ * 0..98 (kind 0 = real roots, 1 = DFT roots, 2 = DFT roots in packed pairs,
+ * 3 = DFT roots in factored form, cos(phi) - i y sin(phi) scaled per lane)
+ * plus 100, the checkpointed kernel for real-root buckets.  An invalid map
+ * is rejected with CLS_ERR_INVALID. */
 int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* ws,
                  size_t ws_bytes, void* stream);
 int cls_tuning_get(const cls_problem* p, int32_t* cfg, int32_t n);

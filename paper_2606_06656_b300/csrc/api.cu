@@ -329,6 +329,7 @@ int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const in
   D.n_ranges = H.score_ranges.empty() ? 0 : (int32_t)H.score_ranges.size() - 1;
   up(H.satbits, &D.satbits);
   up(H.root_tab, &D.root_tab);
+  up(H.froot_tab, &D.froot_tab);
   up(H.coef_tab, &D.coef_tab);
   up(H.fixed, &D.fixed);
   up(H.fixed_val, &D.fixed_val);

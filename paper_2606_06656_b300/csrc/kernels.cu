@@ -894,6 +894,7 @@ constexpr size_t group_smem() {
 }  // namespace
 
 size_t group_smem_bytes(int cfg) {
+  if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 3) return fr_smem_bytes(cfg);
   if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 2)
     return (size_t)kGroupCfg[cfg].G * kGroupCfg[cfg].Q * (32 + 32 / kGroupCfg[cfg].G) *
            sizeof(float);
@@ -916,6 +917,7 @@ cudaError_t set_kernel_attributes() {
   CLS_GROUP_CONFIGS(CLS_SET_ATTR)
 #undef CLS_SET_ATTR
   if (err == cudaSuccess) err = set_p2_attributes();
+  if (err == cudaSuccess) err = set_fr_attributes();
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_fe_thread_ckpt, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                8 * 2 * ((1024 + kCkptInterval - 1) / kCkptInterval) * 32 * 4);
@@ -948,6 +950,8 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
   }
   if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 2)
     return launch_group_p2(cfg, d, list, count, R, Rp, x, P, fe_con, ldf, s);
+  if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 3)
+    return launch_group_fr(cfg, d, list, count, R, Rp, x, P, fe_con, ldf, s);
   const dim3 grid(count, ceil_div(R, 32)), block(256);
   switch (cfg) {
 #define CLS_LAUNCH_CASE(id, G, Q, C, Y)                                                      \

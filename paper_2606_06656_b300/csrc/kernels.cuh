@@ -33,6 +33,7 @@ struct DevPlan {
   int32_t n_ranges = 0;
   uint32_t* satbits = nullptr;
   F4* root_tab = nullptr;
+  F4* froot_tab = nullptr;
   F4* coef_tab = nullptr;
   uint8_t* fixed = nullptr;
   float* fixed_val = nullptr;
@@ -55,6 +56,11 @@ struct LaunchHook {
 
 cudaError_t set_kernel_attributes();
 cudaError_t set_p2_attributes();   // kernels_p2.cu
+cudaError_t set_fr_attributes();   // kernels_fr.cu
+cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int count, int R,
+                            int Rp, const float* x, float* P, float* fe_con, int ldf,
+                            cudaStream_t s);
+size_t fr_smem_bytes(int cfg);
 cudaError_t launch_group_p2(int cfg, const DevPlan& d, const int32_t* list, int count, int R,
                             int Rp, const float* x, float* P, float* fe_con, int ldf,
                             cudaStream_t s);

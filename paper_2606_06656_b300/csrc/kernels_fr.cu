@@ -1,0 +1,278 @@
+// kernels_fr.cu -- the lane-group DFT FE+gradient kernel on factored roots.
+//
+// Same work split, staging and output as k_fe_group (kernels.cu): a block
+// takes one constraint and 32 restarts, G lanes share one (constraint,
+// restart), lane lam holds literal slots lam, lam+G, ... (Q of them; slots
+// beyond L are staged as y = 1).  What changes is the arithmetic per root.
+//
+// With phi = pi j/(L+1) (half the root's angle), the Poisson-binomial factor
+// of Sec. 2.3's characteristic function is
+//     alpha + beta w^j = e^{i phi} (cos phi - i y sin phi) = z_j u_j(y),
+//     phi <= pi/4:  z = cos phi e^{i phi},         u = 1 - i y tan phi,
+//     phi >  pi/4:  z = sin phi e^{i(phi - pi/2)}, u = y + i cot phi,
+// so |u| <= sqrt 2 and a padding slot (y = 1) has z u = 1 exactly.  A lane's
+// product of its Q factors is carried in u alone (3 FP32 operations per
+// complex product in the first form, 4 in the second, against 6 for the
+// factor alpha + beta w^j itself) and scaled once by z^Q; the products over
+// all lanes then equal G_j = prod_i (alpha_i + beta_i w^j) with no factor of
+// modulus above sqrt 2 ever accumulated, and the leave-one-out product for
+// literal i is O * z^(Q-1) * (the lane's u-products before and after i), O
+// the other lanes' scaled products.  z^Q and c'_j z^(Q-1) are formed per
+// block in a prologue by repeated squaring.  No division anywhere.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace cls {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float4 ldg4(const F4* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
+__device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// z^E for a compile-time E >= 0 (binary powering)
+template <int E>
+__device__ __forceinline__ float2 cpow(float2 z) {
+  float2 r = make_float2(1.f, 0.f), b = z;
+#pragma unroll
+  for (int e = E; e > 0; e >>= 1) {
+    if (e & 1) r = cmul(r, b);
+    if (e > 1) b = cmul(b, b);
+  }
+  return r;
+}
+
+template <int G>
+struct FrGeom {
+  static constexpr int LDR = 32 + 32 / G;
+  static constexpr int GPW = 32 / G;
+  static constexpr int GPB = 8 * GPW;
+  static constexpr int PASSES = 32 / GPB;
+};
+
+// One root for one lane: forward u-products, scale by z^Q, butterfly over
+// the G lanes, FE term, backward sweep of the leave-one-out products into
+// acc.  FA selects the first factored form.  rt = {tan or cot phi, z^Q},
+// cf = {b'_j, c'_j z^(Q-1)}.  Returns Re(b'_j G_j).
+template <int G, int Q, bool YS, bool FA>
+__device__ __forceinline__ float fr_root(const float4 rt, const float4 cf,
+                                         const float (&yreg)[YS ? 1 : Q], const float* ycol,
+                                         float (&acc)[Q]) {
+  constexpr int YST = G * FrGeom<G>::LDR;
+  auto Y = [&](int s) -> float {
+    if constexpr (YS) return ycol[s * YST];
+    else return yreg[s];
+  };
+  const float tk = rt.x;
+  float pr[Q], pim[Q];
+  float qr, qi;
+  if constexpr (FA) {
+    qr = 1.f;
+    qi = -Y(0) * tk;
+  } else {
+    qr = Y(0);
+    qi = tk;
+  }
+#pragma unroll
+  for (int s = 1; s < Q; ++s) {
+    pr[s] = qr;
+    pim[s] = qi;
+    const float y = Y(s);
+    if constexpr (FA) {
+      const float w = y * tk;                     // (qr + i qi)(1 - i w)
+      const float nr = fmaf(qi, w, qr), ni = fmaf(-qr, w, qi);
+      qr = nr;
+      qi = ni;
+    } else {                                      // (qr + i qi)(y + i k)
+      const float nr = fmaf(qr, y, -qi * tk), ni = fmaf(qi, y, qr * tk);
+      qr = nr;
+      qi = ni;
+    }
+  }
+  // the lane's chunk times z^Q, then total (Pt) and others' product (O)
+  float Ptr = qr * rt.y - qi * rt.z, Pti = qr * rt.z + qi * rt.y;
+  float Or = 1.f, Oi = 0.f;
+#pragma unroll
+  for (int d = 1; d < G; d <<= 1) {
+    const float tr = __shfl_xor_sync(kFull, Ptr, d);
+    const float ti = __shfl_xor_sync(kFull, Pti, d);
+    if (d == 1) {
+      Or = tr;
+      Oi = ti;
+    } else {
+      const float a = Or * tr - Oi * ti, b = Or * ti + Oi * tr;
+      Or = a;
+      Oi = b;
+    }
+    const float a = Ptr * tr - Pti * ti, b = Ptr * ti + Pti * tr;
+    Ptr = a;
+    Pti = b;
+  }
+  const float val = cf.x * Ptr - cf.y * Pti;
+  float hr = cf.z * Or - cf.w * Oi, hi = cf.z * Oi + cf.w * Or;
+#pragma unroll
+  for (int s = Q - 1; s >= 1; --s) {
+    acc[s] = fmaf(pr[s], hr, acc[s]);
+    acc[s] = fmaf(-pim[s], hi, acc[s]);
+    const float y = Y(s);
+    if constexpr (FA) {
+      const float w = y * tk;
+      const float a = fmaf(hi, w, hr), b = fmaf(-hr, w, hi);
+      hr = a;
+      hi = b;
+    } else {
+      const float a = fmaf(hr, y, -hi * tk), b = fmaf(hi, y, hr * tk);
+      hr = a;
+      hi = b;
+    }
+  }
+  acc[0] += hr;
+  return val;
+}
+
+template <int G, int Q>
+struct FrCap {
+  static constexpr int JC = (G * Q + 1) / 2;   // most roots of a constraint that fits
+};
+
+template <int G, int Q>
+constexpr size_t fr_smem() {
+  return (size_t)2 * FrCap<G, Q>::JC * sizeof(float4) +
+         (size_t)G * Q * FrGeom<G>::LDR * sizeof(float);
+}
+
+template <int G, int Q, bool YS>
+__global__ void __launch_bounds__(256) k_fe_group_fr(
+    const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
+    const F4* __restrict__ froot, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
+    const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
+    float* __restrict__ fe_con, int ldf) {
+  using Geo = FrGeom<G>;
+  constexpr int LS = G * Q;
+  constexpr int JC = FrCap<G, Q>::JC;
+  extern __shared__ float4 smem4[];
+  float4* rs = smem4;                                        // [JC]
+  float4* cs = smem4 + JC;                                   // [JC]
+  float* ys = reinterpret_cast<float*>(smem4 + 2 * JC);     // [LS][LDR]
+  __shared__ float fe_s[32];
+  const FeItem it = fe[list[blockIdx.x]];
+  const int L = it.L, J = it.J;
+  const int r0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  // per-root constants for this Q
+  for (int j = threadIdx.x; j < J; j += 256) {
+    const float4 fr = ldg4(&froot[it.root_off + j]);
+    const float4 cf = ldg4(&coef[it.coef_off + j]);
+    const float2 z = make_float2(fr.y, fr.z);
+    const float2 zq1 = cpow<Q - 1>(z);
+    const float2 zq = cmul(zq1, z);
+    const float2 cz = cmul(make_float2(cf.z, cf.w), zq1);
+    rs[j] = make_float4(fr.x, zq.x, zq.y, 0.f);
+    cs[j] = make_float4(cf.x, cf.y, cz.x, cz.y);
+  }
+  // stage literal values y = s * x (coalesced rows of 32 restarts)
+  for (int i = warp; i < LS; i += 8) {
+    float v = 1.0f;
+    if (i < L) {
+      const LitRec rc = lit[it.lit0 + i];
+      const int r = r0 + lane;
+      if (r < R) v = rec_sgn(rc.dst) * x[(size_t)rc.var * R + r];
+    }
+    ys[i * Geo::LDR + lane] = v;
+  }
+  __syncthreads();
+
+  const int lam = lane % G;
+  const int gi = lane / G;
+  const int nA = (L + 1) / 4;        // roots with phi <= pi/4 come first
+#pragma unroll 1
+  for (int pass = 0; pass < Geo::PASSES; ++pass) {
+    const int rr = pass * Geo::GPB + warp * Geo::GPW + gi;
+    const float* ycol = ys + lam * Geo::LDR + rr;
+    float yreg[YS ? 1 : Q], acc[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      if constexpr (!YS) yreg[s] = ycol[s * G * Geo::LDR];
+      acc[s] = 0.f;
+    }
+    float val = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < nA; ++j) val += fr_root<G, Q, YS, true>(rs[j], cs[j], yreg, ycol, acc);
+#pragma unroll 1
+    for (int j = nA; j < J; ++j) val += fr_root<G, Q, YS, false>(rs[j], cs[j], yreg, ycol, acc);
+    // partials back into the staging slots (each slot is owned by one lane)
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int i = lam + G * s;
+      if (i < L) ys[i * Geo::LDR + rr] = acc[s];
+    }
+    if (lam == 0) fe_s[rr] = it.b0 + val;
+  }
+  __syncthreads();
+  // write partials w * s_e * dFE/dy_e to their variable-major rows
+  for (int i = warp; i < L; i += 8) {
+    const LitRec rc = lit[it.lit0 + i];
+    const int r = r0 + lane;
+    if (r < R)
+      P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
+  }
+  if (fe_con && warp == 0 && r0 + lane < R) fe_con[(size_t)it.c * ldf + r0 + lane] = fe_s[lane];
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+size_t fr_smem_bytes(int cfg) {
+  switch (cfg) {
+#define CLS_FR_SMEM(id, G, Q, C, Y) \
+  case id: return fr_smem<G, Q>();
+    CLS_FR_CONFIGS(CLS_FR_SMEM)
+#undef CLS_FR_SMEM
+    default: return 0;
+  }
+}
+
+cudaError_t set_fr_attributes() {
+  cudaError_t err = cudaSuccess;
+#define CLS_FR_ATTR(id, G, Q, C, Y)                                                \
+  if (err == cudaSuccess)                                                          \
+    err = cudaFuncSetAttribute(k_fe_group_fr<G, Q, (Y != 0)>,                      \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                               (int)fr_smem<G, Q>());
+  CLS_FR_CONFIGS(CLS_FR_ATTR)
+#undef CLS_FR_ATTR
+  return err;
+}
+
+cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int count, int R,
+                            int Rp, const float* x, float* P, float* fe_con, int ldf,
+                            cudaStream_t s) {
+  if (count == 0 || R == 0) return cudaSuccess;
+  const dim3 grid(count, ceil_div(R, 32)), block(256);
+  switch (cfg) {
+#define CLS_FR_CASE(id, G, Q, C, Y)                                                       \
+  case id:                                                                                \
+    k_fe_group_fr<G, Q, (Y != 0)><<<grid, block, fr_smem<G, Q>(), s>>>(                   \
+        list, d.fe, d.froot_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf);         \
+    break;
+    CLS_FR_CONFIGS(CLS_FR_CASE)
+#undef CLS_FR_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cls

@@ -13,7 +13,7 @@ namespace cls {
 
 const GroupCfg kGroupCfg[kNumGroupCfg] = {
 #define CLS_CFG_ENTRY(id, G, Q, C, Y) {G, Q, C, Y},
-    CLS_GROUP_CONFIGS(CLS_CFG_ENTRY) CLS_P2_CONFIGS(CLS_CFG_ENTRY)
+    CLS_GROUP_CONFIGS(CLS_CFG_ENTRY) CLS_P2_CONFIGS(CLS_CFG_ENTRY) CLS_FR_CONFIGS(CLS_CFG_ENTRY)
 #undef CLS_CFG_ENTRY
 };
 
@@ -197,6 +197,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
 
   // fixed real roots and their coefficients
   P.root_tab = {{0.5f, 0.5f, 0.f, 0.f}, {0.5f, -0.5f, 0.f, 0.f}, {0.f, 1.f, 0.f, 0.f}};
+  P.froot_tab.assign(P.root_tab.size(), F4{0.f, 0.f, 0.f, 0.f});
   P.coef_tab = {{2.f, 0.f, 1.f, 0.f},  {1.f, 0.f, 1.f, 0.f},   {2.f, 0.f, 1.f, 0.f},
                 {2.f, 0.f, -1.f, 0.f}, {-1.f, 0.f, -1.f, 0.f}, {-2.f, 0.f, -1.f, 0.f},
                 {-2.f, 0.f, 1.f, 0.f}};
@@ -350,6 +351,17 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
         float A = 1.0f - B;
         float C = (float)(sn[j] * 0.5);
         P.root_tab.push_back({A, B, C, 0.f});
+        // factored form, phi = theta_j / 2: alpha + beta w = e^{i phi}
+        // (cos phi - i y sin phi) = z u(y) with
+        //   phi <= pi/4: z = cos phi e^{i phi},          u = 1 - i y tan phi
+        //   phi >  pi/4: z = sin phi e^{i(phi - pi/2)},  u = y + i cot phi
+        // (|u| <= sqrt 2 either way; y = 1 gives z u = 1 exactly)
+        const double ph = M_PI * (double)j / (double)N;
+        const double c = (2 * j == N) ? 0.0 : std::cos(ph), s = std::sin(ph);
+        if (4 * j <= N)
+          P.froot_tab.push_back({(float)(s / c), (float)(c * c), (float)(c * s), 0.f});
+        else
+          P.froot_tab.push_back({(float)(c / s), (float)(s * s), (float)(-s * c), 0.f});
       }
       rit = root_of_len.emplace(L, off).first;
     }

@@ -136,8 +136,42 @@ struct ScoreItem {
   X(66, 32, 16, 2, 1) \
   X(67, 32, 20, 2, 1) \
   X(68, 8, 2, 2, 0)   \
-  X(69, 8, 1, 2, 0)   
-constexpr int kNumGroupCfg = 70;
+  X(69, 8, 1, 2, 0)
+// DFT roots in factored form (CPLX = 3), instantiated in kernels_fr.cu: per
+// root the factor alpha + beta w^j is written z_j u_j(y) with a root constant
+// z_j and u = 1 - i y tan(phi) (phi = pi j/(L+1) <= pi/4) or u = y + i cot(phi)
+// (phi > pi/4): 3 or 4 FP32 operations per complex product instead of 6.
+#define CLS_FR_CONFIGS(X) \
+  X(70, 8, 1, 3, 0)   \
+  X(71, 8, 2, 3, 0)   \
+  X(72, 8, 4, 3, 0)   \
+  X(73, 8, 6, 3, 0)   \
+  X(74, 8, 8, 3, 0)   \
+  X(75, 8, 12, 3, 0)  \
+  X(76, 8, 16, 3, 0)  \
+  X(77, 16, 8, 3, 0)  \
+  X(78, 16, 10, 3, 0) \
+  X(79, 16, 12, 3, 0) \
+  X(80, 16, 14, 3, 0) \
+  X(81, 16, 16, 3, 0) \
+  X(82, 16, 18, 3, 0) \
+  X(83, 16, 20, 3, 0) \
+  X(84, 8, 20, 3, 0)  \
+  X(85, 8, 24, 3, 0)  \
+  X(86, 16, 24, 3, 1) \
+  X(87, 16, 16, 3, 1) \
+  X(88, 16, 20, 3, 1) \
+  X(89, 32, 12, 3, 0) \
+  X(90, 32, 14, 3, 1) \
+  X(91, 32, 16, 3, 1) \
+  X(92, 32, 20, 3, 1) \
+  X(93, 32, 24, 3, 1) \
+  X(94, 32, 32, 3, 1) \
+  X(95, 8, 32, 3, 1)  \
+  X(96, 16, 28, 3, 1) \
+  X(97, 32, 16, 3, 0) \
+  X(98, 16, 12, 3, 1)
+constexpr int kNumGroupCfg = 99;
 // Configuration id of the restart-parallel checkpointed kernel for real-root
 // (closed-form) constraints of any length; valid only for real buckets.
 constexpr int kCkptCfg = 100;
@@ -200,6 +234,7 @@ struct HostPlan {
   std::vector<int32_t> score_ranges;     // constraint boundaries of the ranges
   std::vector<uint32_t> satbits;  // truth tables of SPECTRUM constraints
   std::vector<F4> root_tab, coef_tab;
+  std::vector<F4> froot_tab;      // parallel to root_tab: {tan or cot phi, z.re, z.im, 0}
   std::vector<FeItem> thread_items[kNumThreadCls];   // items in launch order
   // lane-group buckets: [0, kNumDftBuckets) DFT, then real
   std::vector<int32_t> bucket_list[kNumDftBuckets + kNumRealBuckets];

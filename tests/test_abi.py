@@ -103,13 +103,13 @@ def test_null_arguments_do_not_crash():
 def test_config_table_describes_buckets_and_configs():
     from paper_2606_06656_b300 import binding as B
     seen_dft = seen_real = 0
-    for cid in range(70):
+    for cid in range(99):
         G, Q, cplx, ys = B.cls_config_info(cid)
-        assert G in (8, 16, 32) and Q >= 1 and cplx in (0, 1, 2) and ys in (0, 1)
+        assert G in (8, 16, 32) and Q >= 1 and cplx in (0, 1, 2, 3) and ys in (0, 1)
         seen_dft += cplx > 0
         seen_real += cplx == 0
     assert seen_dft > 0 and seen_real > 0
     maxes = [B.cls_config_info(1000 + b)[1] for b in range(B.N_BUCKETS)]
     assert maxes[-1] == 1024
     with pytest.raises(Exception):
-        B.cls_config_info(70)
+        B.cls_config_info(99)

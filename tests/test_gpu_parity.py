@@ -218,7 +218,7 @@ def test_autotune_and_tuning_roundtrip(P):
     # every admissible configuration of every bucket gives the same results
     for b in range(B.N_BUCKETS):
         kind, bmax, _, _ = B.cls_config_info(1000 + b)
-        for cid in range(80):
+        for cid in range(100):
             try:
                 G, Q, cplx, ys = B.cls_config_info(cid)
             except Exception:

@@ -57,7 +57,7 @@ def test_persistent_equals_step(P, name, make, R, steps):
 
 @pytest.mark.parametrize("simplify", [False, True])
 def test_persistent_partial_assignment(P, simplify):
-    inst = W.partial_assignment(W.random_ksat(n=2000, m=8520, seed=9), 0.5)
+    inst = W.partial_assignment(W.redundant_5sat(n=2000, m=9000, seed=9), 0.5)
     p = P(inst, simplify_fixed=simplify)
     X0 = ocls.init_uniform(inst.n, 160, 4)
     X0[inst.fixed != 0] = inst.fixed_val[inst.fixed != 0][:, None]
