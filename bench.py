@@ -35,7 +35,6 @@ SM_MAX_MHZ = 2032.0
 # algorithmic FP32 flops per (literal, root) of the DFT evaluation: factor
 # (2 FMA), prefix complex product (2 MUL + 2 FMA), suffix complex product
 # (2 MUL + 2 FMA), gradient accumulation (2 FMA); FMA = 2 flops.
-FLOPS_PER_LIT_ROOT = 20
 
 
 def workload(name):
@@ -276,7 +275,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kstats, key=lambda k: kstats[k]["ms_per_step"])
     pk = peaks()
     if dom == "fe_group_dft":
-        flops = FLOPS_PER_LIT_ROOT * info["dft_lroots"] * R
+        flops = B.cls_dft_work(p.handle)[0] * R
         t = kstats[dom]["ms_per_step"] / 1e3
         peak = 2 * SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": "k_fe_group<DFT>", "achieved": flops / t / 1e12,

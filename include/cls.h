@@ -295,6 +295,14 @@ int cls_tuning_get(const cls_problem* p, int32_t* cfg, int32_t n);
 int cls_tuning_set(cls_problem* p, const int32_t* cfg, int32_t n);
 int cls_config_info(int32_t id, int32_t* out);
 
+/* Algorithmic FP32 work of the DFT buckets under the current tuning (no
+ * counterpart in the paper; for roofline accounting): out[0] = flops per
+ * restart of one FE+gradient evaluation (a fused multiply-add counts 2):
+ * per (literal, root) 20 for the direct factor alpha + beta w^j (kinds 1
+ * and 2), 14 or 16 for the factored forms (kind 3); out[1] = the number of
+ * (literal, root) pairs per restart.  Host-only; CLS_ERR_INVALID on NULL. */
+int cls_dft_work(const cls_problem* p, int64_t* out);
+
 /* cls_step without any allocation, for callers that cannot allocate device
  * memory while they run (a real-time loop that must not touch the allocator
  * after start-up, a process confined to a fixed device-memory budget owned

@@ -295,3 +295,11 @@ def cls_grid_barrier_check(rounds, extra, spin_limit, scratch):
                                                   _ptr(scratch), scratch.numel(), C.byref(st),
                                                   C.byref(passed)), "cls_grid_barrier_check")
     return int(st.value), int(passed.value)
+
+
+def cls_dft_work(h):
+    """(flops per restart, (literal, root) pairs per restart) of the DFT
+    buckets under the current tuning."""
+    out = (C.c_int64 * 2)()
+    _lib.check(_lib.load().cls_dft_work(h, out), "cls_dft_work")
+    return int(out[0]), int(out[1])

@@ -329,7 +329,7 @@ int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const in
   D.n_ranges = H.score_ranges.empty() ? 0 : (int32_t)H.score_ranges.size() - 1;
   up(H.satbits, &D.satbits);
   up(H.root_tab, &D.root_tab);
-  up(H.froot_tab, &D.froot_tab);
+  up(H.zpow_tab, &D.zpow_tab);
   up(H.coef_tab, &D.coef_tab);
   up(H.fixed, &D.fixed);
   up(H.fixed_val, &D.fixed_val);
@@ -364,6 +364,27 @@ int cls_problem_info(const cls_problem* p, int64_t* info) {
   info[7] = H.dft_lroots;
   info[8] = H.nnz_fe;
   info[9] = (int64_t)H.const_list.size();
+  return CLS_OK;
+}
+
+int cls_dft_work(const cls_problem* p, int64_t* out) {
+  if (!p || !out) return set_err(CLS_ERR_INVALID, "NULL argument");
+  const cls::HostPlan& H = p->host;
+  int64_t flops = 0, lroots = 0;
+  for (int b = 0; b < cls::kNumDftBuckets; ++b) {
+    const int cfg = H.bucket_cfg[b];
+    const bool fr = cfg >= 0 && cfg < cls::kNumGroupCfg && cls::kGroupCfg[cfg].cplx == 3;
+    for (int32_t c : H.bucket_list[b]) {
+      const cls::FeItem& it = H.fe[c];
+      const int64_t L = it.L, J = it.J, nA = (it.L + 1) / 4;
+      lroots += L * J;
+      // factored roots: 14 flops per (literal, root) with phi <= pi/4 and 16
+      // beyond; the direct factor alpha + beta w^j: 20
+      flops += fr ? L * (14 * nA + 16 * (J - nA)) : 20 * L * J;
+    }
+  }
+  out[0] = flops;
+  out[1] = lroots;
   return CLS_OK;
 }
 

@@ -33,7 +33,7 @@ struct DevPlan {
   int32_t n_ranges = 0;
   uint32_t* satbits = nullptr;
   F4* root_tab = nullptr;
-  F4* froot_tab = nullptr;
+  F4* zpow_tab = nullptr;
   F4* coef_tab = nullptr;
   uint8_t* fixed = nullptr;
   float* fixed_val = nullptr;

@@ -17,8 +17,10 @@
 // all lanes then equal G_j = prod_i (alpha_i + beta_i w^j) with no factor of
 // modulus above sqrt 2 ever accumulated, and the leave-one-out product for
 // literal i is O * z^(Q-1) * (the lane's u-products before and after i), O
-// the other lanes' scaled products.  z^Q and c'_j z^(Q-1) are formed per
-// block in a prologue by repeated squaring.  No division anywhere.
+// the other lanes' scaled products.  z is defined from the FP32-rounded
+// t itself (z = 1/u(1)), so padding is neutral up to one rounding of z^Q;
+// z^Q and z^(Q-1) come from an FP64 host table, c'_j z^(Q-1) is formed per
+// block in a prologue.  No division in the kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,17 +43,26 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// z^E for a compile-time E >= 0 (binary powering)
-template <int E>
-__device__ __forceinline__ float2 cpow(float2 z) {
-  float2 r = make_float2(1.f, 0.f), b = z;
-#pragma unroll
-  for (int e = E; e > 0; e >>= 1) {
-    if (e & 1) r = cmul(r, b);
-    if (e > 1) b = cmul(b, b);
-  }
-  return r;
-}
+// index of Q in kFrQ (compile time)
+template <int Q>
+struct FrQIndex {
+  static constexpr int value = Q == 1    ? 0
+                               : Q == 2  ? 1
+                               : Q == 4  ? 2
+                               : Q == 6  ? 3
+                               : Q == 8  ? 4
+                               : Q == 10 ? 5
+                               : Q == 12 ? 6
+                               : Q == 14 ? 7
+                               : Q == 16 ? 8
+                               : Q == 18 ? 9
+                               : Q == 20 ? 10
+                               : Q == 24 ? 11
+                               : Q == 28 ? 12
+                               : Q == 32 ? 13
+                                         : -1;
+  static_assert(value >= 0, "slot count without a root-power table");
+};
 
 template <int G>
 struct FrGeom {
@@ -155,7 +166,8 @@ constexpr size_t fr_smem() {
 template <int G, int Q, bool YS>
 __global__ void __launch_bounds__(256) k_fe_group_fr(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
-    const F4* __restrict__ froot, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
+    const F4* __restrict__ root, const F4* __restrict__ zpow, const F4* __restrict__ coef,
+    const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
     float* __restrict__ fe_con, int ldf) {
   using Geo = FrGeom<G>;
@@ -173,13 +185,11 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
 
   // per-root constants for this Q
   for (int j = threadIdx.x; j < J; j += 256) {
-    const float4 fr = ldg4(&froot[it.root_off + j]);
+    const float4 rt = ldg4(&root[it.root_off + j]);
+    const float4 zp = ldg4(&zpow[(size_t)(it.root_off + j) * kNumFrQ + FrQIndex<Q>::value]);
     const float4 cf = ldg4(&coef[it.coef_off + j]);
-    const float2 z = make_float2(fr.y, fr.z);
-    const float2 zq1 = cpow<Q - 1>(z);
-    const float2 zq = cmul(zq1, z);
-    const float2 cz = cmul(make_float2(cf.z, cf.w), zq1);
-    rs[j] = make_float4(fr.x, zq.x, zq.y, 0.f);
+    const float2 cz = cmul(make_float2(cf.z, cf.w), make_float2(zp.z, zp.w));
+    rs[j] = make_float4(rt.w, zp.x, zp.y, 0.f);
     cs[j] = make_float4(cf.x, cf.y, cz.x, cz.y);
   }
   // stage literal values y = s * x (coalesced rows of 32 restarts)
@@ -266,7 +276,7 @@ cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int 
 #define CLS_FR_CASE(id, G, Q, C, Y)                                                       \
   case id:                                                                                \
     k_fe_group_fr<G, Q, (Y != 0)><<<grid, block, fr_smem<G, Q>(), s>>>(                   \
-        list, d.fe, d.froot_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf);         \
+        list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf);\
     break;
     CLS_FR_CONFIGS(CLS_FR_CASE)
 #undef CLS_FR_CASE

@@ -197,7 +197,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
 
   // fixed real roots and their coefficients
   P.root_tab = {{0.5f, 0.5f, 0.f, 0.f}, {0.5f, -0.5f, 0.f, 0.f}, {0.f, 1.f, 0.f, 0.f}};
-  P.froot_tab.assign(P.root_tab.size(), F4{0.f, 0.f, 0.f, 0.f});
+  P.zpow_tab.assign(P.root_tab.size() * kNumFrQ, F4{0.f, 0.f, 0.f, 0.f});
   P.coef_tab = {{2.f, 0.f, 1.f, 0.f},  {1.f, 0.f, 1.f, 0.f},   {2.f, 0.f, 1.f, 0.f},
                 {2.f, 0.f, -1.f, 0.f}, {-1.f, 0.f, -1.f, 0.f}, {-2.f, 0.f, -1.f, 0.f},
                 {-2.f, 0.f, 1.f, 0.f}};
@@ -350,18 +350,35 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
         float B = (float)((1.0 - cs[j]) * 0.5);
         float A = 1.0f - B;
         float C = (float)(sn[j] * 0.5);
-        P.root_tab.push_back({A, B, C, 0.f});
         // factored form, phi = theta_j / 2: alpha + beta w = e^{i phi}
         // (cos phi - i y sin phi) = z u(y) with
-        //   phi <= pi/4: z = cos phi e^{i phi},          u = 1 - i y tan phi
-        //   phi >  pi/4: z = sin phi e^{i(phi - pi/2)},  u = y + i cot phi
-        // (|u| <= sqrt 2 either way; y = 1 gives z u = 1 exactly)
+        //   phi <= pi/4: z = cos phi e^{i phi} = 1/(1 - i t),  u = 1 - i y t,
+        //                t = tan phi
+        //   phi >  pi/4: z = sin phi e^{i(phi - pi/2)} = 1/(1 + i t),
+        //                u = y + i t,  t = cot phi
+        // (|u| <= sqrt 2 either way).  z is taken from the FP32-rounded t,
+        // so that z u(1) = 1 for the value the kernel multiplies by.
         const double ph = M_PI * (double)j / (double)N;
         const double c = (2 * j == N) ? 0.0 : std::cos(ph), s = std::sin(ph);
-        if (4 * j <= N)
-          P.froot_tab.push_back({(float)(s / c), (float)(c * c), (float)(c * s), 0.f});
-        else
-          P.froot_tab.push_back({(float)(c / s), (float)(s * s), (float)(-s * c), 0.f});
+        const bool formA = 4 * j <= N;
+        const float t32 = (float)(formA ? s / c : c / s);
+        const double t = t32, den = 1.0 + t * t;
+        const double zr = 1.0 / den, zi = formA ? t / den : -t / den;
+        P.root_tab.push_back({A, B, C, t32});
+        double pr = 1.0, pi = 0.0;   // z^k, k = 0, 1, ...
+        double prev_r = 1.0, prev_i = 0.0;
+        int k = 0;
+        for (int q = 0; q < kNumFrQ; ++q) {
+          while (k < kFrQ[q]) {
+            prev_r = pr;
+            prev_i = pi;
+            const double nr = pr * zr - pi * zi, ni = pr * zi + pi * zr;
+            pr = nr;
+            pi = ni;
+            ++k;
+          }
+          P.zpow_tab.push_back({(float)pr, (float)pi, (float)prev_r, (float)prev_i});
+        }
       }
       rit = root_of_len.emplace(L, off).first;
     }

@@ -172,6 +172,13 @@ struct ScoreItem {
   X(97, 32, 16, 3, 0) \
   X(98, 16, 12, 3, 1)
 constexpr int kNumGroupCfg = 99;
+// Slot counts Q used by the factored configurations.  For a DFT root the
+// root table's 4th entry holds t = tan(phi) (phi <= pi/4) or t = cot(phi),
+// rounded to FP32, and z' = 1/(1 - i t) or 1/(1 + i t) is the root constant
+// that makes a padding slot (y = 1) exactly neutral for that rounded t; its
+// powers are formed in FP64 and rounded once.
+constexpr int kNumFrQ = 14;
+constexpr int kFrQ[kNumFrQ] = {1, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32};
 // Configuration id of the restart-parallel checkpointed kernel for real-root
 // (closed-form) constraints of any length; valid only for real buckets.
 constexpr int kCkptCfg = 100;
@@ -234,7 +241,10 @@ struct HostPlan {
   std::vector<int32_t> score_ranges;     // constraint boundaries of the ranges
   std::vector<uint32_t> satbits;  // truth tables of SPECTRUM constraints
   std::vector<F4> root_tab, coef_tab;
-  std::vector<F4> froot_tab;      // parallel to root_tab: {tan or cot phi, z.re, z.im, 0}
+  // factored DFT roots: per root-table entry r and per slot count Q of the
+  // factored configurations (kFrQ[q]), zpow_tab[r * kNumFrQ + q] =
+  // {z'^Q, z'^(Q-1)} (see kFrQ)
+  std::vector<F4> zpow_tab;
   std::vector<FeItem> thread_items[kNumThreadCls];   // items in launch order
   // lane-group buckets: [0, kNumDftBuckets) DFT, then real
   std::vector<int32_t> bucket_list[kNumDftBuckets + kNumRealBuckets];

@@ -57,8 +57,34 @@ def P():
     return Problem
 
 
-def gpu_eval(Problem, inst, X):
+def factored_tuning(cfg):
+    """The bucket map with every DFT bucket on its smallest factored-root
+    configuration (kind 3) that holds the bucket's longest constraint."""
+    from paper_2606_06656_b300 import binding as B
+    out = list(cfg)
+    cands = []
+    for cid in range(1000):
+        try:
+            G, Q, kind, ys = B.cls_config_info(cid)
+        except Exception:
+            break
+        if kind == 3:
+            cands.append((G * Q, cid))
+    for b in range(B.N_BUCKETS):
+        dft, bmax, _, _ = B.cls_config_info(1000 + b)
+        if dft:
+            out[b] = min(c for c in cands if c[0] >= bmax)[1]
+    return out
+
+
+KERNELS = ["default", "factored"]
+
+
+def gpu_eval(Problem, inst, X, kernel="default"):
     p = Problem(inst)
+    if kernel == "factored":
+        from paper_2606_06656_b300 import binding as B
+        B.cls_tuning_set(p.handle, factored_tuning(B.cls_tuning_get(p.handle)))
     x = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     obj, grad, fe = p.eval(x, obj=True, grad=True, fe_con=True)
     torch.cuda.synchronize()
@@ -113,20 +139,22 @@ def points(kind, n, R, seed):
     return np.zeros((n, R), np.float32)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("ctype", ALL_TYPES)
 @pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 9, 16, 31, 32, 33, 64, 65, 129, 300])
-def test_fe_grad_by_type_and_length(P, ctype, L):
+def test_fe_grad_by_type_and_length(P, ctype, L, kernel):
     rng = np.random.default_rng(1000 * ctype + L)
     count = max(2, min(12, 600 // L))
     inst = disjoint_instance(rng, ctype, L, count)
     for kind in POINTS:
         R = 50 if kind != "zero" else 33      # ragged restart tails
         X = points(kind, inst.n, R, seed=L + 7 * ctype)
-        check_against_oracle(inst, X, *gpu_eval(P, inst, X), floored=True)
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("L,k", [(1024, 512), (1024, 3), (700, 350), (513, 100)])
-def test_max_length_cardinality(P, L, k):
+def test_max_length_cardinality(P, L, k, kernel):
     rng = np.random.default_rng(L)
     v = rng.permutation(L).astype(np.int32)
     s = np.where(rng.random(L) < 0.5, -1, 1).astype(np.int8)
@@ -134,24 +162,26 @@ def test_max_length_cardinality(P, L, k):
                        (W.TYPE_OR, 0, v.copy(), s)])
     for kind in ["uniform", "near", "corner"]:
         X = points(kind, L, 40, seed=3)
-        check_against_oracle(inst, X, *gpu_eval(P, inst, X), floored=True)
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
 
 
-def test_overlapping_mixed_instance(P):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_overlapping_mixed_instance(P, kernel):
     rng = np.random.default_rng(5)
     inst = W.random_constraint_set(rng, 120, 300, ALL_TYPES, (1, 70), weights="random")
     for kind in POINTS:
         X = points(kind, inst.n, 70, seed=11)
         # realistic overlapping instance: strict relative criterion at
         # interior points, FP32 floor only where the gradient is tiny
-        check_against_oracle(inst, X, *gpu_eval(P, inst, X),
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel),
                              floored=kind in ("corner", "near", "mixed"))
 
 
-def test_planted_mixed_pb_small(P):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_planted_mixed_pb_small(P, kernel):
     inst = W.mixed_pb(n=800, n_or=2000, n_xor=200, n_card=40, card_len=(10, 300), seed=9)
     X = W.uniform_points(inst.n, 64, seed=1)
-    check_against_oracle(inst, X, *gpu_eval(P, inst, X))
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel))
 
 
 def test_init_uniform_bit_exact(P):
@@ -510,3 +540,30 @@ def test_batch_graph_equals_separate_steps(P):
     for a, b, u, v in zip(xa, xb, na, nb):
         assert torch.equal(a, b) and torch.equal(u, v)
     B.cls_graph_destroy(g)
+
+
+def test_dft_work_accounting(P):
+    """cls_dft_work counts 20 flops per (literal, root) for the direct factor
+    and 14 / 16 for the two factored forms, over the DFT buckets."""
+    from paper_2606_06656_b300 import binding as B
+    rng = np.random.default_rng(3)
+    rows = []
+    for L in (10, 37, 100, 301):
+        v = rng.choice(400, L, replace=False).astype(np.int32)
+        rows.append((W.TYPE_CARD_GE, L // 3, v, np.ones(L, np.int8)))
+    inst = W.build(400, rows)
+    p = P(inst)
+    lr = sum(L * ((L + 1) // 2) for L in (10, 37, 100, 301))
+    fr = sum(L * (14 * ((L + 1) // 4) + 16 * ((L + 1) // 2 - (L + 1) // 4))
+             for L in (10, 37, 100, 301))
+    B.cls_tuning_set(p.handle, factored_tuning(B.cls_tuning_get(p.handle)))
+    assert B.cls_dft_work(p.handle) == (fr, lr)
+    cfg = B.cls_tuning_get(p.handle)
+    for b in range(19):
+        G, Q, kind, ys = B.cls_config_info(cfg[b])
+        cands = [c for c in range(99) if B.cls_config_info(c)[2] == 1
+                 and B.cls_config_info(c)[0] * B.cls_config_info(c)[1]
+                 >= B.cls_config_info(1000 + b)[1]]
+        cfg[b] = min(cands, key=lambda c: B.cls_config_info(c)[0] * B.cls_config_info(c)[1])
+    B.cls_tuning_set(p.handle, cfg)
+    assert B.cls_dft_work(p.handle) == (20 * lr, lr)
