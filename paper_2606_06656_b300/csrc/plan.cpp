@@ -19,8 +19,10 @@ const GroupCfg kGroupCfg[kNumGroupCfg] = {
 
 Tuning default_tuning() {
   Tuning t;
-  const int dft[kNumDftBuckets] = {0,  1,  2,  3,  4,  8,  9,  24, 25, 26,
-                                   27, 28, 29, 30, 33, 34, 35, 36, 37};
+  // measured on a B300 (autotuner, mixed and long cardinality workloads):
+  // the factored-root kernel from 17 literals up
+  const int dft[kNumDftBuckets] = {0,  1,  72, 73, 74, 75, 76, 84, 85, 80,
+                                   87, 82, 83, 86, 96, 91, 92, 93, 94};
   const int real[kNumRealBuckets] = {41, kCkptCfg, 48, 43, kCkptCfg, kCkptCfg};
   for (int b = 0; b < kNumDftBuckets; ++b) t.dft[b] = dft[b];
   for (int b = 0; b < kNumRealBuckets; ++b) t.real[b] = real[b];

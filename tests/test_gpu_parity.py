@@ -57,9 +57,10 @@ def P():
     return Problem
 
 
-def factored_tuning(cfg):
-    """The bucket map with every DFT bucket on its smallest factored-root
-    configuration (kind 3) that holds the bucket's longest constraint."""
+def kind_tuning(cfg, want):
+    """The bucket map with every DFT bucket on its smallest configuration of
+    kind `want` (1 = direct factor alpha + beta w^j, 3 = factored roots)
+    that holds the bucket's longest constraint."""
     from paper_2606_06656_b300 import binding as B
     out = list(cfg)
     cands = []
@@ -68,7 +69,7 @@ def factored_tuning(cfg):
             G, Q, kind, ys = B.cls_config_info(cid)
         except Exception:
             break
-        if kind == 3:
+        if kind == want:
             cands.append((G * Q, cid))
     for b in range(B.N_BUCKETS):
         dft, bmax, _, _ = B.cls_config_info(1000 + b)
@@ -77,14 +78,15 @@ def factored_tuning(cfg):
     return out
 
 
-KERNELS = ["default", "factored"]
+KERNELS = ["direct", "factored"]
 
 
-def gpu_eval(Problem, inst, X, kernel="default"):
+def gpu_eval(Problem, inst, X, kernel=None):
     p = Problem(inst)
-    if kernel == "factored":
+    if kernel is not None:
         from paper_2606_06656_b300 import binding as B
-        B.cls_tuning_set(p.handle, factored_tuning(B.cls_tuning_get(p.handle)))
+        B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle),
+                                               1 if kernel == "direct" else 3))
     x = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     obj, grad, fe = p.eval(x, obj=True, grad=True, fe_con=True)
     torch.cuda.synchronize()
@@ -556,14 +558,7 @@ def test_dft_work_accounting(P):
     lr = sum(L * ((L + 1) // 2) for L in (10, 37, 100, 301))
     fr = sum(L * (14 * ((L + 1) // 4) + 16 * ((L + 1) // 2 - (L + 1) // 4))
              for L in (10, 37, 100, 301))
-    B.cls_tuning_set(p.handle, factored_tuning(B.cls_tuning_get(p.handle)))
+    B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle), 3))
     assert B.cls_dft_work(p.handle) == (fr, lr)
-    cfg = B.cls_tuning_get(p.handle)
-    for b in range(19):
-        G, Q, kind, ys = B.cls_config_info(cfg[b])
-        cands = [c for c in range(99) if B.cls_config_info(c)[2] == 1
-                 and B.cls_config_info(c)[0] * B.cls_config_info(c)[1]
-                 >= B.cls_config_info(1000 + b)[1]]
-        cfg[b] = min(cands, key=lambda c: B.cls_config_info(c)[0] * B.cls_config_info(c)[1])
-    B.cls_tuning_set(p.handle, cfg)
+    B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle), 1))
     assert B.cls_dft_work(p.handle) == (20 * lr, lr)
