@@ -333,11 +333,17 @@ __global__ void __launch_bounds__(256) k_fe_group(
   const int r0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-  // stage literal values y = s * x (coalesced rows of 32 restarts)
+  // the constraint's literal records once per block (one coalesced read),
+  // then the literal values y = s * x (coalesced rows of 32 restarts), four
+  // rows in flight per warp
+  __shared__ LitRec lrec_s[LS];
+  for (int i = threadIdx.x; i < L; i += 256) lrec_s[i] = lit[it.lit0 + i];
+  __syncthreads();
+#pragma unroll 4
   for (int i = warp; i < LS; i += 8) {
     float v = 1.0f;
     if (i < L) {
-      const LitRec rc = lit[it.lit0 + i];
+      const LitRec rc = lrec_s[i];
       const int r = r0 + lane;
       if (r < R) v = rec_sgn(rc.dst) * x[(size_t)rc.var * R + r];
     }
@@ -457,8 +463,9 @@ __global__ void __launch_bounds__(256) k_fe_group(
   }
   __syncthreads();
   // write partials w * s_e * dFE/dy_e to their variable-major rows
+#pragma unroll 4
   for (int i = warp; i < L; i += 8) {
-    const LitRec rc = lit[it.lit0 + i];
+    const LitRec rc = lrec_s[i];
     const int r = r0 + lane;
     if (r < R)
       P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
