@@ -224,6 +224,8 @@ int upload_lists(cls_problem* p) {
     D.bucket_count[b] = (int32_t)H.bucket_list[b].size();
     D.bucket_cfg[b] = H.bucket_cfg[b];
     D.bucket_maxL[b] = H.bucket_list[b].empty() ? 0 : H.fe[H.bucket_list[b][0]].L;
+    D.bucket_maxJ[b] = 0;
+    for (int32_t c : H.bucket_list[b]) D.bucket_maxJ[b] = std::max(D.bucket_maxJ[b], H.fe[c].J);
   }
   return CLS_OK;
 }
@@ -697,10 +699,11 @@ int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* 
           continue;
       }
       cudaError_t e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b],
-                                        D.bucket_maxL[b], R, L.Rp, x, P, nullptr, 0, s);
+                                        D.bucket_maxL[b], D.bucket_maxJ[b], R, L.Rp, x, P, nullptr, 0, s);
       if (e == cudaSuccess) e = cudaEventRecord(e0, s);
       for (int k = 0; k < reps && e == cudaSuccess; ++k)
-        e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b], D.bucket_maxL[b], R,
+        e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b], D.bucket_maxL[b],
+                              D.bucket_maxJ[b], R,
                               L.Rp, x, P, nullptr, 0, s);
       if (e == cudaSuccess) e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);

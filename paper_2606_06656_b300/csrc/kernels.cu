@@ -181,32 +181,77 @@ __global__ void __launch_bounds__(256) k_fe_thread(
 }
 
 // ---------------------------------------------------------------------------
-// A2-A5, closed-form products (OR, XOR, NAE) of any length: one thread per
-// (constraint, restart), a warp = one constraint x 32 restarts (kThreadTiles
-// tiles).  The forward pass keeps only every kCkptInterval-th prefix product
-// (in shared memory, lane-minor); the backward pass walks the literal blocks
-// from the end, recomputes a block's prefixes from its checkpoint in
-// registers and combines them with the running suffix product.  Literal
-// values are gathered twice (coalesced rows, L1/L2 hits the second time).
-// Dynamic shared memory: 8 warps x NJ x ceil(maxL / kCkptInterval) x 32.
+// A2-A5, closed-form products (OR, XOR, NAE, ...) of any length: one thread
+// per (constraint, restart).  A block takes one constraint and 8 tiles of 32
+// restarts (a warp per tile).  The block first writes one record per literal
+// to shared memory -- variable, partial row, s*B_j and A_j of the (at most
+// two) real roots, w*s -- so that the inner loops do one broadcast shared
+// load, one 32-bit multiply-add for the address and one coalesced load per
+// literal; padding records (past L, up to a multiple of kCkptInterval) have
+// s*B = 0 and A = 1 and their loaded value is replaced by 0: the factor 1.  The forward pass keeps every
+// kCkptInterval-th prefix product in shared memory; the backward pass walks
+// the literal blocks from the end, recomputes a block's prefix products from
+// its checkpoint in registers (the block's literal values are loaded again,
+// L2 hits) and combines them with the running suffix product.
+// Dynamic shared memory: 32 B x LCAP records + 8 warps x NJ x nck x 32 floats.
 // ---------------------------------------------------------------------------
+struct CkRec {
+  float4 a;   // var (bits), row (bits), s*B_0, A_0
+  float4 b;   // s*B_1, A_1, w*s, -
+};
+
 template <int NJ>
-__device__ __forceinline__ void ckpt_tile(const FeItem& it, const F4* __restrict__ root,
-                                          const F4* __restrict__ coef,
-                                          const LitRec* __restrict__ lit,
-                                          const float* __restrict__ x, int R, int Rp, int r,
-                                          int lane, int nck, float* ck, float* __restrict__ P,
-                                          float* __restrict__ fe_con, int ldf) {
+__global__ void __launch_bounds__(256) k_fe_thread_ckpt(
+    const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
+    const F4* __restrict__ root, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
+    const float* __restrict__ x, int R, int Rp, int RT, int nck, float* __restrict__ P,
+    float* __restrict__ fe_con, int ldf) {
   constexpr int CI = kCkptInterval;
+  extern __shared__ float4 ck_smem[];
+  const int LCAP = nck * CI;
+  CkRec* rec = reinterpret_cast<CkRec*>(ck_smem);
+  const int lane = threadIdx.x, w = threadIdx.y;
+  float* ck = reinterpret_cast<float*>(ck_smem + 2 * LCAP) + (size_t)w * NJ * nck * 32;
+  const FeItem it = fe[list[blockIdx.x]];
   const int L = it.L;
-  const int nb = (L + CI - 1) / CI;
-  const bool act = r < R;
   float4 rt[NJ], cf[NJ];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
-    rt[j] = ldg4(&root[it.root_off + j]);
-    cf[j] = ldg4(&coef[it.coef_off + j]);
+    rt[j] = ldg4(&root[it.root_off + min(j, it.J - 1)]);
+    cf[j] = ldg4(&coef[it.coef_off + min(j, it.J - 1)]);
+    if (j >= it.J) {                 // a one-root constraint in a two-root launch
+      rt[j] = make_float4(1.f, 0.f, 0.f, 0.f);
+      cf[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
+  for (int i = w * 32 + lane; i < LCAP; i += 256) {
+    CkRec q;
+    if (i < L) {
+      const LitRec rc = lit[it.lit0 + i];
+      const float sg = rec_sgn(rc.dst);
+      q.a = make_float4(__int_as_float(rc.var), __int_as_float(rec_row(rc.dst)), sg * rt[0].y,
+                        rt[0].x);
+      q.b = make_float4(NJ > 1 ? sg * rt[NJ - 1].y : 0.f, NJ > 1 ? rt[NJ - 1].x : 1.f,
+                        it.w * sg, 0.f);
+    } else {
+      q.a = make_float4(__int_as_float(0), __int_as_float(0), 0.f, 1.f);
+      q.b = make_float4(0.f, 1.f, 0.f, 0.f);
+    }
+    rec[i] = q;
+  }
+  __syncthreads();
+  const int tile = blockIdx.y * 8 + w;
+  if (tile >= RT) return;
+  const int r = tile * 32 + lane;
+  const bool act = r < R;
+  const int rl = act ? r : R - 1;
+  const float* xr = x + rl;
+  const unsigned xstride = (unsigned)R * 4u, pstride = (unsigned)Rp * 4u;
+  auto xval = [&](const CkRec& q) -> float {
+    return *reinterpret_cast<const float*>(reinterpret_cast<const char*>(xr) +
+                                           (size_t)(unsigned)__float_as_int(q.a.x) * xstride);
+  };
+  const int nb = (L + CI - 1) / CI;
   // forward: running products, checkpoint at each block start
   float run[NJ];
 #pragma unroll
@@ -214,15 +259,18 @@ __device__ __forceinline__ void ckpt_tile(const FeItem& it, const F4* __restrict
   for (int b = 0; b < nb; ++b) {
 #pragma unroll
     for (int j = 0; j < NJ; ++j) ck[(j * nck + b) * 32 + lane] = run[j];
+    const int lim = L - b * CI;      // padding records past it read x[0] but use 0
+    float xv[CI];
 #pragma unroll
     for (int t = 0; t < CI; ++t) {
-      const int i = b * CI + t;
-      if (i < L) {
-        const LitRec rc = lit[it.lit0 + i];
-        const float y = act ? rec_sgn(rc.dst) * x[(size_t)rc.var * R + r] : 1.f;
+      const float v = xval(rec[b * CI + t]);
+      xv[t] = t < lim ? v : 0.f;
+    }
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) run[j] *= fmaf(y, rt[j].y, rt[j].x);
-      }
+    for (int t = 0; t < CI; ++t) {
+      const CkRec& q = rec[b * CI + t];
+      run[0] *= fmaf(xv[t], q.a.z, q.a.w);
+      if constexpr (NJ > 1) run[1] *= fmaf(xv[t], q.b.x, q.b.y);
     }
   }
   float val = it.b0;
@@ -233,62 +281,41 @@ __device__ __forceinline__ void ckpt_tile(const FeItem& it, const F4* __restrict
 #pragma unroll
   for (int j = 0; j < NJ; ++j) suf[j] = cf[j].z;
   for (int b = nb - 1; b >= 0; --b) {
-    float yb[CI], pre[NJ][CI];
-    float p[NJ];
+    float xv[CI], pre[NJ][CI], p[NJ];
 #pragma unroll
     for (int j = 0; j < NJ; ++j) p[j] = ck[(j * nck + b) * 32 + lane];
+    const int lim = L - b * CI;
 #pragma unroll
     for (int t = 0; t < CI; ++t) {
-      const int i = b * CI + t;
-      yb[t] = 1.f;
-      if (i < L) {
-        const LitRec rc = lit[it.lit0 + i];
-        yb[t] = act ? rec_sgn(rc.dst) * x[(size_t)rc.var * R + r] : 1.f;
-      }
+      const float v = xval(rec[b * CI + t]);
+      xv[t] = t < lim ? v : 0.f;
+    }
 #pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        pre[j][t] = p[j];
-        p[j] *= fmaf(yb[t], rt[j].y, rt[j].x);
+    for (int t = 0; t < CI; ++t) {
+      const CkRec& q = rec[b * CI + t];
+      pre[0][t] = p[0];
+      p[0] *= fmaf(xv[t], q.a.z, q.a.w);
+      if constexpr (NJ > 1) {
+        pre[1][t] = p[1];
+        p[1] *= fmaf(xv[t], q.b.x, q.b.y);
       }
     }
 #pragma unroll
     for (int t = CI - 1; t >= 0; --t) {
-      const int i = b * CI + t;
-      if (i < L) {
-        float g = 0.f;
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-          g = fmaf(pre[j][t], suf[j], g);
-          suf[j] *= fmaf(yb[t], rt[j].y, rt[j].x);
-        }
-        const LitRec rc = lit[it.lit0 + i];
-        if (act) P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * g;
+      const CkRec& q = rec[b * CI + t];
+      float g = pre[0][t] * suf[0];
+      suf[0] *= fmaf(xv[t], q.a.z, q.a.w);
+      if constexpr (NJ > 1) {
+        g = fmaf(pre[1][t], suf[1], g);
+        suf[1] *= fmaf(xv[t], q.b.x, q.b.y);
       }
+      if (act && t < lim)
+        *reinterpret_cast<float*>(reinterpret_cast<char*>(P + r) +
+                                  (size_t)(unsigned)__float_as_int(q.a.y) * pstride) =
+            q.b.z * g;
     }
   }
   if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = val;
-}
-
-__global__ void __launch_bounds__(256) k_fe_thread_ckpt(
-    const int32_t* __restrict__ list, int count, const FeItem* __restrict__ fe,
-    const F4* __restrict__ root, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
-    const float* __restrict__ x, int R, int Rp, int RT, int nck, float* __restrict__ P,
-    float* __restrict__ fe_con, int ldf) {
-  extern __shared__ float ck_s[];                  // [warp][root][block][lane]
-  const int lane = threadIdx.x, w = threadIdx.y;
-  float* ck = ck_s + (size_t)w * 2 * nck * 32;
-  for (int ci = blockIdx.y * blockDim.y + w; ci < count; ci += gridDim.y * blockDim.y) {
-    const FeItem it = fe[list[ci]];
-    for (int tt = 0; tt < kThreadTiles; ++tt) {
-      const int tile = blockIdx.x * kThreadTiles + tt;
-      if (tile >= RT) break;
-      const int r = tile * 32 + lane;
-      if (it.J == 1)
-        ckpt_tile<1>(it, root, coef, lit, x, R, Rp, r, lane, nck, ck, P, fe_con, ldf);
-      else
-        ckpt_tile<2>(it, root, coef, lit, x, R, Rp, r, lane, nck, ck, P, fe_con, ldf);
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -893,6 +920,12 @@ struct HookScope {
   }
 };
 
+// records (32 B per literal slot) + checkpoints (8 warps x NJ x nck x 32 floats)
+inline size_t ckpt_smem(int maxL, int nj) {
+  const int nck = std::max(1, (maxL + kCkptInterval - 1) / kCkptInterval);
+  return (size_t)nck * kCkptInterval * 32 + (size_t)8 * nj * nck * 32 * sizeof(float);
+}
+
 template <int G, int Q>
 constexpr size_t group_smem() {
   return (size_t)G * Q * GroupGeom<G>::LDR * sizeof(float);
@@ -926,8 +959,11 @@ cudaError_t set_kernel_attributes() {
   if (err == cudaSuccess) err = set_p2_attributes();
   if (err == cudaSuccess) err = set_fr_attributes();
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_fe_thread_ckpt, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               8 * 2 * ((1024 + kCkptInterval - 1) / kCkptInterval) * 32 * 4);
+    err = cudaFuncSetAttribute(k_fe_thread_ckpt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ckpt_smem(1024, 1));
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_fe_thread_ckpt<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ckpt_smem(1024, 2));
   return err;
 }
 
@@ -941,18 +977,20 @@ cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, f
   return cudaGetLastError();
 }
 
-cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL,
+cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL, int maxJ,
                          int R, int Rp, const float* x, float* P, float* fe_con, int ldf,
                          cudaStream_t s) {
   if (count == 0 || R == 0) return cudaSuccess;
   if (cfg == kCkptCfg) {
     const int RT = ceil_div(R, 32);
     const int nck = std::max(1, ceil_div(maxL, kCkptInterval));
-    const dim3 g2(ceil_div(RT, kThreadTiles), std::min(ceil_div(count, 8), 65535)), b2(32, 8);
-    // NJ = 2 covers NAE; OR and XOR use one root (the second is never read)
-    const size_t smem = (size_t)8 * 2 * nck * 32 * sizeof(float);
-    k_fe_thread_ckpt<<<g2, b2, smem, s>>>(list, count, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R,
-                                          Rp, RT, nck, P, fe_con, ldf);
+    const dim3 g2(count, ceil_div(RT, 8)), b2(32, 8);
+    if (maxJ <= 1)
+      k_fe_thread_ckpt<1><<<g2, b2, ckpt_smem(maxL, 1), s>>>(
+          list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, nck, P, fe_con, ldf);
+    else
+      k_fe_thread_ckpt<2><<<g2, b2, ckpt_smem(maxL, 2), s>>>(
+          list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, nck, P, fe_con, ldf);
     return cudaGetLastError();
   }
   if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 2)
@@ -1006,6 +1044,7 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
   if (b >= kNumBuckets || d.bucket_count[b] == 0) return cudaSuccess;
   HookScope hs(h, b < kNumDftBuckets ? KC_GROUP_DFT : KC_GROUP_REAL, s);
   return launch_group(d.bucket_cfg[b], d, d.bucket_list[b], d.bucket_count[b], d.bucket_maxL[b],
+                      d.bucket_maxJ[b],
                       R, Rp, x, P, fe_con, ldf, s);
 }
 

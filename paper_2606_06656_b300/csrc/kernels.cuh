@@ -28,6 +28,7 @@ struct DevPlan {
   int32_t bucket_count[kNumBuckets] = {};
   int32_t bucket_cfg[kNumBuckets] = {};
   int32_t bucket_maxL[kNumBuckets] = {};
+  int32_t bucket_maxJ[kNumBuckets] = {};
   ScoreItem* score = nullptr;        // constraint order
   int32_t* score_ranges = nullptr;   // n_ranges+1 constraint boundaries
   int32_t n_ranges = 0;
@@ -97,7 +98,7 @@ cudaError_t launch_barrier_check(int rounds, unsigned extra, unsigned spin_limit
 cudaError_t launch_fe_const(const DevPlan& d, int R, float* fe_con, int ldf, cudaStream_t s);
 
 // One lane-group launch over an explicit constraint list (the autotuner).
-cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL,
+cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL, int maxJ,
                          int R, int Rp, const float* x, float* P, float* fe_con, int ldf,
                          cudaStream_t s);
 

@@ -23,7 +23,7 @@ Tuning default_tuning() {
   // the factored-root kernel from 17 literals up
   const int dft[kNumDftBuckets] = {0,  1,  72, 73, 74, 75, 76, 84, 85, 80,
                                    87, 82, 83, 86, 96, 91, 92, 93, 94};
-  const int real[kNumRealBuckets] = {46, 46, 42, 43, 45, 45};
+  const int real[kNumRealBuckets] = {46, kCkptCfg, kCkptCfg, kCkptCfg, kCkptCfg, kCkptCfg};
   for (int b = 0; b < kNumDftBuckets; ++b) t.dft[b] = dft[b];
   for (int b = 0; b < kNumRealBuckets; ++b) t.real[b] = real[b];
   return t;
