@@ -200,13 +200,12 @@ struct CkRec {
   float4 b;   // s*B_1, A_1, w*s, -
 };
 
-template <int NJ>
+template <int NJ, int CI>
 __global__ void __launch_bounds__(256) k_fe_thread_ckpt(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ root, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, int RT, int nck, float* __restrict__ P,
     float* __restrict__ fe_con, int ldf) {
-  constexpr int CI = kCkptInterval;
   extern __shared__ float4 ck_smem[];
   const int LCAP = nck * CI;
   CkRec* rec = reinterpret_cast<CkRec*>(ck_smem);
@@ -921,10 +920,13 @@ struct HookScope {
 };
 
 // records (32 B per literal slot) + checkpoints (8 warps x NJ x nck x 32 floats)
-inline size_t ckpt_smem(int maxL, int nj) {
-  const int nck = std::max(1, (maxL + kCkptInterval - 1) / kCkptInterval);
-  return (size_t)nck * kCkptInterval * 32 + (size_t)8 * nj * nck * 32 * sizeof(float);
+inline size_t ckpt_smem(int maxL, int nj, int ci) {
+  const int nck = std::max(1, (maxL + ci - 1) / ci);
+  return (size_t)nck * ci * 32 + (size_t)8 * nj * nck * 32 * sizeof(float);
 }
+// constraints up to this length use checkpoints every 8 literals (fewer
+// registers); longer ones every kCkptInterval (less shared memory)
+constexpr int kCkptShortMax = 512;
 
 template <int G, int Q>
 constexpr size_t group_smem() {
@@ -959,11 +961,19 @@ cudaError_t set_kernel_attributes() {
   if (err == cudaSuccess) err = set_p2_attributes();
   if (err == cudaSuccess) err = set_fr_attributes();
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_fe_thread_ckpt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)ckpt_smem(1024, 1));
+    err = cudaFuncSetAttribute(k_fe_thread_ckpt<1, 16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ckpt_smem(1024, 1, 16));
   if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_fe_thread_ckpt<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)ckpt_smem(1024, 2));
+    err = cudaFuncSetAttribute(k_fe_thread_ckpt<2, 16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ckpt_smem(1024, 2, 16));
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_fe_thread_ckpt<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ckpt_smem(kCkptShortMax, 1, 8));
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_fe_thread_ckpt<2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)ckpt_smem(kCkptShortMax, 2, 8));
   return err;
 }
 
@@ -983,14 +993,21 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
   if (count == 0 || R == 0) return cudaSuccess;
   if (cfg == kCkptCfg) {
     const int RT = ceil_div(R, 32);
-    const int nck = std::max(1, ceil_div(maxL, kCkptInterval));
+    const int ci = maxL <= kCkptShortMax ? 8 : kCkptInterval;
+    const int nck = std::max(1, ceil_div(maxL, ci));
     const dim3 g2(count, ceil_div(RT, 8)), b2(32, 8);
-    if (maxJ <= 1)
-      k_fe_thread_ckpt<1><<<g2, b2, ckpt_smem(maxL, 1), s>>>(
-          list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, nck, P, fe_con, ldf);
-    else
-      k_fe_thread_ckpt<2><<<g2, b2, ckpt_smem(maxL, 2), s>>>(
-          list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, nck, P, fe_con, ldf);
+    const size_t sm = ckpt_smem(maxL, maxJ <= 1 ? 1 : 2, ci);
+#define CLS_CKPT_LAUNCH(NJ, CI)                                                                 \
+  k_fe_thread_ckpt<NJ, CI><<<g2, b2, sm, s>>>(list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, \
+                                              R, Rp, RT, nck, P, fe_con, ldf)
+    if (maxJ <= 1) {
+      if (ci == 8) CLS_CKPT_LAUNCH(1, 8);
+      else CLS_CKPT_LAUNCH(1, kCkptInterval);
+    } else {
+      if (ci == 8) CLS_CKPT_LAUNCH(2, 8);
+      else CLS_CKPT_LAUNCH(2, kCkptInterval);
+    }
+#undef CLS_CKPT_LAUNCH
     return cudaGetLastError();
   }
   if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 2)
