@@ -125,7 +125,7 @@ struct Layout {
   int R = 0, Rp = 0, RT = 0;
   int nch = 1, chunk = 1;
   size_t P = 0, fe = 0, bits = 0, nsat_part = 0, wsat_part = 0, obj_part = 0, nsat = 0,
-         rpart_n = 0, rpart_w = 0, bar = 0, total = 0;
+         rpart_n = 0, rpart_w = 0, bar = 0, done = 0, total = 0;
 };
 
 Layout layout_for(const cls_problem* p, int R) {
@@ -153,6 +153,8 @@ Layout layout_for(const cls_problem* p, int R) {
   L.wsat_part = take((size_t)nsc * L.Rp * sizeof(double));
   L.obj_part = take((size_t)L.nch * L.Rp * sizeof(double));
   L.nsat = take((size_t)L.Rp * sizeof(int32_t));
+  // corner-pass flags of the factored DFT kernels, one per (constraint, tile)
+  L.done = take((size_t)std::max(1, m) * L.RT);
   // persistent loop: per-range score partials and the grid barrier words
   const size_t nr = (size_t)std::max(1, p->dev.n_ranges);
   L.rpart_n = take(nr * L.Rp * sizeof(int32_t));
@@ -234,7 +236,9 @@ int upload_lists(cls_problem* p) {
 int run_step(const cls_problem* p, const Layout& L, float* x, float lr, uint32_t* bits,
              int32_t* nsat, double* wsat, void* ws, cudaStream_t s, bool score) {
   float* P = at<float>(ws, L.P);
-  CLS_CUDA_TRY(cls::launch_fe(p->dev, L.R, L.Rp, x, P, nullptr, 0, s, hook_of(p)), "fe kernels");
+  CLS_CUDA_TRY(cls::launch_fe(p->dev, L.R, L.Rp, x, P, nullptr, 0, at<uint8_t>(ws, L.done), s,
+                              hook_of(p)),
+               "fe kernels");
   CLS_CUDA_TRY(cls::launch_accum_step(p->dev, L.R, L.Rp, P, x, lr, true, nullptr, bits, s,
                                       hook_of(p)),
                "accumulate/step kernel");
@@ -426,7 +430,9 @@ int cls_eval(const cls_problem* p, int32_t R, const float* x, float* obj, float*
     fe = at<float>(ws, L.fe);
     ldf = L.Rp;
   }
-  CLS_CUDA_TRY(cls::launch_fe(p->dev, R, L.Rp, x, P, fe, ldf, s, hook_of(p)), "fe kernels");
+  CLS_CUDA_TRY(cls::launch_fe(p->dev, R, L.Rp, x, P, fe, ldf, at<uint8_t>(ws, L.done), s,
+                              hook_of(p)),
+               "fe kernels");
   CLS_CUDA_TRY(cls::launch_fe_const(p->dev, R, fe, ldf, s), "constant expansions");
   if (grad)
     CLS_CUDA_TRY(cls::launch_accum_step(p->dev, R, L.Rp, P, nullptr, 0.f, false, grad, nullptr,
@@ -699,12 +705,13 @@ int cls_autotune(cls_problem* p, int32_t R, const float* x, int32_t reps, void* 
           continue;
       }
       cudaError_t e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b],
-                                        D.bucket_maxL[b], D.bucket_maxJ[b], R, L.Rp, x, P, nullptr, 0, s);
+                                        D.bucket_maxL[b], D.bucket_maxJ[b], R, L.Rp, x, P, nullptr, 0,
+                                        at<uint8_t>(ws, L.done), s);
       if (e == cudaSuccess) e = cudaEventRecord(e0, s);
       for (int k = 0; k < reps && e == cudaSuccess; ++k)
         e = cls::launch_group(id, D, D.bucket_list[b], D.bucket_count[b], D.bucket_maxL[b],
-                              D.bucket_maxJ[b], R,
-                              L.Rp, x, P, nullptr, 0, s);
+                              D.bucket_maxJ[b], R, L.Rp, x, P, nullptr, 0,
+                              at<uint8_t>(ws, L.done), s);
       if (e == cudaSuccess) e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -780,7 +787,8 @@ int record_steps(const cls_problem* p, const Layout& L, const Branch& br, int64_
     for (size_t i = 0; i < units.size(); ++i) {
       cudaStream_t s = (i == 0) ? br.main : br.side[(i - 1) % (nside - 1)];
       if (s != br.main) CLS_CUDA_TRY(cudaStreamWaitEvent(s, ev_fork, 0), "fork wait");
-      CLS_CUDA_TRY(cls::launch_fe_unit(D, units[i], L.R, L.Rp, x, P, nullptr, 0, s, nullptr),
+      CLS_CUDA_TRY(cls::launch_fe_unit(D, units[i], L.R, L.Rp, x, P, nullptr, 0,
+                                       at<uint8_t>(ws, L.done), s, nullptr),
                    "fe unit");
       (*launches)++;
     }

@@ -960,6 +960,7 @@ cudaError_t set_kernel_attributes() {
 #undef CLS_SET_ATTR
   if (err == cudaSuccess) err = set_p2_attributes();
   if (err == cudaSuccess) err = set_fr_attributes();
+  if (err == cudaSuccess) err = set_corner_attributes();
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_fe_thread_ckpt<1, 16>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -989,7 +990,7 @@ cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, f
 
 cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL, int maxJ,
                          int R, int Rp, const float* x, float* P, float* fe_con, int ldf,
-                         cudaStream_t s) {
+                         uint8_t* done, cudaStream_t s) {
   if (count == 0 || R == 0) return cudaSuccess;
   if (cfg == kCkptCfg) {
     const int RT = ceil_div(R, 32);
@@ -1013,7 +1014,17 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
   if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 2)
     return launch_group_p2(cfg, d, list, count, R, Rp, x, P, fe_con, ldf, s);
   if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 3)
-    return launch_group_fr(cfg, d, list, count, R, Rp, x, P, fe_con, ldf, s);
+  {
+    // factored configurations of kCornerMinSlots slots or more: the corner
+    // pass first (it flags the tiles it finished), then the dense kernel
+    const bool corner = done && kGroupCfg[cfg].G * kGroupCfg[cfg].Q >= kCornerMinSlots;
+    if (corner) {
+      cudaError_t e = launch_dft_corner(d, list, count, maxL, R, Rp, x, P, fe_con, ldf, done, s);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_group_fr(cfg, d, list, count, R, Rp, x, P, fe_con, ldf, corner ? done : nullptr,
+                           s);
+  }
   const dim3 grid(count, ceil_div(R, 32)), block(256);
   switch (cfg) {
 #define CLS_LAUNCH_CASE(id, G, Q, C, Y)                                                      \
@@ -1029,7 +1040,7 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
 }
 
 cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const float* x, float* P,
-                           float* fe_con, int ldf, cudaStream_t s, LaunchHook* h) {
+                           float* fe_con, int ldf, uint8_t* done, cudaStream_t s, LaunchHook* h) {
   if (R == 0) return cudaSuccess;
   const int RT = ceil_div(R, 32);
   if (unit < kNumThreadCls) {
@@ -1061,8 +1072,7 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
   if (b >= kNumBuckets || d.bucket_count[b] == 0) return cudaSuccess;
   HookScope hs(h, b < kNumDftBuckets ? KC_GROUP_DFT : KC_GROUP_REAL, s);
   return launch_group(d.bucket_cfg[b], d, d.bucket_list[b], d.bucket_count[b], d.bucket_maxL[b],
-                      d.bucket_maxJ[b],
-                      R, Rp, x, P, fe_con, ldf, s);
+                      d.bucket_maxJ[b], R, Rp, x, P, fe_con, ldf, done, s);
 }
 
 bool fe_unit_active(const DevPlan& d, int unit) {
@@ -1072,9 +1082,9 @@ bool fe_unit_active(const DevPlan& d, int unit) {
 }
 
 cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P, float* fe_con,
-                      int ldf, cudaStream_t s, LaunchHook* h) {
+                      int ldf, uint8_t* done, cudaStream_t s, LaunchHook* h) {
   for (int u = 0; u < kNumFeUnits; ++u) {
-    cudaError_t e = launch_fe_unit(d, u, R, Rp, x, P, fe_con, ldf, s, h);
+    cudaError_t e = launch_fe_unit(d, u, R, Rp, x, P, fe_con, ldf, done, s, h);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

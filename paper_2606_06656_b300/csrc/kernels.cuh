@@ -60,8 +60,16 @@ cudaError_t set_p2_attributes();   // kernels_p2.cu
 cudaError_t set_fr_attributes();   // kernels_fr.cu
 cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int count, int R,
                             int Rp, const float* x, float* P, float* fe_con, int ldf,
-                            cudaStream_t s);
+                            uint8_t* done, cudaStream_t s);
 size_t fr_smem_bytes(int cfg);
+// The corner pass (kernels_corner.cu): runs before the dense factored kernel
+// of buckets whose configuration has >= kCornerMinSlots slots.
+constexpr int kCornerMinSlots = 128;
+cudaError_t set_corner_attributes();
+size_t corner_smem_bytes(int maxL);
+cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
+                              int Rp, const float* x, float* P, float* fe_con, int ldf,
+                              uint8_t* done, cudaStream_t s);
 cudaError_t launch_group_p2(int cfg, const DevPlan& d, const int32_t* list, int count, int R,
                             int Rp, const float* x, float* P, float* fe_con, int ldf,
                             cudaStream_t s);
@@ -72,15 +80,17 @@ cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, f
 
 // FE + literal partials: P[row * Rp + r] = w_c s_e dFE_c/dy_e (row = the
 // literal's variable-major row), and (if fe_con) fe_con[c * ldf + r] = FE_c.
+// done: workspace flags [m][ceil(R/32)], one per (constraint, restart tile),
+// set by the corner pass of the factored DFT kernels (see launch_group).
 cudaError_t launch_fe(const DevPlan& d, int R, int Rp, const float* x, float* P, float* fe_con,
-                      int ldf, cudaStream_t s, LaunchHook* h);
+                      int ldf, uint8_t* done, cudaStream_t s, LaunchHook* h);
 
 // The FE stage as independent units (thread-path classes, then lane-group
 // buckets); units write disjoint partial rows and may run concurrently.
 constexpr int kNumFeUnits = kNumThreadCls + kNumBuckets;
 bool fe_unit_active(const DevPlan& d, int unit);
 cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const float* x, float* P,
-                           float* fe_con, int ldf, cudaStream_t s, LaunchHook* h);
+                           float* fe_con, int ldf, uint8_t* done, cudaStream_t s, LaunchHook* h);
 
 // The whole step loop as one cooperative persistent launch; only for
 // problems whose FE work is all on the short closed-form path.
@@ -100,7 +110,7 @@ cudaError_t launch_fe_const(const DevPlan& d, int R, float* fe_con, int ldf, cud
 // One lane-group launch over an explicit constraint list (the autotuner).
 cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL, int maxJ,
                          int R, int Rp, const float* x, float* P, float* fe_con, int ldf,
-                         cudaStream_t s);
+                         uint8_t* done, cudaStream_t s);
 
 // g[v,r] = sum of rows voff[v]..voff[v+1]-1 of P; optional grad output;
 // optional projected step of x in place and bitset of the new x.

@@ -1,0 +1,282 @@
+// kernels_corner.cu -- the corner pass of the factored DFT path.
+//
+// Projected gradient steps pin coordinates to the faces of the cube: after a
+// few dozen steps almost every x_v is exactly +-1.  A literal at a corner has
+// alpha, beta in {0, 1}, so its Poisson-binomial factor is 1 (false literal,
+// y = 1) or w^j (true literal, y = -1), and for a restart with t true-corner
+// literals
+//     G_j = w^(j t) * prod_{non-corner i} F_ij,
+//     prod_{l != i} F_lj = G_j            (i a false corner)
+//                        = w^(-j) G_j     (i a true corner)
+//                        = w^(j t) prod_{non-corner l != i} F_lj  (otherwise).
+// Every corner literal of a restart therefore shares one of two partials,
+// and the products run over the few non-corner literals only.
+//
+// One thread per (constraint, restart), a warp per tile of 32 restarts, a
+// block per constraint and 8 tiles.  Pass 1 reads the restart's literal
+// values (eight loads in flight), counts the true corners, collects the
+// non-corner values (at most kCornerQS; a warp that finds more in any lane
+// gives the tile to the dense kernel by clearing its flag) and keeps the
+// tile's classification of every literal as two ballots in shared memory.
+// Pass 2 runs every root over QS in {4, 8, 16} slots (padding y = 1, exactly
+// neutral in the factored form, as in kernels_fr.cu), with w^(j t) read from
+// the root table.  Pass 3 writes the partials of all literals and sets the
+// tile's flag, which tells the dense factored kernel launched next on the
+// stream to skip the tile.  Exact up to FP32 rounding; no division.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace cls {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCornerQS = 16;   // most non-corner literals per restart
+
+__device__ __forceinline__ float4 ldg4(const F4* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
+__device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// index of QS in kFrQ: 4 -> 2, 8 -> 4, 16 -> 8
+template <int QS>
+struct CornerQ {
+  static constexpr int zq = QS == 4 ? 2 : QS == 8 ? 4 : 8;
+  static constexpr int slot = QS == 4 ? 0 : QS == 8 ? 1 : 2;
+};
+
+// One root for one restart: u-products over the QS non-corner slots (FA:
+// u = 1 - i y t, else u = y + i t), scaled by z^QS; G_j = W times that.
+// Adds Re(b' G_j) to fe, Re(c' G_j) to gF, Re(c' w^-j G_j) to gT and the
+// non-corner partials Re(c' W z^(QS-1) prod_{s' != s} u_s') to acc.
+// rt = {A, B, C, t} (w^j = (1 - 2B) + i 2C), zp = {z^QS, z^(QS-1)},
+// cf = {b', c'}.
+template <int QS, bool FA>
+__device__ __forceinline__ void corner_root(const float4 rt, const float4 zp, const float4 cf,
+                                            const float2 W, const float (&y)[QS],
+                                            float (&acc)[QS], float& fe, float& gF, float& gT) {
+  const float tk = rt.w;
+  float pr[QS], pim[QS];
+  float qr, qi;
+  if constexpr (FA) {
+    qr = 1.f;
+    qi = -y[0] * tk;
+  } else {
+    qr = y[0];
+    qi = tk;
+  }
+#pragma unroll
+  for (int s = 1; s < QS; ++s) {
+    pr[s] = qr;
+    pim[s] = qi;
+    if constexpr (FA) {
+      const float w = y[s] * tk;
+      const float nr = fmaf(qi, w, qr), ni = fmaf(-qr, w, qi);
+      qr = nr;
+      qi = ni;
+    } else {
+      const float nr = fmaf(qr, y[s], -qi * tk), ni = fmaf(qi, y[s], qr * tk);
+      qr = nr;
+      qi = ni;
+    }
+  }
+  const float2 Gj = cmul(W, cmul(make_float2(qr, qi), make_float2(zp.x, zp.y)));
+  fe = fmaf(cf.x, Gj.x, fmaf(-cf.y, Gj.y, fe));
+  gF = fmaf(cf.z, Gj.x, fmaf(-cf.w, Gj.y, gF));
+  const float2 cw = cmul(make_float2(cf.z, cf.w), make_float2(1.f - 2.f * rt.y, -2.f * rt.z));
+  gT = fmaf(cw.x, Gj.x, fmaf(-cw.y, Gj.y, gT));
+  const float2 h0 = cmul(cmul(make_float2(cf.z, cf.w), make_float2(zp.z, zp.w)), W);
+  float hr = h0.x, hi = h0.y;
+#pragma unroll
+  for (int s = QS - 1; s >= 1; --s) {
+    acc[s] = fmaf(pr[s], hr, acc[s]);
+    acc[s] = fmaf(-pim[s], hi, acc[s]);
+    if constexpr (FA) {
+      const float w = y[s] * tk;
+      const float a = fmaf(hi, w, hr), b = fmaf(-hr, w, hi);
+      hr = a;
+      hi = b;
+    } else {
+      const float a = fmaf(hr, y[s], -hi * tk), b = fmaf(hi, y[s], hr * tk);
+      hr = a;
+      hi = b;
+    }
+  }
+  acc[0] += hr;
+}
+
+// Pass 2 for one restart: all roots; the non-corner partials go back into the
+// restart's slots of ncy (slot s at my[s * 32]).
+template <int QS>
+__device__ __forceinline__ void corner_roots(int L, int J, int nnc, int t, const float4* rtab,
+                                             const float4* ctab, const float4* ztab, float* my,
+                                             float& fe, float& gF, float& gT) {
+  const int N = L + 1, nA = (L + 1) / 4;
+  float y[QS], acc[QS];
+#pragma unroll
+  for (int s = 0; s < QS; ++s) {
+    y[s] = s < nnc ? my[s * 32] : 1.f;
+    acc[s] = 0.f;
+  }
+  fe = gF = gT = 0.f;
+  const int dq = t % N;
+  int q = dq;                               // (root number) * t mod N, root 1 first
+#pragma unroll 1
+  for (int j = 0; j < J; ++j) {
+    float2 W = make_float2(1.f, 0.f);
+    if (q != 0) {
+      const bool low = q <= J;
+      const float4 e = rtab[(low ? q : N - q) - 1];
+      W = make_float2(1.f - 2.f * e.y, low ? 2.f * e.z : -2.f * e.z);
+    }
+    const float4 rt = rtab[j], cf = ctab[j], zp = ztab[3 * j + CornerQ<QS>::slot];
+    if (j < nA) corner_root<QS, true>(rt, zp, cf, W, y, acc, fe, gF, gT);
+    else corner_root<QS, false>(rt, zp, cf, W, y, acc, fe, gF, gT);
+    q += dq;
+    if (q >= N) q -= N;
+  }
+#pragma unroll
+  for (int s = 0; s < QS; ++s) my[s * 32] = acc[s];
+}
+
+__global__ void __launch_bounds__(256) k_fe_dft_corner(
+    const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
+    const F4* __restrict__ root, const F4* __restrict__ zpow, const F4* __restrict__ coef,
+    const LitRec* __restrict__ lit, const float* __restrict__ x, int R, int Rp, int RT,
+    int maxL, float* __restrict__ P, float* __restrict__ fe_con, int ldf,
+    uint8_t* __restrict__ done) {
+  extern __shared__ float4 cs4[];
+  const FeItem it = fe[list[blockIdx.x]];
+  const int L = it.L, J = it.J;
+  const int JC = (maxL + 1) / 2;
+  float4* rtab = cs4;                                         // [JC] {A, B, C, t}
+  float4* ctab = rtab + JC;                                   // [JC] {b', c'}
+  float4* ztab = ctab + JC;                                   // [JC][3] QS = 4, 8, 16
+  float* ncy = reinterpret_cast<float*>(ztab + 3 * JC);      // [8][kCornerQS][32]
+  LitRec* recs = reinterpret_cast<LitRec*>(ncy + 8 * kCornerQS * 32);   // [maxL]
+  uint32_t* flags = reinterpret_cast<uint32_t*>(recs + maxL);            // [8][maxL][2]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < L; i += 256) recs[i] = lit[it.lit0 + i];
+  __syncthreads();
+  const int tile = blockIdx.y * 8 + warp;
+  const bool live = tile < RT;
+  const int r = (live ? tile : RT - 1) * 32 + lane;
+  const bool act = r < R;
+  const float* xr = x + (act ? r : R - 1);
+  float* my = ncy + warp * kCornerQS * 32 + lane;
+  // pass 1: true corners and the non-corner values, in literal order; the
+  // per-literal classification of the tile is kept as two ballots (true
+  // corner, non-corner) so that pass 3 need not read x again
+  uint32_t* fl = flags + (size_t)warp * 2 * maxL;
+  int nnc = 0, t = 0;
+  bool over = !live;
+  for (int i0 = 0; i0 < L && live; i0 += 16) {
+    const int i1 = min(L, i0 + 16);
+    for (int b = i0; b < i1; b += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const LitRec rc = recs[min(b + u, L - 1)];
+        v[u] = rec_sgn(rc.dst) * xr[(size_t)rc.var * R];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (b + u < i1) {
+          const float y = act ? v[u] : 1.f;
+          const bool tc = y == -1.f, nc = (y != -1.f) && (y != 1.f);
+          const uint32_t bt = __ballot_sync(kFull, tc), bn = __ballot_sync(kFull, nc);
+          if (lane == 0) {
+            fl[2 * (b + u)] = bt;
+            fl[2 * (b + u) + 1] = bn;
+          }
+          t += tc ? 1 : 0;
+          if (nc) {
+            if (nnc < kCornerQS) my[nnc * 32] = y;
+            ++nnc;
+          }
+        }
+      }
+    }
+    if (__any_sync(kFull, nnc > kCornerQS)) {
+      over = true;
+      break;
+    }
+  }
+  // the root tables only if some tile of the block stays here
+  if (!__syncthreads_or(!over)) {
+    if (live && lane == 0) done[(size_t)it.c * RT + tile] = 0;
+    return;
+  }
+  for (int j = threadIdx.x; j < J; j += 256) {
+    const size_t zi = (size_t)(it.root_off + j) * kNumFrQ;
+    rtab[j] = ldg4(&root[it.root_off + j]);
+    ctab[j] = ldg4(&coef[it.coef_off + j]);
+    ztab[3 * j + 0] = ldg4(&zpow[zi + CornerQ<4>::zq]);
+    ztab[3 * j + 1] = ldg4(&zpow[zi + CornerQ<8>::zq]);
+    ztab[3 * j + 2] = ldg4(&zpow[zi + CornerQ<16>::zq]);
+  }
+  __syncthreads();
+  if (over) {
+    if (live && lane == 0) done[(size_t)it.c * RT + tile] = 0;
+    return;
+  }
+  // pass 2
+  const int qmax = __reduce_max_sync(kFull, nnc);
+  float fev, gF, gT;
+  if (qmax <= 4) corner_roots<4>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+  else if (qmax <= 8) corner_roots<8>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+  else corner_roots<kCornerQS>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+  // pass 3: partials w * s_e * dFE/dy_e of every literal
+  int k = 0;
+  const uint32_t me = 1u << lane;
+#pragma unroll 4
+  for (int i = 0; i < L; ++i) {
+    const LitRec rc = recs[i];
+    const uint32_t bt = fl[2 * i], bn = fl[2 * i + 1];
+    float val = (bt & me) ? gT : gF;
+    if (bn & me) {
+      val = my[k * 32];
+      ++k;
+    }
+    if (act) P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * val;
+  }
+  if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;
+  __syncwarp();
+  if (lane == 0) done[(size_t)it.c * RT + tile] = 1;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+size_t corner_smem_bytes(int maxL) {
+  const int JC = (maxL + 1) / 2;
+  return (size_t)5 * JC * sizeof(float4) + (size_t)8 * kCornerQS * 32 * sizeof(float) +
+         (size_t)maxL * sizeof(LitRec) + (size_t)8 * 2 * maxL * sizeof(uint32_t);
+}
+
+cudaError_t set_corner_attributes() {
+  return cudaFuncSetAttribute(k_fe_dft_corner, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)corner_smem_bytes(1024));
+}
+
+cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
+                              int Rp, const float* x, float* P, float* fe_con, int ldf,
+                              uint8_t* done, cudaStream_t s) {
+  if (count == 0 || R == 0) return cudaSuccess;
+  const int RT = ceil_div(R, 32);
+  const dim3 grid(count, ceil_div(RT, 8)), block(256);
+  k_fe_dft_corner<<<grid, block, corner_smem_bytes(maxL), s>>>(
+      list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
+      ldf, done);
+  return cudaGetLastError();
+}
+
+}  // namespace cls

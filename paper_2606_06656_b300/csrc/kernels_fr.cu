@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
     const F4* __restrict__ root, const F4* __restrict__ zpow, const F4* __restrict__ coef,
     const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
-    float* __restrict__ fe_con, int ldf) {
+    float* __restrict__ fe_con, int ldf, const uint8_t* __restrict__ done) {
   using Geo = FrGeom<G>;
   constexpr int LS = G * Q;
   constexpr int JC = FrCap<G, Q>::JC;
@@ -179,6 +179,8 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   float* ys = reinterpret_cast<float*>(smem4 + 2 * JC);     // [LS][LDR]
   __shared__ float fe_s[32];
   const FeItem it = fe[list[blockIdx.x]];
+  // a tile the corner pass has finished (kernels_corner.cu)
+  if (done && done[(size_t)it.c * gridDim.y + blockIdx.y]) return;
   const int L = it.L, J = it.J;
   const int r0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -276,14 +278,15 @@ cudaError_t set_fr_attributes() {
 
 cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int count, int R,
                             int Rp, const float* x, float* P, float* fe_con, int ldf,
-                            cudaStream_t s) {
+                            uint8_t* done, cudaStream_t s) {
   if (count == 0 || R == 0) return cudaSuccess;
   const dim3 grid(count, ceil_div(R, 32)), block(256);
   switch (cfg) {
 #define CLS_FR_CASE(id, G, Q, C, Y)                                                       \
   case id:                                                                                \
     k_fe_group_fr<G, Q, (Y != 0)><<<grid, block, fr_smem<G, Q>(), s>>>(                   \
-        list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf);\
+        list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf,  \
+        done);                                                                            \
     break;
     CLS_FR_CONFIGS(CLS_FR_CASE)
 #undef CLS_FR_CASE

@@ -562,3 +562,30 @@ def test_dft_work_accounting(P):
     assert B.cls_dft_work(p.handle) == (fr, lr)
     B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle), 1))
     assert B.cls_dft_work(p.handle) == (20 * lr, lr)
+
+
+def corner_dominated_points(n, R, frac, seed):
+    """Points as a projected-gradient run leaves them: a fraction `frac` of
+    the coordinates exactly at +-1 (random signs), the rest uniform."""
+    rng = np.random.default_rng(seed)
+    X = W.uniform_points(n, R, seed)
+    pin = rng.random((n, R)) < np.asarray(frac, np.float64)
+    X[pin] = np.where(rng.random(pin.sum()) < 0.5, -1.0, 1.0).astype(np.float32)
+    return X
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_corner_dominated_points(P, kernel):
+    """Restarts with almost every literal at a corner take the factored
+    kernel's sparse path (non-corner literals only, true corners as the
+    root power w^(j t)); blocks that mix such restarts with dense ones, and
+    restarts with no free literal at all, are included."""
+    inst = W.mixed_pb(n=600, n_or=1500, n_xor=150, n_card=40, card_len=(100, 300), seed=21)
+    R = 96
+    frac = np.ones(R) * 0.995
+    frac[40:48] = 0.6                       # one 32-restart tile mixes dense restarts in
+    frac[64:] = 1.0                         # every literal at a corner
+    X = corner_dominated_points(inst.n, R, frac[None, :], seed=5)
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
+    X2 = corner_dominated_points(inst.n, R, 0.97, seed=6)
+    check_against_oracle(inst, X2, *gpu_eval(P, inst, X2, kernel), floored=True)
