@@ -175,7 +175,8 @@ def run_ours(args, rank, world, local_rank):
         R = args.R
     p = Problem(inst)
     info = p.info
-    x = p.init_uniform(R, seed=42, r_offset=rank * R)   # restarts sharded by global id
+    x0 = p.init_uniform(R, seed=42, r_offset=rank * R)   # restarts sharded by global id
+    x = x0.clone()
     ws = p.workspace(R)
     tune_s = None
     if args.tuning:
@@ -213,30 +214,53 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     def timed(fn, k_steps):
+        """k_steps of one run from the initial points x0 (reset untimed);
+        per-step CUDA-event times on the launching stream, L2 flushed (an
+        untimed 256 MB write) before every step."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(k_steps)]
+        x.copy_(x0)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         for k in range(k_steps):
-            flush.fill_(k & 0xFF)            # untimed: evict L2 before each step
+            flush.fill_(k & 0xFF)
             evs[k][0].record(stream)
             fn()
             evs[k][1].record(stream)
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs) / k_steps
+        return [a.elapsed_time(b) for a, b in evs]
 
-    # timed region: K steps (graph launches unless --eager); then the same
-    # steps run eagerly with a CUDA event pair around every launch on its
-    # stream, for the per-kernel durations (clocks sampled over both)
+    def class_stats(k_steps):
+        out, n_launch = {}, 0
+        for kc, name in enumerate(kc_names):
+            n_l, t_ms = B.cls_profile_read(p.handle, kc)
+            n_launch += n_l
+            out[name] = {"launches_per_step": n_l / k_steps, "ms_per_step": t_ms / k_steps}
+        return out, n_launch
+
+    # timed region: the first K steps of one run from x0 (graph launches
+    # unless --eager); then the same run eagerly with a CUDA event pair around
+    # every launch on its stream, for the per-kernel durations -- once over
+    # its first (dense-phase) steps for the roofline, once over all K steps
+    kc_names = ["fe_thread", "fe_group_real", "fe_group_dft", "accum_step_round", "score",
+                "reduce", "init"]
+    K = args.steps
+    n_dense = min(K, 10)
     with ClockSampler(local_rank) as clk:
         t0 = time.perf_counter()
-        ms_step = timed(step, args.steps)
+        per_step = timed(step, K)
         wall = time.perf_counter() - t0
         B.cls_profile_reset(p.handle)
         B.cls_profile_enable(p.handle, True)
-        ms_eager = timed(step_eager, args.steps)
+        timed(step_eager, n_dense)
+        kstats_dense, _ = class_stats(n_dense)
+        B.cls_profile_reset(p.handle)
+        per_eager = timed(step_eager, K)
         B.cls_profile_enable(p.handle, False)
+    kstats, launches = class_stats(K)
+    ms_step = sum(per_step) / K
+    ms_eager = sum(per_eager) / K
     if args.persistent and B.cls_persistent_status(p.handle, R, ws) != 0:
         raise RuntimeError("persistent loop: a grid barrier timed out")
     if dist:
@@ -244,30 +268,20 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
     graph_launches = B.cls_graph_kernel_count(graph) if graph is not None else None
-    kc_names = ["fe_thread", "fe_group_real", "fe_group_dft", "accum_step_round", "score",
-                "reduce", "init"]
-    kstats = {}
-    launches = 0
-    for kc, name in enumerate(kc_names):
-        n_l, t_ms = B.cls_profile_read(p.handle, kc)
-        launches += n_l
-        kstats[name] = {"launches_per_step": n_l / args.steps, "ms_per_step": t_ms / args.steps}
-    launches_timed = graph_launches * args.steps if graph_launches is not None else launches
+    launches_timed = graph_launches * K if graph_launches is not None else launches
     if args.persistent:
-        launches_timed = args.steps                 # one cooperative kernel per step
+        launches_timed = K                          # one cooperative kernel per step
     clocks = clk.summary()
 
-    # end to end through host buffers: H2D x0 (pinned), one step, D2H nsat
-    xh = x.detach().cpu().pin_memory()
+    # end to end through host buffers: one cls_solve_host call per run --
+    # H2D of x0 from pinned memory, the same K steps, D2H of the counts
+    xh = x0.detach().cpu().pin_memory()
     nh = torch.empty(R, dtype=torch.int32).pin_memory()
     hws = p.workspace(R, host_solve=True)
-    for _ in range(2):
-        B.cls_solve_host(p.handle, R, xh, lr, 1, nh, None, hws)
-    e2e_steps = max(3, min(args.steps, 10))
+    B.cls_solve_host(p.handle, R, xh, lr, 2, nh, None, hws)
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        B.cls_solve_host(p.handle, R, xh, lr, 1, nh, None, hws)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    B.cls_solve_host(p.handle, R, xh, lr, K, nh, None, hws)
+    e2e_s = (time.perf_counter() - t0) / K
 
     units = R * inst.nnz * world
     value = units / (ms_step / 1e3)
@@ -275,13 +289,15 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kstats, key=lambda k: kstats[k]["ms_per_step"])
     pk = peaks()
     if dom == "fe_group_dft":
+        # the dense kernels' exact flop count holds in the run's first steps,
+        # before coordinates reach the cube's faces (no tile on the corner pass)
         flops = B.cls_dft_work(p.handle)[0] * R
-        t = kstats[dom]["ms_per_step"] / 1e3
+        t = kstats_dense[dom]["ms_per_step"] / 1e3
         peak = 2 * SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": "k_fe_group_fr / k_fe_group (DFT buckets)",
                 "achieved": flops / t / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak,
-                "traffic": None,
+                "traffic": None, "window": f"steps 0-{n_dense - 1} of the run (dense phase)",
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flops x 2032 MHz (max SM clock)"}
     # the fused accumulate + step + round kernel: algorithmic bytes = the
     # partial rows read once (4 B per FE literal and restart), x read and
@@ -289,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
     # and 32 restarts
     RT = (R + 31) // 32
     step_bytes = 4 * RT * 32 * info["nnz_fe"] + 8 * inst.n * R + 4 * inst.n * RT
-    t_step = kstats["accum_step_round"]["ms_per_step"] / 1e3
+    t_step = kstats_dense["accum_step_round"]["ms_per_step"] / 1e3
     hbm_peak = pk.get("hbm_gbs", 6400.0)
     roof_step = {"bound": "hbm", "kernel": "k_accum_step", "bytes": step_bytes,
                  "achieved": step_bytes / t_step / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -317,14 +333,20 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": inst.name, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
                    "R_per_gpu": R, "lr": lr, "parallelism": f"restart-replicas x{world}",
                    "l2": "flushed (256 MB write) before every timed step",
+                   "timed": f"steps 0-{K - 1} of one CLS run from uniform initial points "
+                            f"(after {max(3, args.warmup)} untimed warm-up steps)",
                    "tuning": tuning, "autotune_s": tune_s},
         "e2e": {"value": units / e2e_s, "unit": "literal-evals/s",
-                "h2d_bytes_per_step": 4 * inst.n * R, "d2h_bytes_per_step": 4 * R},
+                "h2d_bytes_per_step": 4 * inst.n * R / K, "d2h_bytes_per_step": 4 * R / K,
+                "call": f"cls_solve_host: x0 from pinned host memory, {K} steps, counts back"},
         "gpu_launches": launches_timed,
         "mode": ("cuda-graph (1 step per launch)" if graph is not None else
                  "persistent cooperative kernel (1 step per launch)" if args.persistent
                  else "eager"),
         "ms_per_step_eager": ms_eager,
+        "ms_per_step_phases": {f"steps 0-{n_dense - 1}": sum(per_step[:n_dense]) / n_dense,
+                               f"steps {K - n_dense}-{K - 1}": sum(per_step[-n_dense:]) / n_dense},
+        "kernels_dense_phase": kstats_dense,
         "roofline": roof,
         "roofline_step": roof_step,
         "cpu_baseline": cpu,
@@ -438,7 +460,7 @@ def run_partial(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="mixed")

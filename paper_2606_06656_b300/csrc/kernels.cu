@@ -91,34 +91,41 @@ __global__ void __launch_bounds__(256) k_init_uniform(int n, int R, uint64_t see
 // prefix products in registers, suffix products carried backwards (no
 // division).
 // ---------------------------------------------------------------------------
-template <int L, typename IDX, bool CG = false>
+// The warp's literal records {var, dst} sit in shared memory (trec, one per
+// literal, written by load_trec); addresses are formed with one 32x32->64
+// multiply-add each, so a thread holds only its tile's values and prefixes.
+__device__ __forceinline__ void load_trec(const FeItem& it, const LitRec* __restrict__ lit,
+                                          int2* trec, int lane) {
+  if (lane < it.L) {
+    const LitRec rc = lit[it.lit0 + lane];
+    trec[lane] = make_int2(rc.var, rc.dst);
+  }
+  __syncwarp();
+}
+
+template <int L, bool CG = false>
 __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restrict__ root,
-                                            const F4* __restrict__ coef,
-                                            const LitRec* __restrict__ lit,
+                                            const F4* __restrict__ coef, const int2* trec,
                                             const float* __restrict__ x, int R, int Rp, int RT,
                                             int tile0, int lane, float* __restrict__ P,
                                             float* __restrict__ fe_con, int ldf) {
-  IDX xo[L], po[L];
-  float sg[L];
-#pragma unroll
-  for (int i = 0; i < L; ++i) {
-    const LitRec rc = lit[it.lit0 + i];
-    xo[i] = (IDX)rc.var * (IDX)R;
-    po[i] = (IDX)rec_row(rc.dst) * (IDX)Rp;
-    sg[i] = rec_sgn(rc.dst);
-  }
   const float4 rt0 = ldg4(&root[it.root_off]), cf0 = ldg4(&coef[it.coef_off]);
   const bool two = it.J == 2;
   const float4 rt1 = two ? ldg4(&root[it.root_off + 1]) : make_float4(1.f, 0.f, 0.f, 0.f);
   const float4 cf1 = two ? ldg4(&coef[it.coef_off + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const unsigned xs = (unsigned)R, ps = (unsigned)Rp;
   for (int tt = 0; tt < kThreadTiles; ++tt) {
     const int tile = tile0 + tt;
     if (tile >= RT) break;
     const int r = tile * 32 + lane;
     if (r >= R) continue;
+    const float* xr = x + r;
     float y[L], g[L], pre[L];
 #pragma unroll
-    for (int i = 0; i < L; ++i) y[i] = sg[i] * ldx<CG>(&x[xo[i] + r]);
+    for (int i = 0; i < L; ++i) {
+      const int2 q = trec[i];
+      y[i] = rec_sgn(q.y) * ldx<CG>(xr + (size_t)(unsigned)q.x * xs);
+    }
     float run = 1.f;
 #pragma unroll
     for (int i = 0; i < L; ++i) {
@@ -147,36 +154,44 @@ __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restri
         suf *= fmaf(y[i], rt1.y, rt1.x);
       }
     }
+    float* pr = P + r;
 #pragma unroll
-    for (int i = 0; i < L; ++i) P[po[i] + r] = it.w * sg[i] * g[i];
+    for (int i = 0; i < L; ++i) {
+      const int2 q = trec[i];
+      pr[(size_t)(unsigned)rec_row(q.y) * ps] = it.w * rec_sgn(q.y) * g[i];
+    }
     if (fe_con) fe_con[(size_t)it.c * ldf + r] = val;
   }
 }
 
-template <int LO, int HI, typename IDX, bool CG = false>
+template <int LO, int HI, bool CG = false>
 __device__ __forceinline__ void thread_dispatch(int L, const FeItem& it, const F4* root,
-                                                const F4* coef, const LitRec* lit,
+                                                const F4* coef, const int2* trec,
                                                 const float* x, int R, int Rp, int RT, int tile0,
                                                 int lane, float* P, float* fe_con, int ldf) {
   if constexpr (LO <= HI) {
     if (L == LO)
-      thread_body<LO, IDX, CG>(it, root, coef, lit, x, R, Rp, RT, tile0, lane, P, fe_con, ldf);
+      thread_body<LO, CG>(it, root, coef, trec, x, R, Rp, RT, tile0, lane, P, fe_con, ldf);
     else
-      thread_dispatch<LO + 1, HI, IDX, CG>(L, it, root, coef, lit, x, R, Rp, RT, tile0, lane, P,
-                                       fe_con, ldf);
+      thread_dispatch<LO + 1, HI, CG>(L, it, root, coef, trec, x, R, Rp, RT, tile0, lane, P,
+                                      fe_con, ldf);
   }
 }
 
-template <int LO, int HI, typename IDX>
+template <int LO, int HI>
 __global__ void __launch_bounds__(256) k_fe_thread(
     const FeItem* __restrict__ items, int count, const F4* __restrict__ root,
     const F4* __restrict__ coef, const LitRec* __restrict__ lit, const float* __restrict__ x,
     int R, int Rp, int RT, float* __restrict__ P, float* __restrict__ fe_con, int ldf) {
+  __shared__ int2 trec_s[8][HI];
   const int lane = threadIdx.x;
+  int2* trec = trec_s[threadIdx.y];
   for (int ci = blockIdx.y * blockDim.y + threadIdx.y; ci < count; ci += gridDim.y * blockDim.y) {
     const FeItem it = items[ci];
-    thread_dispatch<LO, HI, IDX>(it.L, it, root, coef, lit, x, R, Rp, RT,
-                                 blockIdx.x * kThreadTiles, lane, P, fe_con, ldf);
+    __syncwarp();
+    load_trec(it, lit, trec, lane);
+    thread_dispatch<LO, HI>(it.L, it, root, coef, trec, x, R, Rp, RT, blockIdx.x * kThreadTiles,
+                            lane, P, fe_con, ldf);
   }
 }
 
@@ -827,29 +842,23 @@ __global__ void __launch_bounds__(256) k_persistent(DevPlan d, PersistArgs a) {
   const int nw = gridDim.x * blockDim.y;
   const int tgroups = (a.RT + kThreadTiles - 1) / kThreadTiles;
   const int n0 = d.thread_count[0], n1 = d.thread_count[1];
-  const bool i32 = (int64_t)d.n * a.R < (int64_t)1 << 31 && d.nnz_fe * a.Rp < (int64_t)1 << 31;
+  __shared__ int2 trec_s[8][16];
+  int2* trec = trec_s[threadIdx.y];
   for (int step = 0; step < a.n_steps; ++step) {
     // FE + literal partials (short closed forms): items (constraint, 4 tiles)
     const int fe_items = (n0 + n1) * tgroups;
     for (int item = gw; item < fe_items; item += nw) {
       const int ci = item / tgroups, tg = item % tgroups;
-      if (ci < n0) {
-        const FeItem it = d.thread_items[0][ci];
-        if (i32)
-          thread_dispatch<1, 8, int, true>(it.L, it, d.root_tab, d.coef_tab, d.fe_lit, a.x, a.R, a.Rp,
-                                     a.RT, tg * kThreadTiles, lane, a.P, nullptr, 0);
-        else
-          thread_dispatch<1, 8, int64_t, true>(it.L, it, d.root_tab, d.coef_tab, d.fe_lit, a.x, a.R,
-                                         a.Rp, a.RT, tg * kThreadTiles, lane, a.P, nullptr, 0);
-      } else {
-        const FeItem it = d.thread_items[1][ci - n0];
-        if (i32)
-          thread_dispatch<9, 16, int, true>(it.L, it, d.root_tab, d.coef_tab, d.fe_lit, a.x, a.R,
-                                      a.Rp, a.RT, tg * kThreadTiles, lane, a.P, nullptr, 0);
-        else
-          thread_dispatch<9, 16, int64_t, true>(it.L, it, d.root_tab, d.coef_tab, d.fe_lit, a.x, a.R,
-                                          a.Rp, a.RT, tg * kThreadTiles, lane, a.P, nullptr, 0);
-      }
+      const bool c0 = ci < n0;
+      const FeItem it = c0 ? d.thread_items[0][ci] : d.thread_items[1][ci - n0];
+      __syncwarp();
+      load_trec(it, d.fe_lit, trec, lane);
+      if (c0)
+        thread_dispatch<1, 8, true>(it.L, it, d.root_tab, d.coef_tab, trec, a.x, a.R, a.Rp, a.RT,
+                                    tg * kThreadTiles, lane, a.P, nullptr, 0);
+      else
+        thread_dispatch<9, 16, true>(it.L, it, d.root_tab, d.coef_tab, trec, a.x, a.R, a.Rp, a.RT,
+                                     tg * kThreadTiles, lane, a.P, nullptr, 0);
     }
     if (!grid_sync(a.bar, a.err, gridDim.x, a.spin_limit)) return;
     // accumulate + projected step + rounding: items (variable, tile)
@@ -1051,15 +1060,9 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
         block(32, 8);
     HookScope hs(h, KC_THREAD, s);
     const FeItem* items = d.thread_items[t];
-    // 32-bit offsets when every x and partial index fits
-    const bool i32 = (int64_t)d.n * R < (int64_t)1 << 31 && d.nnz_fe * Rp < (int64_t)1 << 31;
-#define CLS_THREAD_LAUNCH(LO, HI)                                                            \
-  if (i32)                                                                                 \
-    k_fe_thread<LO, HI, int><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab,      \
-                                                    d.fe_lit, x, R, Rp, RT, P, fe_con, ldf);  \
-  else                                                                                     \
-    k_fe_thread<LO, HI, int64_t><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab,  \
-                                                        d.fe_lit, x, R, Rp, RT, P, fe_con, ldf);
+#define CLS_THREAD_LAUNCH(LO, HI)                                                          \
+  k_fe_thread<LO, HI><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R, \
+                                             Rp, RT, P, fe_con, ldf);
     if (t == 0) {
       CLS_THREAD_LAUNCH(1, 8)
     } else {
