@@ -199,22 +199,18 @@ __global__ void __launch_bounds__(256) k_fe_thread(
 // A2-A5, closed-form products (OR, XOR, NAE, ...) of any length: one thread
 // per (constraint, restart).  A block takes one constraint and 8 tiles of 32
 // restarts (a warp per tile).  The block first writes one record per literal
-// to shared memory -- variable, partial row, s*B_j and A_j of the (at most
-// two) real roots, w*s -- so that the inner loops do one broadcast shared
-// load, one 32-bit multiply-add for the address and one coalesced load per
-// literal; padding records (past L, up to a multiple of kCkptInterval) have
-// s*B = 0 and A = 1 and their loaded value is replaced by 0: the factor 1.  The forward pass keeps every
-// kCkptInterval-th prefix product in shared memory; the backward pass walks
-// the literal blocks from the end, recomputes a block's prefix products from
-// its checkpoint in registers (the block's literal values are loaded again,
-// L2 hits) and combines them with the running suffix product.
-// Dynamic shared memory: 32 B x LCAP records + 8 warps x NJ x nck x 32 floats.
+// to shared memory -- {variable, partial row, s*B_0, w*s} and, for two real
+// roots, s*B_1 -- so that the inner loops do one broadcast shared load, one
+// 32-bit multiply-add for the address and one coalesced load per literal
+// (A_j is the same for every literal).  Literals past L (up to a multiple of
+// the checkpoint interval CI) read x[0] and take the factor 1 by a select.
+// The forward pass keeps every CI-th prefix product in shared memory; the
+// backward pass walks the literal blocks from the end, recomputes a block's
+// prefix products from its checkpoint in registers (the block's values are
+// loaded again, L2 hits) and combines them with the running suffix product.
+// Dynamic shared memory: 16 B x NJ x LCAP records + 8 warps x NJ x nck x 32
+// floats.
 // ---------------------------------------------------------------------------
-struct CkRec {
-  float4 a;   // var (bits), row (bits), s*B_0, A_0
-  float4 b;   // s*B_1, A_1, w*s, -
-};
-
 template <int NJ, int CI>
 __global__ void __launch_bounds__(256) k_fe_thread_ckpt(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
@@ -223,9 +219,11 @@ __global__ void __launch_bounds__(256) k_fe_thread_ckpt(
     float* __restrict__ fe_con, int ldf) {
   extern __shared__ float4 ck_smem[];
   const int LCAP = nck * CI;
-  CkRec* rec = reinterpret_cast<CkRec*>(ck_smem);
+  float4* reca = ck_smem;                    // [LCAP] {var, row, s*B_0, w*s}
+  float* recb = reinterpret_cast<float*>(ck_smem + LCAP);   // [LCAP] s*B_1 (NJ = 2)
   const int lane = threadIdx.x, w = threadIdx.y;
-  float* ck = reinterpret_cast<float*>(ck_smem + 2 * LCAP) + (size_t)w * NJ * nck * 32;
+  float* ck = reinterpret_cast<float*>(ck_smem + LCAP) + (NJ > 1 ? LCAP : 0) +
+              (size_t)w * NJ * nck * 32;
   const FeItem it = fe[list[blockIdx.x]];
   const int L = it.L;
   float4 rt[NJ], cf[NJ];
@@ -239,32 +237,29 @@ __global__ void __launch_bounds__(256) k_fe_thread_ckpt(
     }
   }
   for (int i = w * 32 + lane; i < LCAP; i += 256) {
-    CkRec q;
     if (i < L) {
       const LitRec rc = lit[it.lit0 + i];
       const float sg = rec_sgn(rc.dst);
-      q.a = make_float4(__int_as_float(rc.var), __int_as_float(rec_row(rc.dst)), sg * rt[0].y,
-                        rt[0].x);
-      q.b = make_float4(NJ > 1 ? sg * rt[NJ - 1].y : 0.f, NJ > 1 ? rt[NJ - 1].x : 1.f,
-                        it.w * sg, 0.f);
+      reca[i] = make_float4(__int_as_float(rc.var), __int_as_float(rec_row(rc.dst)),
+                            sg * rt[0].y, it.w * sg);
+      if (NJ > 1) recb[i] = sg * rt[NJ - 1].y;
     } else {
-      q.a = make_float4(__int_as_float(0), __int_as_float(0), 0.f, 1.f);
-      q.b = make_float4(0.f, 1.f, 0.f, 0.f);
+      reca[i] = make_float4(__int_as_float(0), __int_as_float(0), 0.f, 0.f);
+      if (NJ > 1) recb[i] = 0.f;
     }
-    rec[i] = q;
   }
   __syncthreads();
   const int tile = blockIdx.y * 8 + w;
   if (tile >= RT) return;
   const int r = tile * 32 + lane;
   const bool act = r < R;
-  const int rl = act ? r : R - 1;
-  const float* xr = x + rl;
+  const float* xr = x + (act ? r : R - 1);
   const unsigned xstride = (unsigned)R * 4u, pstride = (unsigned)Rp * 4u;
-  auto xval = [&](const CkRec& q) -> float {
+  auto xval = [&](const float4& q) -> float {
     return *reinterpret_cast<const float*>(reinterpret_cast<const char*>(xr) +
-                                           (size_t)(unsigned)__float_as_int(q.a.x) * xstride);
+                                           (size_t)(unsigned)__float_as_int(q.x) * xstride);
   };
+  const float A0 = rt[0].x, A1 = rt[NJ - 1].x;
   const int nb = (L + CI - 1) / CI;
   // forward: running products, checkpoint at each block start
   float run[NJ];
@@ -273,18 +268,15 @@ __global__ void __launch_bounds__(256) k_fe_thread_ckpt(
   for (int b = 0; b < nb; ++b) {
 #pragma unroll
     for (int j = 0; j < NJ; ++j) ck[(j * nck + b) * 32 + lane] = run[j];
-    const int lim = L - b * CI;      // padding records past it read x[0] but use 0
+    const int lim = L - b * CI;
     float xv[CI];
 #pragma unroll
-    for (int t = 0; t < CI; ++t) {
-      const float v = xval(rec[b * CI + t]);
-      xv[t] = t < lim ? v : 0.f;
-    }
+    for (int t = 0; t < CI; ++t) xv[t] = xval(reca[b * CI + t]);
 #pragma unroll
     for (int t = 0; t < CI; ++t) {
-      const CkRec& q = rec[b * CI + t];
-      run[0] *= fmaf(xv[t], q.a.z, q.a.w);
-      if constexpr (NJ > 1) run[1] *= fmaf(xv[t], q.b.x, q.b.y);
+      const float4 q = reca[b * CI + t];
+      run[0] *= t < lim ? fmaf(xv[t], q.z, A0) : 1.f;
+      if constexpr (NJ > 1) run[1] *= t < lim ? fmaf(xv[t], recb[b * CI + t], A1) : 1.f;
     }
   }
   float val = it.b0;
@@ -301,32 +293,31 @@ __global__ void __launch_bounds__(256) k_fe_thread_ckpt(
     const int lim = L - b * CI;
 #pragma unroll
     for (int t = 0; t < CI; ++t) {
-      const float v = xval(rec[b * CI + t]);
+      const float v = xval(reca[b * CI + t]);
       xv[t] = t < lim ? v : 0.f;
     }
 #pragma unroll
     for (int t = 0; t < CI; ++t) {
-      const CkRec& q = rec[b * CI + t];
+      const float4 q = reca[b * CI + t];
       pre[0][t] = p[0];
-      p[0] *= fmaf(xv[t], q.a.z, q.a.w);
+      p[0] *= t < lim ? fmaf(xv[t], q.z, A0) : 1.f;
       if constexpr (NJ > 1) {
         pre[1][t] = p[1];
-        p[1] *= fmaf(xv[t], q.b.x, q.b.y);
+        p[1] *= t < lim ? fmaf(xv[t], recb[b * CI + t], A1) : 1.f;
       }
     }
 #pragma unroll
     for (int t = CI - 1; t >= 0; --t) {
-      const CkRec& q = rec[b * CI + t];
+      const float4 q = reca[b * CI + t];
       float g = pre[0][t] * suf[0];
-      suf[0] *= fmaf(xv[t], q.a.z, q.a.w);
+      suf[0] *= t < lim ? fmaf(xv[t], q.z, A0) : 1.f;
       if constexpr (NJ > 1) {
         g = fmaf(pre[1][t], suf[1], g);
-        suf[1] *= fmaf(xv[t], q.b.x, q.b.y);
+        suf[1] *= t < lim ? fmaf(xv[t], recb[b * CI + t], A1) : 1.f;
       }
       if (act && t < lim)
         *reinterpret_cast<float*>(reinterpret_cast<char*>(P + r) +
-                                  (size_t)(unsigned)__float_as_int(q.a.y) * pstride) =
-            q.b.z * g;
+                                  (size_t)(unsigned)__float_as_int(q.y) * pstride) = q.w * g;
     }
   }
   if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = val;
@@ -928,10 +919,11 @@ struct HookScope {
   }
 };
 
-// records (32 B per literal slot) + checkpoints (8 warps x NJ x nck x 32 floats)
+// records (16 B, plus 4 B for a second root, per literal slot) + checkpoints
+// (8 warps x NJ x nck x 32 floats)
 inline size_t ckpt_smem(int maxL, int nj, int ci) {
   const int nck = std::max(1, (maxL + ci - 1) / ci);
-  return (size_t)nck * ci * 32 + (size_t)8 * nj * nck * 32 * sizeof(float);
+  return (size_t)nck * ci * (nj > 1 ? 20 : 16) + (size_t)8 * nj * nck * 32 * sizeof(float);
 }
 // constraints up to this length use checkpoints every 8 literals (fewer
 // registers); longer ones every kCkptInterval (less shared memory)
