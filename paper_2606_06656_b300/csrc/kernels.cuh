@@ -66,7 +66,7 @@ size_t fr_smem_bytes(int cfg);
 // of buckets whose configuration has >= kCornerMinSlots slots.
 constexpr int kCornerMinSlots = 128;
 cudaError_t set_corner_attributes();
-size_t corner_smem_bytes(int maxL);
+size_t corner_smem_bytes(int maxL, int gc);
 cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
                               int Rp, const float* x, float* P, float* fe_con, int ldf,
                               uint8_t* done, cudaStream_t s);

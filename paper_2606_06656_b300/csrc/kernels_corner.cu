@@ -34,7 +34,8 @@ namespace cls {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kCornerQS = 16;   // most non-corner literals per restart
+constexpr int kCornerQS = 16;   // non-corner slots per lane
+constexpr int kCornerGroup = 4; // lanes per restart in the second pass
 
 __device__ __forceinline__ float4 ldg4(const F4* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -146,6 +147,130 @@ __device__ __forceinline__ void corner_roots(int L, int J, int nnc, int t, const
   for (int s = 0; s < QS; ++s) my[s * 32] = acc[s];
 }
 
+// One root for a group of G lanes sharing a restart (lane lam holds the
+// restart's non-corner slots lam, lam + G, ...; QS per lane): u-products,
+// z^QS scaling, butterfly over the G lanes for the total and the other
+// lanes' product O, then as corner_root with W = w^(j t).  czq = c' z^(QS-1).
+template <int G, int QS, bool FA>
+__device__ __forceinline__ void group_root(const float4 rt, const float4 zp, const float4 cf,
+                                           const float2 W, const float (&y)[QS],
+                                           float (&acc)[QS], float& fe, float& gF, float& gT) {
+  const float tk = rt.w;
+  float pr[QS], pim[QS];
+  float qr, qi;
+  if constexpr (FA) {
+    qr = 1.f;
+    qi = -y[0] * tk;
+  } else {
+    qr = y[0];
+    qi = tk;
+  }
+#pragma unroll
+  for (int s = 1; s < QS; ++s) {
+    pr[s] = qr;
+    pim[s] = qi;
+    if constexpr (FA) {
+      const float w = y[s] * tk;
+      const float nr = fmaf(qi, w, qr), ni = fmaf(-qr, w, qi);
+      qr = nr;
+      qi = ni;
+    } else {
+      const float nr = fmaf(qr, y[s], -qi * tk), ni = fmaf(qi, y[s], qr * tk);
+      qr = nr;
+      qi = ni;
+    }
+  }
+  float2 Pt = cmul(make_float2(qr, qi), make_float2(zp.x, zp.y));
+  float2 O = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int d = 1; d < G; d <<= 1) {
+    const float2 o = make_float2(__shfl_xor_sync(kFull, Pt.x, d), __shfl_xor_sync(kFull, Pt.y, d));
+    O = (d == 1) ? o : cmul(O, o);
+    Pt = cmul(Pt, o);
+  }
+  const float2 Gj = cmul(W, Pt);
+  fe = fmaf(cf.x, Gj.x, fmaf(-cf.y, Gj.y, fe));
+  gF = fmaf(cf.z, Gj.x, fmaf(-cf.w, Gj.y, gF));
+  const float2 cw = cmul(make_float2(cf.z, cf.w), make_float2(1.f - 2.f * rt.y, -2.f * rt.z));
+  gT = fmaf(cw.x, Gj.x, fmaf(-cw.y, Gj.y, gT));
+  const float2 h0 = cmul(cmul(cmul(make_float2(cf.z, cf.w), make_float2(zp.z, zp.w)), W), O);
+  float hr = h0.x, hi = h0.y;
+#pragma unroll
+  for (int s = QS - 1; s >= 1; --s) {
+    acc[s] = fmaf(pr[s], hr, acc[s]);
+    acc[s] = fmaf(-pim[s], hi, acc[s]);
+    if constexpr (FA) {
+      const float w = y[s] * tk;
+      const float a = fmaf(hi, w, hr), b = fmaf(-hr, w, hi);
+      hr = a;
+      hi = b;
+    } else {
+      const float a = fmaf(hr, y[s], -hi * tk), b = fmaf(hi, y[s], hr * tk);
+      hr = a;
+      hi = b;
+    }
+  }
+  acc[0] += hr;
+}
+
+// Pass 2 with G lanes per restart: G rounds over the tile's 32 restarts, 32/G
+// restarts per round.  ncw = the warp's slots (slot k of restart r at
+// ncw[k * 32 + r]); the restart's values are replaced by its partials; fe,
+// gF, gT of restart r go to vals[0..2][r].
+template <int G>
+__device__ __forceinline__ void group_roots(int L, int J, int nnc_own, int t_own, int lane,
+                                            const float4* rtab, const float4* ctab,
+                                            const float4* ztab, float* ncw, float* vals) {
+  constexpr int QS = kCornerQS;
+  const int N = L + 1, nA = (L + 1) / 4;
+  const int lam = lane % G;
+#pragma unroll 1
+  for (int round = 0; round < G; ++round) {
+    const int rr = round * (32 / G) + lane / G;
+    const int nnc = __shfl_sync(kFull, nnc_own, rr), t = __shfl_sync(kFull, t_own, rr);
+    float y[QS], acc[QS];
+#pragma unroll
+    for (int s = 0; s < QS; ++s) {
+      const int k = lam + G * s;
+      y[s] = k < nnc ? ncw[k * 32 + rr] : 1.f;
+      acc[s] = 0.f;
+    }
+    float fe = 0.f, gF = 0.f, gT = 0.f;
+    const int dq = t % N;
+    int q = dq;
+#pragma unroll 1
+    for (int j = 0; j < J; ++j) {
+      float2 W = make_float2(1.f, 0.f);
+      if (q != 0) {
+        const bool low = q <= J;
+        const float4 e = rtab[(low ? q : N - q) - 1];
+        W = make_float2(1.f - 2.f * e.y, low ? 2.f * e.z : -2.f * e.z);
+      }
+      const float4 rt = rtab[j], cf = ctab[j], zp = ztab[3 * j + CornerQ<QS>::slot];
+      if (j < nA) group_root<G, QS, true>(rt, zp, cf, W, y, acc, fe, gF, gT);
+      else group_root<G, QS, false>(rt, zp, cf, W, y, acc, fe, gF, gT);
+      q += dq;
+      if (q >= N) q -= N;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < QS; ++s) {
+      const int k = lam + G * s;
+      if (k < nnc) ncw[k * 32 + rr] = acc[s];
+    }
+    if (lam == 0) {
+      vals[rr] = fe;
+      vals[32 + rr] = gF;
+      vals[64 + rr] = gT;
+    }
+    __syncwarp();
+  }
+}
+
+// GC = 1: one thread per restart, at most kCornerQS non-corner literals;
+// GC > 1: GC lanes per restart, at most GC * kCornerQS, for the tiles the
+// GC = 1 pass left (GC > 1 only reads the flags; GC = 1 writes every flag).
+template <int GC>
 __global__ void __launch_bounds__(256) k_fe_dft_corner(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ root, const F4* __restrict__ zpow, const F4* __restrict__ coef,
@@ -159,8 +284,10 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
   float4* rtab = cs4;                                         // [JC] {A, B, C, t}
   float4* ctab = rtab + JC;                                   // [JC] {b', c'}
   float4* ztab = ctab + JC;                                   // [JC][3] QS = 4, 8, 16
-  float* ncy = reinterpret_cast<float*>(ztab + 3 * JC);      // [8][kCornerQS][32]
-  LitRec* recs = reinterpret_cast<LitRec*>(ncy + 8 * kCornerQS * 32);   // [maxL]
+  constexpr int CAP = GC * kCornerQS;                          // non-corner literals
+  float* ncy = reinterpret_cast<float*>(ztab + 3 * JC);      // [8][CAP][32]
+  float* vals = ncy + 8 * CAP * 32;                           // [8][3][32] fe, gF, gT
+  LitRec* recs = reinterpret_cast<LitRec*>(vals + 8 * 3 * 32);          // [maxL]
   uint32_t* flags = reinterpret_cast<uint32_t*>(recs + maxL);            // [8][maxL][2]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < L; i += 256) recs[i] = lit[it.lit0 + i];
@@ -170,14 +297,16 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
   const int r = (live ? tile : RT - 1) * 32 + lane;
   const bool act = r < R;
   const float* xr = x + (act ? r : R - 1);
-  float* my = ncy + warp * kCornerQS * 32 + lane;
+  float* my = ncy + warp * CAP * 32 + lane;
   // pass 1: true corners and the non-corner values, in literal order; the
   // per-literal classification of the tile is kept as two ballots (true
   // corner, non-corner) so that pass 3 need not read x again
   uint32_t* fl = flags + (size_t)warp * 2 * maxL;
   int nnc = 0, t = 0;
-  bool over = !live;
-  for (int i0 = 0; i0 < L && live; i0 += 16) {
+  // GC > 1: tiles the one-thread pass finished are left alone
+  const bool skip = GC > 1 && live && done[(size_t)it.c * RT + tile];
+  bool over = !live || skip;
+  for (int i0 = 0; i0 < L && !over; i0 += 16) {
     const int i1 = min(L, i0 + 16);
     for (int b = i0; b < i1; b += 8) {
       float v[8];
@@ -198,20 +327,20 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
           }
           t += tc ? 1 : 0;
           if (nc) {
-            if (nnc < kCornerQS) my[nnc * 32] = y;
+            if (nnc < CAP) my[nnc * 32] = y;
             ++nnc;
           }
         }
       }
     }
-    if (__any_sync(kFull, nnc > kCornerQS)) {
+    if (__any_sync(kFull, nnc > CAP)) {
       over = true;
       break;
     }
   }
   // the root tables only if some tile of the block stays here
   if (!__syncthreads_or(!over)) {
-    if (live && lane == 0) done[(size_t)it.c * RT + tile] = 0;
+    if (GC == 1 && live && lane == 0) done[(size_t)it.c * RT + tile] = 0;
     return;
   }
   for (int j = threadIdx.x; j < J; j += 256) {
@@ -224,15 +353,23 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
   }
   __syncthreads();
   if (over) {
-    if (live && lane == 0) done[(size_t)it.c * RT + tile] = 0;
+    if (GC == 1 && live && lane == 0) done[(size_t)it.c * RT + tile] = 0;
     return;
   }
   // pass 2
-  const int qmax = __reduce_max_sync(kFull, nnc);
   float fev, gF, gT;
-  if (qmax <= 4) corner_roots<4>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
-  else if (qmax <= 8) corner_roots<8>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
-  else corner_roots<kCornerQS>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+  if constexpr (GC == 1) {
+    const int qmax = __reduce_max_sync(kFull, nnc);
+    if (qmax <= 4) corner_roots<4>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+    else if (qmax <= 8) corner_roots<8>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+    else corner_roots<kCornerQS>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+  } else {
+    float* vw = vals + warp * 96;
+    group_roots<GC>(L, J, nnc, t, lane, rtab, ctab, ztab, ncy + warp * CAP * 32, vw);
+    fev = vw[lane];
+    gF = vw[32 + lane];
+    gT = vw[64 + lane];
+  }
   // pass 3: partials w * s_e * dFE/dy_e of every literal
   int k = 0;
   const uint32_t me = 1u << lane;
@@ -256,15 +393,22 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
-size_t corner_smem_bytes(int maxL) {
+size_t corner_smem_bytes(int maxL, int gc) {
   const int JC = (maxL + 1) / 2;
-  return (size_t)5 * JC * sizeof(float4) + (size_t)8 * kCornerQS * 32 * sizeof(float) +
-         (size_t)maxL * sizeof(LitRec) + (size_t)8 * 2 * maxL * sizeof(uint32_t);
+  return (size_t)5 * JC * sizeof(float4) + (size_t)8 * gc * kCornerQS * 32 * sizeof(float) +
+         (size_t)8 * 3 * 32 * sizeof(float) + (size_t)maxL * sizeof(LitRec) +
+         (size_t)8 * 2 * maxL * sizeof(uint32_t);
 }
 
 cudaError_t set_corner_attributes() {
-  return cudaFuncSetAttribute(k_fe_dft_corner, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)corner_smem_bytes(1024));
+  cudaError_t e = cudaFuncSetAttribute(k_fe_dft_corner<1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)corner_smem_bytes(1024, 1));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fe_dft_corner<kCornerGroup>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)corner_smem_bytes(1024, kCornerGroup));
+  return e;
 }
 
 cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
@@ -273,7 +417,12 @@ cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, 
   if (count == 0 || R == 0) return cudaSuccess;
   const int RT = ceil_div(R, 32);
   const dim3 grid(count, ceil_div(RT, 8)), block(256);
-  k_fe_dft_corner<<<grid, block, corner_smem_bytes(maxL), s>>>(
+  k_fe_dft_corner<1><<<grid, block, corner_smem_bytes(maxL, 1), s>>>(
+      list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
+      ldf, done);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_fe_dft_corner<kCornerGroup><<<grid, block, corner_smem_bytes(maxL, kCornerGroup), s>>>(
       list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
       ldf, done);
   return cudaGetLastError();
