@@ -64,7 +64,11 @@ cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int 
 size_t fr_smem_bytes(int cfg);
 // The corner pass (kernels_corner.cu): runs before the dense factored kernel
 // of buckets whose configuration has >= kCornerMinSlots slots.
-constexpr int kCornerMinSlots = 128;
+constexpr int kCornerMinSlots = 32;
+// per-(constraint, tile) flag values: open (the next pass may try), done
+// (partials written; later passes and the dense kernel skip it), dense
+// (left to the dense kernel)
+constexpr uint8_t kTileOpen = 0, kTileDone = 1, kTileDense = 2;
 cudaError_t set_corner_attributes();
 size_t corner_smem_bytes(int maxL, int gc);
 cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,

@@ -304,8 +304,9 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
   uint32_t* fl = flags + (size_t)warp * 2 * maxL;
   int nnc = 0, t = 0;
   // GC > 1: tiles the one-thread pass finished are left alone
-  const bool skip = GC > 1 && live && done[(size_t)it.c * RT + tile];
+  const bool skip = GC > 1 && live && done[(size_t)it.c * RT + tile] != kTileOpen;
   bool over = !live || skip;
+  int i_over = L;
   for (int i0 = 0; i0 < L && !over; i0 += 16) {
     const int i1 = min(L, i0 + 16);
     for (int b = i0; b < i1; b += 8) {
@@ -335,12 +336,19 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
     }
     if (__any_sync(kFull, nnc > CAP)) {
       over = true;
+      i_over = i1;
       break;
     }
   }
   // the root tables only if some tile of the block stays here
+  // GC = 1 marks a tile whose non-corner density projects past the second
+  // pass's capacity (more than 5/4 of it over L literals) as dense outright
+  const uint8_t gave_up =
+      (GC == 1 && (int64_t)(CAP + 1) * L > (int64_t)i_over * (kCornerGroup * kCornerQS * 5 / 4))
+          ? kTileDense
+          : kTileOpen;
   if (!__syncthreads_or(!over)) {
-    if (GC == 1 && live && lane == 0) done[(size_t)it.c * RT + tile] = 0;
+    if (GC == 1 && live && lane == 0) done[(size_t)it.c * RT + tile] = gave_up;
     return;
   }
   for (int j = threadIdx.x; j < J; j += 256) {
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
   }
   __syncthreads();
   if (over) {
-    if (GC == 1 && live && lane == 0) done[(size_t)it.c * RT + tile] = 0;
+    if (GC == 1 && live && lane == 0) done[(size_t)it.c * RT + tile] = gave_up;
     return;
   }
   // pass 2
@@ -386,7 +394,7 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
   }
   if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;
   __syncwarp();
-  if (lane == 0) done[(size_t)it.c * RT + tile] = 1;
+  if (lane == 0) done[(size_t)it.c * RT + tile] = kTileDone;
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

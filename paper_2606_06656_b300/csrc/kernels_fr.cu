@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   __shared__ float fe_s[32];
   const FeItem it = fe[list[blockIdx.x]];
   // a tile the corner pass has finished (kernels_corner.cu)
-  if (done && done[(size_t)it.c * gridDim.y + blockIdx.y]) return;
+  if (done && done[(size_t)it.c * gridDim.y + blockIdx.y] == kTileDone) return;
   const int L = it.L, J = it.J;
   const int r0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
