@@ -290,6 +290,12 @@ __global__ void __launch_bounds__(256) k_fe_dft_corner(
   LitRec* recs = reinterpret_cast<LitRec*>(vals + 8 * 3 * 32);          // [maxL]
   uint32_t* flags = reinterpret_cast<uint32_t*>(recs + maxL);            // [8][maxL][2]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (GC > 1) {
+    // nothing to do unless one of the block's tiles is still open
+    const int tl = blockIdx.y * 8 + (threadIdx.x & 7);
+    const bool open = (threadIdx.x < 8) && tl < RT && done[(size_t)it.c * RT + tl] == kTileOpen;
+    if (!__syncthreads_or(open)) return;
+  }
   for (int i = threadIdx.x; i < L; i += 256) recs[i] = lit[it.lit0 + i];
   __syncthreads();
   const int tile = blockIdx.y * 8 + warp;

@@ -178,9 +178,11 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   float4* cs = smem4 + JC;                                   // [JC]
   float* ys = reinterpret_cast<float*>(smem4 + 2 * JC);     // [LS][LDR]
   __shared__ float fe_s[32];
-  const FeItem it = fe[list[blockIdx.x]];
-  // a tile the corner pass has finished (kernels_corner.cu)
-  if (done && done[(size_t)it.c * gridDim.y + blockIdx.y] == kTileDone) return;
+  // a tile the corner pass has finished (kernels_corner.cu); the flag is
+  // indexed by the constraint id, which is also the FE item's index
+  const int ci = list[blockIdx.x];
+  if (done && done[(size_t)ci * gridDim.y + blockIdx.y] == kTileDone) return;
+  const FeItem it = fe[ci];
   const int L = it.L, J = it.J;
   const int r0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
