@@ -271,7 +271,7 @@ __device__ __forceinline__ void group_roots(int L, int J, int nnc_own, int t_own
 // GC > 1: GC lanes per restart, at most GC * kCornerQS, for the tiles the
 // GC = 1 pass left (GC > 1 only reads the flags; GC = 1 writes every flag).
 template <int GC>
-__global__ void __launch_bounds__(256) k_fe_dft_corner(
+__global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ root, const F4* __restrict__ zpow, const F4* __restrict__ coef,
     const LitRec* __restrict__ lit, const float* __restrict__ x, int R, int Rp, int RT,
