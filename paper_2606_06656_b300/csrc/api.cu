@@ -333,6 +333,9 @@ int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const in
   up(H.score, &D.score);
   up(H.score_ranges, &D.score_ranges);
   D.n_ranges = H.score_ranges.empty() ? 0 : (int32_t)H.score_ranges.size() - 1;
+  D.unit_weights = 1;
+  for (float w : H.weight)
+    if (w != 1.0f) D.unit_weights = 0;
   up(H.satbits, &D.satbits);
   up(H.root_tab, &D.root_tab);
   up(H.zpow_tab, &D.zpow_tab);

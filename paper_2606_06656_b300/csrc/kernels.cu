@@ -622,8 +622,9 @@ __device__ __forceinline__ bool sat_of(const ScoreItem& s, int t,
 }
 
 // one range of constraints for one tile of 32 restarts (whole warp); returns
-// the lane's satisfied count and satisfied weight
-template <bool CG = false>
+// the lane's satisfied count and satisfied weight (UNIT: all weights are 1,
+// the weight is the count -- the same FP64 value, without FP64 adds)
+template <bool CG = false, bool UNIT = false>
 __device__ __forceinline__ void score_range(int rg, int tile, int lane, int RW,
                                             const int32_t* __restrict__ ranges,
                                             const ScoreItem* __restrict__ sc,
@@ -658,7 +659,7 @@ __device__ __forceinline__ void score_range(int rg, int tile, int lane, int RW,
       run = 0;
       const bool sat = sat_of(s, t, satbits);
       cnt += sat ? 1 : 0;
-      ws += sat ? (double)s.w : 0.0;
+      if constexpr (!UNIT) ws += sat ? (double)s.w : 0.0;
       ++c;
       if (c < c_end) s = sc[c];
     }
@@ -670,9 +671,10 @@ __device__ __forceinline__ void score_range(int rg, int tile, int lane, int RW,
     e = chunk_end;
   }
   *cnt_out = cnt;
-  *ws_out = ws;
+  *ws_out = UNIT ? (double)cnt : ws;
 }
 
+template <bool UNIT>
 __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
                                                const int32_t* __restrict__ ranges,
                                                const ScoreItem* __restrict__ sc,
@@ -688,7 +690,8 @@ __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
   const int rg = blockIdx.y * kScoreWarps + ty;
   int cnt = 0;
   double ws = 0.0;
-  if (rg < n_ranges) score_range(rg, tile, lane, RW, ranges, sc, lit, satbits, bits, &cnt, &ws);
+  if (rg < n_ranges)
+    score_range<false, UNIT>(rg, tile, lane, RW, ranges, sc, lit, satbits, bits, &cnt, &ws);
   cnt_s[ty][lane] = cnt;
   w_s[ty][lane] = ws;
   __syncthreads();
@@ -1134,9 +1137,14 @@ cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
   const int nch = score_chunks(d.n_ranges);
   {
     HookScope hs(h, KC_SCORE, s);
-    k_score<<<dim3(RT, nch), dim3(32, kScoreWarps), 0, s>>>(RT, Rp, d.n_ranges, d.score_ranges,
-                                                            d.score, d.lit, d.satbits, bits,
-                                                            nsat_part, wsat_part);
+    if (d.unit_weights)
+      k_score<true><<<dim3(RT, nch), dim3(32, kScoreWarps), 0, s>>>(
+          RT, Rp, d.n_ranges, d.score_ranges, d.score, d.lit, d.satbits, bits, nsat_part,
+          wsat_part);
+    else
+      k_score<false><<<dim3(RT, nch), dim3(32, kScoreWarps), 0, s>>>(
+          RT, Rp, d.n_ranges, d.score_ranges, d.score, d.lit, d.satbits, bits, nsat_part,
+          wsat_part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -32,6 +32,7 @@ struct DevPlan {
   ScoreItem* score = nullptr;        // constraint order
   int32_t* score_ranges = nullptr;   // n_ranges+1 constraint boundaries
   int32_t n_ranges = 0;
+  int32_t unit_weights = 0;          // every constraint weight is exactly 1
   uint32_t* satbits = nullptr;
   F4* root_tab = nullptr;
   F4* zpow_tab = nullptr;
