@@ -303,6 +303,15 @@ int cls_config_info(int32_t id, int32_t* out);
  * (literal, root) pairs per restart.  Host-only; CLS_ERR_INVALID on NULL. */
 int cls_dft_work(const cls_problem* p, int64_t* out);
 
+/* Flops of the DFT roots the dense factored kernel has evaluated since the
+ * last reset (no counterpart in the paper; for roofline accounting): the
+ * kernel skips, per restart, the roots whose terms are provably below 2^-30
+ * in total (see kernels_fr.cu), so its work depends on the point; it adds
+ * 14 or 16 flops per (literal, evaluated root) of every restart to a
+ * per-problem device counter.  Synchronises the device; *flops = the count;
+ * reset != 0 zeroes it afterwards.  CLS_ERR_INVALID on NULL. */
+int cls_dft_flops_counter(cls_problem* p, int64_t* flops, int32_t reset);
+
 /* cls_step without any allocation, for callers that cannot allocate device
  * memory while they run (a real-time loop that must not touch the allocator
  * after start-up, a process confined to a fixed device-memory budget owned

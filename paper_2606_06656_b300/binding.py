@@ -303,3 +303,12 @@ def cls_dft_work(h):
     out = (C.c_int64 * 2)()
     _lib.check(_lib.load().cls_dft_work(h, out), "cls_dft_work")
     return int(out[0]), int(out[1])
+
+
+def cls_dft_flops_counter(h, reset=False):
+    """Flops of the DFT roots evaluated by the dense factored kernel since the
+    last reset (synchronises the device)."""
+    v = C.c_int64()
+    _lib.check(_lib.load().cls_dft_flops_counter(h, C.byref(v), 1 if reset else 0),
+               "cls_dft_flops_counter")
+    return int(v.value)

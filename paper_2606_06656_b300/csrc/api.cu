@@ -342,6 +342,11 @@ int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const in
   up(H.coef_tab, &D.coef_tab);
   up(H.fixed, &D.fixed);
   up(H.fixed_val, &D.fixed_val);
+  {
+    // statistics: flops of the DFT roots the dense factored kernel evaluated
+    const std::vector<unsigned long long> zero(1, 0ull);
+    up(zero, &D.dft_flops);
+  }
   if (r2 == CLS_OK) r2 = upload_lists(p);
   if (r2 != CLS_OK) {
     free_problem(p);
@@ -394,6 +399,16 @@ int cls_dft_work(const cls_problem* p, int64_t* out) {
   }
   out[0] = flops;
   out[1] = lroots;
+  return CLS_OK;
+}
+
+int cls_dft_flops_counter(cls_problem* p, int64_t* flops, int32_t reset) {
+  if (!p || !flops) return set_err(CLS_ERR_INVALID, "NULL argument");
+  unsigned long long v = 0;
+  CLS_CUDA_TRY(cudaDeviceSynchronize(), "synchronize");
+  CLS_CUDA_TRY(cudaMemcpy(&v, p->dev.dft_flops, sizeof(v), cudaMemcpyDeviceToHost), "copy");
+  *flops = (int64_t)v;
+  if (reset) CLS_CUDA_TRY(cudaMemset(p->dev.dft_flops, 0, sizeof(v)), "memset");
   return CLS_OK;
 }
 

@@ -33,6 +33,7 @@ struct DevPlan {
   int32_t* score_ranges = nullptr;   // n_ranges+1 constraint boundaries
   int32_t n_ranges = 0;
   int32_t unit_weights = 0;          // every constraint weight is exactly 1
+  unsigned long long* dft_flops = nullptr;   // flops of the evaluated DFT roots
   uint32_t* satbits = nullptr;
   F4* root_tab = nullptr;
   F4* zpow_tab = nullptr;

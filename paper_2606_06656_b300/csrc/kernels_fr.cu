@@ -32,6 +32,9 @@ namespace cls {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// bound on the sum of the skipped tail terms: kTailEps = 2^-30 (the
+// threshold uses ln(1 / kTailEps) = 30 ln 2, rounded up)
+constexpr float kTailLogInvEps = 20.80f;
 
 __device__ __forceinline__ float4 ldg4(const F4* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -169,7 +172,8 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
     const F4* __restrict__ root, const F4* __restrict__ zpow, const F4* __restrict__ coef,
     const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
-    float* __restrict__ fe_con, int ldf, const uint8_t* __restrict__ done) {
+    float* __restrict__ fe_con, int ldf, const uint8_t* __restrict__ done,
+    unsigned long long* __restrict__ flops) {
   using Geo = FrGeom<G>;
   constexpr int LS = G * Q;
   constexpr int JC = FrCap<G, Q>::JC;
@@ -217,6 +221,7 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   const int lam = lane % G;
   const int gi = lane / G;
   const int nA = (L + 1) / 4;        // roots with phi <= pi/4 come first
+  const float tailT = logf(2.f * (float)J) + kTailLogInvEps;
 #pragma unroll 1
   for (int pass = 0; pass < Geo::PASSES; ++pass) {
     const int rr = pass * Geo::GPB + warp * Geo::GPW + gi;
@@ -227,11 +232,43 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
       if constexpr (!YS) yreg[s] = ycol[s * G * Geo::LDR];
       acc[s] = 0.f;
     }
+    // Tail cutoff.  |alpha + beta w^j|^2 = 1 - 2 alpha beta (1 - cos theta_j),
+    // so with S = sum_i alpha_i beta_i = sum_i (1 - y_i^2)/4 every product
+    // over all or all-but-one factors has modulus <= exp(-(S - 1/4)(1 - cos
+    // theta_j)), and |b'_j|, |c'_j| <= 2.  Roots with 2 sin^2(phi_j)(S - 1/4)
+    // >= T = ln(2J / kTailEps) therefore add at most kTailEps in total to FE
+    // and to every partial; they are skipped.  The warp runs to the largest
+    // cutoff of its groups (extra roots are exact terms).
+    float S = 0.f;
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const float y = YS ? ycol[s * G * Geo::LDR] : yreg[s];
+      S = fmaf(-0.25f * y, y, S + 0.25f);
+    }
+#pragma unroll
+    for (int d = 1; d < G; d <<= 1) S += __shfl_xor_sync(kFull, S, d);
+    int jc = J;
+    const float S1 = S - 0.25f;
+    if (S1 > 0.f) {
+      const float q = tailT / (2.f * S1);
+      if (q < 1.f)
+        jc = min(J, (int)ceilf(asinf(sqrtf(q)) * (float)(L + 1) * 0.318309886f) + 1);
+    }
+    const int jw = __reduce_max_sync(kFull, jc);
+    if (flops) {
+      // algorithmic work of the roots each restart needs: 14 / 16 flops per
+      // (literal, root) in the two factored forms (counted once per group)
+      // (per group <= 1024 * 16 * 512 < 2^24, so the warp sum fits 32 bits)
+      const unsigned f = lam == 0 ? (unsigned)L * (14u * min(nA, jc) + 16u * max(0, jc - nA)) : 0u;
+      const unsigned tot = __reduce_add_sync(kFull, f);
+      if (lane == 0) atomicAdd(flops, (unsigned long long)tot);
+    }
     float val = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < nA; ++j) val += fr_root<G, Q, YS, true>(rs[j], cs[j], yreg, ycol, acc);
+    for (int j = 0; j < min(nA, jw); ++j)
+      val += fr_root<G, Q, YS, true>(rs[j], cs[j], yreg, ycol, acc);
 #pragma unroll 1
-    for (int j = nA; j < J; ++j) val += fr_root<G, Q, YS, false>(rs[j], cs[j], yreg, ycol, acc);
+    for (int j = nA; j < jw; ++j) val += fr_root<G, Q, YS, false>(rs[j], cs[j], yreg, ycol, acc);
     // partials back into the staging slots (each slot is owned by one lane)
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
@@ -288,7 +325,7 @@ cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int 
   case id:                                                                                \
     k_fe_group_fr<G, Q, (Y != 0)><<<grid, block, fr_smem<G, Q>(), s>>>(                   \
         list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf,  \
-        done);                                                                            \
+        done, d.dft_flops);                                                               \
     break;
     CLS_FR_CONFIGS(CLS_FR_CASE)
 #undef CLS_FR_CASE

@@ -589,3 +589,26 @@ def test_corner_dominated_points(P, kernel):
     check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
     X2 = corner_dominated_points(inst.n, R, 0.97, seed=6)
     check_against_oracle(inst, X2, *gpu_eval(P, inst, X2, kernel), floored=True)
+
+
+def test_dft_flops_counter_counts_truncated_work(P):
+    """At uniform points long cardinality constraints need far fewer roots
+    than J (the tail cutoff); at corner points every root is kept."""
+    from paper_2606_06656_b300 import binding as B
+    rng = np.random.default_rng(4)
+    n = 600
+    rows = [(W.TYPE_CARD_GE, L // 2, rng.choice(n, L, replace=False).astype(np.int32),
+             np.ones(L, np.int8)) for L in (150, 220, 300)]
+    inst = W.build(n, rows)
+    p = P(inst)
+    B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle), 3))
+    full = B.cls_dft_work(p.handle)[0]
+    R = 64
+    B.cls_dft_flops_counter(p.handle, reset=True)
+    x = torch.from_numpy(W.uniform_points(n, R, seed=1)).cuda()
+    p.eval(x, obj=False, grad=True)
+    part = B.cls_dft_flops_counter(p.handle, reset=True)
+    assert 0 < part < 0.8 * full * R
+    x = torch.from_numpy(W.near_corner_points(n, R, seed=2)).cuda()
+    p.eval(x, obj=False, grad=True)
+    assert B.cls_dft_flops_counter(p.handle, reset=True) == full * R
