@@ -42,6 +42,15 @@ __device__ __forceinline__ float4 ldg4(const F4* p) {
 __device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
 __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
 
+// global -> shared copy of 4 bytes without a register round trip (sm_80+)
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -206,15 +215,20 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   __shared__ LitRec lrec_s[LS];
   for (int i = threadIdx.x; i < L; i += 256) lrec_s[i] = lit[it.lit0 + i];
   __syncthreads();
-#pragma unroll 4
-  for (int i = warp; i < LS; i += 8) {
-    float v = 1.0f;
-    if (i < L) {
-      const LitRec rc = lrec_s[i];
-      const int r = r0 + lane;
-      if (r < R) v = rec_sgn(rc.dst) * x[(size_t)rc.var * R + r];
+  // rows of x go to shared memory as asynchronous 4-byte copies (all of a
+  // thread's rows in flight at once); the signs are applied afterwards
+  {
+    const int r = r0 + lane;
+    for (int i = warp; i < LS; i += 8) {
+      float* dst = &ys[i * Geo::LDR + lane];
+      if (i < L && r < R) cp_async4(dst, &x[(size_t)lrec_s[i].var * R + r]);
+      else *dst = 1.0f;
     }
-    ys[i * Geo::LDR + lane] = v;
+    cp_async_wait_all();
+    __syncthreads();
+    if (r < R)
+      for (int i = warp; i < L; i += 8)
+        if (lrec_s[i].dst < 0) ys[i * Geo::LDR + lane] = -ys[i * Geo::LDR + lane];
   }
   __syncthreads();
 
