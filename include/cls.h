@@ -299,7 +299,8 @@ int cls_config_info(int32_t id, int32_t* out);
  * counterpart in the paper; for roofline accounting): out[0] = flops per
  * restart of one FE+gradient evaluation (a fused multiply-add counts 2):
  * per (literal, root) 20 for the direct factor alpha + beta w^j (kinds 1
- * and 2), 14 or 16 for the factored forms (kind 3); out[1] = the number of
+ * and 2), 14 or 16 for the factored forms (kind 3; 14 in the two
+ * forms with 3-operation complex products); out[1] = the number of
  * (literal, root) pairs per restart.  Host-only; CLS_ERR_INVALID on NULL. */
 int cls_dft_work(const cls_problem* p, int64_t* out);
 

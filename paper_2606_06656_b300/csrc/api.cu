@@ -390,10 +390,10 @@ int cls_dft_work(const cls_problem* p, int64_t* out) {
     const bool fr = cfg >= 0 && cfg < cls::kNumGroupCfg && cls::kGroupCfg[cfg].cplx == 3;
     for (int32_t c : H.bucket_list[b]) {
       const cls::FeItem& it = H.fe[c];
-      const int64_t L = it.L, J = it.J, nA = (it.L + 1) / 4;
+      const int64_t L = it.L, J = it.J, nA = cls::fr_roots_form01(it.L);
       lroots += L * J;
-      // factored roots: 14 flops per (literal, root) with phi <= pi/4 and 16
-      // beyond; the direct factor alpha + beta w^j: 20
+      // factored roots: 14 flops per (literal, root) in forms 0 and 1 and 16
+      // in form 2; the direct factor alpha + beta w^j: 20
       flops += fr ? L * (14 * nA + 16 * (J - nA)) : 20 * L * J;
     }
   }

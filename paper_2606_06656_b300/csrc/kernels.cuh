@@ -64,6 +64,50 @@ cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int 
                             int Rp, const float* x, float* P, float* fe_con, int ldf,
                             uint8_t* done, cudaStream_t s);
 size_t fr_smem_bytes(int cfg);
+
+// Factored root forms (kernels_fr.cu, kernels_corner.cu).  With phi = pi j/N,
+// N = L + 1, a root j = 1..J uses
+//   form 0 (4j <= N):            u = 1 - i y t,  t = tan phi
+//   form 1 (N < 4j, 50j <= 21N):  u = y t + i,   t = tan phi  (t <= 3.9)
+//   form 2 (otherwise):           u = y + i t,   t = cot phi
+// (3 FP32 operations per complex product in forms 0 and 1, 4 in form 2).
+__host__ __device__ inline int fr_roots_form0(int L) { return (L + 1) / 4; }
+__host__ __device__ inline int fr_roots_form01(int L) {
+  const int J = (L + 1) / 2, n = 21 * (L + 1) / 50;
+  return n < J ? n : J;
+}
+template <int F>
+__device__ __forceinline__ void fr_uinit(float& qr, float& qi, float y, float t) {
+  if constexpr (F == 0) {
+    qr = 1.f;
+    qi = -y * t;
+  } else if constexpr (F == 1) {
+    qr = y * t;
+    qi = 1.f;
+  } else {
+    qr = y;
+    qi = t;
+  }
+}
+// (qr + i qi) *= u_F(y)
+template <int F>
+__device__ __forceinline__ void fr_umul(float& qr, float& qi, float y, float t) {
+  if constexpr (F == 0) {
+    const float w = y * t;
+    const float nr = fmaf(qi, w, qr), ni = fmaf(-qr, w, qi);
+    qr = nr;
+    qi = ni;
+  } else if constexpr (F == 1) {
+    const float w = y * t;
+    const float nr = fmaf(qr, w, -qi), ni = fmaf(qi, w, qr);
+    qr = nr;
+    qi = ni;
+  } else {
+    const float nr = fmaf(qr, y, -qi * t), ni = fmaf(qi, y, qr * t);
+    qr = nr;
+    qi = ni;
+  }
+}
 // The corner pass (kernels_corner.cu): runs before the dense factored kernel
 // of buckets whose configuration has >= kCornerMinSlots slots.
 constexpr int kCornerMinSlots = 32;

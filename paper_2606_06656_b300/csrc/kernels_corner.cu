@@ -53,40 +53,25 @@ struct CornerQ {
   static constexpr int slot = QS == 4 ? 0 : QS == 8 ? 1 : 2;
 };
 
-// One root for one restart: u-products over the QS non-corner slots (FA:
-// u = 1 - i y t, else u = y + i t), scaled by z^QS; G_j = W times that.
+// One root for one restart: u-products over the QS non-corner slots (form F
+// of the factored roots, kernels.cuh), scaled by z^QS; G_j = W times that.
 // Adds Re(b' G_j) to fe, Re(c' G_j) to gF, Re(c' w^-j G_j) to gT and the
 // non-corner partials Re(c' W z^(QS-1) prod_{s' != s} u_s') to acc.
 // rt = {A, B, C, t} (w^j = (1 - 2B) + i 2C), zp = {z^QS, z^(QS-1)},
 // cf = {b', c'}.
-template <int QS, bool FA>
+template <int QS, int F>
 __device__ __forceinline__ void corner_root(const float4 rt, const float4 zp, const float4 cf,
                                             const float2 W, const float (&y)[QS],
                                             float (&acc)[QS], float& fe, float& gF, float& gT) {
   const float tk = rt.w;
   float pr[QS], pim[QS];
   float qr, qi;
-  if constexpr (FA) {
-    qr = 1.f;
-    qi = -y[0] * tk;
-  } else {
-    qr = y[0];
-    qi = tk;
-  }
+  fr_uinit<F>(qr, qi, y[0], tk);
 #pragma unroll
   for (int s = 1; s < QS; ++s) {
     pr[s] = qr;
     pim[s] = qi;
-    if constexpr (FA) {
-      const float w = y[s] * tk;
-      const float nr = fmaf(qi, w, qr), ni = fmaf(-qr, w, qi);
-      qr = nr;
-      qi = ni;
-    } else {
-      const float nr = fmaf(qr, y[s], -qi * tk), ni = fmaf(qi, y[s], qr * tk);
-      qr = nr;
-      qi = ni;
-    }
+    fr_umul<F>(qr, qi, y[s], tk);
   }
   const float2 Gj = cmul(W, cmul(make_float2(qr, qi), make_float2(zp.x, zp.y)));
   fe = fmaf(cf.x, Gj.x, fmaf(-cf.y, Gj.y, fe));
@@ -99,16 +84,7 @@ __device__ __forceinline__ void corner_root(const float4 rt, const float4 zp, co
   for (int s = QS - 1; s >= 1; --s) {
     acc[s] = fmaf(pr[s], hr, acc[s]);
     acc[s] = fmaf(-pim[s], hi, acc[s]);
-    if constexpr (FA) {
-      const float w = y[s] * tk;
-      const float a = fmaf(hi, w, hr), b = fmaf(-hr, w, hi);
-      hr = a;
-      hi = b;
-    } else {
-      const float a = fmaf(hr, y[s], -hi * tk), b = fmaf(hi, y[s], hr * tk);
-      hr = a;
-      hi = b;
-    }
+    fr_umul<F>(hr, hi, y[s], tk);
   }
   acc[0] += hr;
 }
@@ -119,7 +95,7 @@ template <int QS>
 __device__ __forceinline__ void corner_roots(int L, int J, int nnc, int t, const float4* rtab,
                                              const float4* ctab, const float4* ztab, float* my,
                                              float& fe, float& gF, float& gT) {
-  const int N = L + 1, nA = (L + 1) / 4;
+  const int N = L + 1, nA = fr_roots_form0(L), nB = fr_roots_form01(L);
   float y[QS], acc[QS];
 #pragma unroll
   for (int s = 0; s < QS; ++s) {
@@ -138,8 +114,9 @@ __device__ __forceinline__ void corner_roots(int L, int J, int nnc, int t, const
       W = make_float2(1.f - 2.f * e.y, low ? 2.f * e.z : -2.f * e.z);
     }
     const float4 rt = rtab[j], cf = ctab[j], zp = ztab[3 * j + CornerQ<QS>::slot];
-    if (j < nA) corner_root<QS, true>(rt, zp, cf, W, y, acc, fe, gF, gT);
-    else corner_root<QS, false>(rt, zp, cf, W, y, acc, fe, gF, gT);
+    if (j < nA) corner_root<QS, 0>(rt, zp, cf, W, y, acc, fe, gF, gT);
+    else if (j < nB) corner_root<QS, 1>(rt, zp, cf, W, y, acc, fe, gF, gT);
+    else corner_root<QS, 2>(rt, zp, cf, W, y, acc, fe, gF, gT);
     q += dq;
     if (q >= N) q -= N;
   }
@@ -151,34 +128,19 @@ __device__ __forceinline__ void corner_roots(int L, int J, int nnc, int t, const
 // restart's non-corner slots lam, lam + G, ...; QS per lane): u-products,
 // z^QS scaling, butterfly over the G lanes for the total and the other
 // lanes' product O, then as corner_root with W = w^(j t).  czq = c' z^(QS-1).
-template <int G, int QS, bool FA>
+template <int G, int QS, int F>
 __device__ __forceinline__ void group_root(const float4 rt, const float4 zp, const float4 cf,
                                            const float2 W, const float (&y)[QS],
                                            float (&acc)[QS], float& fe, float& gF, float& gT) {
   const float tk = rt.w;
   float pr[QS], pim[QS];
   float qr, qi;
-  if constexpr (FA) {
-    qr = 1.f;
-    qi = -y[0] * tk;
-  } else {
-    qr = y[0];
-    qi = tk;
-  }
+  fr_uinit<F>(qr, qi, y[0], tk);
 #pragma unroll
   for (int s = 1; s < QS; ++s) {
     pr[s] = qr;
     pim[s] = qi;
-    if constexpr (FA) {
-      const float w = y[s] * tk;
-      const float nr = fmaf(qi, w, qr), ni = fmaf(-qr, w, qi);
-      qr = nr;
-      qi = ni;
-    } else {
-      const float nr = fmaf(qr, y[s], -qi * tk), ni = fmaf(qi, y[s], qr * tk);
-      qr = nr;
-      qi = ni;
-    }
+    fr_umul<F>(qr, qi, y[s], tk);
   }
   float2 Pt = cmul(make_float2(qr, qi), make_float2(zp.x, zp.y));
   float2 O = make_float2(1.f, 0.f);
@@ -199,16 +161,7 @@ __device__ __forceinline__ void group_root(const float4 rt, const float4 zp, con
   for (int s = QS - 1; s >= 1; --s) {
     acc[s] = fmaf(pr[s], hr, acc[s]);
     acc[s] = fmaf(-pim[s], hi, acc[s]);
-    if constexpr (FA) {
-      const float w = y[s] * tk;
-      const float a = fmaf(hi, w, hr), b = fmaf(-hr, w, hi);
-      hr = a;
-      hi = b;
-    } else {
-      const float a = fmaf(hr, y[s], -hi * tk), b = fmaf(hi, y[s], hr * tk);
-      hr = a;
-      hi = b;
-    }
+    fr_umul<F>(hr, hi, y[s], tk);
   }
   acc[0] += hr;
 }
@@ -222,7 +175,7 @@ __device__ __forceinline__ void group_roots(int L, int J, int nnc_own, int t_own
                                             const float4* rtab, const float4* ctab,
                                             const float4* ztab, float* ncw, float* vals) {
   constexpr int QS = kCornerQS;
-  const int N = L + 1, nA = (L + 1) / 4;
+  const int N = L + 1, nA = fr_roots_form0(L), nB = fr_roots_form01(L);
   const int lam = lane % G;
 #pragma unroll 1
   for (int round = 0; round < G; ++round) {
@@ -247,8 +200,9 @@ __device__ __forceinline__ void group_roots(int L, int J, int nnc_own, int t_own
         W = make_float2(1.f - 2.f * e.y, low ? 2.f * e.z : -2.f * e.z);
       }
       const float4 rt = rtab[j], cf = ctab[j], zp = ztab[3 * j + CornerQ<QS>::slot];
-      if (j < nA) group_root<G, QS, true>(rt, zp, cf, W, y, acc, fe, gF, gT);
-      else group_root<G, QS, false>(rt, zp, cf, W, y, acc, fe, gF, gT);
+      if (j < nA) group_root<G, QS, 0>(rt, zp, cf, W, y, acc, fe, gF, gT);
+      else if (j < nB) group_root<G, QS, 1>(rt, zp, cf, W, y, acc, fe, gF, gT);
+      else group_root<G, QS, 2>(rt, zp, cf, W, y, acc, fe, gF, gT);
       q += dq;
       if (q >= N) q -= N;
     }

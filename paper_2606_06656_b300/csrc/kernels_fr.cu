@@ -8,16 +8,18 @@
 // With phi = pi j/(L+1) (half the root's angle), the Poisson-binomial factor
 // of Sec. 2.3's characteristic function is
 //     alpha + beta w^j = e^{i phi} (cos phi - i y sin phi) = z_j u_j(y),
-//     phi <= pi/4:  z = cos phi e^{i phi},         u = 1 - i y tan phi,
-//     phi >  pi/4:  z = sin phi e^{i(phi - pi/2)}, u = y + i cot phi,
-// so |u| <= sqrt 2 and a padding slot (y = 1) has z u = 1 exactly.  A lane's
+//     phi <= pi/4:           z = 1/(1 - i t), u = 1 - i y t,  t = tan phi,
+//     pi/4 < phi <= 0.42 pi: z = 1/(t + i),   u = y t + i,    t = tan phi,
+//     phi > 0.42 pi:         z = 1/(1 + i t), u = y + i t,    t = cot phi,
+// so |u| <= 4.02 and a padding slot (y = 1) has z u = 1 exactly.  A lane's
 // product of its Q factors is carried in u alone (3 FP32 operations per
-// complex product in the first form, 4 in the second, against 6 for the
+// complex product in the first two forms, 4 in the third, against 6 for the
 // factor alpha + beta w^j itself) and scaled once by z^Q; the products over
-// all lanes then equal G_j = prod_i (alpha_i + beta_i w^j) with no factor of
-// modulus above sqrt 2 ever accumulated, and the leave-one-out product for
-// literal i is O * z^(Q-1) * (the lane's u-products before and after i), O
-// the other lanes' scaled products.  z is defined from the FP32-rounded
+// all lanes then equal G_j = prod_i (alpha_i + beta_i w^j), and the
+// leave-one-out product for literal i is O * z^(Q-1) * (the lane's
+// u-products before and after i), O the other lanes' scaled products.
+// Products of up to 32 factors of modulus <= 4.02 stay far inside the FP32
+// range (and z^Q far above its underflow).  z is defined from the FP32-rounded
 // t itself (z = 1/u(1)), so padding is neutral up to one rounding of z^Q;
 // z^Q and z^(Q-1) come from an FP64 host table, c'_j z^(Q-1) is formed per
 // block in a prologue.  No division in the kernel.
@@ -86,9 +88,9 @@ struct FrGeom {
 
 // One root for one lane: forward u-products, scale by z^Q, butterfly over
 // the G lanes, FE term, backward sweep of the leave-one-out products into
-// acc.  FA selects the first factored form.  rt = {tan or cot phi, z^Q},
+// acc.  F selects the factored form (kernels.cuh).  rt = {t, z^Q},
 // cf = {b'_j, c'_j z^(Q-1)}.  Returns Re(b'_j G_j).
-template <int G, int Q, bool YS, bool FA>
+template <int G, int Q, bool YS, int F>
 __device__ __forceinline__ float fr_root(const float4 rt, const float4 cf,
                                          const float (&yreg)[YS ? 1 : Q], const float* ycol,
                                          float (&acc)[Q]) {
@@ -100,28 +102,12 @@ __device__ __forceinline__ float fr_root(const float4 rt, const float4 cf,
   const float tk = rt.x;
   float pr[Q], pim[Q];
   float qr, qi;
-  if constexpr (FA) {
-    qr = 1.f;
-    qi = -Y(0) * tk;
-  } else {
-    qr = Y(0);
-    qi = tk;
-  }
+  fr_uinit<F>(qr, qi, Y(0), tk);
 #pragma unroll
   for (int s = 1; s < Q; ++s) {
     pr[s] = qr;
     pim[s] = qi;
-    const float y = Y(s);
-    if constexpr (FA) {
-      const float w = y * tk;                     // (qr + i qi)(1 - i w)
-      const float nr = fmaf(qi, w, qr), ni = fmaf(-qr, w, qi);
-      qr = nr;
-      qi = ni;
-    } else {                                      // (qr + i qi)(y + i k)
-      const float nr = fmaf(qr, y, -qi * tk), ni = fmaf(qi, y, qr * tk);
-      qr = nr;
-      qi = ni;
-    }
+    fr_umul<F>(qr, qi, Y(s), tk);
   }
   // the lane's chunk times z^Q, then total (Pt) and others' product (O)
   float Ptr = qr * rt.y - qi * rt.z, Pti = qr * rt.z + qi * rt.y;
@@ -148,17 +134,7 @@ __device__ __forceinline__ float fr_root(const float4 rt, const float4 cf,
   for (int s = Q - 1; s >= 1; --s) {
     acc[s] = fmaf(pr[s], hr, acc[s]);
     acc[s] = fmaf(-pim[s], hi, acc[s]);
-    const float y = Y(s);
-    if constexpr (FA) {
-      const float w = y * tk;
-      const float a = fmaf(hi, w, hr), b = fmaf(-hr, w, hi);
-      hr = a;
-      hi = b;
-    } else {
-      const float a = fmaf(hr, y, -hi * tk), b = fmaf(hi, y, hr * tk);
-      hr = a;
-      hi = b;
-    }
+    fr_umul<F>(hr, hi, Y(s), tk);
   }
   acc[0] += hr;
   return val;
@@ -234,7 +210,7 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
 
   const int lam = lane % G;
   const int gi = lane / G;
-  const int nA = (L + 1) / 4;        // roots with phi <= pi/4 come first
+  const int nA = fr_roots_form0(L), nB = fr_roots_form01(L);   // root forms 0 | 1 | 2
   const float tailT = logf(2.f * (float)J) + kTailLogInvEps;
 #pragma unroll 1
   for (int pass = 0; pass < Geo::PASSES; ++pass) {
@@ -273,16 +249,18 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
       // algorithmic work of the roots each restart needs: 14 / 16 flops per
       // (literal, root) in the two factored forms (counted once per group)
       // (per group <= 1024 * 16 * 512 < 2^24, so the warp sum fits 32 bits)
-      const unsigned f = lam == 0 ? (unsigned)L * (14u * min(nA, jc) + 16u * max(0, jc - nA)) : 0u;
+      const unsigned f = lam == 0 ? (unsigned)L * (14u * min(nB, jc) + 16u * max(0, jc - nB)) : 0u;
       const unsigned tot = __reduce_add_sync(kFull, f);
       if (lane == 0) atomicAdd(flops, (unsigned long long)tot);
     }
     float val = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < min(nA, jw); ++j)
-      val += fr_root<G, Q, YS, true>(rs[j], cs[j], yreg, ycol, acc);
+    for (int j = 0; j < min(nA, jw); ++j) val += fr_root<G, Q, YS, 0>(rs[j], cs[j], yreg, ycol, acc);
 #pragma unroll 1
-    for (int j = nA; j < jw; ++j) val += fr_root<G, Q, YS, false>(rs[j], cs[j], yreg, ycol, acc);
+    for (int j = nA; j < min(nB, jw); ++j)
+      val += fr_root<G, Q, YS, 1>(rs[j], cs[j], yreg, ycol, acc);
+#pragma unroll 1
+    for (int j = nB; j < jw; ++j) val += fr_root<G, Q, YS, 2>(rs[j], cs[j], yreg, ycol, acc);
     // partials back into the staging slots (each slot is owned by one lane)
 #pragma unroll
     for (int s = 0; s < Q; ++s) {

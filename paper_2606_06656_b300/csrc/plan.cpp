@@ -354,18 +354,21 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
         float C = (float)(sn[j] * 0.5);
         // factored form, phi = theta_j / 2: alpha + beta w = e^{i phi}
         // (cos phi - i y sin phi) = z u(y) with
-        //   phi <= pi/4: z = cos phi e^{i phi} = 1/(1 - i t),  u = 1 - i y t,
-        //                t = tan phi
-        //   phi >  pi/4: z = sin phi e^{i(phi - pi/2)} = 1/(1 + i t),
-        //                u = y + i t,  t = cot phi
-        // (|u| <= sqrt 2 either way).  z is taken from the FP32-rounded t,
-        // so that z u(1) = 1 for the value the kernel multiplies by.
+        //   phi <= pi/4:         z = 1/(1 - i t),  u = 1 - i y t,  t = tan phi
+        //   pi/4 < phi <= 0.42pi: z = 1/(t + i),   u = y t + i,    t = tan phi
+        //   phi > 0.42 pi:       z = 1/(1 + i t),  u = y + i t,    t = cot phi
+        // (|u| <= 4.02 in the middle form, sqrt 2 in the others).  z is taken
+        // from the FP32-rounded t, so that z u(1) = 1 for the value the
+        // kernel multiplies by.
         const double ph = M_PI * (double)j / (double)N;
         const double c = (2 * j == N) ? 0.0 : std::cos(ph), s = std::sin(ph);
-        const bool formA = 4 * j <= N;
-        const float t32 = (float)(formA ? s / c : c / s);
+        // forms 0 / 1 / 2 (see the device helpers): t = tan phi, tan phi,
+        // cot phi; z = 1/u(1) = 1/(1 - i t), 1/(t + i), 1/(1 + i t)
+        const int form = (4 * j <= N) ? 0 : (50 * j <= 21 * N) ? 1 : 2;
+        const float t32 = (float)(form < 2 ? s / c : c / s);
         const double t = t32, den = 1.0 + t * t;
-        const double zr = 1.0 / den, zi = formA ? t / den : -t / den;
+        const double zr = form == 1 ? t / den : 1.0 / den;
+        const double zi = form == 0 ? t / den : -(form == 1 ? 1.0 : t) / den;
         P.root_tab.push_back({A, B, C, t32});
         double pr = 1.0, pi = 0.0;   // z^k, k = 0, 1, ...
         double prev_r = 1.0, prev_i = 0.0;

@@ -546,7 +546,8 @@ def test_batch_graph_equals_separate_steps(P):
 
 def test_dft_work_accounting(P):
     """cls_dft_work counts 20 flops per (literal, root) for the direct factor
-    and 14 / 16 for the two factored forms, over the DFT buckets."""
+    and 14 / 16 for the factored forms (14 in the two 3-operation forms),
+    over the DFT buckets."""
     from paper_2606_06656_b300 import binding as B
     rng = np.random.default_rng(3)
     rows = []
@@ -556,8 +557,9 @@ def test_dft_work_accounting(P):
     inst = W.build(400, rows)
     p = P(inst)
     lr = sum(L * ((L + 1) // 2) for L in (10, 37, 100, 301))
-    fr = sum(L * (14 * ((L + 1) // 4) + 16 * ((L + 1) // 2 - (L + 1) // 4))
-             for L in (10, 37, 100, 301))
+    def n01(L):          # roots in the two 3-operation forms: 50 j <= 21 (L + 1)
+        return min((L + 1) // 2, 21 * (L + 1) // 50)
+    fr = sum(L * (14 * n01(L) + 16 * ((L + 1) // 2 - n01(L))) for L in (10, 37, 100, 301))
     B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle), 3))
     assert B.cls_dft_work(p.handle) == (fr, lr)
     B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle), 1))
