@@ -34,6 +34,8 @@ struct DevPlan {
   int32_t n_ranges = 0;
   int32_t unit_weights = 0;          // every constraint weight is exactly 1
   unsigned long long* dft_flops = nullptr;   // flops of the evaluated DFT roots
+  int8_t* spec_tab = nullptr;        // spectra of the DFT constraints (+-1, t = 0..L)
+  int32_t* spec_off = nullptr;       // per constraint, -1 if not a DFT constraint
   uint32_t* satbits = nullptr;
   F4* root_tab = nullptr;
   F4* zpow_tab = nullptr;

@@ -18,11 +18,13 @@
 // non-corner values (at most kCornerQS; a warp that finds more in any lane
 // gives the tile to the dense kernel by clearing its flag) and keeps the
 // tile's classification of every literal as two ballots in shared memory.
-// Pass 2 runs every root over QS in {4, 8, 16} slots (padding y = 1, exactly
-// neutral in the factored form, as in kernels_fr.cu), with w^(j t) read from
-// the root table.  Pass 3 writes the partials of all literals and sets the
-// tile's flag, which tells the dense factored kernel launched next on the
-// stream to skip the tile.  Exact up to FP32 rounding; no division.
+// Pass 2: with at most 8 interior literals in every lane of the warp, an
+// exact small Poisson-binomial DP over them (corner_dp, no roots at all);
+// otherwise every root over 16 slots (padding y = 1, exactly neutral in the
+// factored form, as in kernels_fr.cu), with w^(j t) read from the root
+// table.  Pass 3 writes the partials of all literals and sets the tile's
+// flag, which tells the dense factored kernel launched next on the stream to
+// skip the tile.  Exact up to FP32 rounding; no division.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,12 +48,8 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// index of QS in kFrQ: 4 -> 2, 8 -> 4, 16 -> 8
-template <int QS>
-struct CornerQ {
-  static constexpr int zq = QS == 4 ? 2 : QS == 8 ? 4 : 8;
-  static constexpr int slot = QS == 4 ? 0 : QS == 8 ? 1 : 2;
-};
+// index of the 16-slot root powers in kFrQ
+constexpr int kCornerZq = 8;
 
 // One root for one restart: u-products over the QS non-corner slots (form F
 // of the factored roots, kernels.cuh), scaled by z^QS; G_j = W times that.
@@ -113,7 +111,7 @@ __device__ __forceinline__ void corner_roots(int L, int J, int nnc, int t, const
       const float4 e = rtab[(low ? q : N - q) - 1];
       W = make_float2(1.f - 2.f * e.y, low ? 2.f * e.z : -2.f * e.z);
     }
-    const float4 rt = rtab[j], cf = ctab[j], zp = ztab[3 * j + CornerQ<QS>::slot];
+    const float4 rt = rtab[j], cf = ctab[j], zp = ztab[j];
     if (j < nA) corner_root<QS, 0>(rt, zp, cf, W, y, acc, fe, gF, gT);
     else if (j < nB) corner_root<QS, 1>(rt, zp, cf, W, y, acc, fe, gF, gT);
     else corner_root<QS, 2>(rt, zp, cf, W, y, acc, fe, gF, gT);
@@ -122,6 +120,74 @@ __device__ __forceinline__ void corner_roots(int L, int J, int nnc, int t, const
   }
 #pragma unroll
   for (int s = 0; s < QS; ++s) my[s * 32] = acc[s];
+}
+
+// Pass 2 without roots, for at most QS <= 8 interior literals: with t true
+// corners T = t + T_int, and the restart's FE and partials are expectations
+// over the small Poisson-binomial distribution of the interior literals,
+//   FE = E[sp_T],  dFE/dy_i = E[d_{T_{-i}}],  d_s = (sp_s - sp_{s+1}) / 2,
+// a false corner's T_{-i} = t + T_int, a true corner's t - 1 + T_int.  The
+// prefix distributions are kept and an adjoint sweep gives the interior
+// partials (no division); padding slots are literals false with
+// probability 1.  Exact up to FP32 rounding of nonnegative terms.
+template <int QS>
+__device__ __forceinline__ void corner_dp(int L, int t, const int8_t* __restrict__ sp,
+                                          float* my, int nnc, float& fe, float& gF, float& gT) {
+  float al[QS], be[QS];
+#pragma unroll
+  for (int s = 0; s < QS; ++s) {
+    const float y = s < nnc ? my[s * 32] : 1.f;
+    al[s] = fmaf(0.5f, y, 0.5f);
+    be[s] = fmaf(-0.5f, y, 0.5f);
+  }
+  // spectrum values sp_{t-1 .. t+QS}; outside 0..L they never meet a
+  // nonzero probability except through d, which is 0 there
+  float sv[QS + 2];
+  bool ok[QS + 2];
+#pragma unroll
+  for (int a = 0; a < QS + 2; ++a) {
+    const int idx = t - 1 + a;
+    ok[a] = idx >= 0 && idx <= L;
+    sv[a] = ok[a] ? (float)sp[idx] : 0.f;
+  }
+  auto dv = [&](int a) -> float {       // d_{t - 1 + a}
+    return (ok[a] && ok[a + 1]) ? 0.5f * (sv[a] - sv[a + 1]) : 0.f;
+  };
+  // forward: pre[k] = distribution of interior literals 0..k-1 (support 0..k)
+  float pre[QS][QS], cur[QS + 1];
+  cur[0] = 1.f;
+#pragma unroll
+  for (int a = 1; a <= QS; ++a) cur[a] = 0.f;
+#pragma unroll
+  for (int k = 0; k < QS; ++k) {
+#pragma unroll
+    for (int a = 0; a <= k; ++a) pre[k][a] = cur[a];
+#pragma unroll
+    for (int a = k + 1; a >= 1; --a) cur[a] = fmaf(be[k], cur[a - 1], al[k] * cur[a]);
+    cur[0] *= al[k];
+  }
+  fe = 0.f;
+  gF = 0.f;
+  gT = 0.f;
+#pragma unroll
+  for (int a = 0; a <= QS; ++a) {
+    fe = fmaf(sv[a + 1], cur[a], fe);
+    gF = fmaf(dv(a + 1), cur[a], gF);
+    gT = fmaf(dv(a), cur[a], gT);
+  }
+  // adjoint: D(a) = E[d_{t + a + T_{k..}}], starting after the last literal
+  float D[QS];
+#pragma unroll
+  for (int a = 0; a < QS; ++a) D[a] = dv(a + 1);
+#pragma unroll
+  for (int k = QS - 1; k >= 0; --k) {
+    float g = 0.f;
+#pragma unroll
+    for (int a = 0; a <= k; ++a) g = fmaf(pre[k][a], D[a], g);
+    my[k * 32] = g;                     // the interior partial of slot k
+#pragma unroll
+    for (int a = 0; a < k; ++a) D[a] = fmaf(be[k], D[a + 1], al[k] * D[a]);
+  }
 }
 
 // One root for a group of G lanes sharing a restart (lane lam holds the
@@ -199,7 +265,7 @@ __device__ __forceinline__ void group_roots(int L, int J, int nnc_own, int t_own
         const float4 e = rtab[(low ? q : N - q) - 1];
         W = make_float2(1.f - 2.f * e.y, low ? 2.f * e.z : -2.f * e.z);
       }
-      const float4 rt = rtab[j], cf = ctab[j], zp = ztab[3 * j + CornerQ<QS>::slot];
+      const float4 rt = rtab[j], cf = ctab[j], zp = ztab[j];
       if (j < nA) group_root<G, QS, 0>(rt, zp, cf, W, y, acc, fe, gF, gT);
       else if (j < nB) group_root<G, QS, 1>(rt, zp, cf, W, y, acc, fe, gF, gT);
       else group_root<G, QS, 2>(rt, zp, cf, W, y, acc, fe, gF, gT);
@@ -230,16 +296,17 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
     const F4* __restrict__ root, const F4* __restrict__ zpow, const F4* __restrict__ coef,
     const LitRec* __restrict__ lit, const float* __restrict__ x, int R, int Rp, int RT,
     int maxL, float* __restrict__ P, float* __restrict__ fe_con, int ldf,
-    uint8_t* __restrict__ done) {
+    uint8_t* __restrict__ done, const int8_t* __restrict__ spec_tab,
+    const int32_t* __restrict__ spec_off) {
   extern __shared__ float4 cs4[];
   const FeItem it = fe[list[blockIdx.x]];
   const int L = it.L, J = it.J;
   const int JC = (maxL + 1) / 2;
   float4* rtab = cs4;                                         // [JC] {A, B, C, t}
   float4* ctab = rtab + JC;                                   // [JC] {b', c'}
-  float4* ztab = ctab + JC;                                   // [JC][3] QS = 4, 8, 16
+  float4* ztab = ctab + JC;                                   // [JC] {z^16, z^15}
   constexpr int CAP = GC * kCornerQS;                          // non-corner literals
-  float* ncy = reinterpret_cast<float*>(ztab + 3 * JC);      // [8][CAP][32]
+  float* ncy = reinterpret_cast<float*>(ztab + JC);          // [8][CAP][32]
   float* vals = ncy + 8 * CAP * 32;                           // [8][3][32] fe, gF, gT
   LitRec* recs = reinterpret_cast<LitRec*>(vals + 8 * 3 * 32);          // [maxL]
   uint32_t* flags = reinterpret_cast<uint32_t*>(recs + maxL);            // [8][maxL][2]
@@ -312,12 +379,9 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
     return;
   }
   for (int j = threadIdx.x; j < J; j += 256) {
-    const size_t zi = (size_t)(it.root_off + j) * kNumFrQ;
     rtab[j] = ldg4(&root[it.root_off + j]);
     ctab[j] = ldg4(&coef[it.coef_off + j]);
-    ztab[3 * j + 0] = ldg4(&zpow[zi + CornerQ<4>::zq]);
-    ztab[3 * j + 1] = ldg4(&zpow[zi + CornerQ<8>::zq]);
-    ztab[3 * j + 2] = ldg4(&zpow[zi + CornerQ<16>::zq]);
+    ztab[j] = ldg4(&zpow[(size_t)(it.root_off + j) * kNumFrQ + kCornerZq]);
   }
   __syncthreads();
   if (over) {
@@ -328,9 +392,15 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
   float fev, gF, gT;
   if constexpr (GC == 1) {
     const int qmax = __reduce_max_sync(kFull, nnc);
-    if (qmax <= 4) corner_roots<4>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
-    else if (qmax <= 8) corner_roots<8>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
-    else corner_roots<kCornerQS>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+    const int8_t* sp = spec_tab + spec_off[it.c];
+    if (qmax <= 8) {
+      // the DP gives FE itself; the write-out below adds the constant term
+      if (qmax <= 4) corner_dp<4>(L, t, sp, my, nnc, fev, gF, gT);
+      else corner_dp<8>(L, t, sp, my, nnc, fev, gF, gT);
+      fev -= it.b0;
+    } else {
+      corner_roots<kCornerQS>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
+    }
   } else {
     float* vw = vals + warp * 96;
     group_roots<GC>(L, J, nnc, t, lane, rtab, ctab, ztab, ncy + warp * CAP * 32, vw);
@@ -363,7 +433,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 size_t corner_smem_bytes(int maxL, int gc) {
   const int JC = (maxL + 1) / 2;
-  return (size_t)5 * JC * sizeof(float4) + (size_t)8 * gc * kCornerQS * 32 * sizeof(float) +
+  return (size_t)3 * JC * sizeof(float4) + (size_t)8 * gc * kCornerQS * 32 * sizeof(float) +
          (size_t)8 * 3 * 32 * sizeof(float) + (size_t)maxL * sizeof(LitRec) +
          (size_t)8 * 2 * maxL * sizeof(uint32_t);
 }
@@ -387,12 +457,12 @@ cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, 
   const dim3 grid(count, ceil_div(RT, 8)), block(256);
   k_fe_dft_corner<1><<<grid, block, corner_smem_bytes(maxL, 1), s>>>(
       list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
-      ldf, done);
+      ldf, done, d.spec_tab, d.spec_off);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_fe_dft_corner<kCornerGroup><<<grid, block, corner_smem_bytes(maxL, kCornerGroup), s>>>(
       list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
-      ldf, done);
+      ldf, done, d.spec_tab, d.spec_off);
   return cudaGetLastError();
 }
 

@@ -200,6 +200,8 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   // fixed real roots and their coefficients
   P.root_tab = {{0.5f, 0.5f, 0.f, 0.f}, {0.5f, -0.5f, 0.f, 0.f}, {0.f, 1.f, 0.f, 0.f}};
   P.zpow_tab.assign(P.root_tab.size() * kNumFrQ, F4{0.f, 0.f, 0.f, 0.f});
+  P.spec_tab.clear();
+  P.spec_off.assign(m, -1);
   P.coef_tab = {{2.f, 0.f, 1.f, 0.f},  {1.f, 0.f, 1.f, 0.f},   {2.f, 0.f, 1.f, 0.f},
                 {2.f, 0.f, -1.f, 0.f}, {-1.f, 0.f, -1.f, 0.f}, {-2.f, 0.f, -1.f, 0.f},
                 {-2.f, 0.f, 1.f, 0.f}};
@@ -325,6 +327,8 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
     }
     sp.swap(spf);   // the DFT below works on sp with L = Lf
     L = Lf;
+    P.spec_off[c] = (int32_t)P.spec_tab.size();
+    for (int tt = 0; tt <= L; ++tt) P.spec_tab.push_back((int8_t)sp[tt]);
     // DFT of the spectrum at the L+1 roots of unity, FP64 (Sec. 2.3):
     //   b_j = 1/(L+1) sum_t sp_t w^(-jt),  FE = sum_{j=0}^{L} b_j G_j with
     //   G_j = prod_i (alpha_i + beta_i w^j) (G_0 = 1).  b_{L+1-j} =

@@ -245,6 +245,10 @@ struct HostPlan {
   // factored configurations (kFrQ[q]), zpow_tab[r * kNumFrQ + q] =
   // {z'^Q, z'^(Q-1)} (see kFrQ)
   std::vector<F4> zpow_tab;
+  // spectra of the DFT constraints (after folding), +-1 per t = 0..L, at
+  // spec_off[c] (-1 for the others); the corner passes' exact small DP
+  std::vector<int8_t> spec_tab;
+  std::vector<int32_t> spec_off;
   std::vector<FeItem> thread_items[kNumThreadCls];   // items in launch order
   // lane-group buckets: [0, kNumDftBuckets) DFT, then real
   std::vector<int32_t> bucket_list[kNumDftBuckets + kNumRealBuckets];
