@@ -18,13 +18,16 @@
 // non-corner values (at most kCornerQS; a warp that finds more in any lane
 // gives the tile to the dense kernel by clearing its flag) and keeps the
 // tile's classification of every literal as two ballots in shared memory.
-// Pass 2: with at most 8 interior literals in every lane of the warp, an
-// exact small Poisson-binomial DP over them (corner_dp, no roots at all);
-// otherwise every root over 16 slots (padding y = 1, exactly neutral in the
-// factored form, as in kernels_fr.cu), with w^(j t) read from the root
-// table.  Pass 3 writes the partials of all literals and sets the tile's
-// flag, which tells the dense factored kernel launched next on the stream to
-// skip the tile.  Exact up to FP32 rounding; no division.
+// Pass 2, decided per warp from the largest interior count q: q <= 8, an
+// exact small Poisson-binomial DP over the interior literals that keeps its
+// prefix distributions (corner_dp); q <= 16 (and q <= 32 in the 4-lane
+// pass), the same DP without them, each literal's factor divided back out of
+// the distribution in the stable direction (corner_dpx), where that costs
+// less than the roots; otherwise every root over 16 slots (padding y = 1,
+// exactly neutral in the factored form, as in kernels_fr.cu), with w^(j t)
+// read from the root table.  Pass 3 writes the partials of all literals and
+// sets the tile's flag, which tells the dense factored kernel launched next
+// on the stream to skip the tile.  Exact up to FP32 rounding.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +41,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCornerQS = 16;   // non-corner slots per lane
 constexpr int kCornerGroup = 4; // lanes per restart in the second pass
+constexpr int kCornerDpx = 32;  // interior literals of the second pass's root-free DP
 
 __device__ __forceinline__ float4 ldg4(const F4* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -140,12 +144,12 @@ __device__ __forceinline__ void corner_dp(int L, int t, const int8_t* __restrict
     al[s] = fmaf(0.5f, y, 0.5f);
     be[s] = fmaf(-0.5f, y, 0.5f);
   }
-  // spectrum values sp_{t-1 .. t+QS}; outside 0..L they never meet a
-  // nonzero probability except through d, which is 0 there
-  float sv[QS + 2];
-  bool ok[QS + 2];
+  // spectrum values sp_{t-1 .. t+QS+1} (gF reads d_{t+QS}); outside 0..L
+  // they never meet a nonzero probability except through d, which is 0 there
+  float sv[QS + 3];
+  bool ok[QS + 3];
 #pragma unroll
-  for (int a = 0; a < QS + 2; ++a) {
+  for (int a = 0; a < QS + 3; ++a) {
     const int idx = t - 1 + a;
     ok[a] = idx >= 0 && idx <= L;
     sv[a] = ok[a] ? (float)sp[idx] : 0.f;
@@ -188,6 +192,86 @@ __device__ __forceinline__ void corner_dp(int L, int t, const int8_t* __restrict
 #pragma unroll
     for (int a = 0; a < k; ++a) D[a] = fmaf(be[k], D[a + 1], al[k] * D[a]);
   }
+}
+
+// Pass 2 without roots for up to NI interior literals, without keeping the
+// prefix distributions: P = the distribution of T_int over all interior
+// slots (padding literals are false with probability 1, so P vanishes above
+// nnc), FE and the corner partials as in corner_dp, and the leave-one-out
+// distribution of slot k by dividing its factor (alpha + beta z) back out of
+// P.  The division runs upwards, x_a = (P_a - beta x_{a-1}) / alpha, when
+// alpha >= beta, and downwards from the top, x_{a-1} = (P_a - alpha x_a) /
+// beta, otherwise: the ratio that multiplies a carried error is then at most
+// 1, so rounding errors add up over the NI cells instead of growing.  Both
+// start exactly (x_{-1} = 0, x_NI = 0).  qmax = the warp's largest nnc.
+template <int NI>
+__device__ __forceinline__ void corner_dpx(int L, int t, int qmax, const int8_t* __restrict__ sp,
+                                           float* my, int nnc, float& fe, float& gF, float& gT) {
+  float P[NI + 1];
+  P[0] = 1.f;
+#pragma unroll
+  for (int a = 1; a <= NI; ++a) P[a] = 0.f;
+#pragma unroll
+  for (int k = 0; k < NI; ++k) {
+    if (k >= qmax) break;
+    const float y = k < nnc ? my[k * 32] : 1.f;
+    const float al = fmaf(0.5f, y, 0.5f), be = fmaf(-0.5f, y, 0.5f);
+#pragma unroll
+    for (int a = k + 1; a >= 1; --a) P[a] = fmaf(be, P[a - 1], al * P[a]);
+    P[0] *= al;
+  }
+  // D[a] = d_{t-1+a}, a = 0..NI+1 (0 where the index leaves 0..L-1)
+  float D[NI + 2];
+  {
+    float sprev = t >= 1 ? (float)sp[t - 1] : 0.f;
+#pragma unroll
+    for (int a = 0; a <= NI + 1; ++a) {
+      const int i = t + a;                     // index of the upper spectrum value
+      const float snext = i <= L ? (float)sp[i] : 0.f;
+      D[a] = (i >= 1 && i <= L) ? 0.5f * (sprev - snext) : 0.f;
+      sprev = snext;
+    }
+  }
+  fe = 0.f;
+  gF = 0.f;
+  gT = 0.f;
+#pragma unroll
+  for (int a = 0; a <= NI; ++a) {
+    const int i = t + a;
+    fe = fmaf(i <= L ? (float)sp[i] : 0.f, P[a], fe);
+    gF = fmaf(D[a + 1], P[a], gF);
+    gT = fmaf(D[a], P[a], gT);
+  }
+#pragma unroll 1
+  for (int k = 0; k < qmax; ++k) {
+    const float y = k < nnc ? my[k * 32] : 1.f;
+    const float al = fmaf(0.5f, y, 0.5f), be = fmaf(-0.5f, y, 0.5f);
+    float g = 0.f;
+    if (al >= be) {
+      const float ia = 1.f / al, r = -be * ia;
+      float xv = 0.f;
+#pragma unroll
+      for (int a = 0; a < NI; ++a) {
+        xv = fmaf(r, xv, P[a] * ia);           // x_a
+        g = fmaf(D[a + 1], xv, g);
+      }
+    } else {
+      const float ib = 1.f / be, r = -al * ib;
+      float xv = 0.f;
+#pragma unroll
+      for (int a = NI; a >= 1; --a) {
+        xv = fmaf(r, xv, P[a] * ib);           // x_{a-1}
+        g = fmaf(D[a], xv, g);
+      }
+    }
+    if (k < nnc) my[k * 32] = g;
+  }
+}
+
+// Whether the root-free pass costs less than the roots: about NI (NI + 1) * 7
+// operations per restart against J roots over the pass's slots at 8 each.
+__device__ __forceinline__ bool dp_pays(int J, int ni, int slots) {
+  return ni * (ni + 1) * 7 <= J * slots * 8;
 }
 
 // One root for a group of G lanes sharing a restart (lane lam holds the
@@ -393,20 +477,29 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
   if constexpr (GC == 1) {
     const int qmax = __reduce_max_sync(kFull, nnc);
     const int8_t* sp = spec_tab + spec_off[it.c];
+    // the DPs give FE itself; the write-out below adds the constant term
     if (qmax <= 8) {
-      // the DP gives FE itself; the write-out below adds the constant term
       if (qmax <= 4) corner_dp<4>(L, t, sp, my, nnc, fev, gF, gT);
       else corner_dp<8>(L, t, sp, my, nnc, fev, gF, gT);
+      fev -= it.b0;
+    } else if (dp_pays(J, kCornerQS, kCornerQS)) {
+      corner_dpx<kCornerQS>(L, t, qmax, sp, my, nnc, fev, gF, gT);
       fev -= it.b0;
     } else {
       corner_roots<kCornerQS>(L, J, nnc, t, rtab, ctab, ztab, my, fev, gF, gT);
     }
   } else {
-    float* vw = vals + warp * 96;
-    group_roots<GC>(L, J, nnc, t, lane, rtab, ctab, ztab, ncy + warp * CAP * 32, vw);
-    fev = vw[lane];
-    gF = vw[32 + lane];
-    gT = vw[64 + lane];
+    const int qmax = __reduce_max_sync(kFull, nnc);
+    if (qmax <= kCornerDpx && dp_pays(J, kCornerDpx, CAP)) {
+      corner_dpx<kCornerDpx>(L, t, qmax, spec_tab + spec_off[it.c], my, nnc, fev, gF, gT);
+      fev -= it.b0;
+    } else {
+      float* vw = vals + warp * 96;
+      group_roots<GC>(L, J, nnc, t, lane, rtab, ctab, ztab, ncy + warp * CAP * 32, vw);
+      fev = vw[lane];
+      gF = vw[32 + lane];
+      gT = vw[64 + lane];
+    }
   }
   // pass 3: partials w * s_e * dFE/dy_e of every literal
   int k = 0;

@@ -593,6 +593,30 @@ def test_corner_dominated_points(P, kernel):
     check_against_oracle(inst, X2, *gpu_eval(P, inst, X2, kernel), floored=True)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_corner_pass_interior_counts(P, kernel):
+    """Tiles whose restarts keep from a few up to ~75 interior literals of
+    constraints of length 20..300 walk through every branch of the corner
+    passes: the exact small DPs (up to 8, 16 and 32 interior literals, the
+    larger two dividing a literal's factor back out of the distribution in
+    either direction), the roots over 16 and 64 slots, and the dense kernel.
+    Cardinality, exactly-k and random spectra (many nonzero differences)."""
+    rng = np.random.default_rng(31)
+    inst = W.random_constraint_set(rng, 700, 70, [W.TYPE_CARD_GE, W.TYPE_CARD_LE, W.TYPE_EK,
+                                                  W.TYPE_SPECTRUM], (20, 300), weights="rand")
+    fr = [0.995, 0.97, 0.95, 0.92, 0.88, 0.83, 0.75]
+    R = 32 * (len(fr) + 2)
+    frac = np.repeat(np.asarray(fr + [0.9, 0.9]), 32)
+    frac[32 * len(fr):32 * (len(fr) + 1)] = rng.uniform(0.75, 1.0, 32)   # lanes differ
+    X = corner_dominated_points(inst.n, R, frac[None, :], seed=7)
+    # last tile: interior values close to the corners (one factor nearly 0)
+    last = slice(32 * (len(fr) + 1), R)
+    inner = np.abs(X[:, last]) < 1.0
+    u = rng.uniform(1e-6, 1e-2, inner.sum()).astype(np.float32)
+    X[:, last][inner] = (np.sign(X[:, last][inner]) * (1.0 - u)).astype(np.float32)
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
+
+
 def test_dft_flops_counter_counts_truncated_work(P):
     """At uniform points long cardinality constraints need far fewer roots
     than J (the tail cutoff); at corner points every root is kept."""
