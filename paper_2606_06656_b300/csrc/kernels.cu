@@ -164,6 +164,117 @@ __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restri
   }
 }
 
+// global -> shared copy of 4 bytes without a register round trip
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// thread_body with the gathers of all kThreadTiles tiles issued up front as
+// cp.async copies into the warp's shared buffer (slot (tile, literal) at
+// xb[(tt * L + i) * 32 + lane]), so that kThreadTiles * L loads per thread
+// are in flight without holding registers; each literal record is read from
+// shared memory once (its variable for the copies, its destination kept in a
+// register for the tiles when L <= 8; longer constraints read it again per
+// tile).  Each thread reads back only what it copied itself.  Not for data written earlier in the same launch (the copies go
+// through L1).
+template <int L>
+__device__ __forceinline__ void thread_body_async(const FeItem& it, const F4* __restrict__ root,
+                                                  const F4* __restrict__ coef, const int2* trec,
+                                                  const float* __restrict__ x, int R, int Rp,
+                                                  int tile0, int lane, float* __restrict__ P,
+                                                  float* __restrict__ fe_con, int ldf,
+                                                  float* xb) {
+  const unsigned xs = (unsigned)R, ps = (unsigned)Rp;
+  constexpr bool kHold = L <= 8;
+  int32_t dst[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const int2 q = trec[i];
+    dst[i] = q.y;
+    const float* xv = x + (size_t)(unsigned)q.x * xs;
+#pragma unroll
+    for (int tt = 0; tt < kThreadTiles; ++tt) {
+      const int r = (tile0 + tt) * 32 + lane;
+      if (r < R) cp_async4(&xb[(tt * L + i) * 32 + lane], xv + r);
+    }
+  }
+  cp_async_commit();
+  const float4 rt0 = ldg4(&root[it.root_off]), cf0 = ldg4(&coef[it.coef_off]);
+  const bool two = it.J == 2;
+  const float4 rt1 = two ? ldg4(&root[it.root_off + 1]) : make_float4(1.f, 0.f, 0.f, 0.f);
+  const float4 cf1 = two ? ldg4(&coef[it.coef_off + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  cp_async_wait<0>();
+#pragma unroll 1
+  for (int tt = 0; tt < kThreadTiles; ++tt) {
+    const int r = (tile0 + tt) * 32 + lane;
+    if (r >= R) break;
+    float y[L], g[L], pre[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      if constexpr (!kHold) dst[i] = trec[i].y;   // re-read per tile, fewer registers
+      y[i] = rec_sgn(dst[i]) * xb[(tt * L + i) * 32 + lane];
+    }
+    float run = 1.f;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      pre[i] = run;
+      run *= fmaf(y[i], rt0.y, rt0.x);
+    }
+    float val = fmaf(cf0.x, run, it.b0);
+    float suf = cf0.z;
+#pragma unroll
+    for (int i = L - 1; i >= 0; --i) {
+      g[i] = pre[i] * suf;
+      suf *= fmaf(y[i], rt0.y, rt0.x);
+    }
+    if (two) {
+      run = 1.f;
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        pre[i] = run;
+        run *= fmaf(y[i], rt1.y, rt1.x);
+      }
+      val = fmaf(cf1.x, run, val);
+      suf = cf1.z;
+#pragma unroll
+      for (int i = L - 1; i >= 0; --i) {
+        g[i] = fmaf(pre[i], suf, g[i]);
+        suf *= fmaf(y[i], rt1.y, rt1.x);
+      }
+    }
+    float* pr = P + r;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      const int32_t d = kHold ? dst[i] : trec[i].y;
+      pr[(size_t)(unsigned)rec_row(d) * ps] = it.w * rec_sgn(d) * g[i];
+    }
+    if (fe_con) fe_con[(size_t)it.c * ldf + r] = val;
+  }
+}
+
+template <int LO, int HI>
+__device__ __forceinline__ void thread_dispatch_async(int L, const FeItem& it, const F4* root,
+                                                      const F4* coef, const int2* trec,
+                                                      const float* x, int R, int Rp, int tile0,
+                                                      int lane, float* P, float* fe_con, int ldf,
+                                                      float* xb) {
+  if constexpr (LO <= HI) {
+    if (L == LO)
+      thread_body_async<LO>(it, root, coef, trec, x, R, Rp, tile0, lane, P, fe_con, ldf, xb);
+    else
+      thread_dispatch_async<LO + 1, HI>(L, it, root, coef, trec, x, R, Rp, tile0, lane, P,
+                                        fe_con, ldf, xb);
+  }
+}
+
 template <int LO, int HI, bool CG = false>
 __device__ __forceinline__ void thread_dispatch(int L, const FeItem& it, const F4* root,
                                                 const F4* coef, const int2* trec,
@@ -178,21 +289,30 @@ __device__ __forceinline__ void thread_dispatch(int L, const FeItem& it, const F
   }
 }
 
+// Dynamic shared memory: 8 warps x kThreadTiles x HI x 32 floats (the staged
+// literal values).
 template <int LO, int HI>
 __global__ void __launch_bounds__(256) k_fe_thread(
     const FeItem* __restrict__ items, int count, const F4* __restrict__ root,
     const F4* __restrict__ coef, const LitRec* __restrict__ lit, const float* __restrict__ x,
     int R, int Rp, int RT, float* __restrict__ P, float* __restrict__ fe_con, int ldf) {
   __shared__ int2 trec_s[8][HI];
+  extern __shared__ float thread_xbuf[];
   const int lane = threadIdx.x;
   int2* trec = trec_s[threadIdx.y];
+  float* xb = thread_xbuf + (size_t)threadIdx.y * kThreadTiles * HI * 32;
   for (int ci = blockIdx.y * blockDim.y + threadIdx.y; ci < count; ci += gridDim.y * blockDim.y) {
     const FeItem it = items[ci];
     __syncwarp();
     load_trec(it, lit, trec, lane);
-    thread_dispatch<LO, HI>(it.L, it, root, coef, trec, x, R, Rp, RT, blockIdx.x * kThreadTiles,
-                            lane, P, fe_con, ldf);
+    thread_dispatch_async<LO, HI>(it.L, it, root, coef, trec, x, R, Rp,
+                                  blockIdx.x * kThreadTiles, lane, P, fe_con, ldf, xb);
   }
+}
+
+template <int HI>
+constexpr size_t thread_xbuf_bytes() {
+  return (size_t)8 * kThreadTiles * HI * 32 * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -966,6 +1086,12 @@ cudaError_t set_kernel_attributes() {
   if (err == cudaSuccess) err = set_fr_attributes();
   if (err == cudaSuccess) err = set_corner_attributes();
   if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_fe_thread<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)thread_xbuf_bytes<8>());
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_fe_thread<9, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)thread_xbuf_bytes<16>());
+  if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_fe_thread_ckpt<1, 16>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)ckpt_smem(1024, 1, 16));
@@ -1056,7 +1182,8 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
     HookScope hs(h, KC_THREAD, s);
     const FeItem* items = d.thread_items[t];
 #define CLS_THREAD_LAUNCH(LO, HI)                                                          \
-  k_fe_thread<LO, HI><<<grid, block, 0, s>>>(items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R, \
+  k_fe_thread<LO, HI><<<grid, block, thread_xbuf_bytes<HI>(), s>>>(                       \
+      items, cnt, d.root_tab, d.coef_tab, d.fe_lit, x, R,                                 \
                                              Rp, RT, P, fe_con, ldf);
     if (t == 0) {
       CLS_THREAD_LAUNCH(1, 8)
