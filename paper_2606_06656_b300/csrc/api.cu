@@ -344,6 +344,8 @@ int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const in
   up(H.fixed_val, &D.fixed_val);
   up(H.spec_tab, &D.spec_tab);
   up(H.spec_off, &D.spec_off);
+  up(H.ser_tab, &D.ser_tab);
+  up(H.ser_info, &D.ser_info);
   {
     // statistics: flops of the DFT roots the dense factored kernel evaluated
     const std::vector<unsigned long long> zero(1, 0ull);

@@ -21,8 +21,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcls_b300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["kernels.cu", "kernels_p2.cu", "kernels_fr.cu", "kernels_corner.cu", "api.cu",
-                "noalloc.cu", "mpnn.cu"]
+CUDA_SOURCES = ["kernels.cu", "kernels_p2.cu", "kernels_fr.cu", "kernels_corner.cu",
+                "kernels_series.cu", "api.cu", "noalloc.cu", "mpnn.cu"]
 CXX_SOURCES = ["plan.cpp"]
 
 

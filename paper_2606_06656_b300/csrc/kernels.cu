@@ -164,19 +164,6 @@ __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restri
   }
 }
 
-// global -> shared copy of 4 bytes without a register round trip
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // thread_body with the gathers of all kThreadTiles tiles issued up front as
 // cp.async copies into the warp's shared buffer (slot (tile, literal) at
 // xb[(tt * L + i) * 32 + lane]), so that kThreadTiles * L loads per thread
@@ -1085,6 +1072,7 @@ cudaError_t set_kernel_attributes() {
   if (err == cudaSuccess) err = set_p2_attributes();
   if (err == cudaSuccess) err = set_fr_attributes();
   if (err == cudaSuccess) err = set_corner_attributes();
+  if (err == cudaSuccess) err = set_series_attributes();
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_fe_thread<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)thread_xbuf_bytes<8>());
@@ -1146,10 +1134,13 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
   if (cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 3)
   {
     // factored configurations of kCornerMinSlots slots or more: the corner
-    // pass first (it flags the tiles it finished), then the dense kernel
+    // passes first (they flag the tiles they finished), then the power-sum
+    // pass on long constraints, then the dense kernel on what is left
     const bool corner = done && kGroupCfg[cfg].G * kGroupCfg[cfg].Q >= kCornerMinSlots;
     if (corner) {
       cudaError_t e = launch_dft_corner(d, list, count, maxL, R, Rp, x, P, fe_con, ldf, done, s);
+      if (e == cudaSuccess)
+        e = launch_dft_series(d, list, count, maxL, R, Rp, x, P, fe_con, ldf, done, s);
       if (e != cudaSuccess) return e;
     }
     return launch_group_fr(cfg, d, list, count, R, Rp, x, P, fe_con, ldf, corner ? done : nullptr,

@@ -36,6 +36,8 @@ struct DevPlan {
   unsigned long long* dft_flops = nullptr;   // flops of the evaluated DFT roots
   int8_t* spec_tab = nullptr;        // spectra of the DFT constraints (+-1, t = 0..L)
   int32_t* spec_off = nullptr;       // per constraint, -1 if not a DFT constraint
+  F4* ser_tab = nullptr;             // power-sum tables (plan.h, kSeriesK0)
+  SerInfo* ser_info = nullptr;       // per constraint
   uint32_t* satbits = nullptr;
   F4* root_tab = nullptr;
   F4* zpow_tab = nullptr;
@@ -78,6 +80,21 @@ __host__ __device__ inline int fr_roots_form01(int L) {
   const int J = (L + 1) / 2, n = 21 * (L + 1) / 50;
   return n < J ? n : J;
 }
+// Asynchronous global -> shared copies of 4 bytes (no register round trip):
+// issue, close a group, wait until at most N groups are pending.  A thread
+// sees its own copies after the wait.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <int F>
 __device__ __forceinline__ void fr_uinit(float& qr, float& qi, float y, float t) {
   if constexpr (F == 0) {
@@ -120,6 +137,12 @@ constexpr uint8_t kTileOpen = 0, kTileDone = 1, kTileDense = 2;
 cudaError_t set_corner_attributes();
 size_t corner_smem_bytes(int maxL, int gc);
 cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
+                              int Rp, const float* x, float* P, float* fe_con, int ldf,
+                              uint8_t* done, cudaStream_t s);
+// The power-sum pass (kernels_series.cu): after the corner passes, on the
+// tiles they left, for constraints of kSeriesMinL literals or more.
+cudaError_t set_series_attributes();
+cudaError_t launch_dft_series(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
                               int Rp, const float* x, float* P, float* fe_con, int ldf,
                               uint8_t* done, cudaStream_t s);
 cudaError_t launch_group_p2(int cfg, const DevPlan& d, const int32_t* list, int count, int R,

@@ -44,15 +44,6 @@ __device__ __forceinline__ float4 ldg4(const F4* p) {
 __device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
 __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
 
-// global -> shared copy of 4 bytes without a register round trip (sm_80+)
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -200,7 +191,8 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
       if (i < L && r < R) cp_async4(dst, &x[(size_t)lrec_s[i].var * R + r]);
       else *dst = 1.0f;
     }
-    cp_async_wait_all();
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     if (r < R)
       for (int i = warp; i < L; i += 8)

@@ -1,0 +1,274 @@
+// kernels_series.cu -- the low roots of long DFT constraints by power sums.
+//
+// FE = b0 + sum_j Re(b'_j G_j) and dFE/dy_i = sum_j Re(b'_j G_j dlog F_ij /
+// dy_i) (the Fourier form of the expansion, Sec. 2.3), G_j = prod_i F_ij,
+// F_ij = alpha_i + beta_i w^j.  Expanding each factor about the centre c of
+// its half of the cube (c = 1/2 for y >= 0, -1/2 for y < 0; d = |y| - 1/2,
+// y - c = +-d):
+//   F_j(y)            = F_j(c) (1 + (y - c) z_c),   z_c = (1 - w^j) / (2 F_j(c))
+//   log F_j(y)        = log F_j(c) + sum_{k>=1} E_{k-1} (y - c)^k / k
+//   dlog F_j(y) / dy  = sum_{k>=0} E_k (y - c)^k,    E_k = (-1)^k z_c^(k+1),
+// so with the power sums M+_k = sum_{y>=0, interior} d^k, M-_k = sum_{y<0,
+// interior} (-d)^k (interior: |y| < 1)
+//   log G_j = n+ log F_j(1/2) + n- log F_j(-1/2) + i theta_j n_true
+//             + sum_k E+_{k-1} M+_k / k + E-_{k-1} M-_k / k,
+// (a literal at a corner contributes log 1 = 0 or log w^j = i theta_j
+// exactly) and every literal's partial is a polynomial in d:
+//   dFE/dy_i = sum_k d^k C_k,   C_k = Re sum_j b'_j G_j E+_k   (y_i >= 0)
+//                                     (-1)^k Re sum_j b'_j G_j E-_k (y_i < 0).
+// The series have ratio rho_j = sin phi_j / (2 sqrt(1 - 3/4 sin^2 phi_j));
+// the host keeps, per length, the roots whose truncation after K terms is
+// bounded by 2^-24 (plan.cpp, series_roots).  The cost per restart is about
+// 5K per literal and 8K per root instead of 7 per (literal, root).
+//
+// One thread per (constraint, restart), a warp per tile of 32 restarts, a
+// block per constraint and 8 tiles.  Pass A computes the tail cutoff of
+// kernels_fr.cu (S = sum (1 - y^2) / 4); a tile whose largest cutoff lies in
+// the range of 16 (else 24) terms is taken, any other is left to the dense
+// factored kernel.  Pass B forms the power sums, the root loop G_j and the
+// coefficients C_k, pass C the partials; the tile's flag is then set to done.
+// Phases: arg F_j(+-1/2) and theta_j are tabulated as uint32 fractions of a
+// turn, so n arg mod 2 pi is an exact integer product (error <= n/2 2^-32
+// turns); sincosf only sees that plus the series' part.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace cls {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kTailLogInvEps = 20.80f;          // as in kernels_fr.cu
+constexpr float kTwoPiOver2p32 = 1.4629180792671596e-9f;
+
+__device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
+// a table row entry from shared memory, loaded where it is used (volatile, so
+// that the compiler does not keep a root's K entries live across both loops)
+__device__ __forceinline__ float4 lds4(const float4* p) {
+  float4 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
+
+// one restart's K-term pass: power sums, the root loop over jw roots, the
+// partials of all L literals (written to P) and FE - b0 (returned)
+template <int K>
+__device__ __forceinline__ float series_restart(int L, int jw, const LitRec* recs,
+                                                const float* xr, int R, bool act,
+                                                const float4* tab, const float2* bsm,
+                                                float* __restrict__ P, int Rp, int r, float wgt) {
+  // pass B: power sums of d over the interior literals of each half
+  float Mp[K], Mm[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) Mp[k] = Mm[k] = 0.f;
+  uint32_t np = 0, nn = 0, nt = 0;
+  for (int i0 = 0; i0 < L; i0 += 4) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const LitRec rc = recs[min(i0 + u, L - 1)];
+      v[u] = act ? rec_sgn(rc.dst) * xr[(size_t)rc.var * R] : 1.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (i0 + u >= L) break;
+      const float y = v[u], a = fabsf(y);
+      const bool corner = a == 1.f, neg = y < 0.f;
+      nt += (corner && neg) ? 1u : 0u;
+      np += (!corner && !neg) ? 1u : 0u;
+      nn += (!corner && neg) ? 1u : 0u;
+      const float d = corner ? 0.f : a - 0.5f;
+      const float mn = neg ? 1.f : 0.f, mp = 1.f - mn;   // the literal's half
+      float p = d;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        Mp[k] = fmaf(mp, p, Mp[k]);
+        Mm[k] = fmaf(mn, p, Mm[k]);
+        p *= d;
+      }
+    }
+  }
+  // M+_k / k and M-_k / k, M-_k = (-1)^k sum_{y<0} d^k (array index k - 1)
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float inv = 1.0f / (float)(k + 1);
+    Mp[k] *= inv;
+    Mm[k] *= (k & 1) ? inv : -inv;
+  }
+  // roots: log G_j, G_j, w = b'_j G_j, FE and C_k
+  float Cp[K], Cm[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) Cp[k] = Cm[k] = 0.f;
+  float fe = 0.f;
+  const float fnp = (float)np, fnn = (float)nn;
+#pragma unroll 1
+  for (int j = 0; j < jw; ++j) {
+    const float4* row = tab + j * kSerRow;
+    const float4 h0 = row[0], h1 = row[1];
+    const uint32_t turns = np * __float_as_uint(h0.z) + nn * __float_as_uint(h0.w) +
+                           nt * __float_as_uint(h1.x);
+    float lr = fmaf(fnp, h0.x, fnn * h0.y), li = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float4 e = lds4(row + 2 + k);
+      lr = fmaf(e.x, Mp[k], lr);
+      li = fmaf(e.y, Mp[k], li);
+      lr = fmaf(e.z, Mm[k], lr);
+      li = fmaf(e.w, Mm[k], li);
+    }
+    float sn, cs;
+    sincosf(fmaf((float)(int32_t)turns, kTwoPiOver2p32, li), &sn, &cs);
+    const float mag = expf(lr);
+    const float2 b = bsm[j];
+    const float gr = mag * cs, gi = mag * sn;
+    const float wr = fmaf(b.x, gr, -b.y * gi), wi = fmaf(b.x, gi, b.y * gr);
+    fe += wr;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float4 e = lds4(row + 2 + k);
+      Cp[k] = fmaf(e.x, wr, fmaf(-e.y, wi, Cp[k]));
+      Cm[k] = fmaf(e.z, wr, fmaf(-e.w, wi, Cm[k]));
+    }
+  }
+#pragma unroll
+  for (int k = 1; k < K; k += 2) Cm[k] = -Cm[k];
+  // pass C: partials, Horner in d with the coefficients of the literal's half
+  for (int i0 = 0; i0 < L; i0 += 4) {
+    float v[4];
+    LitRec rcs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      rcs[u] = recs[min(i0 + u, L - 1)];
+      v[u] = act ? rec_sgn(rcs[u].dst) * xr[(size_t)rcs[u].var * R] : 1.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (i0 + u >= L) break;
+      const float y = v[u], d = fabsf(y) - 0.5f;
+      const bool neg = y < 0.f;
+      float g = neg ? Cm[K - 1] : Cp[K - 1];
+#pragma unroll
+      for (int k = K - 2; k >= 0; --k) g = fmaf(g, d, neg ? Cm[k] : Cp[k]);
+      if (act) P[(size_t)rec_row(rcs[u].dst) * Rp + r] = wgt * rec_sgn(rcs[u].dst) * g;
+    }
+  }
+  return fe;
+}
+
+// Dynamic shared memory: kSeriesMaxRoots * kSerRow float4 (rows), as many
+// float2 (b'_j), maxL LitRec.
+__global__ void __launch_bounds__(256, 2) k_fe_series(
+    const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
+    const F4* __restrict__ coef, const F4* __restrict__ ser_tab,
+    const SerInfo* __restrict__ ser_info, const LitRec* __restrict__ lit,
+    const float* __restrict__ x, int R, int Rp, int RT, float* __restrict__ P,
+    float* __restrict__ fe_con, int ldf, uint8_t* __restrict__ done,
+    unsigned long long* __restrict__ flops) {
+  extern __shared__ float4 ss4[];
+  float4* tab = ss4;                                                  // [96][kSerRow]
+  float2* bsm = reinterpret_cast<float2*>(tab + kSeriesMaxRoots * kSerRow);  // [96]
+  LitRec* recs = reinterpret_cast<LitRec*>(bsm + kSeriesMaxRoots);    // [maxL]
+  __shared__ int jneed_s[8];
+  const int ci = list[blockIdx.x];
+  const SerInfo si = ser_info[ci];
+  if (si.off < 0) return;
+  const FeItem it = fe[ci];
+  const int L = it.L, J = it.J;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.y * 8 + warp;
+  const bool live = tile < RT;
+  const bool mine = live && done[(size_t)ci * RT + tile] != kTileDone;
+  if (!__syncthreads_or(mine)) return;
+  for (int i = threadIdx.x; i < L; i += 256) recs[i] = lit[it.lit0 + i];
+  __syncthreads();
+  const int r = (live ? tile : RT - 1) * 32 + lane;
+  const bool act = r < R;
+  const float* xr = x + (act ? r : R - 1);
+  // pass A: the tail cutoff (as in kernels_fr.cu) and the terms it needs
+  int jw = 0, K = 0;
+  if (mine) {
+    float S = 0.f;
+    for (int i0 = 0; i0 < L; i0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = act ? xr[(size_t)recs[min(i0 + u, L - 1)].var * R] : 1.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u < L) S = fmaf(-0.25f * v[u], v[u], S + 0.25f);
+    }
+    int jc = J;
+    const float S1 = S - 0.25f;
+    if (S1 > 0.f) {
+      const float q = (logf(2.f * (float)J) + kTailLogInvEps) / (2.f * S1);
+      if (q < 1.f)
+        jc = min(J, (int)ceilf(asinf(sqrtf(q)) * (float)(L + 1) * 0.318309886f) + 1);
+    }
+    jw = __reduce_max_sync(kFull, act ? jc : 0);
+    K = jw <= si.js0 ? kSeriesK0 : (jw <= si.js1 ? kSeriesK1 : 0);
+  }
+  if (lane == 0) jneed_s[warp] = K ? jw : 0;
+  __syncthreads();
+  int jb = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) jb = max(jb, jneed_s[w]);
+  if (jb == 0) return;
+  for (int e = threadIdx.x; e < jb * kSerRow; e += 256)
+    tab[e] = *reinterpret_cast<const float4*>(&ser_tab[si.off + e]);
+  for (int j = threadIdx.x; j < jb; j += 256) {
+    const F4 cf = coef[it.coef_off + j];
+    bsm[j] = make_float2(cf.x, cf.y);
+  }
+  __syncthreads();
+  if (K == 0) return;
+  float fev;
+  if (K == kSeriesK0)
+    fev = series_restart<kSeriesK0>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w);
+  else
+    fev = series_restart<kSeriesK1>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w);
+  if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;
+  // (K is uniform over the warp, so every lane is here)
+  const unsigned nact = (unsigned)__popc(__ballot_sync(kFull, act));
+  if (flops && lane == 0) {
+    // per restart: L (4 + 6K) for the passes, jw (16K + 40) for the roots
+    const unsigned long long per = (unsigned long long)L * (4 + 6 * K) +
+                                   (unsigned long long)jw * (16 * K + 40);
+    atomicAdd(flops, per * (unsigned long long)nact);
+  }
+  __syncwarp();
+  if (lane == 0) done[(size_t)ci * RT + tile] = kTileDone;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+size_t series_smem_bytes(int maxL) {
+  return (size_t)kSeriesMaxRoots * kSerRow * sizeof(float4) +
+         (size_t)kSeriesMaxRoots * sizeof(float2) + (size_t)maxL * sizeof(LitRec);
+}
+
+}  // namespace
+
+cudaError_t set_series_attributes() {
+  return cudaFuncSetAttribute(k_fe_series, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)series_smem_bytes(1024));
+}
+
+cudaError_t launch_dft_series(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
+                              int Rp, const float* x, float* P, float* fe_con, int ldf,
+                              uint8_t* done, cudaStream_t s) {
+  if (count == 0 || R == 0 || maxL < kSeriesMinL || !d.ser_info) return cudaSuccess;
+  const int RT = ceil_div(R, 32);
+  const dim3 grid(count, ceil_div(RT, 8)), block(256);
+  k_fe_series<<<grid, block, series_smem_bytes(maxL), s>>>(
+      list, d.fe, d.coef_tab, d.ser_tab, d.ser_info, d.fe_lit, x, R, Rp, RT, P, fe_con, ldf,
+      done, d.dft_flops);
+  return cudaGetLastError();
+}
+
+}  // namespace cls

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -118,6 +119,62 @@ void assign_groups(HostPlan* P, const Tuning& tun) {
   for (auto& v : P->bucket_list) std::stable_sort(v.begin(), v.end(), byL);
 }
 
+// Roots in range of the power-sum pass with K terms (see kSeriesK0): the
+// largest js such that for every root j <= js both truncation bounds hold,
+//   L rho^(K+1) / ((K+1)(1 - rho)) <= 2^-24   (log G_j, relative to G_j)
+//   (1 + rho) rho^K / (1 - rho)      <= 2^-24   (each literal's partial)
+// with rho = sin phi / (2 sqrt(1 - 3/4 sin^2 phi)), phi = pi j / (L + 1)
+// (rho grows with j below the middle root).
+static int series_roots(int L, int K) {
+  const int N = L + 1;
+  const double eps = std::ldexp(1.0, -24);
+  int js = 0;
+  for (int j = 1; 2 * j < N && j <= kSeriesMaxRoots; ++j) {
+    const double s = std::sin(M_PI * (double)j / (double)N);
+    const double rho = 0.5 * s / std::sqrt(1.0 - 0.75 * s * s);
+    const double tl = (double)L * std::pow(rho, K + 1) / ((double)(K + 1) * (1.0 - rho));
+    const double td = (1.0 + rho) * std::pow(rho, K) / (1.0 - rho);
+    if (tl > eps || td > eps) break;
+    js = j;
+  }
+  return js;
+}
+
+// a fraction of a turn as a uint32 (mod 2^32), stored in a float's bits
+static float turn_bits(double turns) {
+  double f = turns - std::floor(turns);
+  uint64_t q = (uint64_t)std::llround(f * 4294967296.0);
+  uint32_t u = (uint32_t)(q & 0xffffffffull);
+  float out;
+  std::memcpy(&out, &u, sizeof(out));
+  return out;
+}
+
+// Appends the power-sum rows of length L (root j = 1..js1, see kSeriesK0).
+static SerInfo series_table(int L, std::vector<F4>& tab) {
+  SerInfo si{-1, series_roots(L, kSeriesK0), series_roots(L, kSeriesK1), 0};
+  if (si.js1 == 0) return SerInfo{-1, 0, 0, 0};
+  si.off = (int32_t)tab.size();
+  const int N = L + 1;
+  for (int j = 1; j <= si.js1; ++j) {
+    const double th = 2.0 * M_PI * (double)j / (double)N;
+    const std::complex<double> w(std::cos(th), std::sin(th));
+    const std::complex<double> Fp = (3.0 + w) / 4.0, Fm = (1.0 + 3.0 * w) / 4.0;
+    const std::complex<double> dF = (1.0 - w) / 2.0;        // dF/dy
+    const std::complex<double> zp = dF / Fp, zm = dF / Fm;
+    tab.push_back({(float)std::log(std::abs(Fp)), (float)std::log(std::abs(Fm)),
+                   turn_bits(std::arg(Fp) / (2.0 * M_PI)), turn_bits(std::arg(Fm) / (2.0 * M_PI))});
+    tab.push_back({turn_bits((double)j / (double)N), 0.f, 0.f, 0.f});
+    std::complex<double> ep = zp, em = zm;                  // E_0 = z
+    for (int k = 0; k < kSeriesK1; ++k) {
+      tab.push_back({(float)ep.real(), (float)ep.imag(), (float)em.real(), (float)em.imag()});
+      ep *= -zp;
+      em *= -zm;
+    }
+  }
+  return si;
+}
+
 int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_var,
                const int8_t* lit_sign, const int32_t* type, const int32_t* kk,
                const float* weight, const int8_t* spectra, const uint8_t* fixed,
@@ -202,6 +259,8 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   P.zpow_tab.assign(P.root_tab.size() * kNumFrQ, F4{0.f, 0.f, 0.f, 0.f});
   P.spec_tab.clear();
   P.spec_off.assign(m, -1);
+  P.ser_tab.clear();
+  P.ser_info.assign(m, SerInfo{-1, 0, 0, 0});
   P.coef_tab = {{2.f, 0.f, 1.f, 0.f},  {1.f, 0.f, 1.f, 0.f},   {2.f, 0.f, 1.f, 0.f},
                 {2.f, 0.f, -1.f, 0.f}, {-1.f, 0.f, -1.f, 0.f}, {-2.f, 0.f, -1.f, 0.f},
                 {-2.f, 0.f, 1.f, 0.f}};
@@ -209,6 +268,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   std::vector<LitRec> fe_lit_tmp;      // FE literals: var, sign bit (rows later)
   fe_lit_tmp.reserve(nnz);
   std::map<int, int> root_of_len;
+  std::map<int, SerInfo> ser_of_len;
   std::map<std::pair<int, std::string>, int> coef_of_spec;
 
   P.fe.resize(m);
@@ -417,6 +477,11 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
       cit = coef_of_spec.emplace(std::make_pair(L, key), off).first;
     }
     it.coef_off = cit->second;
+    if (L >= kSeriesMinL) {
+      auto sit = ser_of_len.find(L);
+      if (sit == ser_of_len.end()) sit = ser_of_len.emplace(L, series_table(L, P.ser_tab)).first;
+      P.ser_info[c] = sit->second;
+    }
     P.dft_roots += J;
     P.dft_lroots += (int64_t)J * L;
   }

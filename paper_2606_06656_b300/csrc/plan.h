@@ -177,6 +177,28 @@ constexpr int kNumGroupCfg = 99;
 // rounded to FP32, and z' = 1/(1 - i t) or 1/(1 + i t) is the root constant
 // that makes a padding slot (y = 1) exactly neutral for that rounded t; its
 // powers are formed in FP64 and rounded once.
+// Power-sum (series) pass for the low roots of long DFT constraints: every
+// factor alpha + beta w^j = F_j(c) (1 + (y - c) z_c) is expanded about the
+// centre c = +1/2 (y >= 0) or -1/2 (y < 0), |y - c| <= 1/2, so log G_j and
+// the partials are series in (y - c) of ratio rho_j = sin(phi_j) / (2 sqrt(1
+// - 3/4 sin^2 phi_j)), phi_j = pi j / (L + 1).  A root is in the range of K
+// terms when both truncation bounds (the log series over L literals, the
+// derivative series) are at most 2^-24.  Per length L the table holds, for
+// root j = 1..kSeriesK1-range, kSerRow float4: {ln|F_j(1/2)|, ln|F_j(-1/2)|,
+// arg F_j(1/2), arg F_j(-1/2)} (arguments as uint32 fractions of a turn),
+// {j/(L+1) as a uint32 fraction of a turn, 0, 0, 0}, then for k = 0..K1-1
+// {E+_k, E-_k} with E_k = (-1)^k z_c^(k+1).
+constexpr int kSeriesK0 = 16, kSeriesK1 = 24;
+constexpr int kSeriesMaxRoots = 96;   // rows a block stages
+constexpr int kSeriesMinL = 64;       // shorter constraints keep the root products
+constexpr int kSerRow = 2 + kSeriesK1;
+struct SerInfo {
+  int32_t off;    // first row in ser_tab, -1 if the constraint has none
+  int32_t js0;    // roots in range of kSeriesK0 terms
+  int32_t js1;    // roots in range of kSeriesK1 terms
+  int32_t pad;
+};
+
 constexpr int kNumFrQ = 14;
 constexpr int kFrQ[kNumFrQ] = {1, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32};
 // Configuration id of the restart-parallel checkpointed kernel for real-root
@@ -249,6 +271,9 @@ struct HostPlan {
   // spec_off[c] (-1 for the others); the corner passes' exact small DP
   std::vector<int8_t> spec_tab;
   std::vector<int32_t> spec_off;
+  // power-sum tables of the DFT constraints (see kSeriesK0), per constraint
+  std::vector<F4> ser_tab;
+  std::vector<SerInfo> ser_info;
   std::vector<FeItem> thread_items[kNumThreadCls];   // items in launch order
   // lane-group buckets: [0, kNumDftBuckets) DFT, then real
   std::vector<int32_t> bucket_list[kNumDftBuckets + kNumRealBuckets];
