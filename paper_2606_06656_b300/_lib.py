@@ -37,6 +37,7 @@ SIGNATURES = {
     "cls_grid_barrier_check": (i32, [i32, i32, u32, vp, sz, P(i32), P(i32)]),
     "cls_dft_work": (i32, [vp, P(i64)]),
     "cls_dft_flops_counter": (i32, [vp, P(i64), i32]),
+    "cls_series_range": (i32, [i32, i32]),
     "cls_solve_host_workspace_size": (i32, [vp, i32, P(sz)]),
     "cls_solve_host": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, sz, vp]),
     "cls_autotune": (i32, [vp, i32, vp, i32, vp, sz, vp]),

@@ -305,6 +305,15 @@ def cls_dft_work(h):
     return int(out[0]), int(out[1])
 
 
+def cls_series_range(L, K):
+    """Low roots j = 1..js of a length-L constraint in range of the power-sum
+    pass with K terms (host-only)."""
+    js = _lib.load().cls_series_range(int(L), int(K))
+    if js < 0:
+        _lib.check(js, "cls_series_range")
+    return int(js)
+
+
 def cls_dft_flops_counter(h, reset=False):
     """Flops of the DFT roots evaluated by the dense factored kernel since the
     last reset (synchronises the device)."""

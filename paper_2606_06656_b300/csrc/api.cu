@@ -416,6 +416,11 @@ int cls_dft_flops_counter(cls_problem* p, int64_t* flops, int32_t reset) {
   return CLS_OK;
 }
 
+int cls_series_range(int32_t L, int32_t K) {
+  if (L < 1 || K < 1) return set_err(CLS_ERR_INVALID, "L and K must be >= 1");
+  return cls::series_roots(L, K);
+}
+
 int cls_workspace_size(const cls_problem* p, int32_t R, size_t* bytes) {
   int rc = check_R(p, R);
   if (rc != CLS_OK) return rc;

@@ -132,8 +132,9 @@ __device__ __forceinline__ void fr_umul(float& qr, float& qi, float y, float t) 
 constexpr int kCornerMinSlots = 32;
 // per-(constraint, tile) flag values: open (the next pass may try), done
 // (partials written; later passes and the dense kernel skip it), dense
-// (left to the dense kernel)
-constexpr uint8_t kTileOpen = 0, kTileDone = 1, kTileDense = 2;
+// (left to the dense kernel), low (the power-sum pass wrote the terms of the
+// roots 1..js1 of kernels_series.cu; the dense kernel adds the others)
+constexpr uint8_t kTileOpen = 0, kTileDone = 1, kTileDense = 2, kTileLow = 3;
 cudaError_t set_corner_attributes();
 size_t corner_smem_bytes(int maxL, int gc);
 cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,

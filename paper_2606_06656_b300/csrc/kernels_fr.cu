@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
     const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
     float* __restrict__ fe_con, int ldf, const uint8_t* __restrict__ done,
-    unsigned long long* __restrict__ flops) {
+    const SerInfo* __restrict__ ser_info, unsigned long long* __restrict__ flops) {
   using Geo = FrGeom<G>;
   constexpr int LS = G * Q;
   constexpr int JC = FrCap<G, Q>::JC;
@@ -161,7 +161,12 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   // a tile the corner pass has finished (kernels_corner.cu); the flag is
   // indexed by the constraint id, which is also the FE item's index
   const int ci = list[blockIdx.x];
-  if (done && done[(size_t)ci * gridDim.y + blockIdx.y] == kTileDone) return;
+  const uint8_t tflag = done ? done[(size_t)ci * gridDim.y + blockIdx.y] : kTileOpen;
+  if (tflag == kTileDone) return;
+  // a tile whose low roots the power-sum pass evaluated: start after them and
+  // add to its partials and FE
+  const bool low = tflag == kTileLow;
+  const int j0 = low ? ser_info[ci].js1 : 0;
   const FeItem it = fe[ci];
   const int L = it.L, J = it.J;
   const int r0 = blockIdx.y * 32;
@@ -241,25 +246,30 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
       // algorithmic work of the roots each restart needs: 14 / 16 flops per
       // (literal, root) in the two factored forms (counted once per group)
       // (per group <= 1024 * 16 * 512 < 2^24, so the warp sum fits 32 bits)
-      const unsigned f = lam == 0 ? (unsigned)L * (14u * min(nB, jc) + 16u * max(0, jc - nB)) : 0u;
+      const int jl = min(jc, j0);   // roots the power-sum pass took
+      const unsigned f = lam == 0 ? (unsigned)L * (14u * (min(nB, jc) - min(nB, jl)) +
+                                                   16u * (max(0, jc - nB) - max(0, jl - nB)))
+                                  : 0u;
       const unsigned tot = __reduce_add_sync(kFull, f);
       if (lane == 0) atomicAdd(flops, (unsigned long long)tot);
     }
     float val = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < min(nA, jw); ++j) val += fr_root<G, Q, YS, 0>(rs[j], cs[j], yreg, ycol, acc);
+    for (int j = j0; j < min(nA, jw); ++j)
+      val += fr_root<G, Q, YS, 0>(rs[j], cs[j], yreg, ycol, acc);
 #pragma unroll 1
-    for (int j = nA; j < min(nB, jw); ++j)
+    for (int j = max(nA, j0); j < min(nB, jw); ++j)
       val += fr_root<G, Q, YS, 1>(rs[j], cs[j], yreg, ycol, acc);
 #pragma unroll 1
-    for (int j = nB; j < jw; ++j) val += fr_root<G, Q, YS, 2>(rs[j], cs[j], yreg, ycol, acc);
+    for (int j = max(nB, j0); j < jw; ++j)
+      val += fr_root<G, Q, YS, 2>(rs[j], cs[j], yreg, ycol, acc);
     // partials back into the staging slots (each slot is owned by one lane)
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
       const int i = lam + G * s;
       if (i < L) ys[i * Geo::LDR + rr] = acc[s];
     }
-    if (lam == 0) fe_s[rr] = it.b0 + val;
+    if (lam == 0) fe_s[rr] = low ? val : it.b0 + val;
   }
   __syncthreads();
   // write partials w * s_e * dFE/dy_e to their variable-major rows
@@ -267,10 +277,16 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   for (int i = warp; i < L; i += 8) {
     const LitRec rc = lrec_s[i];
     const int r = r0 + lane;
-    if (r < R)
-      P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
+    if (r < R) {
+      float* pp = &P[(size_t)rec_row(rc.dst) * Rp + r];
+      const float v = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
+      *pp = low ? *pp + v : v;
+    }
   }
-  if (fe_con && warp == 0 && r0 + lane < R) fe_con[(size_t)it.c * ldf + r0 + lane] = fe_s[lane];
+  if (fe_con && warp == 0 && r0 + lane < R) {
+    float* fp = &fe_con[(size_t)it.c * ldf + r0 + lane];
+    *fp = low ? *fp + fe_s[lane] : fe_s[lane];
+  }
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -309,7 +325,7 @@ cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int 
   case id:                                                                                \
     k_fe_group_fr<G, Q, (Y != 0)><<<grid, block, fr_smem<G, Q>(), s>>>(                   \
         list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf,  \
-        done, d.dft_flops);                                                               \
+        done, d.ser_info, d.dft_flops);                                                   \
     break;
     CLS_FR_CONFIGS(CLS_FR_CASE)
 #undef CLS_FR_CASE

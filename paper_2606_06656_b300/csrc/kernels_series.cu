@@ -24,9 +24,11 @@
 // One thread per (constraint, restart), a warp per tile of 32 restarts, a
 // block per constraint and 8 tiles.  Pass A computes the tail cutoff of
 // kernels_fr.cu (S = sum (1 - y^2) / 4); a tile whose largest cutoff lies in
-// the range of 16 (else 24) terms is taken, any other is left to the dense
-// factored kernel.  Pass B forms the power sums, the root loop G_j and the
-// coefficients C_k, pass C the partials; the tile's flag is then set to done.
+// the range of 16 (else 24) terms is finished here (flag done).  A tile that
+// needs more roots gets the terms of the roots 1..js1 (24 terms) here when
+// that saves enough root products (flag low: the dense factored kernel adds
+// the rest); any other is left to the dense kernel.  Pass B forms the power
+// sums, the root loop G_j and the coefficients C_k, pass C the partials.
 // Phases: arg F_j(+-1/2) and theta_j are tabulated as uint32 fractions of a
 // turn, so n arg mod 2 pi is an exact integer product (error <= n/2 2^-32
 // turns); sincosf only sees that plus the series' part.
@@ -57,44 +59,68 @@ __device__ __forceinline__ float4 lds4(const float4* p) {
 }
 __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
 
+// Literal values reach the passes as cp.async copies in chunks of kSerChunk
+// literals, double-buffered per warp (stg = the thread's slot of
+// stage[warp][2][kSerChunk][32]); f(i, x_i) is called for i = 0..L-1 in
+// order while the next chunk is in flight.  Each thread reads back only its
+// own copies.  Inactive lanes see x = 1.
+constexpr int kSerChunk = 32;
+template <typename Fn>
+__device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const float* xr, int R,
+                                            bool act, float* stg, Fn&& f) {
+  const int nch = (L + kSerChunk - 1) / kSerChunk;
+  auto issue = [&](int c) {
+    float* dst = stg + (c & 1) * kSerChunk * 32;
+    const int b0 = c * kSerChunk;
+    if (act) {
+#pragma unroll 8
+      for (int u = 0; u < kSerChunk; ++u)
+        if (b0 + u < L) cp_async4(dst + u * 32, xr + (size_t)recs[b0 + u].var * R);
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch) issue(c + 1);
+    else cp_async_commit();                  // an empty group keeps the count
+    cp_async_wait<1>();
+    const float* src = stg + (c & 1) * kSerChunk * 32;
+    const int b0 = c * kSerChunk, n = min(kSerChunk, L - b0);
+#pragma unroll 1
+    for (int u = 0; u < n; ++u) f(b0 + u, act ? src[u * 32] : 1.f);
+  }
+  cp_async_wait<0>();
+}
+
 // one restart's K-term pass: power sums, the root loop over jw roots, the
 // partials of all L literals (written to P) and FE - b0 (returned)
 template <int K>
 __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* recs,
                                                 const float* xr, int R, bool act,
                                                 const float4* tab, const float2* bsm,
-                                                float* __restrict__ P, int Rp, int r, float wgt) {
+                                                float* __restrict__ P, int Rp, int r, float wgt,
+                                                float* stg) {
   // pass B: power sums of d over the interior literals of each half
   float Mp[K], Mm[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) Mp[k] = Mm[k] = 0.f;
   uint32_t np = 0, nn = 0, nt = 0;
-  for (int i0 = 0; i0 < L; i0 += 4) {
-    float v[4];
+  staged_scan(L, recs, xr, R, act, stg, [&](int i, float xv) {
+    const float y = rec_sgn(recs[i].dst) * xv, a = fabsf(y);
+    const bool corner = a == 1.f, neg = y < 0.f;
+    nt += (corner && neg) ? 1u : 0u;
+    np += (!corner && !neg) ? 1u : 0u;
+    nn += (!corner && neg) ? 1u : 0u;
+    const float d = corner ? 0.f : a - 0.5f;
+    const float mn = neg ? 1.f : 0.f, mp = 1.f - mn;   // the literal's half
+    float p = d;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const LitRec rc = recs[min(i0 + u, L - 1)];
-      v[u] = act ? rec_sgn(rc.dst) * xr[(size_t)rc.var * R] : 1.f;
+    for (int k = 0; k < K; ++k) {
+      Mp[k] = fmaf(mp, p, Mp[k]);
+      Mm[k] = fmaf(mn, p, Mm[k]);
+      p *= d;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (i0 + u >= L) break;
-      const float y = v[u], a = fabsf(y);
-      const bool corner = a == 1.f, neg = y < 0.f;
-      nt += (corner && neg) ? 1u : 0u;
-      np += (!corner && !neg) ? 1u : 0u;
-      nn += (!corner && neg) ? 1u : 0u;
-      const float d = corner ? 0.f : a - 0.5f;
-      const float mn = neg ? 1.f : 0.f, mp = 1.f - mn;   // the literal's half
-      float p = d;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        Mp[k] = fmaf(mp, p, Mp[k]);
-        Mm[k] = fmaf(mn, p, Mm[k]);
-        p *= d;
-      }
-    }
-  }
+  });
   // M+_k / k and M-_k / k, M-_k = (-1)^k sum_{y<0} d^k (array index k - 1)
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -140,30 +166,21 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
 #pragma unroll
   for (int k = 1; k < K; k += 2) Cm[k] = -Cm[k];
   // pass C: partials, Horner in d with the coefficients of the literal's half
-  for (int i0 = 0; i0 < L; i0 += 4) {
-    float v[4];
-    LitRec rcs[4];
+  staged_scan(L, recs, xr, R, act, stg, [&](int i, float xv) {
+    const int32_t dst = recs[i].dst;
+    const float y = rec_sgn(dst) * xv, d = fabsf(y) - 0.5f;
+    const bool neg = y < 0.f;
+    float g = neg ? Cm[K - 1] : Cp[K - 1];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      rcs[u] = recs[min(i0 + u, L - 1)];
-      v[u] = act ? rec_sgn(rcs[u].dst) * xr[(size_t)rcs[u].var * R] : 1.f;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (i0 + u >= L) break;
-      const float y = v[u], d = fabsf(y) - 0.5f;
-      const bool neg = y < 0.f;
-      float g = neg ? Cm[K - 1] : Cp[K - 1];
-#pragma unroll
-      for (int k = K - 2; k >= 0; --k) g = fmaf(g, d, neg ? Cm[k] : Cp[k]);
-      if (act) P[(size_t)rec_row(rcs[u].dst) * Rp + r] = wgt * rec_sgn(rcs[u].dst) * g;
-    }
-  }
+    for (int k = K - 2; k >= 0; --k) g = fmaf(g, d, neg ? Cm[k] : Cp[k]);
+    if (act) P[(size_t)rec_row(dst) * Rp + r] = wgt * rec_sgn(dst) * g;
+  });
   return fe;
 }
 
 // Dynamic shared memory: kSeriesMaxRoots * kSerRow float4 (rows), as many
-// float2 (b'_j), maxL LitRec.
+// float2 (b'_j), the staging buffers (8 warps x 2 x kSerChunk x 32 floats),
+// maxL LitRec.
 __global__ void __launch_bounds__(256, 2) k_fe_series(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ coef, const F4* __restrict__ ser_tab,
@@ -174,7 +191,8 @@ __global__ void __launch_bounds__(256, 2) k_fe_series(
   extern __shared__ float4 ss4[];
   float4* tab = ss4;                                                  // [96][kSerRow]
   float2* bsm = reinterpret_cast<float2*>(tab + kSeriesMaxRoots * kSerRow);  // [96]
-  LitRec* recs = reinterpret_cast<LitRec*>(bsm + kSeriesMaxRoots);    // [maxL]
+  float* stage = reinterpret_cast<float*>(bsm + kSeriesMaxRoots);     // [8][2][chunk][32]
+  LitRec* recs = reinterpret_cast<LitRec*>(stage + 8 * 2 * kSerChunk * 32);   // [maxL]
   __shared__ int jneed_s[8];
   const int ci = list[blockIdx.x];
   const SerInfo si = ser_info[ci];
@@ -191,18 +209,14 @@ __global__ void __launch_bounds__(256, 2) k_fe_series(
   const int r = (live ? tile : RT - 1) * 32 + lane;
   const bool act = r < R;
   const float* xr = x + (act ? r : R - 1);
+  float* stg = stage + (size_t)warp * 2 * kSerChunk * 32 + lane;
   // pass A: the tail cutoff (as in kernels_fr.cu) and the terms it needs
   int jw = 0, K = 0;
+  bool part = false;
   if (mine) {
     float S = 0.f;
-    for (int i0 = 0; i0 < L; i0 += 8) {
-      float v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = act ? xr[(size_t)recs[min(i0 + u, L - 1)].var * R] : 1.f;
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (i0 + u < L) S = fmaf(-0.25f * v[u], v[u], S + 0.25f);
-    }
+    staged_scan(L, recs, xr, R, act, stg,
+                [&](int, float xv) { S = fmaf(-0.25f * xv, xv, S + 0.25f); });
     int jc = J;
     const float S1 = S - 0.25f;
     if (S1 > 0.f) {
@@ -212,6 +226,15 @@ __global__ void __launch_bounds__(256, 2) k_fe_series(
     }
     jw = __reduce_max_sync(kFull, act ? jc : 0);
     K = jw <= si.js0 ? kSeriesK0 : (jw <= si.js1 ? kSeriesK1 : 0);
+    // beyond the range: the low roots 1..js1 here, the others in the dense
+    // kernel, when the root products saved (14 flops per literal and root)
+    // outweigh this pass's cost by half again
+    if (K == 0 && 2 * 14 * (int64_t)L * si.js1 >
+                      3 * ((int64_t)L * (4 + 6 * kSeriesK1) + (int64_t)si.js1 * (16 * kSeriesK1 + 40))) {
+      K = kSeriesK1;
+      part = true;
+      jw = si.js1;
+    }
   }
   if (lane == 0) jneed_s[warp] = K ? jw : 0;
   __syncthreads();
@@ -229,9 +252,9 @@ __global__ void __launch_bounds__(256, 2) k_fe_series(
   if (K == 0) return;
   float fev;
   if (K == kSeriesK0)
-    fev = series_restart<kSeriesK0>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w);
+    fev = series_restart<kSeriesK0>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w, stg);
   else
-    fev = series_restart<kSeriesK1>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w);
+    fev = series_restart<kSeriesK1>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w, stg);
   if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;
   // (K is uniform over the warp, so every lane is here)
   const unsigned nact = (unsigned)__popc(__ballot_sync(kFull, act));
@@ -242,14 +265,15 @@ __global__ void __launch_bounds__(256, 2) k_fe_series(
     atomicAdd(flops, per * (unsigned long long)nact);
   }
   __syncwarp();
-  if (lane == 0) done[(size_t)ci * RT + tile] = kTileDone;
+  if (lane == 0) done[(size_t)ci * RT + tile] = part ? kTileLow : kTileDone;
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 size_t series_smem_bytes(int maxL) {
   return (size_t)kSeriesMaxRoots * kSerRow * sizeof(float4) +
-         (size_t)kSeriesMaxRoots * sizeof(float2) + (size_t)maxL * sizeof(LitRec);
+         (size_t)kSeriesMaxRoots * sizeof(float2) +
+         (size_t)8 * 2 * kSerChunk * 32 * sizeof(float) + (size_t)maxL * sizeof(LitRec);
 }
 
 }  // namespace

@@ -125,7 +125,7 @@ void assign_groups(HostPlan* P, const Tuning& tun) {
 //   (1 + rho) rho^K / (1 - rho)      <= 2^-24   (each literal's partial)
 // with rho = sin phi / (2 sqrt(1 - 3/4 sin^2 phi)), phi = pi j / (L + 1)
 // (rho grows with j below the middle root).
-static int series_roots(int L, int K) {
+int series_roots(int L, int K) {
   const int N = L + 1;
   const double eps = std::ldexp(1.0, -24);
   int js = 0;

@@ -199,6 +199,9 @@ struct SerInfo {
   int32_t pad;
 };
 
+// roots in range of the power-sum pass with K terms (plan.cpp)
+int series_roots(int L, int K);
+
 constexpr int kNumFrQ = 14;
 constexpr int kFrQ[kNumFrQ] = {1, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32};
 // Configuration id of the restart-parallel checkpointed kernel for real-root

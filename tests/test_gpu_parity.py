@@ -617,9 +617,26 @@ def test_corner_pass_interior_counts(P, kernel):
     check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_power_sum_pass_modes(P, kernel):
+    """Long constraints (64..300 literals) at points whose spread S ranges
+    from uniform to mostly pinned: the power-sum pass finishes tiles with 16
+    or 24 terms, takes only the low roots of others (the dense kernel adding
+    the rest to the same partials) or leaves them; tiles mixing restarts of
+    both kinds and restarts past R are included."""
+    rng = np.random.default_rng(41)
+    inst = W.random_constraint_set(rng, 900, 40, [W.TYPE_CARD_GE, W.TYPE_CARD_LE, W.TYPE_EK,
+                                                  W.TYPE_SPECTRUM], (64, 300), weights="rand")
+    fr = [0.0, 0.2, 0.4, 0.55, 0.7, 0.85]
+    R = 32 * len(fr) + 32 + 9
+    frac = np.concatenate([np.repeat(np.asarray(fr), 32), rng.uniform(0.0, 0.9, 41)])
+    X = corner_dominated_points(inst.n, R, frac[None, :], seed=8)
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
+
+
 def test_dft_flops_counter_counts_truncated_work(P):
     """At uniform points long cardinality constraints need far fewer roots
-    than J (the tail cutoff); at corner points every root is kept."""
+    than J (the tail cutoff); near corner points every root is kept."""
     from paper_2606_06656_b300 import binding as B
     rng = np.random.default_rng(4)
     n = 600
@@ -635,6 +652,15 @@ def test_dft_flops_counter_counts_truncated_work(P):
     p.eval(x, obj=False, grad=True)
     part = B.cls_dft_flops_counter(p.handle, reset=True)
     assert 0 < part < 0.8 * full * R
+    # near corners every root is kept: the power-sum pass evaluates the low
+    # roots 1..js1 of every tile (24 terms, its own flop count) and the dense
+    # kernel the others
     x = torch.from_numpy(W.near_corner_points(n, R, seed=2)).cuda()
     p.eval(x, obj=False, grad=True)
-    assert B.cls_dft_flops_counter(p.handle, reset=True) == full * R
+    expect = full
+    for L in (150, 220, 300):
+        js1 = B.cls_series_range(L, 24)
+        series = L * (4 + 6 * 24) + js1 * (16 * 24 + 40)
+        assert 2 * 14 * L * js1 > 3 * series          # the pass takes the low roots
+        expect += series - 14 * L * js1
+    assert B.cls_dft_flops_counter(p.handle, reset=True) == expect * R
