@@ -198,6 +198,22 @@ def run_ours(args, rank, world, local_rank):
     def step_persistent():
         B.cls_step_persistent(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
 
+    if args.profile_step >= 0:
+        # profiling window: S untimed steps of the run from x0, then one step
+        # between cudaProfilerStart/Stop (ncu --profile-from-start off); no
+        # bench line
+        x.copy_(x0)
+        if args.profile_step:
+            B.cls_step(p.handle, R, x, lr, args.profile_step, bits, nsat, wsat, ws)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step_eager()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_step": args.profile_step, "workload": inst.name, "R": R,
+                          "tuning": tuning}), flush=True)
+        return
+
     graph = None if (args.eager or args.persistent) else \
         B.cls_graph_create(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
 
@@ -291,13 +307,14 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kstats, key=lambda k: kstats[k]["ms_per_step"])
     pk = peaks()
     if dom == "fe_group_dft":
-        # flops of the roots the dense factored kernel evaluated in the run's
-        # first steps (device counter; the tail cutoff skips the others),
-        # before coordinates reach the cube's faces (no tile on the corner pass)
+        # flops the DFT path evaluated in the run's first steps (device
+        # counter: the dense factored kernel's roots after the tail cutoff and
+        # the power-sum pass's own arithmetic), before coordinates reach the
+        # cube's faces (no tile on the corner passes)
         flops = dft_flops_dense
         t = kstats_dense[dom]["ms_per_step"] / 1e3
         peak = 2 * SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "k_fe_group_fr / k_fe_group (DFT buckets)",
+        roof = {"bound": "alu", "kernel": "k_fe_series / k_fe_group_fr (DFT buckets)",
                 "achieved": flops / t / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak,
                 "traffic": None, "window": f"steps 0-{n_dense - 1} of the run (dense phase)",
@@ -474,6 +491,8 @@ def main():
                     help="time the one-launch persistent step (short closed-form problems)")
     ap.add_argument("--tuning", default="", help="fixed bucket->configuration map (25 ids)")
     ap.add_argument("--R", type=int, default=0, help="override restarts (profiling)")
+    ap.add_argument("--profile-step", type=int, default=-1,
+                    help="run S steps untimed, then one step inside a profiler window")
     ap.add_argument("--train-instances", type=int, default=512)
     ap.add_argument("--held-out", type=int, default=16)
     ap.add_argument("--train-steps", type=int, default=3000)

@@ -1,37 +1,34 @@
-// kernels_series.cu -- the low roots of long DFT constraints by power sums.
+// kernels_series.cu -- the low roots of long DFT constraints by Chebyshev sums.
 //
 // FE = b0 + sum_j Re(b'_j G_j) and dFE/dy_i = sum_j Re(b'_j G_j dlog F_ij /
 // dy_i) (the Fourier form of the expansion, Sec. 2.3), G_j = prod_i F_ij,
-// F_ij = alpha_i + beta_i w^j.  Expanding each factor about the centre c of
-// its half of the cube (c = 1/2 for y >= 0, -1/2 for y < 0; d = |y| - 1/2,
-// y - c = +-d):
-//   F_j(y)            = F_j(c) (1 + (y - c) z_c),   z_c = (1 - w^j) / (2 F_j(c))
-//   log F_j(y)        = log F_j(c) + sum_{k>=1} E_{k-1} (y - c)^k / k
-//   dlog F_j(y) / dy  = sum_{k>=0} E_k (y - c)^k,    E_k = (-1)^k z_c^(k+1),
-// so with the power sums M+_k = sum_{y>=0, interior} d^k, M-_k = sum_{y<0,
-// interior} (-d)^k (interior: |y| < 1)
-//   log G_j = n+ log F_j(1/2) + n- log F_j(-1/2) + i theta_j n_true
-//             + sum_k E+_{k-1} M+_k / k + E-_{k-1} M-_k / k,
-// (a literal at a corner contributes log 1 = 0 or log w^j = i theta_j
-// exactly) and every literal's partial is a polynomial in d:
-//   dFE/dy_i = sum_k d^k C_k,   C_k = Re sum_j b'_j G_j E+_k   (y_i >= 0)
-//                                     (-1)^k Re sum_j b'_j G_j E-_k (y_i < 0).
-// The series have ratio rho_j = sin phi_j / (2 sqrt(1 - 3/4 sin^2 phi_j));
-// the host keeps, per length, the roots whose truncation after K terms is
-// bounded by 2^-24 (plan.cpp, series_roots).  The cost per restart is about
-// 5K per literal and 8K per root instead of 7 per (literal, root).
+// F_ij = alpha_i + beta_i w^j = h_j (1 + q_j y_i).  With r_j as in plan.h
+// (|r_j| = tan(phi_j / 2)) the Chebyshev generating function gives, on all
+// of [-1, 1],
+//   log F_j(y)       = C_j + sum_{k>=1} E_{k-1} T_k(y) / k,
+//   dlog F_j(y) / dy = sum_{k>=0} E_k U_k(y),          E_k = -2 r_j^(k+1),
+// so with the Chebyshev sums M_k = sum_{interior i} T_k(y_i) (interior:
+// |y| < 1; a literal at a corner contributes log 1 = 0 or log w^j =
+// i theta_j exactly)
+//   log G_j = n_int C_j + i theta_j n_true + sum_k E_{k-1} M_k / k,
+// and every literal's partial is a Chebyshev-U series in its own value:
+//   dFE/dy_i = sum_k D_k U_k(y_i),   D_k = Re sum_j b'_j G_j E_k,
+// evaluated by Clenshaw's recurrence.  The host keeps, per length, the roots
+// whose truncation after K terms is bounded by 2^-24 (plan.cpp,
+// series_roots).  Per restart the work is about 4K per literal and 4K per
+// root instead of 7 per (literal, root).
 //
 // One thread per (constraint, restart), a warp per tile of 32 restarts, a
 // block per constraint and 8 tiles.  Pass A computes the tail cutoff of
 // kernels_fr.cu (S = sum (1 - y^2) / 4); a tile whose largest cutoff lies in
-// the range of 16 (else 24) terms is finished here (flag done).  A tile that
-// needs more roots gets the terms of the roots 1..js1 (24 terms) here when
+// the range of 18 (else 26) terms is finished here (flag done).  A tile that
+// needs more roots gets the terms of the roots 1..js1 (26 terms) here when
 // that saves enough root products (flag low: the dense factored kernel adds
-// the rest); any other is left to the dense kernel.  Pass B forms the power
-// sums, the root loop G_j and the coefficients C_k, pass C the partials.
-// Phases: arg F_j(+-1/2) and theta_j are tabulated as uint32 fractions of a
-// turn, so n arg mod 2 pi is an exact integer product (error <= n/2 2^-32
-// turns); sincosf only sees that plus the series' part.
+// the rest); any other is left to the dense kernel.  Pass B forms the
+// Chebyshev sums, the root loop G_j and the coefficients D_k, pass C the
+// partials.  Phases: arg of e^{C_j} and theta_j are tabulated as uint32
+// fractions of a turn, so n arg mod 2 pi is an exact integer product (error
+// <= n/2 2^-32 turns); sincosf only sees that plus the series' part.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -86,13 +83,19 @@ __device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const flo
     cp_async_wait<1>();
     const float* src = stg + (c & 1) * kSerChunk * 32;
     const int b0 = c * kSerChunk, n = min(kSerChunk, L - b0);
+    int u = 0;
 #pragma unroll 1
-    for (int u = 0; u < n; ++u) f(b0 + u, act ? src[u * 32] : 1.f);
+    for (; u + 2 <= n; u += 2) {              // two literals: independent chains
+      const float x0 = act ? src[u * 32] : 1.f, x1 = act ? src[(u + 1) * 32] : 1.f;
+      f(b0 + u, x0);
+      f(b0 + u + 1, x1);
+    }
+    if (u < n) f(b0 + u, act ? src[u * 32] : 1.f);
   }
   cp_async_wait<0>();
 }
 
-// one restart's K-term pass: power sums, the root loop over jw roots, the
+// one restart's K-term pass: Chebyshev sums, the root loop over jw roots, the
 // partials of all L literals (written to P) and FE - b0 (returned)
 template <int K>
 __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* recs,
@@ -100,54 +103,49 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
                                                 const float4* tab, const float2* bsm,
                                                 float* __restrict__ P, int Rp, int r, float wgt,
                                                 float* stg) {
-  // pass B: power sums of d over the interior literals of each half
-  float Mp[K], Mm[K];
+  static_assert(K % 2 == 0, "table rows hold pairs of terms");
+  // pass B: M[k-1] = sum over interior literals of T_k(y)
+  float M[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) Mp[k] = Mm[k] = 0.f;
-  uint32_t np = 0, nn = 0, nt = 0;
+  for (int k = 0; k < K; ++k) M[k] = 0.f;
+  uint32_t ni = 0, nt = 0;
   staged_scan(L, recs, xr, R, act, stg, [&](int i, float xv) {
-    const float y = rec_sgn(recs[i].dst) * xv, a = fabsf(y);
-    const bool corner = a == 1.f, neg = y < 0.f;
-    nt += (corner && neg) ? 1u : 0u;
-    np += (!corner && !neg) ? 1u : 0u;
-    nn += (!corner && neg) ? 1u : 0u;
-    const float d = corner ? 0.f : a - 0.5f;
-    const float mn = neg ? 1.f : 0.f, mp = 1.f - mn;   // the literal's half
-    float p = d;
+    const float y = rec_sgn(recs[i].dst) * xv;
+    const bool corner = fabsf(y) == 1.f;
+    nt += (y == -1.f) ? 1u : 0u;
+    ni += corner ? 0u : 1u;
+    const float m = corner ? 0.f : 1.f, y2 = y + y;
+    float tp = 1.f, t = y;                    // T_0, T_1
+    M[0] = fmaf(m, t, M[0]);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      Mp[k] = fmaf(mp, p, Mp[k]);
-      Mm[k] = fmaf(mn, p, Mm[k]);
-      p *= d;
+    for (int k = 1; k < K; ++k) {
+      const float tn = fmaf(y2, t, -tp);
+      tp = t;
+      t = tn;
+      M[k] = fmaf(m, t, M[k]);
     }
   });
-  // M+_k / k and M-_k / k, M-_k = (-1)^k sum_{y<0} d^k (array index k - 1)
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const float inv = 1.0f / (float)(k + 1);
-    Mp[k] *= inv;
-    Mm[k] *= (k & 1) ? inv : -inv;
-  }
-  // roots: log G_j, G_j, w = b'_j G_j, FE and C_k
-  float Cp[K], Cm[K];
+  for (int k = 0; k < K; ++k) M[k] *= 1.0f / (float)(k + 1);
+  // roots: log G_j, G_j, w = b'_j G_j, FE and D_k
+  float D[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) Cp[k] = Cm[k] = 0.f;
+  for (int k = 0; k < K; ++k) D[k] = 0.f;
   float fe = 0.f;
-  const float fnp = (float)np, fnn = (float)nn;
+  const float fni = (float)ni;
 #pragma unroll 1
   for (int j = 0; j < jw; ++j) {
     const float4* row = tab + j * kSerRow;
-    const float4 h0 = row[0], h1 = row[1];
-    const uint32_t turns = np * __float_as_uint(h0.z) + nn * __float_as_uint(h0.w) +
-                           nt * __float_as_uint(h1.x);
-    float lr = fmaf(fnp, h0.x, fnn * h0.y), li = 0.f;
+    const float4 h = row[0];
+    const uint32_t turns = ni * __float_as_uint(h.y) + nt * __float_as_uint(h.z);
+    float lr = fni * h.x, li = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float4 e = lds4(row + 2 + k);
-      lr = fmaf(e.x, Mp[k], lr);
-      li = fmaf(e.y, Mp[k], li);
-      lr = fmaf(e.z, Mm[k], lr);
-      li = fmaf(e.w, Mm[k], li);
+    for (int m = 0; m < K / 2; ++m) {
+      const float4 e = lds4(row + 1 + m);     // E_2m, E_2m+1
+      lr = fmaf(e.x, M[2 * m], lr);
+      li = fmaf(e.y, M[2 * m], li);
+      lr = fmaf(e.z, M[2 * m + 1], lr);
+      li = fmaf(e.w, M[2 * m + 1], li);
     }
     float sn, cs;
     sincosf(fmaf((float)(int32_t)turns, kTwoPiOver2p32, li), &sn, &cs);
@@ -157,23 +155,24 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
     const float wr = fmaf(b.x, gr, -b.y * gi), wi = fmaf(b.x, gi, b.y * gr);
     fe += wr;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const float4 e = lds4(row + 2 + k);
-      Cp[k] = fmaf(e.x, wr, fmaf(-e.y, wi, Cp[k]));
-      Cm[k] = fmaf(e.z, wr, fmaf(-e.w, wi, Cm[k]));
+    for (int m = 0; m < K / 2; ++m) {
+      const float4 e = lds4(row + 1 + m);
+      D[2 * m] = fmaf(e.x, wr, fmaf(-e.y, wi, D[2 * m]));
+      D[2 * m + 1] = fmaf(e.z, wr, fmaf(-e.w, wi, D[2 * m + 1]));
     }
   }
-#pragma unroll
-  for (int k = 1; k < K; k += 2) Cm[k] = -Cm[k];
-  // pass C: partials, Horner in d with the coefficients of the literal's half
+  // pass C: partials, sum_k D_k U_k(y) by Clenshaw's recurrence
   staged_scan(L, recs, xr, R, act, stg, [&](int i, float xv) {
     const int32_t dst = recs[i].dst;
-    const float y = rec_sgn(dst) * xv, d = fabsf(y) - 0.5f;
-    const bool neg = y < 0.f;
-    float g = neg ? Cm[K - 1] : Cp[K - 1];
+    const float y = rec_sgn(dst) * xv, y2 = y + y;
+    float b1 = 0.f, b2 = 0.f;
 #pragma unroll
-    for (int k = K - 2; k >= 0; --k) g = fmaf(g, d, neg ? Cm[k] : Cp[k]);
-    if (act) P[(size_t)rec_row(dst) * Rp + r] = wgt * rec_sgn(dst) * g;
+    for (int k = K - 1; k >= 0; --k) {
+      const float b0 = fmaf(y2, b1, D[k] - b2);
+      b2 = b1;
+      b1 = b0;
+    }
+    if (act) P[(size_t)rec_row(dst) * Rp + r] = wgt * rec_sgn(dst) * b1;
   });
   return fe;
 }
@@ -230,7 +229,7 @@ __global__ void __launch_bounds__(256, 2) k_fe_series(
     // kernel, when the root products saved (14 flops per literal and root)
     // outweigh this pass's cost by half again
     if (K == 0 && 2 * 14 * (int64_t)L * si.js1 >
-                      3 * ((int64_t)L * (4 + 6 * kSeriesK1) + (int64_t)si.js1 * (16 * kSeriesK1 + 40))) {
+                      3 * ((int64_t)L * (4 + 8 * kSeriesK1) + (int64_t)si.js1 * (8 * kSeriesK1 + 40))) {
       K = kSeriesK1;
       part = true;
       jw = si.js1;
@@ -259,9 +258,9 @@ __global__ void __launch_bounds__(256, 2) k_fe_series(
   // (K is uniform over the warp, so every lane is here)
   const unsigned nact = (unsigned)__popc(__ballot_sync(kFull, act));
   if (flops && lane == 0) {
-    // per restart: L (4 + 6K) for the passes, jw (16K + 40) for the roots
-    const unsigned long long per = (unsigned long long)L * (4 + 6 * K) +
-                                   (unsigned long long)jw * (16 * K + 40);
+    // per restart: L (4 + 8K) for the passes, jw (8K + 40) for the roots
+    const unsigned long long per = (unsigned long long)L * (4 + 8 * K) +
+                                   (unsigned long long)jw * (8 * K + 40);
     atomicAdd(flops, per * (unsigned long long)nact);
   }
   __syncwarp();

@@ -120,20 +120,23 @@ void assign_groups(HostPlan* P, const Tuning& tun) {
 }
 
 // Roots in range of the power-sum pass with K terms (see kSeriesK0): the
-// largest js such that for every root j <= js both truncation bounds hold,
-//   L rho^(K+1) / ((K+1)(1 - rho)) <= 2^-24   (log G_j, relative to G_j)
-//   (1 + rho) rho^K / (1 - rho)      <= 2^-24   (each literal's partial)
-// with rho = sin phi / (2 sqrt(1 - 3/4 sin^2 phi)), phi = pi j / (L + 1)
-// (rho grows with j below the middle root).
+// largest js such that for every root j <= js, with rho = tan(phi/2),
+//   L 2 rho^(K+1) / ((K+1)(1 - rho))                          <= 2^-24
+//     (the log series summed over L literals, |T_k| <= 1), and
+//   2 rho^(K+1) ((K+1)/(1 - rho) + rho/(1 - rho)^2) / sin phi <= 2^-24
+//     (the derivative series, |U_k| <= k + 1, relative to its smallest
+//     modulus sin phi on [-1, 1]); rho grows with j below the middle root.
 int series_roots(int L, int K) {
   const int N = L + 1;
   const double eps = std::ldexp(1.0, -24);
   int js = 0;
   for (int j = 1; 2 * j < N && j <= kSeriesMaxRoots; ++j) {
-    const double s = std::sin(M_PI * (double)j / (double)N);
-    const double rho = 0.5 * s / std::sqrt(1.0 - 0.75 * s * s);
-    const double tl = (double)L * std::pow(rho, K + 1) / ((double)(K + 1) * (1.0 - rho));
-    const double td = (1.0 + rho) * std::pow(rho, K) / (1.0 - rho);
+    const double phi = M_PI * (double)j / (double)N;
+    const double rho = std::tan(0.5 * phi);
+    const double pk = std::pow(rho, K + 1);
+    const double tl = (double)L * 2.0 * pk / ((double)(K + 1) * (1.0 - rho));
+    const double td = 2.0 * pk * ((double)(K + 1) / (1.0 - rho) + rho / ((1.0 - rho) * (1.0 - rho))) /
+                      std::sin(phi);
     if (tl > eps || td > eps) break;
     js = j;
   }
@@ -159,17 +162,16 @@ static SerInfo series_table(int L, std::vector<F4>& tab) {
   for (int j = 1; j <= si.js1; ++j) {
     const double th = 2.0 * M_PI * (double)j / (double)N;
     const std::complex<double> w(std::cos(th), std::sin(th));
-    const std::complex<double> Fp = (3.0 + w) / 4.0, Fm = (1.0 + 3.0 * w) / 4.0;
-    const std::complex<double> dF = (1.0 - w) / 2.0;        // dF/dy
-    const std::complex<double> zp = dF / Fp, zm = dF / Fm;
-    tab.push_back({(float)std::log(std::abs(Fp)), (float)std::log(std::abs(Fm)),
-                   turn_bits(std::arg(Fp) / (2.0 * M_PI)), turn_bits(std::arg(Fm) / (2.0 * M_PI))});
-    tab.push_back({turn_bits((double)j / (double)N), 0.f, 0.f, 0.f});
-    std::complex<double> ep = zp, em = zm;                  // E_0 = z
-    for (int k = 0; k < kSeriesK1; ++k) {
-      tab.push_back({(float)ep.real(), (float)ep.imag(), (float)em.real(), (float)em.imag()});
-      ep *= -zp;
-      em *= -zm;
+    const std::complex<double> h = (1.0 + w) / 2.0, q = (1.0 - w) / (1.0 + w);
+    const std::complex<double> r = -q / (1.0 + std::sqrt(1.0 - q * q));
+    const std::complex<double> Cj = std::log(h) - std::log(1.0 + r * r);
+    tab.push_back({(float)Cj.real(), turn_bits(Cj.imag() / (2.0 * M_PI)),
+                   turn_bits((double)j / (double)N), 0.f});
+    std::complex<double> e = -2.0 * r;                      // E_0
+    for (int k = 0; k < kSeriesK1; k += 2) {
+      const std::complex<double> e1 = e * r;
+      tab.push_back({(float)e.real(), (float)e.imag(), (float)e1.real(), (float)e1.imag()});
+      e = e1 * r;
     }
   }
   return si;

@@ -177,21 +177,23 @@ constexpr int kNumGroupCfg = 99;
 // rounded to FP32, and z' = 1/(1 - i t) or 1/(1 + i t) is the root constant
 // that makes a padding slot (y = 1) exactly neutral for that rounded t; its
 // powers are formed in FP64 and rounded once.
-// Power-sum (series) pass for the low roots of long DFT constraints: every
-// factor alpha + beta w^j = F_j(c) (1 + (y - c) z_c) is expanded about the
-// centre c = +1/2 (y >= 0) or -1/2 (y < 0), |y - c| <= 1/2, so log G_j and
-// the partials are series in (y - c) of ratio rho_j = sin(phi_j) / (2 sqrt(1
-// - 3/4 sin^2 phi_j)), phi_j = pi j / (L + 1).  A root is in the range of K
-// terms when both truncation bounds (the log series over L literals, the
-// derivative series) are at most 2^-24.  Per length L the table holds, for
-// root j = 1..kSeriesK1-range, kSerRow float4: {ln|F_j(1/2)|, ln|F_j(-1/2)|,
-// arg F_j(1/2), arg F_j(-1/2)} (arguments as uint32 fractions of a turn),
-// {j/(L+1) as a uint32 fraction of a turn, 0, 0, 0}, then for k = 0..K1-1
-// {E+_k, E-_k} with E_k = (-1)^k z_c^(k+1).
-constexpr int kSeriesK0 = 16, kSeriesK1 = 24;
+// Power-sum (series) pass for the low roots of long DFT constraints.  With
+// phi = pi j / (L + 1), every factor is alpha + beta w^j = h_j (1 + q_j y),
+// h_j = (1 + w^j)/2, q_j = -i tan phi, and with r_j = -q_j / (1 + sqrt(1 -
+// q_j^2)), |r_j| = tan(phi/2), the Chebyshev generating function gives on
+// all of [-1, 1]
+//   log(1 + q y) = -log(1 + r^2) - 2 sum_{k>=1} r^k T_k(y) / k,
+//   d/dy log(1 + q y) = sum_{k>=0} E_k U_k(y),   E_k = -2 r^(k+1).
+// A root is in the range of K terms when both truncation bounds (the log
+// series over L literals, the derivative series relative to |dlog F/dy| >=
+// sin phi) are at most 2^-24.  Per length L the table holds, for root j =
+// 1..js1, kSerRow float4: {Re C_j, Im C_j and theta_j as uint32 fractions of
+// a turn, 0} with C_j = log h_j - log(1 + r_j^2), then {E_2m, E_2m+1} for
+// m = 0..K1/2 - 1.
+constexpr int kSeriesK0 = 18, kSeriesK1 = 26;
 constexpr int kSeriesMaxRoots = 96;   // rows a block stages
 constexpr int kSeriesMinL = 64;       // shorter constraints keep the root products
-constexpr int kSerRow = 2 + kSeriesK1;
+constexpr int kSerRow = 1 + kSeriesK1 / 2;
 struct SerInfo {
   int32_t off;    // first row in ser_tab, -1 if the constraint has none
   int32_t js0;    // roots in range of kSeriesK0 terms

@@ -653,14 +653,14 @@ def test_dft_flops_counter_counts_truncated_work(P):
     part = B.cls_dft_flops_counter(p.handle, reset=True)
     assert 0 < part < 0.8 * full * R
     # near corners every root is kept: the power-sum pass evaluates the low
-    # roots 1..js1 of every tile (24 terms, its own flop count) and the dense
+    # roots 1..js1 of every tile (26 terms, its own flop count) and the dense
     # kernel the others
     x = torch.from_numpy(W.near_corner_points(n, R, seed=2)).cuda()
     p.eval(x, obj=False, grad=True)
     expect = full
     for L in (150, 220, 300):
-        js1 = B.cls_series_range(L, 24)
-        series = L * (4 + 6 * 24) + js1 * (16 * 24 + 40)
+        js1 = B.cls_series_range(L, 26)
+        series = L * (4 + 8 * 26) + js1 * (8 * 26 + 40)
         assert 2 * 14 * L * js1 > 3 * series          # the pass takes the low roots
         expect += series - 14 * L * js1
     assert B.cls_dft_flops_counter(p.handle, reset=True) == expect * R
