@@ -61,7 +61,7 @@ __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f :
 // stage[warp][2][kSerChunk][32]); f(i, x_i) is called for i = 0..L-1 in
 // order while the next chunk is in flight.  Each thread reads back only its
 // own copies.  Inactive lanes see x = 1.
-constexpr int kSerChunk = 32;
+constexpr int kSerChunk = 16;
 template <typename Fn>
 __device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const float* xr, int R,
                                             bool act, float* stg, Fn&& f) {
@@ -180,7 +180,7 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
 // Dynamic shared memory: kSeriesMaxRoots * kSerRow float4 (rows), as many
 // float2 (b'_j), the staging buffers (8 warps x 2 x kSerChunk x 32 floats),
 // maxL LitRec.
-__global__ void __launch_bounds__(256, 2) k_fe_series(
+__global__ void __launch_bounds__(256, 3) k_fe_series(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ coef, const F4* __restrict__ ser_tab,
     const SerInfo* __restrict__ ser_info, const LitRec* __restrict__ lit,
