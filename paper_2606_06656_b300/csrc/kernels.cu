@@ -164,15 +164,22 @@ __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restri
   }
 }
 
-// thread_body with the gathers of all kThreadTiles tiles issued up front as
+// Restart tiles (of 32) per warp of k_fe_thread<LO, HI>: 8 up to 8
+// literals, 4 beyond (the staging buffer stays at 64 KB per block).
+template <int HI>
+struct AsyncTiles {
+  static constexpr int value = HI <= 8 ? 8 : 4;
+};
+
+// thread_body with the gathers of all NT tiles issued up front as
 // cp.async copies into the warp's shared buffer (slot (tile, literal) at
-// xb[(tt * L + i) * 32 + lane]), so that kThreadTiles * L loads per thread
+// xb[(tt * L + i) * 32 + lane]), so that NT * L loads per thread
 // are in flight without holding registers; each literal record is read from
 // shared memory once (its variable for the copies, its destination kept in a
 // register for the tiles when L <= 8; longer constraints read it again per
 // tile).  Each thread reads back only what it copied itself.  Not for data written earlier in the same launch (the copies go
 // through L1).
-template <int L>
+template <int L, int NT>
 __device__ __forceinline__ void thread_body_async(const FeItem& it, const F4* __restrict__ root,
                                                   const F4* __restrict__ coef, const int2* trec,
                                                   const float* __restrict__ x, int R, int Rp,
@@ -188,7 +195,7 @@ __device__ __forceinline__ void thread_body_async(const FeItem& it, const F4* __
     dst[i] = q.y;
     const float* xv = x + (size_t)(unsigned)q.x * xs;
 #pragma unroll
-    for (int tt = 0; tt < kThreadTiles; ++tt) {
+    for (int tt = 0; tt < NT; ++tt) {
       const int r = (tile0 + tt) * 32 + lane;
       if (r < R) cp_async4(&xb[(tt * L + i) * 32 + lane], xv + r);
     }
@@ -200,7 +207,7 @@ __device__ __forceinline__ void thread_body_async(const FeItem& it, const F4* __
   const float4 cf1 = two ? ldg4(&coef[it.coef_off + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
   cp_async_wait<0>();
 #pragma unroll 1
-  for (int tt = 0; tt < kThreadTiles; ++tt) {
+  for (int tt = 0; tt < NT; ++tt) {
     const int r = (tile0 + tt) * 32 + lane;
     if (r >= R) break;
     float y[L], g[L], pre[L];
@@ -247,7 +254,7 @@ __device__ __forceinline__ void thread_body_async(const FeItem& it, const F4* __
   }
 }
 
-template <int LO, int HI>
+template <int LO, int HI, int NT>
 __device__ __forceinline__ void thread_dispatch_async(int L, const FeItem& it, const F4* root,
                                                       const F4* coef, const int2* trec,
                                                       const float* x, int R, int Rp, int tile0,
@@ -255,9 +262,9 @@ __device__ __forceinline__ void thread_dispatch_async(int L, const FeItem& it, c
                                                       float* xb) {
   if constexpr (LO <= HI) {
     if (L == LO)
-      thread_body_async<LO>(it, root, coef, trec, x, R, Rp, tile0, lane, P, fe_con, ldf, xb);
+      thread_body_async<LO, NT>(it, root, coef, trec, x, R, Rp, tile0, lane, P, fe_con, ldf, xb);
     else
-      thread_dispatch_async<LO + 1, HI>(L, it, root, coef, trec, x, R, Rp, tile0, lane, P,
+      thread_dispatch_async<LO + 1, HI, NT>(L, it, root, coef, trec, x, R, Rp, tile0, lane, P,
                                         fe_con, ldf, xb);
   }
 }
@@ -276,8 +283,8 @@ __device__ __forceinline__ void thread_dispatch(int L, const FeItem& it, const F
   }
 }
 
-// Dynamic shared memory: 8 warps x kThreadTiles x HI x 32 floats (the staged
-// literal values).
+// Dynamic shared memory: 8 warps x AsyncTiles<HI>::value x HI x 32 floats (the
+// staged literal values).
 template <int LO, int HI>
 __global__ void __launch_bounds__(256) k_fe_thread(
     const FeItem* __restrict__ items, int count, const F4* __restrict__ root,
@@ -287,19 +294,20 @@ __global__ void __launch_bounds__(256) k_fe_thread(
   extern __shared__ float thread_xbuf[];
   const int lane = threadIdx.x;
   int2* trec = trec_s[threadIdx.y];
-  float* xb = thread_xbuf + (size_t)threadIdx.y * kThreadTiles * HI * 32;
+  constexpr int NT = AsyncTiles<HI>::value;
+  float* xb = thread_xbuf + (size_t)threadIdx.y * NT * HI * 32;
   for (int ci = blockIdx.y * blockDim.y + threadIdx.y; ci < count; ci += gridDim.y * blockDim.y) {
     const FeItem it = items[ci];
     __syncwarp();
     load_trec(it, lit, trec, lane);
-    thread_dispatch_async<LO, HI>(it.L, it, root, coef, trec, x, R, Rp,
-                                  blockIdx.x * kThreadTiles, lane, P, fe_con, ldf, xb);
+    thread_dispatch_async<LO, HI, NT>(it.L, it, root, coef, trec, x, R, Rp,
+                                      blockIdx.x * NT, lane, P, fe_con, ldf, xb);
   }
 }
 
 template <int HI>
 constexpr size_t thread_xbuf_bytes() {
-  return (size_t)8 * kThreadTiles * HI * 32 * sizeof(float);
+  return (size_t)8 * AsyncTiles<HI>::value * HI * 32 * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -1168,8 +1176,8 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
     const int t = unit;
     const int cnt = d.thread_count[t];
     if (cnt == 0) return cudaSuccess;
-    const dim3 grid(ceil_div(RT, kThreadTiles), std::min(ceil_div(cnt, 8), 65535)),
-        block(32, 8);
+    const int nt = t == 0 ? AsyncTiles<8>::value : AsyncTiles<16>::value;
+    const dim3 grid(ceil_div(RT, nt), std::min(ceil_div(cnt, 8), 65535)), block(32, 8);
     HookScope hs(h, KC_THREAD, s);
     const FeItem* items = d.thread_items[t];
 #define CLS_THREAD_LAUNCH(LO, HI)                                                          \
