@@ -62,9 +62,11 @@ __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f :
 // order while the next chunk is in flight.  Each thread reads back only its
 // own copies.  Inactive lanes see x = 1.
 constexpr int kSerChunk = 16;
-template <typename Fn>
+// f2(i, x_i, x_{i+1}) takes two consecutive literals, f1(i, x_i) the last one
+// of an odd chunk.
+template <typename F2, typename F1>
 __device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const float* xr, int R,
-                                            bool act, float* stg, Fn&& f) {
+                                            bool act, float* stg, F2&& f2, F1&& f1) {
   const int nch = (L + kSerChunk - 1) / kSerChunk;
   auto issue = [&](int c) {
     float* dst = stg + (c & 1) * kSerChunk * 32;
@@ -85,12 +87,9 @@ __device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const flo
     const int b0 = c * kSerChunk, n = min(kSerChunk, L - b0);
     int u = 0;
 #pragma unroll 1
-    for (; u + 2 <= n; u += 2) {              // two literals: independent chains
-      const float x0 = act ? src[u * 32] : 1.f, x1 = act ? src[(u + 1) * 32] : 1.f;
-      f(b0 + u, x0);
-      f(b0 + u + 1, x1);
-    }
-    if (u < n) f(b0 + u, act ? src[u * 32] : 1.f);
+    for (; u + 2 <= n; u += 2)
+      f2(b0 + u, act ? src[u * 32] : 1.f, act ? src[(u + 1) * 32] : 1.f);
+    if (u < n) f1(b0 + u, act ? src[u * 32] : 1.f);
   }
   cp_async_wait<0>();
 }
@@ -104,29 +103,47 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
                                                 float* __restrict__ P, int Rp, int r, float wgt,
                                                 float* stg) {
   static_assert(K % 2 == 0, "table rows hold pairs of terms");
-  // pass B: M[k-1] = sum over interior literals of T_k(y)
-  float M[K];
+  // pass B: M[k-1] = sum over interior literals of T_k(y); two literals per
+  // packed FP32x2 instruction (float2 sums, folded afterwards)
+  float2 M2[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) M[k] = 0.f;
+  for (int k = 0; k < K; ++k) M2[k] = make_float2(0.f, 0.f);
   uint32_t ni = 0, nt = 0;
-  staged_scan(L, recs, xr, R, act, stg, [&](int i, float xv) {
-    const float y = rec_sgn(recs[i].dst) * xv;
+  auto cls1 = [&](int i, float xv, float& y, float& m) {
+    y = rec_sgn(recs[i].dst) * xv;
     const bool corner = fabsf(y) == 1.f;
     nt += (y == -1.f) ? 1u : 0u;
     ni += corner ? 0u : 1u;
-    const float m = corner ? 0.f : 1.f, y2 = y + y;
-    float tp = 1.f, t = y;                    // T_0, T_1
-    M[0] = fmaf(m, t, M[0]);
+    m = corner ? 0.f : 1.f;
+  };
+  auto sums = [&](float2 y, float2 m) {
+    const float2 y2 = __fadd2_rn(y, y);
+    float2 tp = make_float2(1.f, 1.f), t = y;          // T_0, T_1
+    M2[0] = __ffma2_rn(m, t, M2[0]);
 #pragma unroll
     for (int k = 1; k < K; ++k) {
-      const float tn = fmaf(y2, t, -tp);
+      const float2 tn = __ffma2_rn(y2, t, make_float2(-tp.x, -tp.y));
       tp = t;
       t = tn;
-      M[k] = fmaf(m, t, M[k]);
+      M2[k] = __ffma2_rn(m, t, M2[k]);
     }
-  });
+  };
+  staged_scan(
+      L, recs, xr, R, act, stg,
+      [&](int i, float x0, float x1) {
+        float ya, yb, ma, mb;
+        cls1(i, x0, ya, ma);
+        cls1(i + 1, x1, yb, mb);
+        sums(make_float2(ya, yb), make_float2(ma, mb));
+      },
+      [&](int i, float x0) {
+        float ya, ma;
+        cls1(i, x0, ya, ma);
+        sums(make_float2(ya, 0.f), make_float2(ma, 0.f));
+      });
+  float M[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) M[k] *= 1.0f / (float)(k + 1);
+  for (int k = 0; k < K; ++k) M[k] = (M2[k].x + M2[k].y) * (1.0f / (float)(k + 1));
   // roots: log G_j, G_j, w = b'_j G_j, FE and D_k
   float D[K];
 #pragma unroll
@@ -161,19 +178,33 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
       D[2 * m + 1] = fmaf(e.z, wr, fmaf(-e.w, wi, D[2 * m + 1]));
     }
   }
-  // pass C: partials, sum_k D_k U_k(y) by Clenshaw's recurrence
-  staged_scan(L, recs, xr, R, act, stg, [&](int i, float xv) {
-    const int32_t dst = recs[i].dst;
-    const float y = rec_sgn(dst) * xv, y2 = y + y;
-    float b1 = 0.f, b2 = 0.f;
+  // pass C: partials, sum_k D_k U_k(y) by Clenshaw's recurrence, two
+  // literals per packed instruction
+  auto clenshaw = [&](float2 y) -> float2 {
+    const float2 y2 = __fadd2_rn(y, y);
+    float2 b1 = make_float2(0.f, 0.f), b2 = b1;
 #pragma unroll
     for (int k = K - 1; k >= 0; --k) {
-      const float b0 = fmaf(y2, b1, D[k] - b2);
+      const float2 b0 = __ffma2_rn(y2, b1, __fadd2_rn(make_float2(D[k], D[k]),
+                                                      make_float2(-b2.x, -b2.y)));
       b2 = b1;
       b1 = b0;
     }
-    if (act) P[(size_t)rec_row(dst) * Rp + r] = wgt * rec_sgn(dst) * b1;
-  });
+    return b1;
+  };
+  auto put = [&](int i, float g) {
+    const int32_t dst = recs[i].dst;
+    if (act) P[(size_t)rec_row(dst) * Rp + r] = wgt * rec_sgn(dst) * g;
+  };
+  staged_scan(
+      L, recs, xr, R, act, stg,
+      [&](int i, float x0, float x1) {
+        const float2 g = clenshaw(make_float2(rec_sgn(recs[i].dst) * x0,
+                                              rec_sgn(recs[i + 1].dst) * x1));
+        put(i, g.x);
+        put(i + 1, g.y);
+      },
+      [&](int i, float x0) { put(i, clenshaw(make_float2(rec_sgn(recs[i].dst) * x0, 0.f)).x); });
   return fe;
 }
 
@@ -214,8 +245,9 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
   bool part = false;
   if (mine) {
     float S = 0.f;
-    staged_scan(L, recs, xr, R, act, stg,
-                [&](int, float xv) { S = fmaf(-0.25f * xv, xv, S + 0.25f); });
+    auto acc = [&](float xv) { S = fmaf(-0.25f * xv, xv, S + 0.25f); };
+    staged_scan(L, recs, xr, R, act, stg, [&](int, float x0, float x1) { acc(x0); acc(x1); },
+                [&](int, float x0) { acc(x0); });
     int jc = J;
     const float S1 = S - 0.25f;
     if (S1 > 0.f) {
