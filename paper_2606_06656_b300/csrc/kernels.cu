@@ -1088,6 +1088,9 @@ cudaError_t set_kernel_attributes() {
     err = cudaFuncSetAttribute(k_fe_thread<9, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)thread_xbuf_bytes<16>());
   if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_fe_thread<17, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)thread_xbuf_bytes<24>());
+  if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_fe_thread_ckpt<1, 16>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)ckpt_smem(1024, 1, 16));
@@ -1176,7 +1179,7 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
     const int t = unit;
     const int cnt = d.thread_count[t];
     if (cnt == 0) return cudaSuccess;
-    const int nt = t == 0 ? AsyncTiles<8>::value : AsyncTiles<16>::value;
+    const int nt = t == 0 ? AsyncTiles<8>::value : AsyncTiles<16>::value;   // 24: as 16
     const dim3 grid(ceil_div(RT, nt), std::min(ceil_div(cnt, 8), 65535)), block(32, 8);
     HookScope hs(h, KC_THREAD, s);
     const FeItem* items = d.thread_items[t];
@@ -1186,8 +1189,10 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
                                              Rp, RT, P, fe_con, ldf);
     if (t == 0) {
       CLS_THREAD_LAUNCH(1, 8)
-    } else {
+    } else if (t == 1) {
       CLS_THREAD_LAUNCH(9, 16)
+    } else {
+      CLS_THREAD_LAUNCH(17, 24)
     }
 #undef CLS_THREAD_LAUNCH
     return cudaGetLastError();
@@ -1282,6 +1287,8 @@ cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
 bool persistent_eligible(const DevPlan& d) {
   for (int b = 0; b < kNumBuckets; ++b)
     if (d.bucket_count[b] > 0) return false;
+  for (int t = 2; t < kNumThreadCls; ++t)   // the loop's body covers <= 16 literals
+    if (d.thread_count[t] > 0) return false;
   return d.m > 0 && d.n > 0;
 }
 

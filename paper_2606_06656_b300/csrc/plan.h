@@ -216,8 +216,8 @@ struct GroupCfg {
 extern const GroupCfg kGroupCfg[kNumGroupCfg];
 
 // Thread-path (one thread per (constraint, restart)) length classes.
-constexpr int kNumThreadCls = 2;
-constexpr int kThreadMaxL[kNumThreadCls] = {8, 16};
+constexpr int kNumThreadCls = 3;
+constexpr int kThreadMaxL[kNumThreadCls] = {8, 16, 24};
 constexpr int kThreadTiles = 4;   // restart tiles (of 32) per warp
 
 // Score path: consecutive constraints are grouped into ranges of about this
