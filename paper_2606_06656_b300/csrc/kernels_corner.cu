@@ -48,6 +48,10 @@ __device__ __forceinline__ float4 ldg4(const F4* p) {
 }
 __device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
 __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
+// v * rec_sgn(dst) as one sign-bit flip
+__device__ __forceinline__ float apply_sgn(float v, int32_t dst) {
+  return __int_as_float(__float_as_int(v) ^ (dst & (int32_t)0x80000000));
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -393,7 +397,8 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
   float* ncy = reinterpret_cast<float*>(ztab + JC);          // [8][CAP][32]
   float* vals = ncy + 8 * CAP * 32;                           // [8][3][32] fe, gF, gT
   LitRec* recs = reinterpret_cast<LitRec*>(vals + 8 * 3 * 32);          // [maxL]
-  uint32_t* flags = reinterpret_cast<uint32_t*>(recs + maxL);            // [8][maxL][2]
+  const int FLW = (maxL + 15) / 16;
+  uint32_t* flags = reinterpret_cast<uint32_t*>(recs + maxL);            // [8][FLW][32]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if constexpr (GC > 1) {
     // nothing to do unless one of the block's tiles is still open
@@ -409,10 +414,11 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
   const bool act = r < R;
   const float* xr = x + (act ? r : R - 1);
   float* my = ncy + warp * CAP * 32 + lane;
-  // pass 1: true corners and the non-corner values, in literal order; the
-  // per-literal classification of the tile is kept as two ballots (true
-  // corner, non-corner) so that pass 3 need not read x again
-  uint32_t* fl = flags + (size_t)warp * 2 * maxL;
+  // pass 1: true corners and the non-corner values, in literal order; each
+  // lane keeps its restart's classification of every literal as a 2-bit code
+  // (bit 0 true corner, bit 1 non-corner), 16 literals per word in its own
+  // column of shared memory, so that pass 3 need not read x again
+  uint32_t* fl = flags + (size_t)warp * FLW * 32 + lane;
   int nnc = 0, t = 0;
   // GC > 1: tiles the one-thread pass finished are left alone
   const bool skip = GC > 1 && live && done[(size_t)it.c * RT + tile] != kTileOpen;
@@ -420,24 +426,24 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
   int i_over = L;
   for (int i0 = 0; i0 < L && !over; i0 += 16) {
     const int i1 = min(L, i0 + 16);
-    for (int b = i0; b < i1; b += 8) {
+    uint32_t code = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int b = i0 + 8 * h;
+      if (b >= i1) break;
       float v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const LitRec rc = recs[min(b + u, L - 1)];
-        v[u] = rec_sgn(rc.dst) * xr[(size_t)rc.var * R];
+        v[u] = apply_sgn(xr[(size_t)rc.var * R], rc.dst);
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         if (b + u < i1) {
           const float y = act ? v[u] : 1.f;
-          const bool tc = y == -1.f, nc = (y != -1.f) && (y != 1.f);
-          const uint32_t bt = __ballot_sync(kFull, tc), bn = __ballot_sync(kFull, nc);
-          if (lane == 0) {
-            fl[2 * (b + u)] = bt;
-            fl[2 * (b + u) + 1] = bn;
-          }
-          t += tc ? 1 : 0;
+          const bool tc = y == -1.f, nc = fabsf(y) != 1.f;
+          code |= (tc ? 1u : 0u) << (16 * h + 2 * u);
+          code |= (nc ? 2u : 0u) << (16 * h + 2 * u);
           if (nc) {
             if (nnc < CAP) my[nnc * 32] = y;
             ++nnc;
@@ -445,6 +451,8 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
         }
       }
     }
+    fl[(i0 >> 4) * 32] = code;
+    t += __popc(code & 0x55555555u);
     if (__any_sync(kFull, nnc > CAP)) {
       over = true;
       i_over = i1;
@@ -503,17 +511,21 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
   }
   // pass 3: partials w * s_e * dFE/dy_e of every literal
   int k = 0;
-  const uint32_t me = 1u << lane;
+  const float wgF = it.w * gF, wgT = it.w * gT;
+  for (int i0 = 0; i0 < L; i0 += 16) {
+    const uint32_t code = fl[(i0 >> 4) * 32];
+    const int n = min(16, L - i0);
 #pragma unroll 4
-  for (int i = 0; i < L; ++i) {
-    const LitRec rc = recs[i];
-    const uint32_t bt = fl[2 * i], bn = fl[2 * i + 1];
-    float val = (bt & me) ? gT : gF;
-    if (bn & me) {
-      val = my[k * 32];
-      ++k;
+    for (int u = 0; u < n; ++u) {
+      const LitRec rc = recs[i0 + u];
+      const uint32_t cu = code >> (2 * u);
+      float val = (cu & 1u) ? wgT : wgF;
+      if (cu & 2u) {
+        val = it.w * my[k * 32];
+        ++k;
+      }
+      if (act) P[(size_t)rec_row(rc.dst) * Rp + r] = apply_sgn(val, rc.dst);
     }
-    if (act) P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * val;
   }
   if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;
   __syncwarp();
@@ -528,7 +540,7 @@ size_t corner_smem_bytes(int maxL, int gc) {
   const int JC = (maxL + 1) / 2;
   return (size_t)3 * JC * sizeof(float4) + (size_t)8 * gc * kCornerQS * 32 * sizeof(float) +
          (size_t)8 * 3 * 32 * sizeof(float) + (size_t)maxL * sizeof(LitRec) +
-         (size_t)8 * 2 * maxL * sizeof(uint32_t);
+         (size_t)8 * ((maxL + 15) / 16) * 32 * sizeof(uint32_t);
 }
 
 cudaError_t set_corner_attributes() {
