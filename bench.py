@@ -182,8 +182,22 @@ def run_ours(args, rank, world, local_rank):
     if args.tuning:
         B.cls_tuning_set(p.handle, [int(v) for v in args.tuning.split(",")])
     elif not args.no_tune:
+        # tune on the phases the timed run goes through: four blocks of
+        # restarts taken from the same run at steps 0, 12, 25 and 60 (dense,
+        # middle and corner-dominated points), so each configuration is
+        # weighed on the mix of work a run sees, not on its first step only
         t0 = time.perf_counter()
-        B.cls_autotune(p.handle, R, x, 2, ws)
+        xt = x0.clone()
+        if R >= 64 and args.steps >= 20:
+            xs, done_steps = x0.clone(), 0
+            q = R // 4
+            for blk, at in enumerate((0, 12, 25, 60)):
+                if at > done_steps:
+                    B.cls_step(p.handle, R, xs, lr, at - done_steps, None, None, None, ws)
+                    done_steps = at
+                xt[:, blk * q:(blk + 1) * q if blk < 3 else R] = \
+                    xs[:, blk * q:(blk + 1) * q if blk < 3 else R]
+        B.cls_autotune(p.handle, R, xt, 2, ws)
         tune_s = time.perf_counter() - t0
     tuning = B.cls_tuning_get(p.handle)
     nsat = torch.empty(R, dtype=torch.int32, device="cuda")
@@ -355,7 +369,10 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed (256 MB write) before every timed step",
                    "timed": f"steps 0-{K - 1} of one CLS run from uniform initial points "
                             f"(after {max(3, args.warmup)} untimed warm-up steps)",
-                   "tuning": tuning, "autotune_s": tune_s},
+                   "tuning": tuning, "autotune_s": tune_s,
+                   "autotune_points": None if (args.tuning or args.no_tune) else
+                   ("four restart blocks of the timed run's own trajectory, at steps 0, 12, "
+                    "25 and 60 (untimed)" if R >= 64 and args.steps >= 20 else "x0")},
         "e2e": {"value": units / e2e_s, "unit": "literal-evals/s",
                 "h2d_bytes_per_step": 4 * inst.n * R / K, "d2h_bytes_per_step": 4 * R / K,
                 "call": f"cls_solve_host: x0 from pinned host memory, {K} steps, counts back"},
