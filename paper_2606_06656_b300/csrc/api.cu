@@ -125,7 +125,7 @@ struct Layout {
   int R = 0, Rp = 0, RT = 0;
   int nch = 1, chunk = 1;
   size_t P = 0, fe = 0, bits = 0, nsat_part = 0, wsat_part = 0, obj_part = 0, nsat = 0,
-         rpart_n = 0, rpart_w = 0, bar = 0, done = 0, total = 0;
+         rpart_n = 0, rpart_w = 0, bar = 0, done = 0, ser = 0, total = 0;
 };
 
 Layout layout_for(const cls_problem* p, int R) {
@@ -155,6 +155,9 @@ Layout layout_for(const cls_problem* p, int R) {
   L.nsat = take((size_t)L.Rp * sizeof(int32_t));
   // corner-pass flags of the factored DFT kernels, one per (constraint, tile)
   L.done = take((size_t)std::max(1, m) * L.RT);
+  // directly after the flags (cls::ser_terms locates it from them): the
+  // Chebyshev pass's saved low-root terms, kSeriesK1 + 1 rows per slot
+  L.ser = take((size_t)p->host.n_ser_slots * (cls::kSeriesK1 + 1) * L.Rp * sizeof(float));
   // persistent loop: per-range score partials and the grid barrier words
   const size_t nr = (size_t)std::max(1, p->dev.n_ranges);
   L.rpart_n = take(nr * L.Rp * sizeof(int32_t));

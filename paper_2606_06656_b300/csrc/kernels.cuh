@@ -135,6 +135,15 @@ constexpr int kCornerMinSlots = 32;
 // (left to the dense kernel), low (the power-sum pass wrote the terms of the
 // roots 1..js1 of kernels_series.cu; the dense kernel adds the others)
 constexpr uint8_t kTileOpen = 0, kTileDone = 1, kTileDense = 2, kTileLow = 3;
+// In the workspace the flags (max(1, m) x RT bytes) are followed, 256-byte
+// aligned, by the Chebyshev pass's terms of the low tiles: per constraint
+// slot (SerInfo::slot) kSeriesK1 + 1 rows of Rp floats, D_0 .. D_{K1-1} and
+// then FE - b0 of the low roots, which the dense factored kernel adds.
+inline float* ser_terms(const DevPlan& d, uint8_t* done, int RT) {
+  uintptr_t a = reinterpret_cast<uintptr_t>(done) + (size_t)(d.m > 1 ? d.m : 1) * RT;
+  a = (a + 255) & ~(uintptr_t)255;
+  return reinterpret_cast<float*>(a);
+}
 cudaError_t set_corner_attributes();
 size_t corner_smem_bytes(int maxL, int gc);
 cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,

@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
     const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
     float* __restrict__ fe_con, int ldf, const uint8_t* __restrict__ done,
-    const SerInfo* __restrict__ ser_info, unsigned long long* __restrict__ flops) {
+    const SerInfo* __restrict__ ser_info, const float* __restrict__ ser_d,
+    unsigned long long* __restrict__ flops) {
   using Geo = FrGeom<G>;
   constexpr int LS = G * Q;
   constexpr int JC = FrCap<G, Q>::JC;
@@ -163,10 +164,11 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   const int ci = list[blockIdx.x];
   const uint8_t tflag = done ? done[(size_t)ci * gridDim.y + blockIdx.y] : kTileOpen;
   if (tflag == kTileDone) return;
-  // a tile whose low roots the power-sum pass evaluated: start after them and
-  // add to its partials and FE
+  // a tile whose low roots the Chebyshev pass evaluated: start after them
+  // and add its saved terms (D_k, FE - b0 per restart) to the partials and FE
   const bool low = tflag == kTileLow;
   const int j0 = low ? ser_info[ci].js1 : 0;
+  __shared__ float sD[(kSeriesK1 + 1) * 32];
   const FeItem it = fe[ci];
   const int L = it.L, J = it.J;
   const int r0 = blockIdx.y * 32;
@@ -186,6 +188,11 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   // rows in flight per warp
   __shared__ LitRec lrec_s[LS];
   for (int i = threadIdx.x; i < L; i += 256) lrec_s[i] = lit[it.lit0 + i];
+  if (low) {
+    const float* sdg = ser_d + (size_t)ser_info[ci].slot * (kSeriesK1 + 1) * Rp + r0;
+    for (int e = threadIdx.x; e < (kSeriesK1 + 1) * 32; e += 256)
+      sD[e] = (r0 + (e & 31) < R) ? sdg[(size_t)(e >> 5) * Rp + (e & 31)] : 0.f;
+  }
   __syncthreads();
   // rows of x go to shared memory as asynchronous 4-byte copies (all of a
   // thread's rows in flight at once); the signs are applied afterwards
@@ -248,7 +255,8 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
       // (per group <= 1024 * 16 * 512 < 2^24, so the warp sum fits 32 bits)
       const int jl = min(jc, j0);   // roots the power-sum pass took
       const unsigned f = lam == 0 ? (unsigned)L * (14u * (min(nB, jc) - min(nB, jl)) +
-                                                   16u * (max(0, jc - nB) - max(0, jl - nB)))
+                                                   16u * (max(0, jc - nB) - max(0, jl - nB)) +
+                                                   (low ? 4u * kSeriesK1 : 0u))
                                   : 0u;
       const unsigned tot = __reduce_add_sync(kFull, f);
       if (lane == 0) atomicAdd(flops, (unsigned long long)tot);
@@ -263,13 +271,29 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
 #pragma unroll 1
     for (int j = max(nB, j0); j < jw; ++j)
       val += fr_root<G, Q, YS, 2>(rs[j], cs[j], yreg, ycol, acc);
+    if (low) {
+      // the low roots' share of each partial, sum_k D_k U_k(y) (Clenshaw)
+#pragma unroll
+      for (int s = 0; s < Q; ++s) {
+        const float y = YS ? ycol[s * G * Geo::LDR] : yreg[s], y2 = y + y;
+        float b1 = 0.f, b2 = 0.f;
+#pragma unroll
+        for (int k = kSeriesK1 - 1; k >= 0; --k) {
+          const float b0 = fmaf(y2, b1, sD[k * 32 + rr] - b2);
+          b2 = b1;
+          b1 = b0;
+        }
+        acc[s] += b1;
+      }
+      val += sD[kSeriesK1 * 32 + rr];
+    }
     // partials back into the staging slots (each slot is owned by one lane)
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
       const int i = lam + G * s;
       if (i < L) ys[i * Geo::LDR + rr] = acc[s];
     }
-    if (lam == 0) fe_s[rr] = low ? val : it.b0 + val;
+    if (lam == 0) fe_s[rr] = it.b0 + val;
   }
   __syncthreads();
   // write partials w * s_e * dFE/dy_e to their variable-major rows
@@ -277,16 +301,10 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
   for (int i = warp; i < L; i += 8) {
     const LitRec rc = lrec_s[i];
     const int r = r0 + lane;
-    if (r < R) {
-      float* pp = &P[(size_t)rec_row(rc.dst) * Rp + r];
-      const float v = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
-      *pp = low ? *pp + v : v;
-    }
+    if (r < R)
+      P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
   }
-  if (fe_con && warp == 0 && r0 + lane < R) {
-    float* fp = &fe_con[(size_t)it.c * ldf + r0 + lane];
-    *fp = low ? *fp + fe_s[lane] : fe_s[lane];
-  }
+  if (fe_con && warp == 0 && r0 + lane < R) fe_con[(size_t)it.c * ldf + r0 + lane] = fe_s[lane];
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -325,7 +343,8 @@ cudaError_t launch_group_fr(int cfg, const DevPlan& d, const int32_t* list, int 
   case id:                                                                                \
     k_fe_group_fr<G, Q, (Y != 0)><<<grid, block, fr_smem<G, Q>(), s>>>(                   \
         list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf,  \
-        done, d.ser_info, d.dft_flops);                                                   \
+        done, d.ser_info, done ? ser_terms(d, done, ceil_div(R, 32)) : nullptr,           \
+        d.dft_flops);                                                                     \
     break;
     CLS_FR_CONFIGS(CLS_FR_CASE)
 #undef CLS_FR_CASE

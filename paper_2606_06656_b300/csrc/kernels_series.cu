@@ -95,13 +95,15 @@ __device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const flo
 }
 
 // one restart's K-term pass: Chebyshev sums, the root loop over jw roots, the
-// partials of all L literals (written to P) and FE - b0 (returned)
+// partials of all L literals (written to P) and FE - b0 (returned).  With sd
+// (a low tile) the pass stops after the roots and saves D_0..D_{K-1} and
+// FE - b0 at sd[k * Rp] instead; the dense factored kernel adds them.
 template <int K>
 __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* recs,
                                                 const float* xr, int R, bool act,
                                                 const float4* tab, const float2* bsm,
                                                 float* __restrict__ P, int Rp, int r, float wgt,
-                                                float* stg) {
+                                                float* stg, float* sd) {
   static_assert(K % 2 == 0, "table rows hold pairs of terms");
   // pass B: M[k-1] = sum over interior literals of T_k(y); two literals per
   // packed FP32x2 instruction (float2 sums, folded afterwards)
@@ -178,6 +180,14 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
       D[2 * m + 1] = fmaf(e.z, wr, fmaf(-e.w, wi, D[2 * m + 1]));
     }
   }
+  if (sd) {
+    if (act) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) sd[(size_t)k * Rp] = D[k];
+      sd[(size_t)K * Rp] = fe;
+    }
+    return fe;
+  }
   // pass C: partials, sum_k D_k U_k(y) by Clenshaw's recurrence, two
   // literals per packed instruction
   auto clenshaw = [&](float2 y) -> float2 {
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
     const SerInfo* __restrict__ ser_info, const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, int RT, float* __restrict__ P,
     float* __restrict__ fe_con, int ldf, uint8_t* __restrict__ done,
-    unsigned long long* __restrict__ flops) {
+    float* __restrict__ ser_d, unsigned long long* __restrict__ flops) {
   extern __shared__ float4 ss4[];
   float4* tab = ss4;                                                  // [96][kSerRow]
   float2* bsm = reinterpret_cast<float2*>(tab + kSeriesMaxRoots * kSerRow);  // [96]
@@ -282,16 +292,18 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
   __syncthreads();
   if (K == 0) return;
   float fev;
+  float* sd = part ? ser_d + (size_t)si.slot * (kSeriesK1 + 1) * Rp + r : nullptr;
   if (K == kSeriesK0)
-    fev = series_restart<kSeriesK0>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w, stg);
+    fev = series_restart<kSeriesK0>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w, stg, sd);
   else
-    fev = series_restart<kSeriesK1>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w, stg);
-  if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;
+    fev = series_restart<kSeriesK1>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w, stg, sd);
+  if (fe_con && act && !part) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;
   // (K is uniform over the warp, so every lane is here)
   const unsigned nact = (unsigned)__popc(__ballot_sync(kFull, act));
   if (flops && lane == 0) {
-    // per restart: L (4 + 8K) for the passes, jw (8K + 40) for the roots
-    const unsigned long long per = (unsigned long long)L * (4 + 8 * K) +
+    // per restart: L (4 + 8K) for the passes (L (4 + 4K) on a low tile, whose
+    // Clenshaw pass the dense kernel counts), jw (8K + 40) for the roots
+    const unsigned long long per = (unsigned long long)L * (4 + (part ? 4 : 8) * K) +
                                    (unsigned long long)jw * (8 * K + 40);
     atomicAdd(flops, per * (unsigned long long)nact);
   }
@@ -322,7 +334,7 @@ cudaError_t launch_dft_series(const DevPlan& d, const int32_t* list, int count, 
   const dim3 grid(count, ceil_div(RT, 8)), block(256);
   k_fe_series<<<grid, block, series_smem_bytes(maxL), s>>>(
       list, d.fe, d.coef_tab, d.ser_tab, d.ser_info, d.fe_lit, x, R, Rp, RT, P, fe_con, ldf,
-      done, d.dft_flops);
+      done, ser_terms(d, done, RT), d.dft_flops);
   return cudaGetLastError();
 }
 

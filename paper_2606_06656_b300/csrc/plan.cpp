@@ -263,6 +263,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   P.spec_off.assign(m, -1);
   P.ser_tab.clear();
   P.ser_info.assign(m, SerInfo{-1, 0, 0, 0});
+  P.n_ser_slots = 0;
   P.coef_tab = {{2.f, 0.f, 1.f, 0.f},  {1.f, 0.f, 1.f, 0.f},   {2.f, 0.f, 1.f, 0.f},
                 {2.f, 0.f, -1.f, 0.f}, {-1.f, 0.f, -1.f, 0.f}, {-2.f, 0.f, -1.f, 0.f},
                 {-2.f, 0.f, 1.f, 0.f}};
@@ -483,6 +484,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
       auto sit = ser_of_len.find(L);
       if (sit == ser_of_len.end()) sit = ser_of_len.emplace(L, series_table(L, P.ser_tab)).first;
       P.ser_info[c] = sit->second;
+      if (P.ser_info[c].off >= 0) P.ser_info[c].slot = P.n_ser_slots++;
     }
     P.dft_roots += J;
     P.dft_lroots += (int64_t)J * L;

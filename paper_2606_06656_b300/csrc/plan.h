@@ -198,7 +198,7 @@ struct SerInfo {
   int32_t off;    // first row in ser_tab, -1 if the constraint has none
   int32_t js0;    // roots in range of kSeriesK0 terms
   int32_t js1;    // roots in range of kSeriesK1 terms
-  int32_t pad;
+  int32_t slot;   // this constraint's rows of saved low-root terms (workspace)
 };
 
 // roots in range of the power-sum pass with K terms (plan.cpp)
@@ -279,6 +279,7 @@ struct HostPlan {
   // power-sum tables of the DFT constraints (see kSeriesK0), per constraint
   std::vector<F4> ser_tab;
   std::vector<SerInfo> ser_info;
+  int32_t n_ser_slots = 0;        // constraints with a power-sum table
   std::vector<FeItem> thread_items[kNumThreadCls];   // items in launch order
   // lane-group buckets: [0, kNumDftBuckets) DFT, then real
   std::vector<int32_t> bucket_list[kNumDftBuckets + kNumRealBuckets];
