@@ -42,6 +42,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCornerQS = 16;   // non-corner slots per lane
 constexpr int kCornerGroup = 4; // lanes per restart in the second pass
 constexpr int kCornerDpx = 32;  // interior literals of the second pass's root-free DP
+constexpr int kCornerChebMin = 24; // fewest low roots worth the 4-lane pass's Chebyshev sums
 
 __device__ __forceinline__ float4 ldg4(const F4* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -320,14 +321,110 @@ __device__ __forceinline__ void group_root(const float4 rt, const float4 zp, con
   acc[0] += hr;
 }
 
+// The low roots 1..jlo of one restart by Chebyshev sums over its interior
+// slots (the expansions of kernels_series.cu; corner literals exact: log 1
+// and i theta_j), spread over the restart's G lanes: each lane sums its own
+// slots and evaluates the roots j = lam, lam + G, ...; butterflies combine
+// the sums, FE and the coefficients D_k.  Sets fe and, in each lane, the
+// partials of its slots (acc) and of the two kinds of corner literal
+// (gF = sum_k D_k U_k(1), gT = sum_k D_k U_k(-1)).  ser = the length's rows.
+template <int G, int QS>
+__device__ __forceinline__ void group_low_cheb(int jlo, int nnc, int t, int lam,
+                                               const float (&y)[QS], const F4* __restrict__ ser,
+                                               const float4* ctab, float (&acc)[QS], float& fe,
+                                               float& gF, float& gT) {
+  constexpr int K = kSeriesK1;
+  float M[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) M[k] = 0.f;
+#pragma unroll
+  for (int s = 0; s < QS; ++s) {
+    const float m = lam + G * s < nnc ? 1.f : 0.f, y2 = y[s] + y[s];
+    float tp = 1.f, tt = y[s];
+    M[0] = fmaf(m, tt, M[0]);
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+      const float tn = fmaf(y2, tt, -tp);
+      tp = tt;
+      tt = tn;
+      M[k] = fmaf(m, tt, M[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int d = 1; d < G; d <<= 1) M[k] += __shfl_xor_sync(kFull, M[k], d);
+    M[k] *= 1.0f / (float)(k + 1);
+  }
+  float D[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) D[k] = 0.f;
+  float fl = 0.f;
+#pragma unroll 1
+  for (int j = lam; j < jlo; j += G) {
+    const float4* row = reinterpret_cast<const float4*>(ser + (size_t)j * kSerRow);
+    const float4 h = __ldg(row);
+    const uint32_t turns = (uint32_t)nnc * __float_as_uint(h.y) + (uint32_t)t * __float_as_uint(h.z);
+    float lr = (float)nnc * h.x, li = 0.f;
+#pragma unroll
+    for (int m = 0; m < K / 2; ++m) {
+      const float4 e = __ldg(row + 1 + m);
+      lr = fmaf(e.x, M[2 * m], lr);
+      li = fmaf(e.y, M[2 * m], li);
+      lr = fmaf(e.z, M[2 * m + 1], lr);
+      li = fmaf(e.w, M[2 * m + 1], li);
+    }
+    float sn, cs;
+    sincosf(fmaf((float)(int32_t)turns, 1.4629180792671596e-9f, li), &sn, &cs);
+    const float mag = expf(lr);
+    const float4 b = ctab[j];
+    const float gr = mag * cs, gi = mag * sn;
+    const float wr = fmaf(b.x, gr, -b.y * gi), wi = fmaf(b.x, gi, b.y * gr);
+    fl += wr;
+#pragma unroll
+    for (int m = 0; m < K / 2; ++m) {
+      const float4 e = __ldg(row + 1 + m);
+      D[2 * m] = fmaf(e.x, wr, fmaf(-e.y, wi, D[2 * m]));
+      D[2 * m + 1] = fmaf(e.z, wr, fmaf(-e.w, wi, D[2 * m + 1]));
+    }
+  }
+#pragma unroll
+  for (int d = 1; d < G; d <<= 1) fl += __shfl_xor_sync(kFull, fl, d);
+  fe = fl;
+  gF = 0.f;
+  gT = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int d = 1; d < G; d <<= 1) D[k] += __shfl_xor_sync(kFull, D[k], d);
+    gF = fmaf((float)(k + 1), D[k], gF);
+    gT = fmaf((k & 1) ? -(float)(k + 1) : (float)(k + 1), D[k], gT);
+  }
+#pragma unroll
+  for (int s = 0; s < QS; ++s) {
+    const float y2 = y[s] + y[s];
+    float b1 = 0.f, b2 = 0.f;
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k) {
+      const float b0 = fmaf(y2, b1, D[k] - b2);
+      b2 = b1;
+      b1 = b0;
+    }
+    acc[s] = b1;
+  }
+}
+
 // Pass 2 with G lanes per restart: G rounds over the tile's 32 restarts, 32/G
 // restarts per round.  ncw = the warp's slots (slot k of restart r at
 // ncw[k * 32 + r]); the restart's values are replaced by its partials; fe,
 // gF, gT of restart r go to vals[0..2][r].
+// With jlo > 0 the roots 1..jlo come from group_low_cheb (ser = the
+// length's Chebyshev rows) and the root loop starts after them.
 template <int G>
 __device__ __forceinline__ void group_roots(int L, int J, int nnc_own, int t_own, int lane,
                                             const float4* rtab, const float4* ctab,
-                                            const float4* ztab, float* ncw, float* vals) {
+                                            const float4* ztab, float* ncw, float* vals, int jlo,
+                                            const F4* __restrict__ ser) {
   constexpr int QS = kCornerQS;
   const int N = L + 1, nA = fr_roots_form0(L), nB = fr_roots_form01(L);
   const int lam = lane % G;
@@ -343,10 +440,11 @@ __device__ __forceinline__ void group_roots(int L, int J, int nnc_own, int t_own
       acc[s] = 0.f;
     }
     float fe = 0.f, gF = 0.f, gT = 0.f;
+    if (jlo > 0) group_low_cheb<G, QS>(jlo, nnc, t, lam, y, ser, ctab, acc, fe, gF, gT);
     const int dq = t % N;
-    int q = dq;
+    int q = (int)(((int64_t)(jlo + 1) * t) % N);   // (root number) * t mod N
 #pragma unroll 1
-    for (int j = 0; j < J; ++j) {
+    for (int j = jlo; j < J; ++j) {
       float2 W = make_float2(1.f, 0.f);
       if (q != 0) {
         const bool low = q <= J;
@@ -385,7 +483,8 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
     const LitRec* __restrict__ lit, const float* __restrict__ x, int R, int Rp, int RT,
     int maxL, float* __restrict__ P, float* __restrict__ fe_con, int ldf,
     uint8_t* __restrict__ done, const int8_t* __restrict__ spec_tab,
-    const int32_t* __restrict__ spec_off) {
+    const int32_t* __restrict__ spec_off, const SerInfo* __restrict__ ser_info,
+    const F4* __restrict__ ser_tab) {
   extern __shared__ float4 cs4[];
   const FeItem it = fe[list[blockIdx.x]];
   const int L = it.L, J = it.J;
@@ -503,7 +602,11 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
       fev -= it.b0;
     } else {
       float* vw = vals + warp * 96;
-      group_roots<GC>(L, J, nnc, t, lane, rtab, ctab, ztab, ncy + warp * CAP * 32, vw);
+      // long constraints: the low roots by Chebyshev sums over the interior
+      const SerInfo si = ser_info[it.c];
+      const int jlo = (si.off >= 0 && si.js1 >= kCornerChebMin) ? si.js1 : 0;
+      group_roots<GC>(L, J, nnc, t, lane, rtab, ctab, ztab, ncy + warp * CAP * 32, vw, jlo,
+                      ser_tab + (si.off >= 0 ? si.off : 0));
       fev = vw[lane];
       gF = vw[32 + lane];
       gT = vw[64 + lane];
@@ -562,12 +665,12 @@ cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, 
   const dim3 grid(count, ceil_div(RT, 8)), block(256);
   k_fe_dft_corner<1><<<grid, block, corner_smem_bytes(maxL, 1), s>>>(
       list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
-      ldf, done, d.spec_tab, d.spec_off);
+      ldf, done, d.spec_tab, d.spec_off, d.ser_info, d.ser_tab);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_fe_dft_corner<kCornerGroup><<<grid, block, corner_smem_bytes(maxL, kCornerGroup), s>>>(
       list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
-      ldf, done, d.spec_tab, d.spec_off);
+      ldf, done, d.spec_tab, d.spec_off, d.ser_info, d.ser_tab);
   return cudaGetLastError();
 }
 
