@@ -158,7 +158,7 @@ __device__ __forceinline__ void thread_body(const FeItem& it, const F4* __restri
 #pragma unroll
     for (int i = 0; i < L; ++i) {
       const int2 q = trec[i];
-      pr[(size_t)(unsigned)rec_row(q.y) * ps] = it.w * rec_sgn(q.y) * g[i];
+      st_partial(&pr[(size_t)(unsigned)rec_row(q.y) * ps], it.w * rec_sgn(q.y) * g[i]);
     }
     if (fe_con) fe_con[(size_t)it.c * ldf + r] = val;
   }
@@ -248,7 +248,7 @@ __device__ __forceinline__ void thread_body_async(const FeItem& it, const F4* __
 #pragma unroll
     for (int i = 0; i < L; ++i) {
       const int32_t d = kHold ? dst[i] : trec[i].y;
-      pr[(size_t)(unsigned)rec_row(d) * ps] = it.w * rec_sgn(d) * g[i];
+      st_partial(&pr[(size_t)(unsigned)rec_row(d) * ps], it.w * rec_sgn(d) * g[i]);
     }
     if (fe_con) fe_con[(size_t)it.c * ldf + r] = val;
   }
@@ -431,8 +431,9 @@ __global__ void __launch_bounds__(256) k_fe_thread_ckpt(
         suf[1] *= t < lim ? fmaf(xv[t], recb[b * CI + t], A1) : 1.f;
       }
       if (act && t < lim)
-        *reinterpret_cast<float*>(reinterpret_cast<char*>(P + r) +
-                                  (size_t)(unsigned)__float_as_int(q.y) * pstride) = q.w * g;
+        st_partial(reinterpret_cast<float*>(reinterpret_cast<char*>(P + r) +
+                                            (size_t)(unsigned)__float_as_int(q.y) * pstride),
+                   q.w * g);
     }
   }
   if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = val;
@@ -615,7 +616,7 @@ __global__ void __launch_bounds__(256) k_fe_group(
     const LitRec rc = lrec_s[i];
     const int r = r0 + lane;
     if (r < R)
-      P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
+      st_partial(&P[(size_t)rec_row(rc.dst) * Rp + r], it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane]);
   }
   if (fe_con && warp == 0 && r0 + lane < R) fe_con[(size_t)it.c * ldf + r0 + lane] = fe_s[lane];
 }

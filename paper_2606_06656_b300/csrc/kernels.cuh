@@ -80,6 +80,11 @@ __host__ __device__ inline int fr_roots_form01(int L) {
   const int J = (L + 1) / 2, n = 21 * (L + 1) / 50;
   return n < J ? n : J;
 }
+// A partial row entry: written once per step and read once, by the
+// accumulate kernel; evict-first (st.global.cs) so that the partials do not
+// push the point array x, which the FE kernels gather, out of L2.
+__device__ __forceinline__ void st_partial(float* p, float v) { __stcs(p, v); }
+
 // Asynchronous global -> shared copies of 4 bytes (no register round trip):
 // issue, close a group, wait until at most N groups are pending.  A thread
 // sees its own copies after the wait.

@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(256, GC == 1 ? 3 : 2) k_fe_dft_corner(
         val = it.w * my[k * 32];
         ++k;
       }
-      if (act) P[(size_t)rec_row(rc.dst) * Rp + r] = apply_sgn(val, rc.dst);
+      if (act) st_partial(&P[(size_t)rec_row(rc.dst) * Rp + r], apply_sgn(val, rc.dst));
     }
   }
   if (fe_con && act) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;

@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) k_fe_group_fr(
     const LitRec rc = lrec_s[i];
     const int r = r0 + lane;
     if (r < R)
-      P[(size_t)rec_row(rc.dst) * Rp + r] = it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane];
+      st_partial(&P[(size_t)rec_row(rc.dst) * Rp + r], it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane]);
   }
   if (fe_con && warp == 0 && r0 + lane < R) fe_con[(size_t)it.c * ldf + r0 + lane] = fe_s[lane];
 }

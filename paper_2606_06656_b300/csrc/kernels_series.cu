@@ -204,7 +204,7 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
   };
   auto put = [&](int i, float g) {
     const int32_t dst = recs[i].dst;
-    if (act) P[(size_t)rec_row(dst) * Rp + r] = wgt * rec_sgn(dst) * g;
+    if (act) st_partial(&P[(size_t)rec_row(dst) * Rp + r], wgt * rec_sgn(dst) * g);
   };
   staged_scan(
       L, recs, xr, R, act, stg,
