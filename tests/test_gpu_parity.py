@@ -143,7 +143,7 @@ def points(kind, n, R, seed):
 
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("ctype", ALL_TYPES)
-@pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 9, 16, 31, 32, 33, 64, 65, 129, 300])
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 9, 16, 17, 24, 25, 31, 32, 33, 64, 65, 129, 300])
 def test_fe_grad_by_type_and_length(P, ctype, L, kernel):
     rng = np.random.default_rng(1000 * ctype + L)
     count = max(2, min(12, 600 // L))

@@ -78,6 +78,22 @@ def test_persistent_rejects_long_constraints(P):
         p.step_persistent(x, 0.1, 2)
 
 
+def test_persistent_covers_only_short_closed_forms(P):
+    """Closed forms of up to 16 literals run in the persistent loop; one of
+    17-24 literals (its own thread class in cls_step) is rejected."""
+    rng = np.random.default_rng(12)
+    n = 300
+    def xor_rows(L, count):
+        return [(W.TYPE_XOR, 0, rng.choice(n, L, replace=False).astype(np.int32),
+                 np.where(rng.random(L) < 0.5, -1, 1).astype(np.int8)) for _ in range(count)]
+    ok = P(W.build(n, xor_rows(16, 40)))
+    x = torch.from_numpy(W.uniform_points(n, 32, seed=3)).cuda()
+    ok.step_persistent(x, 0.1, 2)
+    bad = P(W.build(n, xor_rows(16, 40) + xor_rows(20, 5)))
+    with pytest.raises(RuntimeError, match="closed-form"):
+        bad.step_persistent(x, 0.1, 2)
+
+
 def test_persistent_zero_steps_leaves_x(P):
     inst = W.random_ksat(n=100, m=426, seed=11)
     p = P(inst)
