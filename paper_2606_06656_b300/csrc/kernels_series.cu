@@ -269,9 +269,9 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
     K = jw <= si.js0 ? kSeriesK0 : (jw <= si.js1 ? kSeriesK1 : 0);
     // beyond the range: the low roots 1..js1 here, the others in the dense
     // kernel, when the root products saved (14 flops per literal and root)
-    // outweigh this pass's cost by half again
-    if (K == 0 && 2 * 14 * (int64_t)L * si.js1 >
-                      3 * ((int64_t)L * (4 + 8 * kSeriesK1) + (int64_t)si.js1 * (8 * kSeriesK1 + 40))) {
+    // outweigh the cost of this pass and of the Clenshaw share
+    if (K == 0 && 14 * (int64_t)L * si.js1 >
+                      (int64_t)L * (4 + 8 * kSeriesK1) + (int64_t)si.js1 * (8 * kSeriesK1 + 40)) {
       K = kSeriesK1;
       part = true;
       jw = si.js1;
