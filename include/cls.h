@@ -157,6 +157,39 @@ int cls_workspace_size(const cls_problem* p, int32_t R, size_t* bytes);
 int cls_init_uniform(const cls_problem* p, int32_t R, uint64_t seed,
                      int64_t r_offset, float* x, void* stream);
 
+/* Per-restart convergence tracking and refills (Sec. 3.3: in a lockstep
+ * batch, restarts that have converged idle and waste the batch's compute;
+ * the section studies the distribution of steps to convergence).  The state
+ * is a caller-owned device int32[4*R]: trk[r] = best satisfied count so far,
+ * trk[R+r] = the step it was reached, trk[2R+r] = steps since the last
+ * improvement, trk[3R+r] = first step at which every constraint was
+ * satisfied (-1 = none yet).
+ *   cls_track_reset      best = -1, its step = -1, since = 0, solved = -1.
+ *   cls_track_step       with this step's nsat (cls_step / cls_round_score):
+ *                        nsat > best: best = nsat, its step = step, since = 0;
+ *                        otherwise since += 1; nsat == m and solved < 0:
+ *                        solved = step.  step >= 0.
+ *   cls_refill           every restart with solved < 0 and since >= patience
+ *                        (>= 1) gets fresh points: the cls_init_uniform draw
+ *                        with the Philox counter's third word = generation
+ *                        (>= 1; the first draw is generation 0), pinned
+ *                        variables untouched; its best, best step and since
+ *                        restart (-1, -1, 0); *count (device int32) is
+ *                        increased by the number refilled.
+ *   cls_unsat_histogram  hist[k] = number of restarts with exactly k
+ *                        unsatisfied constraints, k = 0..m (device
+ *                        int32[m+1], overwritten).
+ * All asynchronous on stream; integer results are exact.  CLS_ERR_INVALID
+ * on NULL pointers (R > 0) or out-of-range patience / generation / step. */
+int cls_track_reset(const cls_problem* p, int32_t R, int32_t* trk, void* stream);
+int cls_track_step(const cls_problem* p, int32_t R, const int32_t* nsat, int32_t step,
+                   int32_t* trk, void* stream);
+int cls_refill(const cls_problem* p, int32_t R, float* x, int32_t* trk, int32_t patience,
+               uint64_t seed, int64_t r_offset, int32_t generation, int32_t* count,
+               void* stream);
+int cls_unsat_histogram(const cls_problem* p, int32_t R, const int32_t* nsat, int32_t* hist,
+                        void* stream);
+
 /* Objective and gradient at x (Sec. 2.3, Eq. 5 with weights):
  *   obj[r]        = sum_c w_c FE_c(s_c o x_r)            (device float[R] or NULL)
  *   grad[v*R+r]   = dF/dx_v at restart r                 (device float[n*R] or NULL)

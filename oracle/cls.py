@@ -137,3 +137,58 @@ def init_uniform(n, R, seed, r_offset=0, fixed=None, fixed_val=None):
         f = np.asarray(fixed).astype(bool)
         X[f] = np.asarray(fixed_val, dtype=np.float32)[f][:, None]
     return X
+
+
+# --- per-restart convergence tracking and refills (Sec. 3.3) -------------
+# Sec. 3.3 observes that in a lockstep batch converged restarts idle and
+# waste compute, and studies the distribution of steps to convergence.
+# These are the plain definitions the tracking kernels must reproduce.
+
+def track_reset(R):
+    """State rows: best satisfied count (-1), step it was reached (-1),
+    steps since the last improvement (0), first step with every constraint
+    satisfied (-1)."""
+    S = np.zeros((4, R), dtype=np.int64)
+    S[0] = -1
+    S[1] = -1
+    S[3] = -1
+    return S
+
+
+def track_step(S, nsat, step, m):
+    """One step's counts: improve or age, and record the first solution."""
+    S = S.copy()
+    nsat = np.asarray(nsat, dtype=np.int64)
+    up = nsat > S[0]
+    S[0] = np.where(up, nsat, S[0])
+    S[1] = np.where(up, step, S[1])
+    S[2] = np.where(up, 0, S[2] + 1)
+    S[3] = np.where((nsat == m) & (S[3] < 0), step, S[3])
+    return S
+
+
+def refill(X, S, patience, seed, generation, r_offset=0, fixed=None, fixed_val=None):
+    """Restarts not solved and without improvement for `patience` steps get
+    fresh uniform points: the draw of init_uniform with counter word 2 =
+    generation (>= 1; generation 0 is the first draw); their tracking
+    restarts.  Returns (X', S', number refilled)."""
+    X = np.array(X, dtype=np.float32, copy=True)
+    S = S.copy()
+    n, R = X.shape
+    mask = (S[3] < 0) & (S[2] >= patience)
+    for r in np.nonzero(mask)[0]:
+        for q in range((n + 3) // 4):
+            words = philox4x64((int(r) + r_offset, q, generation, 0), (seed, 0))
+            for j in range(4):
+                v = 4 * q + j
+                if v < n and not (fixed is not None and fixed[v]):
+                    X[v, r] = np.float32((words[j] >> 40) * 2.0 ** -23 - 1.0)
+    S[0, mask] = -1
+    S[1, mask] = -1
+    S[2, mask] = 0
+    return X, S, int(mask.sum())
+
+
+def unsat_histogram(nsat, m):
+    """h[k] = number of restarts with exactly k unsatisfied constraints."""
+    return np.bincount(m - np.asarray(nsat, dtype=np.int64), minlength=m + 1)

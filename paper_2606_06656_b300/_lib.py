@@ -38,6 +38,10 @@ SIGNATURES = {
     "cls_dft_work": (i32, [vp, P(i64)]),
     "cls_dft_flops_counter": (i32, [vp, P(i64), i32]),
     "cls_series_range": (i32, [i32, i32]),
+    "cls_track_reset": (i32, [vp, i32, vp, vp]),
+    "cls_track_step": (i32, [vp, i32, vp, i32, vp, vp]),
+    "cls_refill": (i32, [vp, i32, vp, vp, i32, u64, i64, i32, vp, vp]),
+    "cls_unsat_histogram": (i32, [vp, i32, vp, vp, vp]),
     "cls_solve_host_workspace_size": (i32, [vp, i32, P(sz)]),
     "cls_solve_host": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, sz, vp]),
     "cls_autotune": (i32, [vp, i32, vp, i32, vp, sz, vp]),

@@ -106,6 +106,32 @@ def cls_init_uniform(h, R, seed, r_offset, x, stream=None):
                                             _stream(stream)), "cls_init_uniform")
 
 
+def cls_track_reset(h, R, trk, stream=None):
+    """Per-restart tracking state (int32[4, R] device tensor) to its start."""
+    _lib.check(_lib.load().cls_track_reset(h, int(R), _ptr(trk), _stream(stream)),
+               "cls_track_reset")
+
+
+def cls_track_step(h, R, nsat, step, trk, stream=None):
+    """Fold one step's satisfied counts into the tracking state."""
+    _lib.check(_lib.load().cls_track_step(h, int(R), _ptr(nsat), int(step), _ptr(trk),
+                                          _stream(stream)), "cls_track_step")
+
+
+def cls_refill(h, R, x, trk, patience, seed, r_offset, generation, count, stream=None):
+    """Fresh points for the unsolved restarts without improvement for
+    `patience` steps; count (device int32[1]) is increased by their number."""
+    _lib.check(_lib.load().cls_refill(h, int(R), _ptr(x), _ptr(trk), int(patience), int(seed),
+                                      int(r_offset), int(generation), _ptr(count),
+                                      _stream(stream)), "cls_refill")
+
+
+def cls_unsat_histogram(h, R, nsat, hist, stream=None):
+    """hist[k] = restarts with k unsatisfied constraints (device int32[m + 1])."""
+    _lib.check(_lib.load().cls_unsat_histogram(h, int(R), _ptr(nsat), _ptr(hist),
+                                               _stream(stream)), "cls_unsat_histogram")
+
+
 def cls_eval(h, R, x, obj, grad, fe_con, ws, stream=None):
     _lib.check(_lib.load().cls_eval(h, int(R), _ptr(x), _ptr(obj), _ptr(grad), _ptr(fe_con),
                                     _ptr(ws), ws.numel() if ws is not None else 0,

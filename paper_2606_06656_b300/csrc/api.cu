@@ -443,6 +443,51 @@ int cls_init_uniform(const cls_problem* p, int32_t R, uint64_t seed, int64_t r_o
   return CLS_OK;
 }
 
+int cls_track_reset(const cls_problem* p, int32_t R, int32_t* trk, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (!trk && R > 0) return set_err(CLS_ERR_INVALID, "trk is NULL");
+  CLS_CUDA_TRY(cls::launch_track_reset(R, trk, (cudaStream_t)stream), "track reset kernel");
+  return CLS_OK;
+}
+
+int cls_track_step(const cls_problem* p, int32_t R, const int32_t* nsat, int32_t step,
+                   int32_t* trk, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (step < 0) return set_err(CLS_ERR_INVALID, "step must be >= 0");
+  if (R > 0 && (!nsat || !trk)) return set_err(CLS_ERR_INVALID, "nsat or trk is NULL");
+  CLS_CUDA_TRY(cls::launch_track_step(p->dev, R, step, nsat, trk, (cudaStream_t)stream),
+               "track kernel");
+  return CLS_OK;
+}
+
+int cls_refill(const cls_problem* p, int32_t R, float* x, int32_t* trk, int32_t patience,
+               uint64_t seed, int64_t r_offset, int32_t generation, int32_t* count,
+               void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (patience < 1) return set_err(CLS_ERR_INVALID, "patience must be >= 1");
+  if (generation < 1) return set_err(CLS_ERR_INVALID, "generation must be >= 1");
+  if (r_offset < 0) return set_err(CLS_ERR_INVALID, "r_offset must be >= 0");
+  if (R > 0 && (!trk || !count || (!x && p->host.n > 0)))
+    return set_err(CLS_ERR_INVALID, "x, trk or count is NULL");
+  CLS_CUDA_TRY(cls::launch_refill(p->dev, R, seed, r_offset, (uint64_t)generation, patience, trk,
+                                  x, count, (cudaStream_t)stream),
+               "refill kernels");
+  return CLS_OK;
+}
+
+int cls_unsat_histogram(const cls_problem* p, int32_t R, const int32_t* nsat, int32_t* hist,
+                        void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (!hist || (R > 0 && !nsat)) return set_err(CLS_ERR_INVALID, "nsat or hist is NULL");
+  CLS_CUDA_TRY(cls::launch_unsat_hist(p->dev, R, nsat, hist, (cudaStream_t)stream),
+               "histogram kernel");
+  return CLS_OK;
+}
+
 int cls_eval(const cls_problem* p, int32_t R, const float* x, float* obj, float* grad,
              float* fe_con, void* ws, size_t ws_bytes, void* stream) {
   int rc = check_R(p, R);

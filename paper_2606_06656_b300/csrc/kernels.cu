@@ -81,6 +81,88 @@ __global__ void __launch_bounds__(256) k_init_uniform(int n, int R, uint64_t see
 }
 
 // ---------------------------------------------------------------------------
+// Per-restart convergence tracking and refills (Sec. 3.3: in a lockstep
+// batch converged restarts idle; the distribution of steps to convergence).
+// trk = int32[4][R]: best satisfied count, the step it was reached, steps
+// since the last improvement, first step with every constraint satisfied
+// (-1 = none yet).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_track_reset(int R, int32_t* __restrict__ trk) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  trk[r] = -1;
+  trk[R + r] = -1;
+  trk[2 * R + r] = 0;
+  trk[3 * R + r] = -1;
+}
+
+__global__ void __launch_bounds__(256) k_track_step(int R, int m, int step,
+                                                    const int32_t* __restrict__ nsat,
+                                                    int32_t* __restrict__ trk) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int32_t n = nsat[r];
+  if (n > trk[r]) {
+    trk[r] = n;
+    trk[R + r] = step;
+    trk[2 * R + r] = 0;
+  } else {
+    trk[2 * R + r] += 1;
+  }
+  if (n == m && trk[3 * R + r] < 0) trk[3 * R + r] = step;
+}
+
+__device__ __forceinline__ bool refill_due(int R, int r, int patience,
+                                           const int32_t* __restrict__ trk) {
+  return trk[3 * R + r] < 0 && trk[2 * R + r] >= patience;
+}
+
+// fresh points for the restarts due: the draw of k_init_uniform with the
+// counter's third word = generation (>= 1); pinned variables untouched
+__global__ void __launch_bounds__(256) k_refill(int n, int R, uint64_t seed, int64_t r_off,
+                                                uint64_t gen, int patience,
+                                                const uint8_t* __restrict__ fixed,
+                                                const int32_t* __restrict__ trk,
+                                                float* __restrict__ x) {
+  const int64_t nq = (n + 3) / 4;
+  const int64_t total = nq * (int64_t)R;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % R);
+    if (!refill_due(R, r, patience, trk)) continue;
+    const int64_t q = idx / R;
+    uint64_t w0 = (uint64_t)(r + r_off), w1 = (uint64_t)q, w2 = gen, w3 = 0;
+    philox4x64_10(w0, w1, w2, w3, seed, 0ull);
+    const uint64_t w[4] = {w0, w1, w2, w3};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t v = 4 * q + j;
+      if (v < n && !(fixed && fixed[v])) x[v * R + r] = (float)(w[j] >> 40) * 0x1p-23f - 1.0f;
+    }
+  }
+}
+
+// after k_refill: the refilled restarts start their tracking again
+__global__ void __launch_bounds__(256) k_refill_reset(int R, int patience,
+                                                      int32_t* __restrict__ trk,
+                                                      int32_t* __restrict__ count) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R || !refill_due(R, r, patience, trk)) return;
+  trk[r] = -1;
+  trk[R + r] = -1;
+  trk[2 * R + r] = 0;
+  atomicAdd(count, 1);
+}
+
+__global__ void __launch_bounds__(256) k_unsat_hist(int R, int m, const int32_t* __restrict__ nsat,
+                                                    int32_t* __restrict__ hist) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const int k = m - nsat[r];
+  if (k >= 0 && k <= m) atomicAdd(&hist[k], 1);
+}
+
+// ---------------------------------------------------------------------------
 // A2-A5, closed-form products (clause, XOR, NAE and complements) of short
 // constraints: one thread per (constraint, restart), a warp = one constraint x
 // 32 restarts, looping over kThreadTiles restart tiles.  The body is
@@ -1115,6 +1197,41 @@ cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, f
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
   HookScope hs(h, KC_INIT, s);
   k_init_uniform<<<blocks, 256, 0, s>>>(d.n, R, seed, r_off, d.fixed, d.fixed_val, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_track_reset(int R, int32_t* trk, cudaStream_t s) {
+  if (R == 0) return cudaSuccess;
+  k_track_reset<<<(R + 255) / 256, 256, 0, s>>>(R, trk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_track_step(const DevPlan& d, int R, int step, const int32_t* nsat,
+                              int32_t* trk, cudaStream_t s) {
+  if (R == 0) return cudaSuccess;
+  k_track_step<<<(R + 255) / 256, 256, 0, s>>>(R, d.m, step, nsat, trk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refill(const DevPlan& d, int R, uint64_t seed, int64_t r_off, uint64_t gen,
+                          int patience, int32_t* trk, float* x, int32_t* count, cudaStream_t s) {
+  if (R == 0) return cudaSuccess;
+  if (d.n > 0) {
+    const int64_t total = (int64_t)((d.n + 3) / 4) * R;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
+    k_refill<<<blocks, 256, 0, s>>>(d.n, R, seed, r_off, gen, patience, d.fixed, trk, x);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_refill_reset<<<(R + 255) / 256, 256, 0, s>>>(R, patience, trk, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unsat_hist(const DevPlan& d, int R, const int32_t* nsat, int32_t* hist,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * ((size_t)d.m + 1), s);
+  if (e != cudaSuccess || R == 0) return e;
+  k_unsat_hist<<<(R + 255) / 256, 256, 0, s>>>(R, d.m, nsat, hist);
   return cudaGetLastError();
 }
 

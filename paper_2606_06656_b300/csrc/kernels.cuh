@@ -167,6 +167,14 @@ size_t group_smem_bytes(int cfg);
 
 cudaError_t launch_init(const DevPlan& d, int R, uint64_t seed, int64_t r_off, float* x,
                         cudaStream_t s, LaunchHook* h);
+// per-restart convergence tracking and refills (kernels.cu)
+cudaError_t launch_track_reset(int R, int32_t* trk, cudaStream_t s);
+cudaError_t launch_track_step(const DevPlan& d, int R, int step, const int32_t* nsat,
+                              int32_t* trk, cudaStream_t s);
+cudaError_t launch_refill(const DevPlan& d, int R, uint64_t seed, int64_t r_off, uint64_t gen,
+                          int patience, int32_t* trk, float* x, int32_t* count, cudaStream_t s);
+cudaError_t launch_unsat_hist(const DevPlan& d, int R, const int32_t* nsat, int32_t* hist,
+                              cudaStream_t s);
 
 // FE + literal partials: P[row * Rp + r] = w_c s_e dFE_c/dy_e (row = the
 // literal's variable-major row), and (if fe_con) fe_con[c * ldf + r] = FE_c.
