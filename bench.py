@@ -517,6 +517,166 @@ def run_refill(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ramsey(args):
+    """Redundant-constraint study on the paper's own structure (Sec. 4.1):
+    balanced 3-colouring of K_16 (EO per edge, CARD_GE 5 per vertex and
+    colour), plain and with the decomposed edge encoding added
+    (CARD>=2(not x) + OR(x) = EO - 1, doubling the edge gradient).  R
+    independent restarts, K lockstep steps each, for a few step sizes (the
+    paper gives none), and with adaptive constraint weighting
+    (cls_constraint_stats + cls_reweight every 10 steps, inside the timed
+    loop).  Per arm: the fraction of restarts that reached a satisfying
+    point, the median step at which they did, and, for restarts unsolved at
+    the end, how many balance constraints they violate while every edge
+    constraint holds."""
+    import torch
+    from paper_2606_06656_b300 import Problem
+    from paper_2606_06656_b300 import binding as B
+    R = args.R or 16384
+    K = args.steps if args.steps != 100 else 300
+    lrs = [0.02, 0.05, 0.1, 0.2, 0.5]
+    rw_sets = [(0.5, 4.0, 10.0), (2.0, 4.0, 10.0)]
+    every = 10
+
+    def sub(inst, cs):
+        return W.build(inst.n, [(int(inst.ctype[c]), int(inst.k[c]),
+                                 inst.lit_var[inst.offsets[c]:inst.offsets[c + 1]],
+                                 inst.lit_sign[inst.offsets[c]:inst.offsets[c + 1]])
+                                for c in cs])
+
+    out = {}
+    t_all = 0.0
+    steps_all = 0
+    lit_evals = 0
+    for red in (False, True):
+        inst = W.ramsey_balanced(16, 3, redundant=red)
+        E, VC = 120, 48
+        edge_cs = list(range(E)) + (list(range(E + VC, inst.m)) if red else [])
+        pe, pb = Problem(sub(inst, edge_cs)), Problem(sub(inst, range(E, E + VC)))
+        nsat = torch.empty(R, dtype=torch.int32, device="cuda")
+        wsat = torch.empty(R, dtype=torch.float64, device="cuda")
+        bits = torch.empty((inst.n, (R + 31) // 32), dtype=torch.int32, device="cuda")
+        trk = torch.empty((4, R), dtype=torch.int32, device="cuda")
+        gn = torch.empty(inst.m, dtype=torch.float64, device="cuda")
+        un = torch.empty(inst.m, dtype=torch.int32, device="cuda")
+        wv = torch.empty(inst.m, dtype=torch.float32, device="cuda")
+        arms = [(lr, None) for lr in lrs] + [(lr, rw) for rw in rw_sets for lr in (0.05, 0.1, 0.2)]
+        res = {}
+        for lr, rw in arms:
+            p = Problem(inst)                       # fresh weights per arm
+            ws = p.workspace(R)
+            x = p.init_uniform(R, seed=7)
+            B.cls_track_reset(p.handle, R, trk)
+            xs = x.clone()
+            for _ in range(3):                      # warm-up on a scratch copy
+                B.cls_step(p.handle, R, xs, lr, 1, bits, nsat, wsat, ws)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(K):
+                B.cls_step(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
+                B.cls_track_step(p.handle, R, nsat, k, trk)
+                if rw is not None and (k + 1) % every == 0:
+                    B.cls_constraint_stats(p.handle, R, bits, ws, gn, un)
+                    B.cls_reweight(p.handle, R, gn, un, rw[0], rw[1], rw[2], wv)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            t_all += ms
+            steps_all += K
+            lit_evals += R * inst.nnz * K
+            solved_at = trk[3].cpu().numpy()
+            ok = solved_at >= 0
+            ne, _, _ = pe.round_score(x)
+            nb, _, _ = pb.round_score(x)
+            ne, nb = ne.cpu().numpy(), nb.cpu().numpy()
+            unsolved = ~ok
+            edges_ok = unsolved & (ne == len(edge_cs))
+            viol = VC - nb[edges_ok]
+            key = f"lr={lr}" + ("" if rw is None else f",reweight(eta={rw[0]},kappa={rw[1]},w_max={rw[2]})")
+            ent = {"solved_frac": float(ok.mean()),
+                   "median_solve_step": float(np.median(solved_at[ok]) + 1) if ok.any() else None,
+                   "unsolved_with_all_edges_ok_frac": float(edges_ok.sum() / max(1, unsolved.sum())),
+                   "balance_violations_hist": {int(a): int(b) for a, b in
+                                               zip(*np.unique(viol, return_counts=True))},
+                   "ms_per_step": ms / K}
+            if rw is not None:
+                w = wv.cpu().numpy()
+                ent["final_weight_mean"] = {"edge": float(w[edge_cs].mean()),
+                                            "balance": float(w[E:E + VC].mean())}
+            res[key] = ent
+            p.close()
+        out["redundant" if red else "plain"] = res
+    line = {"metric": "fraction of restarts solved (balanced Ramsey colouring, 16 vertices, 3 colours)",
+            "value": out["plain"]["lr=0.1"]["solved_frac"], "unit": "fraction",
+            "higher_is_better": True, "n_gpus": 1, "steps": K, "dtype": "f32",
+            "data": "synthetic",
+            "throughput": {"value": lit_evals / (t_all / 1e3), "unit": "literal-evals/s"},
+            "ms_per_step": t_all / steps_all,
+            "encodings": out,
+            "config": {"workload": "ramsey_V16_C3 plain and redundant", "R": R,
+                       "reweight_every": every,
+                       "launches": "eager cls_step + cls_track_step per step"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reweight(args):
+    """Cost of adaptive constraint weighting on the mixed PB workload
+    (n = 5000, m = 22500, R = 4096): the step alone, and the statistics pass
+    (one read of every literal partial) plus the weight update, each timed
+    with CUDA events over K repetitions after warm-up.  The statistics
+    kernel is HBM-bound: its algorithmic bytes are the partials (nnz_fe * R
+    * 4 B), the bitset (n * ceil(R/32) * 4 B) and the outputs (12 B per
+    constraint)."""
+    import torch
+    from paper_2606_06656_b300 import Problem
+    from paper_2606_06656_b300 import binding as B
+    inst, R, lr = workload("mixed")
+    if args.R:
+        R = args.R
+    K = args.steps if args.steps != 100 else 50
+    p = Problem(inst)
+    x = p.init_uniform(R, seed=42)
+    ws = p.workspace(R)
+    nsat = torch.empty(R, dtype=torch.int32, device="cuda")
+    wsat = torch.empty(R, dtype=torch.float64, device="cuda")
+    bits = torch.empty((inst.n, (R + 31) // 32), dtype=torch.int32, device="cuda")
+    gn = torch.empty(inst.m, dtype=torch.float64, device="cuda")
+    un = torch.empty(inst.m, dtype=torch.int32, device="cuda")
+    wv = torch.empty(inst.m, dtype=torch.float32, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        B.cls_step(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
+        B.cls_constraint_stats(p.handle, R, bits, ws, gn, un)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    t_step = timed(lambda: B.cls_step(p.handle, R, x, lr, 1, bits, nsat, wsat, ws))
+    t_stats = timed(lambda: B.cls_constraint_stats(p.handle, R, bits, ws, gn, un))
+    t_rw = timed(lambda: B.cls_reweight(p.handle, R, gn, un, 0.0, 4.0, 10.0, wv))
+    nnz_fe = int(p.info["nnz_fe"])
+    byts = nnz_fe * R * 4 + inst.n * ((R + 31) // 32) * 4 + inst.m * 12
+    peak = float(peaks().get("hbm_gbs", 6400.0))
+    ach = byts / (t_stats * 1e-3) / 1e9
+    line = {"metric": "constraint statistics pass, fraction of HBM peak",
+            "value": ach / peak, "unit": "fraction", "higher_is_better": True, "n_gpus": 1,
+            "steps": K, "dtype": "f32", "data": "synthetic",
+            "ms_step": t_step, "ms_constraint_stats": t_stats, "ms_reweight": t_rw,
+            "overhead_every_10_steps": (t_stats + t_rw) / (10 * t_step),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "traffic": None,
+                         "kernel": "k_con_stats", "algorithmic_bytes": byts},
+            "config": {"workload": inst.name, "R": R, "inputs": "partials of the last step"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_partial(args):
     """Partial-assignment completion: 16 planted mixed-PB instances, n ~
     U{10000..30000}, m = 4.5 n, 90% of the variables pinned to the plant,
@@ -603,6 +763,10 @@ def main():
         run_partial(args)
     elif args.config == "refill":
         run_refill(args)
+    elif args.config == "ramsey":
+        run_ramsey(args)
+    elif args.config == "reweight":
+        run_reweight(args)
     else:
         run_ours(args, rank, world, local_rank)
 

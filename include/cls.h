@@ -190,6 +190,51 @@ int cls_refill(const cls_problem* p, int32_t R, float* x, int32_t* trk, int32_t 
 int cls_unsat_histogram(const cls_problem* p, int32_t R, const int32_t* nsat, int32_t* hist,
                         void* stream);
 
+/* Adaptive constraint weighting (Sec. 4.1 proposes weights informed by the
+ * constraints' gradient magnitudes, after observing that a doubled edge
+ * gradient overwhelms the balancing constraints; the paper gives no rule,
+ * so the rule below is this library's).  Weights are per constraint, shared
+ * by all restarts; they enter the objective, the gradient and wsat as the
+ * weights given at creation do.
+ *   cls_constraint_stats  per constraint c over the R restarts:
+ *       gnorm[c] = sum_r || dFE_c/dy (x_r) ||_2 over the literals entering
+ *                  FE (all literals; the free ones with CLS_SIMPLIFY_FIXED),
+ *                  from the literal partials that the last cls_eval or
+ *                  cls_step with this workspace and R left in it, divided
+ *                  by |w_c| (0 where w_c = 0 or FE_c is constant);
+ *       unsat[c] = number of restarts whose rounded point (bits, the
+ *                  bitset format of cls_round_score) violates c.
+ *     gnorm device double[m], unsat device int32[m], overwritten.  Each
+ *     restart's norm is computed in FP32 from the FP32 partials; the 32
+ *     norms of a restart tile are added in FP32, the tiles in FP64, both in
+ *     a fixed order (deterministic).  unsat is exact.  The partials are
+ *     only read; the workspace's objective scratch holds per-tile sums.
+ *   cls_reweight  from those statistics, with u_c = unsat[c]/R,
+ *     g_c = gnorm[c]/R and gbar the mean of g_c over the constraints with
+ *     FE work:
+ *       rho_c = kappa            if g_c * kappa <= gbar   (weak or no pull)
+ *             = gbar / g_c       otherwise
+ *       w_c  <- min(w_max, w_c (1 + eta u_c rho_c))      (FP64, stored FP32)
+ *     so constraints violated in many restarts gain weight, the more the
+ *     weaker their gradient.  The new weights go to w_out (device
+ *     float[m]) and into the problem.  Needs 0 <= eta, 0 < kappa,
+ *     0 < w_max, all finite.
+ *   cls_set_weights  w (device float[m], finite; not checked) become
+ *     the weights.
+ * Both weight calls are asynchronous on stream and change the problem:
+ * calls on one problem must be ordered (one stream).  A graph created while
+ * every weight was 1 recorded the unweighted score kernel: once weights
+ * change, cls_graph_launch refuses it (CLS_ERR_INVALID) and it must be
+ * created again.  cls_tuning_set / cls_autotune first synchronise the
+ * device and read the current weights back into the host plan.  Errors:
+ * CLS_ERR_INVALID on NULL pointers, R < 1 or out-of-range parameters;
+ * CLS_ERR_WORKSPACE as cls_eval. */
+int cls_constraint_stats(const cls_problem* p, int32_t R, const uint32_t* bits, void* ws,
+                         size_t ws_bytes, double* gnorm, int32_t* unsat, void* stream);
+int cls_reweight(cls_problem* p, int32_t R, const double* gnorm, const int32_t* unsat, double eta,
+                 double kappa, double w_max, float* w_out, void* stream);
+int cls_set_weights(cls_problem* p, const float* w, void* stream);
+
 /* Objective and gradient at x (Sec. 2.3, Eq. 5 with weights):
  *   obj[r]        = sum_c w_c FE_c(s_c o x_r)            (device float[R] or NULL)
  *   grad[v*R+r]   = dF/dx_v at restart r                 (device float[n*R] or NULL)

@@ -192,3 +192,59 @@ def refill(X, S, patience, seed, generation, r_offset=0, fixed=None, fixed_val=N
 def unsat_histogram(nsat, m):
     """h[k] = number of restarts with exactly k unsatisfied constraints."""
     return np.bincount(m - np.asarray(nsat, dtype=np.int64), minlength=m + 1)
+
+
+# --- adaptive constraint weighting (Sec. 4.1) -------------------------------
+# Sec. 4.1 finds that a doubled edge-constraint gradient overwhelms the
+# balancing constraints and proposes weights informed by the constraints'
+# gradient magnitudes, without a rule.  The statistics are plain
+# definitions; the update is the library's rule (stated in reweight).
+
+def constraint_stats(inst, X, free_only=False, spectra=None):
+    """gnorm[c] = sum_r ||dFE_c/dy(x_r)||_2 over the literals entering FE
+    (all, or with free_only those on unpinned variables; 0 where w_c = 0);
+    unsat[c] = restarts whose rounded point violates c.  Also returns
+    has_fe[c]: the constraint's spectrum, restricted to the counts its free
+    literals can reach, is not constant (it has a gradient at all)."""
+    X = np.asarray(X, dtype=np.float32)
+    n, R = X.shape
+    sps = spectra if spectra is not None else _sp.instance_spectra(inst)
+    Y = literal_values(inst, X)
+    fixed = np.zeros(n, bool) if (not free_only or inst.fixed is None) \
+        else np.asarray(inst.fixed).astype(bool)
+    gnorm = np.zeros(inst.m)
+    has_fe = np.zeros(inst.m, bool)
+    for c in range(inst.m):
+        a, b = int(inst.offsets[c]), int(inst.offsets[c + 1])
+        free = ~fixed[inst.lit_var[a:b]]
+        # pinned literals that are true shift the reachable counts
+        if free.all():
+            f_true = 0
+        else:
+            fv = np.asarray(inst.fixed_val, np.float64)[inst.lit_var[a:b]]
+            f_true = int(((inst.lit_sign[a:b] * fv == -1.0) & ~free).sum())
+        sp = np.asarray(sps[c])
+        reach = sp[f_true:f_true + int(free.sum()) + 1]
+        has_fe[c] = len(np.unique(reach)) > 1
+        if not has_fe[c] or float(inst.weight[c]) == 0.0:
+            continue
+        _, g = _fe.fe_grad_dp(sps[c], Y[a:b])
+        gnorm[c] = np.sqrt((g[free] ** 2).sum(axis=0)).sum()
+    _, _, sat = score(inst, X, spectra=sps)
+    unsat = (~sat).sum(axis=1).astype(np.int64)
+    return gnorm, unsat, has_fe
+
+
+def reweight(w, gnorm, unsat, has_fe, R, eta, kappa, w_max):
+    """w'_c = min(w_max, w_c (1 + eta u_c rho_c)) with u_c = unsat_c / R,
+    g_c = gnorm_c / R, gbar = mean of g_c over the constraints with FE work,
+    rho_c = kappa if g_c kappa <= gbar else gbar / g_c: constraints that many
+    restarts violate gain weight, the more the weaker their pull.  FP64,
+    result rounded to FP32."""
+    w = np.asarray(w, dtype=np.float64)
+    g = np.asarray(gnorm, dtype=np.float64) / R
+    u = np.asarray(unsat, dtype=np.float64) / R
+    has_fe = np.asarray(has_fe, bool)
+    gbar = g[has_fe].mean() if has_fe.any() else 0.0
+    rho = np.array([kappa if gc * kappa <= gbar else gbar / gc for gc in g])
+    return np.minimum(w_max, w * (1.0 + eta * u * rho)).astype(np.float32)

@@ -132,6 +132,29 @@ def cls_unsat_histogram(h, R, nsat, hist, stream=None):
                                                _stream(stream)), "cls_unsat_histogram")
 
 
+def cls_constraint_stats(h, R, bits, ws, gnorm, unsat, stream=None):
+    """Per constraint over the restarts: gnorm (device float64[m]) = sum of
+    the restarts' gradient norms from the workspace's partials of the last
+    evaluation; unsat (device int32[m]) = restarts violating it at bits."""
+    _lib.check(_lib.load().cls_constraint_stats(h, int(R), _ptr(bits), _ptr(ws),
+                                                ws.numel() if ws is not None else 0,
+                                                _ptr(gnorm), _ptr(unsat), _stream(stream)),
+               "cls_constraint_stats")
+
+
+def cls_reweight(h, R, gnorm, unsat, eta, kappa, w_max, w_out, stream=None):
+    """Weight update from cls_constraint_stats' output; new weights in w_out
+    (device float32[m]) and in the problem."""
+    _lib.check(_lib.load().cls_reweight(h, int(R), _ptr(gnorm), _ptr(unsat), float(eta),
+                                        float(kappa), float(w_max), _ptr(w_out),
+                                        _stream(stream)), "cls_reweight")
+
+
+def cls_set_weights(h, w, stream=None):
+    """w (device float32[m]) become the constraint weights."""
+    _lib.check(_lib.load().cls_set_weights(h, _ptr(w), _stream(stream)), "cls_set_weights")
+
+
 def cls_eval(h, R, x, obj, grad, fe_con, ws, stream=None):
     _lib.check(_lib.load().cls_eval(h, int(R), _ptr(x), _ptr(obj), _ptr(grad), _ptr(fe_con),
                                     _ptr(ws), ws.numel() if ws is not None else 0,

@@ -90,6 +90,7 @@ struct cls_problem {
   std::vector<void*> allocations;
   EventHook* hook = nullptr;  // non-null while profiling
   EventHook events;
+  bool weights_dirty = false;  // device weights changed since the host plan's copy
 };
 
 namespace {
@@ -235,6 +236,24 @@ int upload_lists(cls_problem* p) {
   return CLS_OK;
 }
 
+// Weights changed on the device (cls_set_weights, cls_reweight) back into the
+// host plan, whose items the short-class lists are rebuilt from on retuning.
+int pull_weights(cls_problem* p) {
+  if (!p->weights_dirty) return CLS_OK;
+  cls::HostPlan& H = p->host;
+  CLS_CUDA_TRY(cudaDeviceSynchronize(), "synchronize before reading weights");
+  if (H.m > 0)
+    CLS_CUDA_TRY(cudaMemcpy(H.fe.data(), p->dev.fe, sizeof(cls::FeItem) * (size_t)H.m,
+                            cudaMemcpyDeviceToHost),
+                 "copy weights");
+  for (int32_t c = 0; c < H.m; ++c) {
+    H.weight[c] = H.fe[c].w;
+    H.score[c].w = H.fe[c].w;
+  }
+  p->weights_dirty = false;
+  return CLS_OK;
+}
+
 // One full CLS step: FE + partials, accumulate + step + round, score.
 int run_step(const cls_problem* p, const Layout& L, float* x, float lr, uint32_t* bits,
              int32_t* nsat, double* wsat, void* ws, cudaStream_t s, bool score) {
@@ -353,6 +372,14 @@ int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const in
     // statistics: flops of the DFT roots the dense factored kernel evaluated
     const std::vector<unsigned long long> zero(1, 0ull);
     up(zero, &D.dft_flops);
+    const std::vector<double> zd(1, 0.0);
+    up(zd, &D.rw_gbar);
+    // work order of the constraint statistics pass
+    std::vector<int32_t> order(H.m);
+    for (int32_t c = 0; c < H.m; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(),
+                     [&H](int32_t a, int32_t b) { return H.fe[a].L > H.fe[b].L; });
+    up(order, &D.stat_order);
   }
   if (r2 == CLS_OK) r2 = upload_lists(p);
   if (r2 != CLS_OK) {
@@ -485,6 +512,52 @@ int cls_unsat_histogram(const cls_problem* p, int32_t R, const int32_t* nsat, in
   if (!hist || (R > 0 && !nsat)) return set_err(CLS_ERR_INVALID, "nsat or hist is NULL");
   CLS_CUDA_TRY(cls::launch_unsat_hist(p->dev, R, nsat, hist, (cudaStream_t)stream),
                "histogram kernel");
+  return CLS_OK;
+}
+
+int cls_constraint_stats(const cls_problem* p, int32_t R, const uint32_t* bits, void* ws,
+                         size_t ws_bytes, double* gnorm, int32_t* unsat, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (p->host.m > 0 && (!gnorm || !unsat)) return set_err(CLS_ERR_INVALID, "gnorm or unsat is NULL");
+  if (R > 0 && p->host.n > 0 && !bits) return set_err(CLS_ERR_INVALID, "bits is NULL");
+  if (R == 0) return set_err(CLS_ERR_INVALID, "R must be >= 1");
+  Layout L = layout_for(p, R);
+  rc = check_ws(L, ws, ws_bytes);
+  if (rc != CLS_OK) return rc;
+  const float* P = at<float>(ws, L.P);
+  // the objective's FE scratch (m x Rp floats) holds the per-tile sums
+  float* scratch = at<float>(ws, L.fe);
+  CLS_CUDA_TRY(cls::launch_con_stats(p->dev, R, L.Rp, bits, P, scratch, gnorm, unsat,
+                                     (cudaStream_t)stream),
+               "constraint statistics kernels");
+  return CLS_OK;
+}
+
+int cls_set_weights(cls_problem* p, const float* w, void* stream) {
+  if (!p) return set_err(CLS_ERR_INVALID, "problem is NULL");
+  if (p->host.m > 0 && !w) return set_err(CLS_ERR_INVALID, "w is NULL");
+  CLS_CUDA_TRY(cls::launch_set_weights(p->dev, w, (cudaStream_t)stream), "weights kernel");
+  p->dev.unit_weights = 0;
+  p->weights_dirty = true;
+  return CLS_OK;
+}
+
+int cls_reweight(cls_problem* p, int32_t R, const double* gnorm, const int32_t* unsat, double eta,
+                 double kappa, double w_max, float* w_out, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (R == 0) return set_err(CLS_ERR_INVALID, "R must be >= 1");
+  if (!(eta >= 0.0 && eta < 1e30) || !(kappa > 0.0 && kappa < 1e30) ||
+      !(w_max > 0.0 && w_max <= 3.0e38))
+    return set_err(CLS_ERR_INVALID, "need 0 <= eta, 0 < kappa, 0 < w_max <= FLT_MAX, all finite");
+  if (p->host.m > 0 && (!gnorm || !unsat || !w_out))
+    return set_err(CLS_ERR_INVALID, "gnorm, unsat or w_out is NULL");
+  CLS_CUDA_TRY(cls::launch_reweight(p->dev, R, gnorm, unsat, eta, kappa, w_max, w_out,
+                                    p->dev.rw_gbar, (cudaStream_t)stream),
+               "reweight kernels");
+  p->dev.unit_weights = 0;
+  p->weights_dirty = true;
   return CLS_OK;
 }
 
@@ -711,6 +784,8 @@ int cls_tuning_set(cls_problem* p, const int32_t* cfg, int32_t n) {
   for (int b = 0; b < cls::kNumRealBuckets; ++b) t.real[b] = cfg[cls::kNumDftBuckets + b];
   std::string msg;
   if (!cls::tuning_valid(t, &msg)) return set_err(CLS_ERR_INVALID, msg);
+  int rc = pull_weights(p);
+  if (rc != CLS_OK) return rc;
   cls::assign_groups(&p->host, t);
   return upload_lists(p);
 }
@@ -818,6 +893,8 @@ struct cls_graph {
   std::vector<cudaStream_t> streams;   // every stream created for the capture
   std::vector<cudaEvent_t> events;     // every event created for the capture
   int64_t launches = 0;
+  // problems whose score was recorded with the all-weights-one kernel
+  std::vector<const cls_problem*> unit_score;
 };
 
 namespace {
@@ -1013,12 +1090,19 @@ int cls_batch_graph_create(int32_t count, const cls_problem* const* ps, const in
     (void)cudaGetLastError();
     return cuda_err(e, "cudaGraphInstantiate");
   }
+  for (int i = 0; i < count; ++i)
+    if (ps[i]->dev.unit_weights) g->unit_score.push_back(ps[i]);
   *out = g;
   return CLS_OK;
 }
 
 int cls_graph_launch(cls_graph* g, void* stream) {
   if (!g || !g->exec) return set_err(CLS_ERR_INVALID, "graph is NULL");
+  for (const cls_problem* p : g->unit_score)
+    if (!p->dev.unit_weights)
+      return set_err(CLS_ERR_INVALID,
+                     "weights changed after the graph was created with all weights 1; "
+                     "create it again");
   CLS_CUDA_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream), "cudaGraphLaunch");
   return CLS_OK;
 }

@@ -872,6 +872,210 @@ __device__ __forceinline__ void score_range(int rg, int tile, int lane, int RW,
   *ws_out = UNIT ? (double)cnt : ws;
 }
 
+// ---------------------------------------------------------------------------
+// Adaptive constraint weighting (Sec. 4.1 suggests weights informed by the
+// constraints' gradient magnitudes).  Per constraint c, over the R restarts:
+//   gnorm[c] = sum_r || dFE_c/dy (x_r) ||_2  over the literals entering FE,
+//              from the partials P (= w_c s_e dFE_c/dy_e) of the last
+//              evaluation, divided by |w_c| (0 where w_c = 0);
+//   unsat[c] = # restarts whose rounded point (bitset) violates c.
+// Pass 1: one warp per (constraint, tile of 32 restarts), pairs in
+// constraint-major order over a grid-stride loop (long and short
+// constraints balance out); each lane's norm in FP32, the warp's 32 norms
+// added in a fixed FP32 tree, written with the tile's violation count to
+// scratch [m][RW].  Pass 2: one warp per constraint adds its RW tile sums
+// in FP64 in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kStatWarps = 8;
+constexpr int kStatTiles = 8;   // restart tiles per warp work item (loads in flight)
+
+__global__ void __launch_bounds__(256) k_con_stats_tile(int m, int RW, int R, int Rp,
+                                                        const FeItem* __restrict__ fe,
+                                                        const ScoreItem* __restrict__ sc,
+                                                        const LitRec* __restrict__ fe_lit,
+                                                        const LitRec* __restrict__ lit,
+                                                        const uint32_t* __restrict__ satbits,
+                                                        const uint32_t* __restrict__ bits,
+                                                        const float* __restrict__ P,
+                                                        const int32_t* __restrict__ order,
+                                                        float* __restrict__ tg,
+                                                        int32_t* __restrict__ tu) {
+  const int lane = threadIdx.x & 31;
+  const int TG = (RW + kStatTiles - 1) / kStatTiles;   // tile groups per constraint
+  const int64_t total = (int64_t)m * TG;
+  const int64_t nw = (int64_t)gridDim.x * kStatWarps;
+  for (int64_t item = (int64_t)blockIdx.x * kStatWarps + (threadIdx.x >> 5); item < total;
+       item += nw) {
+    // constraints longest first, so that the long items start early
+    const int oc = (int)(item / TG);
+    const int c = order[oc];
+    const int tile0 = (int)(item - (int64_t)oc * TG) * kStatTiles;
+    const int nt = min(kStatTiles, RW - tile0);
+    const FeItem it = fe[c];
+    const ScoreItem s = sc[c];
+    // sum of squared partials per (tile, lane): 32 literals at a time, lane k
+    // fetches literal k's partial row, then every row is read for the
+    // item's tiles (independent 128-byte loads)
+    float q[kStatTiles];
+#pragma unroll
+    for (int tt = 0; tt < kStatTiles; ++tt) q[tt] = 0.f;
+    const LitRec* fl = fe_lit + it.lit0;
+    for (int k0 = 0; k0 < it.L; k0 += 32) {
+      const int nk = min(32, it.L - k0);
+      const int myrow = lane < nk ? rec_row(fl[k0 + lane].dst) : 0;
+      int k = 0;
+      for (; k + 2 <= nk; k += 2) {   // two rows' loads issued before their FMAs
+        const float* ra = P + (size_t)__shfl_sync(kFull, myrow, k) * Rp + tile0 * 32 + lane;
+        const float* rb = P + (size_t)__shfl_sync(kFull, myrow, k + 1) * Rp + tile0 * 32 + lane;
+        float va[kStatTiles], vb[kStatTiles];
+#pragma unroll
+        for (int tt = 0; tt < kStatTiles; ++tt) {
+          va[tt] = tt < nt ? ra[tt * 32] : 0.f;
+          vb[tt] = tt < nt ? rb[tt * 32] : 0.f;
+        }
+#pragma unroll
+        for (int tt = 0; tt < kStatTiles; ++tt) q[tt] = fmaf(vb[tt], vb[tt], fmaf(va[tt], va[tt], q[tt]));
+      }
+      if (k < nk) {
+        const float* ra = P + (size_t)__shfl_sync(kFull, myrow, k) * Rp + tile0 * 32 + lane;
+#pragma unroll
+        for (int tt = 0; tt < kStatTiles; ++tt)
+          if (tt < nt) q[tt] = fmaf(ra[tt * 32], ra[tt * 32], q[tt]);
+      }
+    }
+    // true-literal counts: lane k fetches literal k's bitset words, a 32x32
+    // bit transpose gives each lane (restart) its literals' bits
+    int t[kStatTiles];
+#pragma unroll
+    for (int tt = 0; tt < kStatTiles; ++tt) t[tt] = 0;
+    for (int k0 = 0; k0 < s.L; k0 += 32) {
+      uint32_t word[kStatTiles];
+      const bool mine = k0 + lane < s.L;
+      LitRec rc{0, 0};
+      if (mine) rc = lit[s.lit0 + k0 + lane];
+#pragma unroll
+      for (int tt = 0; tt < kStatTiles; ++tt) {
+        word[tt] = 0;
+        if (mine && tt < nt) {
+          word[tt] = bits[(size_t)rc.var * RW + tile0 + tt];
+          if (rc.dst < 0) word[tt] = ~word[tt];
+        }
+      }
+#pragma unroll
+      for (int tt = 0; tt < kStatTiles; ++tt) t[tt] += __popc(transpose32(word[tt], lane));
+    }
+    const float inv_w = it.w != 0.f ? 1.0f / fabsf(it.w) : 0.f;
+#pragma unroll
+    for (int tt = 0; tt < kStatTiles; ++tt) {
+      if (tt >= nt) break;
+      const int r = (tile0 + tt) * 32 + lane;
+      const bool act = r < R;
+      float g = act ? sqrtf(q[tt]) * inv_w : 0.f;
+      const unsigned viol = __ballot_sync(kFull, act && !sat_of(s, t[tt], satbits));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(kFull, g, o);
+      if (lane == 0) {
+        tg[(size_t)c * RW + tile0 + tt] = g;
+        tu[(size_t)c * RW + tile0 + tt] = __popc(viol);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_con_stats_reduce(int m, int RW,
+                                                          const float* __restrict__ tg,
+                                                          const int32_t* __restrict__ tu,
+                                                          double* __restrict__ gnorm,
+                                                          int32_t* __restrict__ unsat) {
+  const int c = blockIdx.x * kStatWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= m) return;
+  double a = 0.0;
+  int u = 0;
+  for (int j = lane; j < RW; j += 32) {
+    a += (double)tg[(size_t)c * RW + j];
+    u += tu[(size_t)c * RW + j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(kFull, a, o);
+    u += __shfl_xor_sync(kFull, u, o);
+  }
+  if (lane == 0) {
+    gnorm[c] = a;
+    unsat[c] = u;
+  }
+}
+
+// mean per-restart gradient norm over the constraints with FE work:
+// gbar = (sum_{c: L_fe > 0} gnorm[c] / R) / #{c: L_fe > 0}; one block, fixed order
+__global__ void __launch_bounds__(1024) k_rw_mean(int m, int R, const FeItem* __restrict__ fe,
+                                                  const double* __restrict__ gnorm,
+                                                  double* __restrict__ gbar) {
+  __shared__ double sa[1024];
+  __shared__ int sn[1024];
+  double a = 0.0;
+  int n = 0;
+  for (int c = threadIdx.x; c < m; c += 1024) {
+    if (fe[c].L > 0) {
+      a += gnorm[c] / (double)R;
+      ++n;
+    }
+  }
+  sa[threadIdx.x] = a;
+  sn[threadIdx.x] = n;
+  __syncthreads();
+  for (int h = 512; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      sa[threadIdx.x] += sa[threadIdx.x + h];
+      sn[threadIdx.x] += sn[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *gbar = sn[0] > 0 ? sa[0] / (double)sn[0] : 0.0;
+}
+
+// w'_c = min(w_max, w_c (1 + eta u_c rho_c)), u_c = unsat[c] / R,
+// rho_c = kappa if g_c kappa <= gbar else gbar / g_c, g_c = gnorm[c] / R (FP64)
+__global__ void __launch_bounds__(256) k_rw_update(int m, int R, const FeItem* __restrict__ fe,
+                                                   const double* __restrict__ gnorm,
+                                                   const int32_t* __restrict__ unsat,
+                                                   const double* __restrict__ gbar, double eta,
+                                                   double kappa, double w_max,
+                                                   float* __restrict__ w_out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  const double gb = *gbar;
+  const double u = (double)unsat[c] / (double)R;
+  const double g = gnorm[c] / (double)R;
+  const double rho = g * kappa <= gb ? kappa : gb / g;
+  const double w = (double)fe[c].w * (1.0 + eta * u * rho);
+  w_out[c] = (float)fmin(w_max, w);
+}
+
+// new weights into every device copy the kernels read: the FE items in
+// constraint order, the score items, and the short closed-form classes'
+// items (in launch order, located by their constraint index)
+__global__ void __launch_bounds__(256) k_set_weights(int m, const float* __restrict__ w,
+                                                     FeItem* __restrict__ fe,
+                                                     ScoreItem* __restrict__ sc, FeItem* t0,
+                                                     int n0, FeItem* t1, int n1, FeItem* t2,
+                                                     int n2) {
+  const int total = m + n0 + n1 + n2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    if (i < m) {
+      fe[i].w = w[i];
+      sc[i].w = w[i];
+    } else if (i < m + n0) {
+      t0[i - m].w = w[t0[i - m].c];
+    } else if (i < m + n0 + n1) {
+      t1[i - m - n0].w = w[t1[i - m - n0].c];
+    } else {
+      t2[i - m - n0 - n1].w = w[t2[i - m - n0 - n1].c];
+    }
+  }
+}
+
 template <bool UNIT>
 __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
                                                const int32_t* __restrict__ ranges,
@@ -1233,6 +1437,50 @@ cudaError_t launch_unsat_hist(const DevPlan& d, int R, const int32_t* nsat, int3
   if (e != cudaSuccess || R == 0) return e;
   k_unsat_hist<<<(R + 255) / 256, 256, 0, s>>>(R, d.m, nsat, hist);
   return cudaGetLastError();
+}
+
+cudaError_t launch_con_stats(const DevPlan& d, int R, int Rp, const uint32_t* bits,
+                             const float* P, float* scratch, double* gnorm, int32_t* unsat,
+                             cudaStream_t s) {
+  if (d.m == 0) return cudaSuccess;
+  const int RW = (R + 31) / 32;
+  const int64_t pairs = (int64_t)d.m * RW;
+  float* tg = scratch;
+  int32_t* tu = reinterpret_cast<int32_t*>(scratch + pairs);
+  const int64_t items = (int64_t)d.m * ((RW + kStatTiles - 1) / kStatTiles);
+  const int blocks = (int)std::min<int64_t>((items + kStatWarps - 1) / kStatWarps, 148 * 8);
+  k_con_stats_tile<<<blocks, 32 * kStatWarps, 0, s>>>(d.m, RW, R, Rp, d.fe, d.score, d.fe_lit,
+                                                      d.lit, d.satbits, bits, P, d.stat_order,
+                                                      tg, tu);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_con_stats_reduce<<<(d.m + kStatWarps - 1) / kStatWarps, 32 * kStatWarps, 0, s>>>(
+      d.m, RW, tg, tu, gnorm, unsat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_weights(const DevPlan& d, const float* w, cudaStream_t s) {
+  const int total = d.m + d.thread_count[0] + d.thread_count[1] + d.thread_count[2];
+  if (total == 0) return cudaSuccess;
+  const int blocks = std::min((total + 255) / 256, 148 * 8);
+  k_set_weights<<<blocks, 256, 0, s>>>(d.m, w, d.fe, d.score, d.thread_items[0],
+                                       d.thread_count[0], d.thread_items[1], d.thread_count[1],
+                                       d.thread_items[2], d.thread_count[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reweight(const DevPlan& d, int R, const double* gnorm, const int32_t* unsat,
+                            double eta, double kappa, double w_max, float* w_out, double* gbar,
+                            cudaStream_t s) {
+  if (d.m == 0) return cudaSuccess;
+  k_rw_mean<<<1, 1024, 0, s>>>(d.m, R, d.fe, gnorm, gbar);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rw_update<<<(d.m + 255) / 256, 256, 0, s>>>(d.m, R, d.fe, gnorm, unsat, gbar, eta, kappa,
+                                                w_max, w_out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_set_weights(d, w_out, s);
 }
 
 cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int count, int maxL, int maxJ,

@@ -34,6 +34,8 @@ struct DevPlan {
   int32_t n_ranges = 0;
   int32_t unit_weights = 0;          // every constraint weight is exactly 1
   unsigned long long* dft_flops = nullptr;   // flops of the evaluated DFT roots
+  double* rw_gbar = nullptr;         // scratch of the weight update (mean gradient norm)
+  int32_t* stat_order = nullptr;     // constraints by FE length, longest first
   int8_t* spec_tab = nullptr;        // spectra of the DFT constraints (+-1, t = 0..L)
   int32_t* spec_off = nullptr;       // per constraint, -1 if not a DFT constraint
   F4* ser_tab = nullptr;             // power-sum tables (plan.h, kSeriesK0)
@@ -175,6 +177,17 @@ cudaError_t launch_refill(const DevPlan& d, int R, uint64_t seed, int64_t r_off,
                           int patience, int32_t* trk, float* x, int32_t* count, cudaStream_t s);
 cudaError_t launch_unsat_hist(const DevPlan& d, int R, const int32_t* nsat, int32_t* hist,
                               cudaStream_t s);
+
+// adaptive constraint weighting (kernels.cu): per-constraint statistics over
+// the restarts, the weight update, and writing weights into the plan's items
+// scratch: at least m * ceil(R/32) * 8 bytes, 4-byte aligned
+cudaError_t launch_con_stats(const DevPlan& d, int R, int Rp, const uint32_t* bits,
+                             const float* P, float* scratch, double* gnorm, int32_t* unsat,
+                             cudaStream_t s);
+cudaError_t launch_set_weights(const DevPlan& d, const float* w, cudaStream_t s);
+cudaError_t launch_reweight(const DevPlan& d, int R, const double* gnorm, const int32_t* unsat,
+                            double eta, double kappa, double w_max, float* w_out, double* gbar,
+                            cudaStream_t s);
 
 // FE + literal partials: P[row * Rp + r] = w_c s_e dFE_c/dy_e (row = the
 // literal's variable-major row), and (if fe_con) fe_con[c * ldf + r] = FE_c.

@@ -195,6 +195,55 @@ def redundant_5sat(n=2000, m=40000, redundancy=0.0, red_len=(50, 200), seed=1300
                  meta=dict(seed=seed, redundancy=redundancy))
 
 
+def ramsey_balanced(V=16, C=3, redundant=False) -> Instance:
+    """Balanced edge colouring of the complete graph K_V with C colours
+    (Sec. 4.1).  Variable c(e, i) = e*C + i is True when edge e (pairs u < v
+    in lexicographic order) takes colour i.  Constraints, in this order:
+      * per edge: EO over c(e, 0..C-1) (each edge takes exactly one colour);
+      * per vertex v and colour i: CARD_GE, k = ceil((V-1)/C), over
+        c({v, w}, i) for the V-1 neighbours w (balanced colour degrees);
+      * redundant=True adds, per edge, the decomposed form of the same
+        exactly-one condition: CARD_GE over the negated literals with
+        k = C-1 (at most one colour; CARD>=2(not x) for C = 3) and OR over
+        the positive ones (at least one colour).
+    With V even and C dividing V-1 the plant is a round-robin
+    1-factorisation of K_V (V-1 perfect matchings, (V-1)/C of them per
+    colour), which gives every vertex exactly (V-1)/C edges of each colour;
+    otherwise plant is None (and for C not dividing V-1 the balance
+    thresholds sum past V-1 at every vertex, so no assignment exists)."""
+    edges = [(u, v) for u in range(V) for v in range(u + 1, V)]
+    eid = {e: i for i, e in enumerate(edges)}
+    E = len(edges)
+    n = E * C
+    pos = np.ones(C, dtype=np.int8)
+    rows = [(TYPE_EO, 0, np.arange(e * C, (e + 1) * C, dtype=np.int32), pos) for e in range(E)]
+    k = -(-(V - 1) // C)
+    for v in range(V):
+        for i in range(C):
+            vs = np.array([eid[(min(v, w), max(v, w))] * C + i for w in range(V) if w != v],
+                          dtype=np.int32)
+            rows.append((TYPE_CARD_GE, k, vs, np.ones(V - 1, dtype=np.int8)))
+    if redundant:
+        for e in range(E):
+            vs = np.arange(e * C, (e + 1) * C, dtype=np.int32)
+            rows.append((TYPE_CARD_GE, C - 1, vs, -pos))
+            rows.append((TYPE_OR, 0, vs.copy(), pos))
+    plant = None
+    if V % 2 == 0 and (V - 1) % C == 0:
+        colour = np.full(E, -1)
+        per = (V - 1) // C
+        inf, mod = V - 1, V - 1
+        for r in range(V - 1):
+            pairs = [(inf, r)] + [((r + j) % mod, (r - j) % mod) for j in range(1, V // 2)]
+            for a, b in pairs:
+                colour[eid[(min(a, b), max(a, b))]] = r // per
+        plant = np.ones(n, dtype=np.int8)
+        plant[np.arange(E) * C + colour] = -1
+    return build(n, rows, plant=plant,
+                 name=f"ramsey_V{V}_C{C}" + ("_redundant" if redundant else ""),
+                 meta=dict(V=V, C=C, redundant=redundant, edges=E, k=k))
+
+
 def partial_assignment(inst: Instance, frac_fixed=0.9, seed=1500) -> Instance:
     """Pin frac_fixed of the variables to the plant (Sec. 3.2's partial
     assignment completion)."""
