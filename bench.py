@@ -528,7 +528,9 @@ def run_ramsey(args):
     loop).  Per arm: the fraction of restarts that reached a satisfying
     point, the median step at which they did, and, for restarts unsolved at
     the end, how many balance constraints they violate while every edge
-    constraint holds."""
+    constraint holds.  Two more arms run 4K steps with refills (cls_refill,
+    patience 20): "solved" then counts restarts solved by any of the points
+    a slot held."""
     import torch
     from paper_2606_06656_b300 import Problem
     from paper_2606_06656_b300 import binding as B
@@ -537,6 +539,7 @@ def run_ramsey(args):
     lrs = [0.02, 0.05, 0.1, 0.2, 0.5]
     rw_sets = [(0.5, 4.0, 10.0), (2.0, 4.0, 10.0)]
     every = 10
+    patience = 20
 
     def sub(inst, cs):
         return W.build(inst.n, [(int(inst.ctype[c]), int(inst.k[c]),
@@ -560,9 +563,15 @@ def run_ramsey(args):
         gn = torch.empty(inst.m, dtype=torch.float64, device="cuda")
         un = torch.empty(inst.m, dtype=torch.int32, device="cuda")
         wv = torch.empty(inst.m, dtype=torch.float32, device="cuda")
-        arms = [(lr, None) for lr in lrs] + [(lr, rw) for rw in rw_sets for lr in (0.05, 0.1, 0.2)]
+        arms = [(lr, None, False) for lr in lrs] + \
+            [(lr, rw, False) for rw in rw_sets for lr in (0.05, 0.1, 0.2)] + \
+            [(0.1, None, True), (0.1, rw_sets[1], True)]
         res = {}
-        for lr, rw in arms:
+        cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for lr, rw, refill in arms:
+            KK = 4 * K if refill else K
+            gen = 0
+            cnt.zero_()
             p = Problem(inst)                       # fresh weights per arm
             ws = p.workspace(R)
             x = p.init_uniform(R, seed=7)
@@ -573,18 +582,21 @@ def run_ramsey(args):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            for k in range(K):
+            for k in range(KK):
                 B.cls_step(p.handle, R, x, lr, 1, bits, nsat, wsat, ws)
                 B.cls_track_step(p.handle, R, nsat, k, trk)
                 if rw is not None and (k + 1) % every == 0:
                     B.cls_constraint_stats(p.handle, R, bits, ws, gn, un)
                     B.cls_reweight(p.handle, R, gn, un, rw[0], rw[1], rw[2], wv)
+                if refill and (k + 1) % every == 0:
+                    gen += 1
+                    B.cls_refill(p.handle, R, x, trk, patience, 7, 0, gen, cnt)
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             t_all += ms
-            steps_all += K
-            lit_evals += R * inst.nnz * K
+            steps_all += KK
+            lit_evals += R * inst.nnz * KK
             solved_at = trk[3].cpu().numpy()
             ok = solved_at >= 0
             ne, _, _ = pe.round_score(x)
@@ -593,13 +605,16 @@ def run_ramsey(args):
             unsolved = ~ok
             edges_ok = unsolved & (ne == len(edge_cs))
             viol = VC - nb[edges_ok]
-            key = f"lr={lr}" + ("" if rw is None else f",reweight(eta={rw[0]},kappa={rw[1]},w_max={rw[2]})")
+            key = f"lr={lr}" + ("" if rw is None else f",reweight(eta={rw[0]},kappa={rw[1]},w_max={rw[2]})") \
+                + (f",refill(patience={patience}),steps={KK}" if refill else "")
             ent = {"solved_frac": float(ok.mean()),
                    "median_solve_step": float(np.median(solved_at[ok]) + 1) if ok.any() else None,
                    "unsolved_with_all_edges_ok_frac": float(edges_ok.sum() / max(1, unsolved.sum())),
                    "balance_violations_hist": {int(a): int(b) for a, b in
                                                zip(*np.unique(viol, return_counts=True))},
-                   "ms_per_step": ms / K}
+                   "ms_per_step": ms / KK}
+            if refill:
+                ent["refilled"] = int(cnt.item())
             if rw is not None:
                 w = wv.cpu().numpy()
                 ent["final_weight_mean"] = {"edge": float(w[edge_cs].mean()),
