@@ -114,3 +114,40 @@ class Problem:
         B.cls_solve_host(self.handle, R, x0_host, lr, n_steps, nsat_host, x_host,
                          self.workspace(R, host_solve=True))
         return nsat_host
+
+    # -- per-restart tracking and refills (Sec. 3.3) ----------------------
+    def track_reset(self, R, trk=None):
+        """Tracking state int32[4, R]: best count, its step, steps since the
+        last improvement, first solved step."""
+        t = trk if trk is not None else torch.empty((4, R), dtype=torch.int32,
+                                                     device=self.device)
+        B.cls_track_reset(self.handle, R, t)
+        return t
+
+    def track_step(self, nsat, step, trk):
+        B.cls_track_step(self.handle, trk.shape[1], nsat, step, trk)
+
+    def refill(self, x, trk, patience, seed, generation, count, r_offset=0):
+        B.cls_refill(self.handle, self._x(x), x, trk, patience, seed, r_offset, generation, count)
+
+    # -- adaptive constraint weighting (Sec. 4.1) -------------------------
+    def constraint_stats(self, bits, R):
+        """(gnorm float64[m], unsat int32[m]) from the partials of the last
+        eval/step with R restarts and the bitset of the rounded points."""
+        g = torch.empty(self.m, dtype=torch.float64, device=self.device)
+        u = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        B.cls_constraint_stats(self.handle, R, bits, self.workspace(R), g, u)
+        return g, u
+
+    def reweight(self, gnorm, unsat, R, eta, kappa=4.0, w_max=10.0):
+        """New weights (float32[m]) from constraint_stats' output; they also
+        become the problem's weights."""
+        w = torch.empty(self.m, dtype=torch.float32, device=self.device)
+        B.cls_reweight(self.handle, R, gnorm, unsat, eta, kappa, w_max, w)
+        return w
+
+    def set_weights(self, w):
+        if not (w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
+                and w.numel() == self.m):
+            raise ValueError("w must be a contiguous float32 CUDA tensor of m entries")
+        B.cls_set_weights(self.handle, w)

@@ -33,9 +33,13 @@ def read_any(path):
 
 
 def solve(inst, restarts=1024, steps=1000, lr=0.1, seed=1, patience=50,
-          refill_every=10, check_every=1, deadline=None):
+          refill_every=10, check_every=1, deadline=None, reweight=0.0):
     """Runs the loop; returns (solved, assignment or None, best unsatisfied
-    count, steps run).  assignment[v] is True where variable v is True."""
+    count, steps run).  assignment[v] is True where variable v is True.
+    reweight > 0: every refill_every steps the constraint weights are
+    updated from the batch's statistics (cls_reweight with eta = reweight,
+    kappa 4, w_max 10), raising often-violated constraints with weak
+    gradients (Sec. 4.1)."""
     import torch
     from .api import Problem
     from . import binding as B
@@ -65,6 +69,9 @@ def solve(inst, restarts=1024, steps=1000, lr=0.1, seed=1, patience=50,
             if deadline is not None and time.monotonic() > deadline:
                 return False, None, m - best, k + 1
         if (k + 1) % refill_every == 0:
+            if reweight > 0:
+                g, u = p.constraint_stats(bits, R)
+                p.reweight(g, u, R, reweight)
             gen += 1
             B.cls_refill(p.handle, R, x, trk, patience, seed, 0, gen, cnt)
     return False, None, m - best, steps
@@ -80,6 +87,8 @@ def main(argv=None):
     ap.add_argument("--patience", type=int, default=50)
     ap.add_argument("--check-every", type=int, default=1)
     ap.add_argument("--time-limit", type=float, default=0.0, help="seconds (0 = none)")
+    ap.add_argument("--reweight", type=float, default=0.0,
+                    help="adaptive constraint weighting rate eta (0 = off)")
     a = ap.parse_args(argv)
     inst, kind = read_any(a.file)
     print(f"c {kind}: n={inst.n} m={inst.m} literals={inst.nnz} dropped={inst.dropped}")
@@ -88,7 +97,8 @@ def main(argv=None):
     t0 = time.monotonic()
     ok, asg, unsat, k = solve(inst, a.restarts, a.steps, a.lr, a.seed, a.patience,
                               check_every=a.check_every,
-                              deadline=t0 + a.time_limit if a.time_limit > 0 else None)
+                              deadline=t0 + a.time_limit if a.time_limit > 0 else None,
+                              reweight=a.reweight)
     print(f"c steps={k} time={time.monotonic() - t0:.3f}s")
     if not ok:
         print(f"c fewest unsatisfied constraints: {unsat}")

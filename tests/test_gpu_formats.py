@@ -97,3 +97,41 @@ def test_solve_cli_finds_a_model(tmp_path, capsys):
     true = {abs(l) for l in lits[:-1] if l > 0}
     for c in clauses:
         assert any((abs(l) in true) == (l > 0) for l in c), c
+
+
+def test_solve_cli_opb_with_weighting(tmp_path, capsys):
+    """The solver with adaptive weighting on a planted OPB file (clauses
+    written as linear constraints, at-most and exactly constraints that the
+    plant satisfies): SATISFIABLE, and the printed model satisfies every
+    linear constraint of the file, evaluated here directly."""
+    from paper_2606_06656_b300.solve import main
+    rng = np.random.default_rng(12)
+    n = 120
+    plant = rng.random(n) < 0.5
+    lines, cons = [f"* #variable= {n} #constraint= 300"], []
+    while len(cons) < 300:
+        L = int(rng.integers(3, 9))
+        v = rng.choice(n, size=L, replace=False)
+        a = rng.choice([-1, 1], size=L)
+        lhs = int(sum(c * int(plant[x]) for c, x in zip(a, v)))
+        rel = str(rng.choice([">=", "<=", "="]))
+        k = lhs - int(rng.integers(0, 2)) if rel == ">=" else (
+            lhs + int(rng.integers(0, 2)) if rel == "<=" else lhs)
+        lo, hi = int((a < 0).sum()) * -1, int((a > 0).sum())
+        if (rel == ">=" and k <= lo) or (rel == "<=" and k >= hi):
+            continue                                   # always true: skip
+        cons.append((a, v, rel, k))
+        lines.append(" ".join(f"{int(c):+d} x{int(x) + 1}" for c, x in zip(a, v))
+                     + f" {rel} {k} ;")
+    f = tmp_path / "planted.opb"
+    f.write_text("\n".join(lines) + "\n")
+    rc = main([str(f), "--restarts", "512", "--steps", "1500", "--reweight", "1.0"])
+    out = capsys.readouterr().out
+    assert rc == 10 and "s SATISFIABLE" in out, out
+    vline = [l for l in out.splitlines() if l.startswith("v ")][0]
+    val = {}
+    for tok in vline.split()[1:]:
+        val[int(tok.lstrip("-x"))] = not tok.startswith("-")
+    for a, v, rel, k in cons:
+        lhs = sum(int(c) * int(val[int(x) + 1]) for c, x in zip(a, v))
+        assert {">=": lhs >= k, "<=": lhs <= k, "=": lhs == k}[rel]

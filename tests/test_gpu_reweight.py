@@ -180,3 +180,41 @@ def test_graph_recorded_with_unit_weights_is_refused_after_a_change():
     torch.cuda.synchronize()
     assert np.allclose(wsat.cpu().numpy(), 2.0 * nsat.cpu().numpy())
     B.cls_graph_destroy(g)
+
+
+def test_weighting_argument_checks_and_empty_set():
+    from paper_2606_06656_b300 import Problem
+    from paper_2606_06656_b300 import binding as B
+    from paper_2606_06656_b300._lib import ClsError
+    inst = W.random_ksat(n=40, m=100)
+    p = Problem(inst)
+    R = 40
+    x = p.init_uniform(R, 2)
+    p.eval(x, obj=False)
+    _, _, bits = p.round_score(x)
+    g, u = p.constraint_stats(bits, R)
+    w = torch.empty(p.m, dtype=torch.float32, device="cuda")
+    for eta, kappa, w_max in [(-1.0, 4.0, 10.0), (1.0, 0.0, 10.0), (1.0, 4.0, float("inf")),
+                              (float("nan"), 4.0, 10.0), (1.0, 4.0, 0.0)]:
+        with pytest.raises(ClsError):
+            B.cls_reweight(p.handle, R, g, u, eta, kappa, w_max, w)
+    with pytest.raises(ClsError):
+        B.cls_reweight(p.handle, 0, g, u, 1.0, 4.0, 10.0, w)
+    with pytest.raises(ClsError):
+        B.cls_constraint_stats(p.handle, 0, bits, p.workspace(R), g, u)
+    with pytest.raises(ClsError):                      # workspace of another R
+        B.cls_constraint_stats(p.handle, 4 * R, bits, p.workspace(R), g, u)
+    with pytest.raises(ValueError):
+        p.set_weights(torch.ones(p.m + 1, device="cuda"))
+    # eta = 0 leaves the weights (and the unit-weight results) alone
+    w1 = p.reweight(g, u, R, 0.0)
+    assert torch.equal(w1, torch.ones_like(w1))
+    # a constraint set without constraints: nothing to do, no error
+    empty = W.build(5, [])
+    q = Problem(empty)
+    xq = q.init_uniform(8, 1)
+    q.eval(xq, obj=False)
+    _, _, bq = q.round_score(xq)
+    g0, u0 = q.constraint_stats(bq, 8)
+    assert g0.numel() == 0 and u0.numel() == 0
+    q.reweight(g0, u0, 8, 1.0)
