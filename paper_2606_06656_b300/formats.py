@@ -76,7 +76,8 @@ def _pack(n, rows, name, dropped, notes) -> ConstraintSet:
 
 def read_dimacs(src: str, name: str = "") -> ConstraintSet:
     """DIMACS CNF ("p cnf n m", clauses of nonzero integers ended by 0; lines
-    starting with c are comments).  Repeated literals in a clause are merged;
+    starting with c are comments; a line starting with % ends the file, as
+    in collections that append "%" and a stray "0").  Repeated literals in a clause are merged;
     a clause holding a variable and its negation is always true and dropped.
     An empty clause raises ValueError (no assignment satisfies it)."""
     text = _text(src)
@@ -101,7 +102,9 @@ def read_dimacs(src: str, name: str = "") -> ConstraintSet:
 
     for line in text.splitlines():
         line = line.strip()
-        if not line or line[0] in "c%":
+        if line.startswith("%"):      # end marker of some benchmark collections
+            break
+        if not line or line[0] == "c":
             continue
         if line[0] == "p":
             parts = line.split()

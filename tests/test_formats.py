@@ -68,6 +68,8 @@ def test_dimacs_errors_and_notes():
     assert s.m == 2 and len(s.notes) == 1
     s = read_dimacs("p cnf 3 1\n1 2 3")
     assert s.offsets.tolist() == [0, 3]
+    s = read_dimacs("p cnf 3 2\n1 -2 0\n2 3 0\n%\n0\n\n")   # end marker
+    assert s.m == 2 and s.notes == []
 
 
 def test_dimacs_reads_a_file(tmp_path):
