@@ -378,12 +378,15 @@ __global__ void __launch_bounds__(256) k_fe_thread(
   int2* trec = trec_s[threadIdx.y];
   constexpr int NT = AsyncTiles<HI>::value;
   float* xb = thread_xbuf + (size_t)threadIdx.y * NT * HI * 32;
-  for (int ci = blockIdx.y * blockDim.y + threadIdx.y; ci < count; ci += gridDim.y * blockDim.y) {
+  // blockIdx.x (fastest in launch order) walks the constraints, blockIdx.y
+  // the restart groups: the blocks in flight share one group's slice of x
+  // (n * NT * 128 B), which stays in L2 while the partial writes stream past
+  for (int ci = blockIdx.x * blockDim.y + threadIdx.y; ci < count; ci += gridDim.x * blockDim.y) {
     const FeItem it = items[ci];
     __syncwarp();
     load_trec(it, lit, trec, lane);
     thread_dispatch_async<LO, HI, NT>(it.L, it, root, coef, trec, x, R, Rp,
-                                      blockIdx.x * NT, lane, P, fe_con, ldf, xb);
+                                      blockIdx.y * NT, lane, P, fe_con, ldf, xb);
   }
 }
 
@@ -1546,7 +1549,7 @@ cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const floa
     const int cnt = d.thread_count[t];
     if (cnt == 0) return cudaSuccess;
     const int nt = t == 0 ? AsyncTiles<8>::value : AsyncTiles<16>::value;   // 24: as 16
-    const dim3 grid(ceil_div(RT, nt), std::min(ceil_div(cnt, 8), 65535)), block(32, 8);
+    const dim3 grid(std::min(ceil_div(cnt, 8), 1 << 30), ceil_div(RT, nt)), block(32, 8);
     HookScope hs(h, KC_THREAD, s);
     const FeItem* items = d.thread_items[t];
 #define CLS_THREAD_LAUNCH(LO, HI)                                                          \
