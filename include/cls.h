@@ -312,6 +312,11 @@ int cls_grid_barrier_check(int32_t rounds, int32_t extra, uint32_t spin_limit, v
  * memory recommended) to the device workspace, runs n_steps as cls_step,
  * and copies the final nsat (host int32[R]) and x (host float[n*R], may be
  * NULL) back, all on stream; synchronises the stream before returning.
+ * Whole chunks of 10 steps run through a step-loop graph (as
+ * cls_graph_create) that the problem records on first use and keeps while
+ * ws, R, lr, the tuning and the weight mode stay the same; the remaining
+ * steps run as cls_step.  Results are those of cls_step.  Recording needs
+ * profiling off; with profiling on every step runs as cls_step.
  * ws must hold cls_workspace_size() + 4*n*R + 4*R + 8*R bytes (see
  * cls_solve_host_workspace_size). */
 int cls_solve_host_workspace_size(const cls_problem* p, int32_t R, size_t* bytes);

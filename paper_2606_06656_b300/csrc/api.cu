@@ -91,6 +91,15 @@ struct cls_problem {
   EventHook* hook = nullptr;  // non-null while profiling
   EventHook events;
   bool weights_dirty = false;  // device weights changed since the host plan's copy
+  int64_t list_epoch = 0;      // bumped whenever the work lists are uploaded again
+  // cls_solve_host's recorded step chunk, reused while its workspace, R, lr,
+  // work lists and weight mode stay the same
+  cls_graph* solve_graph = nullptr;
+  const void* sg_ws = nullptr;
+  int sg_R = 0;
+  float sg_lr = 0.f;
+  int64_t sg_epoch = -1;
+  int sg_unit = -1;
 };
 
 namespace {
@@ -214,6 +223,7 @@ cls::LaunchHook* hook_of(const cls_problem* p) { return p->hook; }
 int upload_lists(cls_problem* p) {
   const cls::HostPlan& H = p->host;
   cls::DevPlan& D = p->dev;
+  ++p->list_epoch;
   for (int t = 0; t < cls::kNumThreadCls; ++t) {
     int rc = upload(p, H.thread_items[t], &D.thread_items[t]);
     if (rc != CLS_OK) return rc;
@@ -394,6 +404,8 @@ int cls_problem_create_ex(int32_t n, int32_t m, const int32_t* offsets, const in
 int cls_problem_destroy(cls_problem* p) {
   if (!p) return CLS_OK;
   cudaDeviceSynchronize();
+  if (p->solve_graph) cls_graph_destroy(p->solve_graph);
+  p->solve_graph = nullptr;
   free_problem(p);
   delete p;
   return CLS_OK;
@@ -753,8 +765,36 @@ int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host, float 
   cudaStream_t s = (cudaStream_t)stream;
   const size_t xbytes = (size_t)p->host.n * R * sizeof(float);
   if (xbytes) CLS_CUDA_TRY(cudaMemcpyAsync(xd, x0_host, xbytes, cudaMemcpyHostToDevice, s), "H2D x0");
-  rc = cls_step(p, R, xd, lr, n_steps, nullptr, nd, nullptr, ws, L.total, stream);
-  if (rc != CLS_OK) return rc;
+  // whole chunks of kSolveChunk steps through a recorded graph (the length
+  // classes' FE launches run concurrently, each step's score overlaps the
+  // next step's FE); the remaining steps as cls_step.  Same results.
+  constexpr int kSolveChunk = 10;
+  int32_t done_steps = 0;
+  if (n_steps >= kSolveChunk && !p->hook) {
+    cls_problem* mp = const_cast<cls_problem*>(p);   // the cache only
+    if (!(mp->solve_graph && mp->sg_ws == ws && mp->sg_R == R && mp->sg_lr == lr &&
+          mp->sg_epoch == p->list_epoch && mp->sg_unit == p->dev.unit_weights)) {
+      if (mp->solve_graph) cls_graph_destroy(mp->solve_graph);
+      mp->solve_graph = nullptr;
+      cls_graph* g = nullptr;
+      rc = cls_graph_create(p, R, xd, lr, kSolveChunk, nullptr, nd, nullptr, ws, L.total, &g);
+      if (rc != CLS_OK) return rc;
+      mp->solve_graph = g;
+      mp->sg_ws = ws;
+      mp->sg_R = R;
+      mp->sg_lr = lr;
+      mp->sg_epoch = p->list_epoch;
+      mp->sg_unit = p->dev.unit_weights;
+    }
+    for (; done_steps + kSolveChunk <= n_steps; done_steps += kSolveChunk) {
+      rc = cls_graph_launch(mp->solve_graph, stream);
+      if (rc != CLS_OK) return rc;
+    }
+  }
+  if (n_steps - done_steps > 0 || n_steps == 0) {
+    rc = cls_step(p, R, xd, lr, n_steps - done_steps, nullptr, nd, nullptr, ws, L.total, stream);
+    if (rc != CLS_OK) return rc;
+  }
   if (n_steps == 0) {
     rc = cls_round_score(p, R, xd, nullptr, nd, nullptr, ws, L.total, stream);
     if (rc != CLS_OK) return rc;

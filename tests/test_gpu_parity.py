@@ -393,6 +393,30 @@ def test_solve_host_matches_device(P):
     assert torch.equal(nh, nsat.cpu()) and torch.equal(xo, xd.cpu())
 
 
+def test_solve_host_recorded_chunks_match_steps(P):
+    """cls_solve_host runs whole 10-step chunks through a recorded graph and
+    the rest as cls_step: bit-identical to cls_step for 23 steps on a mixed
+    instance (DFT, corner and closed-form classes), again after the graph
+    must be recorded anew (another lr, a retuning, another step count)."""
+    from paper_2606_06656_b300 import binding as B
+    inst = W.mixed_pb(n=900, n_or=2500, n_xor=250, n_card=60, card_len=(10, 200), seed=3)
+    p = P(inst)
+    R = 96
+    X0 = W.uniform_points(inst.n, R, seed=6)
+    xh = torch.from_numpy(X0.copy()).pin_memory()
+    nh = torch.empty(R, dtype=torch.int32).pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    for lr, steps, retune in [(0.1, 23, False), (0.1, 23, False), (0.05, 10, False),
+                              (0.05, 31, True), (0.1, 9, False)]:
+        if retune:
+            B.cls_tuning_set(p.handle, B.cls_tuning_get(p.handle))
+        xd = torch.from_numpy(X0.copy()).cuda()
+        nsat, _, _ = p.step(xd, lr, n_steps=steps)
+        p.solve_host(xh, lr, steps, nh, xo)
+        assert torch.equal(nh, nsat.cpu()), (lr, steps)
+        assert torch.equal(xo, xd.cpu()), (lr, steps)
+
+
 def test_full_size_mixed_pb_sampled(P):
     """Batched mixed PB at full size (n=5000, 22500 constraints, 4096
     restarts, one launch per kernel as in the benchmark), checked on sampled
