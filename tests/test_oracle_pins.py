@@ -304,7 +304,8 @@ def test_score_bruteforce_and_fe_identity():
 
 def test_planted_instances_are_satisfied_by_plant():
     for inst in [W.mixed_pb(n=300, n_or=400, n_xor=60, n_card=20, card_len=(10, 120), seed=3),
-                 W.redundant_5sat(n=200, m=900, redundancy=0.1, red_len=(20, 60), seed=4)]:
+                 W.redundant_5sat(n=200, m=900, redundancy=0.1, red_len=(20, 60), seed=4),
+                 W.planted_ksat(n=450, seed=5)]:
         z = inst.plant.astype(np.float32)[:, None]
         nsat, _, _ = ocls.score(inst, z)
         assert nsat[0] == inst.m

@@ -160,6 +160,19 @@ def random_ksat(n=100, m=426, kl=3, seed=1100) -> Instance:
                  meta=dict(seed=seed))
 
 
+def planted_ksat(n=550, m=None, kl=3, seed=1600) -> Instance:
+    """Random k-SAT with a planted solution at clause ratio 4.26 by default
+    (stands in for the satisfiable phase-transition 3-SAT instances of
+    Sec. 4.2, 450-650 variables): kl distinct variables per clause, uniform
+    signs, then each clause the plant violates gets one literal's sign
+    flipped (the generator's planting rule)."""
+    m = int(round(4.26 * n)) if m is None else m
+    rng = np.random.default_rng(seed)
+    z = np.where(rng.random(n) < 0.5, -1, 1).astype(np.int8)
+    rows = _draw_rows(rng, n, [(TYPE_OR, kl, 0)] * m, z)
+    return build(n, rows, plant=z, name=f"planted{kl}sat_n{n}_m{m}", meta=dict(seed=seed))
+
+
 def mixed_pb(n=5000, n_or=20000, or_len=(2, 8), n_xor=2000, xor_len=(3, 20),
              n_card=500, card_len=(10, 300), seed=1200, planted=True) -> Instance:
     """Batched mixed symmetric PB, planted satisfiable: clauses of length
