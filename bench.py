@@ -784,6 +784,7 @@ def run_profile(args):
     from paper_2606_06656_b300 import binding as B
     R = args.R or 4096
     K = 300
+    tol = 1e-4                   # convergence: no coordinate moves more than this
     out = {}
     for frac in (0.1, 0.66):
         inst = W.partial_assignment(W.planted_ksat(550, seed=1900), frac, seed=1901)
@@ -795,10 +796,19 @@ def run_profile(args):
         bits = torch.empty((inst.n, (R + 31) // 32), dtype=torch.int32, device="cuda")
         trk = torch.empty((4, R), dtype=torch.int32, device="cuda")
         B.cls_track_reset(p.handle, R, trk)
+        md = torch.empty(R, dtype=torch.float32, device="cuda")
+        conv = torch.full((R,), -1, dtype=torch.int32, device="cuda")
+        xp = torch.empty_like(x)
         for k in range(K):
+            xp.copy_(x)
             B.cls_step(p.handle, R, x, 0.1, 1, bits, nsat, wsat, ws)
             B.cls_track_step(p.handle, R, nsat, k, trk)
+            B.cls_movement(p.handle, R, xp, x, md)
+            B.cls_track_converged(p.handle, R, md, tol, k, conv)
         t = trk.cpu().numpy()
+        cv = conv.cpu().numpy() + 1                  # steps taken to converge, 0 = never
+        never = cv == 0
+        conv_hist, _ = np.histogram(cv[~never], bins=np.arange(0, K + 21, 20))
         best_step = t[1] + 1
         unsat = inst.m - t[0]
         late = best_step > 0.9 * K
@@ -809,14 +819,21 @@ def run_profile(args):
             "median_best_step": float(np.median(best_step)),
             "unsat_median": {"converged_early": float(np.median(unsat[~late])) if (~late).any() else None,
                              "still_descending": float(np.median(unsat[late])) if late.any() else None},
-            "solved_frac": float((t[3] >= 0).mean())}
+            "solved_frac": float((t[3] >= 0).mean()),
+            "converged_hist_bins_of_20": conv_hist.tolist(),
+            "frac_not_converged_at_limit": float(never.mean()),
+            "median_converge_step": float(np.median(cv[~never])) if (~never).any() else None,
+            "unsat_median_by_convergence": {
+                "converged": float(np.median(unsat[~never])) if (~never).any() else None,
+                "not_converged": float(np.median(unsat[never])) if never.any() else None}}
         p.close()
     line = {"metric": "convergence profile (step of each restart's best count)",
             "value": out["pinned=0.1"]["frac_best_in_last_10pct"], "unit": "fraction",
             "higher_is_better": False, "n_gpus": 1, "steps": K, "dtype": "f32",
             "data": "synthetic", "value_is": "fraction of restarts still improving in the last 10 % of 300 steps, 10 % pinned",
             "profiles": out,
-            "config": {"workload": "planted3sat_n550_m2343, 10 % / 66 % pinned", "R": R, "lr": 0.1}}
+            "config": {"workload": "planted3sat_n550_m2343, 10 % / 66 % pinned", "R": R, "lr": 0.1,
+                       "convergence_tol": tol}}
     print(json.dumps(line), flush=True)
 
 

@@ -248,3 +248,19 @@ def reweight(w, gnorm, unsat, has_fe, R, eta, kappa, w_max):
     gbar = g[has_fe].mean() if has_fe.any() else 0.0
     rho = np.array([kappa if gc * kappa <= gbar else gbar / gc for gc in g])
     return np.minimum(w_max, w * (1.0 + eta * u * rho)).astype(np.float32)
+
+
+# --- convergence of the descent per restart (Sec. 4.3) ----------------------
+
+def movement(X_prev, X):
+    """max over variables of |x - x_prev| per restart, FP32 subtraction."""
+    d = np.abs(np.asarray(X, np.float32) - np.asarray(X_prev, np.float32))
+    return d.max(axis=0) if d.shape[0] else np.zeros(d.shape[1], np.float32)
+
+
+def track_converged(conv, maxdelta, tol, step):
+    """First step at which the movement is at most tol (-1 until then)."""
+    conv = np.array(conv, dtype=np.int64, copy=True)
+    hit = (conv < 0) & (np.asarray(maxdelta, np.float32) <= np.float32(tol))
+    conv[hit] = step
+    return conv

@@ -45,6 +45,8 @@ SIGNATURES = {
     "cls_constraint_stats": (i32, [vp, i32, vp, vp, sz, vp, vp, vp]),
     "cls_reweight": (i32, [vp, i32, vp, vp, C.c_double, C.c_double, C.c_double, vp, vp]),
     "cls_set_weights": (i32, [vp, vp, vp]),
+    "cls_movement": (i32, [vp, i32, vp, vp, vp, vp]),
+    "cls_track_converged": (i32, [vp, i32, vp, f32, i32, vp, vp]),
     "cls_solve_host_workspace_size": (i32, [vp, i32, P(sz)]),
     "cls_solve_host": (i32, [vp, i32, vp, f32, i32, vp, vp, vp, sz, vp]),
     "cls_autotune": (i32, [vp, i32, vp, i32, vp, sz, vp]),

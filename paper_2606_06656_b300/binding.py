@@ -155,6 +155,20 @@ def cls_set_weights(h, w, stream=None):
     _lib.check(_lib.load().cls_set_weights(h, _ptr(w), _stream(stream)), "cls_set_weights")
 
 
+def cls_movement(h, R, x_prev, x, maxdelta, stream=None):
+    """maxdelta (device float32[R]) = per restart max_v |x - x_prev|."""
+    _lib.check(_lib.load().cls_movement(h, int(R), _ptr(x_prev), _ptr(x), _ptr(maxdelta),
+                                        _stream(stream)), "cls_movement")
+
+
+def cls_track_converged(h, R, maxdelta, tol, step, conv, stream=None):
+    """conv (device int32[R], -1 = not yet) takes `step` the first time the
+    restart's movement is at most tol."""
+    _lib.check(_lib.load().cls_track_converged(h, int(R), _ptr(maxdelta), float(tol), int(step),
+                                               _ptr(conv), _stream(stream)),
+               "cls_track_converged")
+
+
 def cls_eval(h, R, x, obj, grad, fe_con, ws, stream=None):
     _lib.check(_lib.load().cls_eval(h, int(R), _ptr(x), _ptr(obj), _ptr(grad), _ptr(fe_con),
                                     _ptr(ws), ws.numel() if ws is not None else 0,

@@ -527,6 +527,28 @@ int cls_unsat_histogram(const cls_problem* p, int32_t R, const int32_t* nsat, in
   return CLS_OK;
 }
 
+int cls_movement(const cls_problem* p, int32_t R, const float* x_prev, const float* x,
+                 float* maxdelta, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (R > 0 && (!maxdelta || (p->host.n > 0 && (!x_prev || !x))))
+    return set_err(CLS_ERR_INVALID, "x_prev, x or maxdelta is NULL");
+  CLS_CUDA_TRY(cls::launch_movement(p->dev, R, x_prev, x, maxdelta, (cudaStream_t)stream),
+               "movement kernel");
+  return CLS_OK;
+}
+
+int cls_track_converged(const cls_problem* p, int32_t R, const float* maxdelta, float tol,
+                        int32_t step, int32_t* conv, void* stream) {
+  int rc = check_R(p, R);
+  if (rc != CLS_OK) return rc;
+  if (step < 0 || !(tol >= 0.f)) return set_err(CLS_ERR_INVALID, "need step >= 0 and tol >= 0");
+  if (R > 0 && (!maxdelta || !conv)) return set_err(CLS_ERR_INVALID, "maxdelta or conv is NULL");
+  CLS_CUDA_TRY(cls::launch_track_conv(R, maxdelta, tol, step, conv, (cudaStream_t)stream),
+               "convergence kernel");
+  return CLS_OK;
+}
+
 int cls_constraint_stats(const cls_problem* p, int32_t R, const uint32_t* bits, void* ws,
                          size_t ws_bytes, double* gnorm, int32_t* unsat, void* stream) {
   int rc = check_R(p, R);

@@ -162,6 +162,40 @@ __global__ void __launch_bounds__(256) k_unsat_hist(int R, int m, const int32_t*
   if (k >= 0 && k <= m) atomicAdd(&hist[k], 1);
 }
 
+// per-restart movement of a step: maxdelta[r] = max_v |x[v, r] - x_prev[v, r]|
+// (FP32, exact); a warp takes 32 restarts of kMoveVars consecutive
+// variables, the maximum goes in by an integer atomicMax on the float's bits
+// (non-negative floats order as their bit patterns), so the result does not
+// depend on the order
+constexpr int kMoveVars = 64;
+
+__global__ void __launch_bounds__(256) k_move_max(int n, int R, const float* __restrict__ xp,
+                                                  const float* __restrict__ x,
+                                                  unsigned* __restrict__ maxdelta) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 32 + lane;
+  if (r >= R) return;
+  const int64_t chunks = ((int64_t)n + kMoveVars - 1) / kMoveVars;
+  float m = 0.f;
+  for (int64_t ch = (int64_t)blockIdx.y * 8 + (threadIdx.x >> 5); ch < chunks;
+       ch += (int64_t)gridDim.y * 8) {
+    const int64_t v0 = ch * kMoveVars, v1 = min((int64_t)n, v0 + kMoveVars);
+    for (int64_t v = v0; v < v1; ++v)
+      m = fmaxf(m, fabsf(x[(size_t)v * R + r] - xp[(size_t)v * R + r]));
+  }
+  atomicMax(&maxdelta[r], __float_as_uint(m));
+}
+
+// first step at which a restart's movement is at most tol (conv[r] = -1
+// until then)
+__global__ void __launch_bounds__(256) k_track_conv(int R, const float* __restrict__ maxdelta,
+                                                    float tol, int step,
+                                                    int32_t* __restrict__ conv) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  if (conv[r] < 0 && maxdelta[r] <= tol) conv[r] = step;
+}
+
 // ---------------------------------------------------------------------------
 // A2-A5, closed-form products (clause, XOR, NAE and complements) of short
 // constraints: one thread per (constraint, restart), a warp = one constraint x
@@ -1439,6 +1473,24 @@ cudaError_t launch_unsat_hist(const DevPlan& d, int R, const int32_t* nsat, int3
   cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * ((size_t)d.m + 1), s);
   if (e != cudaSuccess || R == 0) return e;
   k_unsat_hist<<<(R + 255) / 256, 256, 0, s>>>(R, d.m, nsat, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_movement(const DevPlan& d, int R, const float* xp, const float* x,
+                            float* maxdelta, cudaStream_t s) {
+  if (R == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(maxdelta, 0, sizeof(float) * (size_t)R, s);
+  if (e != cudaSuccess || d.n == 0) return e;
+  const int chunks = ceil_div(d.n, kMoveVars);
+  const dim3 grid(ceil_div(R, 32), std::min(ceil_div(chunks, 8), 65535));
+  k_move_max<<<grid, 256, 0, s>>>(d.n, R, xp, x, reinterpret_cast<unsigned*>(maxdelta));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_track_conv(int R, const float* maxdelta, float tol, int step, int32_t* conv,
+                              cudaStream_t s) {
+  if (R == 0) return cudaSuccess;
+  k_track_conv<<<(R + 255) / 256, 256, 0, s>>>(R, maxdelta, tol, step, conv);
   return cudaGetLastError();
 }
 

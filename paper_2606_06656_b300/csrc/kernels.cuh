@@ -177,6 +177,11 @@ cudaError_t launch_refill(const DevPlan& d, int R, uint64_t seed, int64_t r_off,
                           int patience, int32_t* trk, float* x, int32_t* count, cudaStream_t s);
 cudaError_t launch_unsat_hist(const DevPlan& d, int R, const int32_t* nsat, int32_t* hist,
                               cudaStream_t s);
+// per-restart movement of a step and the first step it fell to tol
+cudaError_t launch_movement(const DevPlan& d, int R, const float* xp, const float* x,
+                            float* maxdelta, cudaStream_t s);
+cudaError_t launch_track_conv(int R, const float* maxdelta, float tol, int step, int32_t* conv,
+                              cudaStream_t s);
 
 // adaptive constraint weighting (kernels.cu): per-constraint statistics over
 // the restarts, the weight update, and writing weights into the plan's items

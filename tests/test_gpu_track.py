@@ -105,3 +105,37 @@ def test_unsat_histogram_matches_oracle(P, R):
     B.cls_unsat_histogram(p.handle, R, torch.from_numpy(nsat).cuda(), hist)
     torch.cuda.synchronize()
     assert np.array_equal(hist.cpu().numpy(), ocls.unsat_histogram(nsat, inst.m).astype(np.int32))
+
+
+@pytest.mark.parametrize("n,R", [(70, 1), (70, 33), (200, 300), (4500, 64)])
+def test_movement_and_convergence_match_oracle(P, n, R):
+    """Bit-exact: movement of a real step (clamped coordinates, pinned ones
+    that never move) and of synthetic pairs with +-0, equal values and
+    extremes; the convergence record over several steps.  n = 4500 spans
+    several 64-variable chunks per restart."""
+    from paper_2606_06656_b300 import binding as B
+    inst = W.random_ksat(n=n, m=4 * n, seed=n)
+    p = P(inst)
+    x = p.init_uniform(R, seed=3)
+    md = torch.empty(R, dtype=torch.float32, device="cuda")
+    conv = torch.full((R,), -1, dtype=torch.int32, device="cuda")
+    oconv = -np.ones(R, np.int64)
+    for step in range(4):
+        xp = x.clone()
+        p.step(x, 0.3 if step < 2 else 1e-6, 1)
+        B.cls_movement(p.handle, R, xp, x, md)
+        B.cls_track_converged(p.handle, R, md, 1e-4, step, conv)
+        torch.cuda.synchronize()
+        want = ocls.movement(xp.cpu().numpy(), x.cpu().numpy())
+        assert np.array_equal(md.cpu().numpy(), want)
+        oconv = ocls.track_converged(oconv, want, 1e-4, step)
+        assert np.array_equal(conv.cpu().numpy(), oconv)
+    rng = np.random.default_rng(R)
+    A = rng.uniform(-1, 1, (n, R)).astype(np.float32)
+    Bm = A.copy()
+    Bm[rng.random((n, R)) < 0.3] *= -1
+    Bm[0] = np.where(A[0] == 0, np.float32(-0.0), A[0])
+    Bm[-1, :] = np.float32(1.0)
+    B.cls_movement(p.handle, R, torch.from_numpy(A).cuda(), torch.from_numpy(Bm).cuda(), md)
+    torch.cuda.synchronize()
+    assert np.array_equal(md.cpu().numpy(), ocls.movement(A, Bm))

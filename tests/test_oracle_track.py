@@ -55,3 +55,28 @@ def test_unsat_histogram_counts():
     nsat = np.array([5, 3, 5, 0, 4])
     h = O.unsat_histogram(nsat, 5)
     assert h.tolist() == [2, 1, 1, 0, 0, 1] and h.sum() == 5
+
+
+def test_movement_and_convergence_definitions():
+    """movement = the largest coordinate change of a restart: zero for no
+    change; for a projected step it is the step size |fl(lr g)| where no
+    bound is hit, and the distance to the bound where one is.  The
+    convergence record takes the first step at or below tol and keeps it."""
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-0.5, 0.5, (30, 7)).astype(np.float32)
+    assert (O.movement(X, X) == 0).all()
+    G = rng.normal(size=(30, 7)).astype(np.float32) * 0.1
+    Xn = O.pgd_step(X, G, 0.5)                        # |0.5 g| < 0.5: no clamp here
+    t = np.abs(np.float32(0.5) * G)
+    inside = np.abs(X.astype(np.float64) - 0.5 * G) < 0.99
+    want = np.where(inside, t, np.abs(Xn - X)).max(axis=0)
+    assert np.allclose(O.movement(X, Xn), want, rtol=1e-6, atol=0)
+    # a coordinate pushed past the bound moves only to the bound
+    Y = np.array([[0.9, -0.2]], np.float32)
+    Yn = O.pgd_step(Y, np.array([[-1.0, 0.0]], np.float32), 1.0)
+    assert O.movement(Y, Yn).tolist() == [np.float32(1.0) - np.float32(0.9), 0.0]
+    conv = -np.ones(4, np.int64)
+    conv = O.track_converged(conv, np.array([0.5, 1e-5, 0.0, 2e-4], np.float32), 1e-4, 3)
+    assert conv.tolist() == [-1, 3, 3, -1]
+    conv = O.track_converged(conv, np.array([1e-6, 1e-6, 1.0, 1e-4], np.float32), 1e-4, 4)
+    assert conv.tolist() == [4, 3, 3, 4]
