@@ -589,13 +589,15 @@ __global__ void __launch_bounds__(256) k_fe_group(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ root, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
-    float* __restrict__ fe_con, int ldf) {
+    float* __restrict__ fe_con, int ldf, const uint8_t* __restrict__ done, int RT) {
   using Geo = GroupGeom<G>;
   constexpr int LS = G * Q;          // staged literal slots
   extern __shared__ float smem[];
   float* ys = smem;                  // [LS][LDR]
   __shared__ float fe_s[32];
   const FeItem it = fe[list[blockIdx.x]];
+  // the one-thread corner pass finished this tile (partials and FE written)
+  if (done && done[(size_t)it.c * RT + blockIdx.y] == kTileDone) return;
   const int L = it.L;
   const int r0 = blockIdx.y * 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1579,11 +1581,22 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
                            s);
   }
   const dim3 grid(count, ceil_div(R, 32)), block(256);
+  // direct-form DFT: the one-thread corner pass first on buckets longer than
+  // its capacity; the direct kernel then skips the tiles it finished
+  const bool dcorner = done && cfg >= 0 && cfg < kNumGroupCfg && kGroupCfg[cfg].cplx == 1 &&
+                       maxL >= kDirectCornerMinL;
+  if (dcorner) {
+    cudaError_t e = launch_dft_corner(d, list, count, maxL, R, Rp, x, P, fe_con, ldf, done, s,
+                                      false);
+    if (e != cudaSuccess) return e;
+  }
+  const uint8_t* dflags = dcorner ? done : nullptr;
+  const int RTg = ceil_div(R, 32);
   switch (cfg) {
 #define CLS_LAUNCH_CASE(id, G, Q, C, Y)                                                      \
   case id:                                                                                   \
     k_fe_group<G, Q, (C != 0), (Y != 0)><<<grid, block, group_smem<G, Q>(), s>>>(            \
-        list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf);             \
+        list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf, dflags, RTg); \
     break;
     CLS_GROUP_CONFIGS(CLS_LAUNCH_CASE)
 #undef CLS_LAUNCH_CASE

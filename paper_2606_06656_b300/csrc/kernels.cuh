@@ -153,9 +153,14 @@ inline float* ser_terms(const DevPlan& d, uint8_t* done, int RT) {
 }
 cudaError_t set_corner_attributes();
 size_t corner_smem_bytes(int maxL, int gc);
+// group = false: only the one-thread pass (before the direct-form kernel)
 cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
                               int Rp, const float* x, float* P, float* fe_con, int ldf,
-                              uint8_t* done, cudaStream_t s);
+                              uint8_t* done, cudaStream_t s, bool group = true);
+// The direct-form DFT kernel runs after the one-thread corner pass for
+// buckets longer than the pass's capacity (kDirectCornerMinL), skipping the
+// tiles it finished; shorter buckets go to the direct kernel alone.
+constexpr int kDirectCornerMinL = 17;
 // The power-sum pass (kernels_series.cu): after the corner passes, on the
 // tiles they left, for constraints of kSeriesMinL literals or more.
 cudaError_t set_series_attributes();

@@ -659,7 +659,7 @@ cudaError_t set_corner_attributes() {
 
 cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, int maxL, int R,
                               int Rp, const float* x, float* P, float* fe_con, int ldf,
-                              uint8_t* done, cudaStream_t s) {
+                              uint8_t* done, cudaStream_t s, bool group) {
   if (count == 0 || R == 0) return cudaSuccess;
   const int RT = ceil_div(R, 32);
   const dim3 grid(count, ceil_div(RT, 8)), block(256);
@@ -667,7 +667,7 @@ cudaError_t launch_dft_corner(const DevPlan& d, const int32_t* list, int count, 
       list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
       ldf, done, d.spec_tab, d.spec_off, d.ser_info, d.ser_tab);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !group) return e;
   k_fe_dft_corner<kCornerGroup><<<grid, block, corner_smem_bytes(maxL, kCornerGroup), s>>>(
       list, d.fe, d.root_tab, d.zpow_tab, d.coef_tab, d.fe_lit, x, R, Rp, RT, maxL, P, fe_con,
       ldf, done, d.spec_tab, d.spec_off, d.ser_info, d.ser_tab);
