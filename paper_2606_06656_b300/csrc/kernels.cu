@@ -1146,7 +1146,29 @@ __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
     }
     const int r = tile * 32 + lane;
     nsat_part[(size_t)blockIdx.y * Rp + r] = a;
-    wsat_part[(size_t)blockIdx.y * Rp + r] = b;
+    if constexpr (!UNIT) wsat_part[(size_t)blockIdx.y * Rp + r] = b;   // UNIT: wsat = nsat
+  }
+}
+
+// all weights 1: wsat = nsat, an integer sum in any order; 8 threads per
+// restart take every 8th chunk and add their sums in a fixed order
+__global__ void __launch_bounds__(256) k_score_final_unit(int R, int Rp, int nch,
+                                                          const int32_t* __restrict__ nsat_part,
+                                                          int32_t* __restrict__ nsat,
+                                                          double* __restrict__ wsat) {
+  __shared__ int32_t part_s[8][32];
+  const int r = blockIdx.x * 32 + threadIdx.x;
+  int a = 0;
+  if (r < R)
+    for (int ch = threadIdx.y; ch < nch; ch += 8) a += nsat_part[(size_t)ch * Rp + r];
+  part_s[threadIdx.y][threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.y == 0 && r < R) {
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += part_s[k][threadIdx.x];
+    if (nsat) nsat[r] = t;
+    if (wsat) wsat[r] = (double)t;
   }
 }
 
@@ -1714,7 +1736,10 @@ cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
     if (e != cudaSuccess) return e;
   }
   HookScope hs(h, KC_REDUCE, s);
-  k_score_final<<<ceil_div(R, 256), 256, 0, s>>>(R, Rp, nch, nsat_part, wsat_part, nsat, wsat);
+  if (d.unit_weights)
+    k_score_final_unit<<<ceil_div(R, 32), dim3(32, 8), 0, s>>>(R, Rp, nch, nsat_part, nsat, wsat);
+  else
+    k_score_final<<<ceil_div(R, 256), 256, 0, s>>>(R, Rp, nch, nsat_part, wsat_part, nsat, wsat);
   return cudaGetLastError();
 }
 
