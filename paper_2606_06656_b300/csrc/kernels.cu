@@ -1115,6 +1115,79 @@ __global__ void __launch_bounds__(256) k_set_weights(int m, const float* __restr
   }
 }
 
+// score_range for NT consecutive restart tiles at once (the k_score path):
+// one literal-record load, one constraint walk and one mask per chunk serve
+// every tile; each tile has its own bitset words, transpose and counts
+template <bool UNIT, int NT>
+__device__ __forceinline__ void score_range_tiles(int rg, int tile0, int lane, int RW,
+                                                  const int32_t* __restrict__ ranges,
+                                                  const ScoreItem* __restrict__ sc,
+                                                  const LitRec* __restrict__ lit,
+                                                  const uint32_t* __restrict__ satbits,
+                                                  const uint32_t* __restrict__ bits,
+                                                  int (&cnt)[NT], double (&ws)[NT]) {
+  int run[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    cnt[t] = 0;
+    ws[t] = 0.0;
+    run[t] = 0;
+  }
+  int c = ranges[rg];
+  const int c_end = ranges[rg + 1];
+  ScoreItem s = sc[c];
+  int e = s.lit0;
+  const ScoreItem last = sc[c_end - 1];
+  const int e_end = last.lit0 + last.L;
+  while (e < e_end) {
+    uint32_t col[NT];
+    {
+      uint32_t word[NT];
+      LitRec rc{0, 0};
+      const bool has = e + lane < e_end;
+      if (has) rc = lit[e + lane];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        word[t] = 0;
+        if (has && tile0 + t < RW) {
+          word[t] = bits[(size_t)rc.var * RW + tile0 + t];
+          if (rc.dst < 0) word[t] = ~word[t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) col[t] = transpose32(word[t], lane);
+    }
+    const int chunk_end = e + 32;
+    while (c < c_end && s.lit0 + s.L <= chunk_end) {
+      const int lo = max(s.lit0, e) - e;
+      const int hi = s.lit0 + s.L - e;
+      const uint32_t mask = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & (kFull << lo);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const bool sat = sat_of(s, run[t] + __popc(col[t] & mask), satbits);
+        run[t] = 0;
+        cnt[t] += sat ? 1 : 0;
+        if constexpr (!UNIT) ws[t] += sat ? (double)s.w : 0.0;
+      }
+      ++c;
+      if (c < c_end) s = sc[c];
+    }
+    if (c < c_end && s.lit0 < chunk_end) {
+      const int lo = max(s.lit0, e) - e;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) run[t] += __popc(col[t] & (kFull << lo));
+    }
+    e = chunk_end;
+  }
+  if constexpr (UNIT) {
+#pragma unroll
+    for (int t = 0; t < NT; ++t) ws[t] = (double)cnt[t];
+  }
+}
+
+// restart tiles per warp of k_score
+constexpr int kScoreTiles = 2;
+
 template <bool UNIT>
 __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
                                                const int32_t* __restrict__ ranges,
@@ -1124,27 +1197,37 @@ __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
                                                const uint32_t* __restrict__ bits,
                                                int32_t* __restrict__ nsat_part,
                                                double* __restrict__ wsat_part) {
-  __shared__ int32_t cnt_s[kScoreWarps][32];
-  __shared__ double w_s[kScoreWarps][32];
+  __shared__ int32_t cnt_s[kScoreTiles][kScoreWarps][32];
+  __shared__ double w_s[UNIT ? 1 : kScoreTiles][kScoreWarps][32];
   const int lane = threadIdx.x, ty = threadIdx.y;
-  const int tile = blockIdx.x;
+  const int tile0 = blockIdx.x * kScoreTiles;
   const int rg = blockIdx.y * kScoreWarps + ty;
-  int cnt = 0;
-  double ws = 0.0;
+  int cnt[kScoreTiles];
+  double ws[kScoreTiles];
+#pragma unroll
+  for (int t = 0; t < kScoreTiles; ++t) {
+    cnt[t] = 0;
+    ws[t] = 0.0;
+  }
   if (rg < n_ranges)
-    score_range<false, UNIT>(rg, tile, lane, RW, ranges, sc, lit, satbits, bits, &cnt, &ws);
-  cnt_s[ty][lane] = cnt;
-  w_s[ty][lane] = ws;
+    score_range_tiles<UNIT, kScoreTiles>(rg, tile0, lane, RW, ranges, sc, lit, satbits, bits,
+                                         cnt, ws);
+#pragma unroll
+  for (int t = 0; t < kScoreTiles; ++t) {
+    cnt_s[t][ty][lane] = cnt[t];
+    if constexpr (!UNIT) w_s[t][ty][lane] = ws[t];
+  }
   __syncthreads();
-  if (ty == 0) {
+  // warp t < kScoreTiles adds tile t's counts over the block's warps
+  if (ty < kScoreTiles && tile0 + ty < RW) {
     int a = 0;
     double b = 0.0;
 #pragma unroll
     for (int k = 0; k < kScoreWarps; ++k) {
-      a += cnt_s[k][lane];
-      b += w_s[k][lane];
+      a += cnt_s[ty][k][lane];
+      if constexpr (!UNIT) b += w_s[ty][k][lane];
     }
-    const int r = tile * 32 + lane;
+    const int r = (tile0 + ty) * 32 + lane;
     nsat_part[(size_t)blockIdx.y * Rp + r] = a;
     if constexpr (!UNIT) wsat_part[(size_t)blockIdx.y * Rp + r] = b;   // UNIT: wsat = nsat
   }
@@ -1725,11 +1808,11 @@ cudaError_t launch_score(const DevPlan& d, int R, int Rp, const uint32_t* bits,
   {
     HookScope hs(h, KC_SCORE, s);
     if (d.unit_weights)
-      k_score<true><<<dim3(RT, nch), dim3(32, kScoreWarps), 0, s>>>(
+      k_score<true><<<dim3(ceil_div(RT, kScoreTiles), nch), dim3(32, kScoreWarps), 0, s>>>(
           RT, Rp, d.n_ranges, d.score_ranges, d.score, d.lit, d.satbits, bits, nsat_part,
           wsat_part);
     else
-      k_score<false><<<dim3(RT, nch), dim3(32, kScoreWarps), 0, s>>>(
+      k_score<false><<<dim3(ceil_div(RT, kScoreTiles), nch), dim3(32, kScoreWarps), 0, s>>>(
           RT, Rp, d.n_ranges, d.score_ranges, d.score, d.lit, d.satbits, bits, nsat_part,
           wsat_part);
     cudaError_t e = cudaGetLastError();
