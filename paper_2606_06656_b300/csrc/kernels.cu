@@ -1186,7 +1186,7 @@ __device__ __forceinline__ void score_range_tiles(int rg, int tile0, int lane, i
 }
 
 // restart tiles per warp of k_score
-constexpr int kScoreTiles = 2;
+constexpr int kScoreTiles = 4;
 
 template <bool UNIT>
 __global__ void __launch_bounds__(256) k_score(int RW, int Rp, int n_ranges,
