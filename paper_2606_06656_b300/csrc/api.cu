@@ -1146,6 +1146,26 @@ int cls_batch_graph_create(int32_t count, const cls_problem* const* ps, const in
     (void)cudaGetLastError();
     return rc != CLS_OK ? rc : cuda_err(e, "cudaStreamEndCapture");
   }
+  // the kernel launches one graph launch performs: its kernel nodes (the
+  // recording counted units, some of which launch several kernels)
+  {
+    size_t nn = 0;
+    e = cudaGraphGetNodes(g->graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g->graph, nodes.data(), &nn);
+    int64_t kernels = 0;
+    for (size_t i = 0; i < nn && e == cudaSuccess; ++i) {
+      cudaGraphNodeType ty;
+      e = cudaGraphNodeGetType(nodes[i], &ty);
+      if (e == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    if (e != cudaSuccess) {
+      graph_release(g);
+      (void)cudaGetLastError();
+      return cuda_err(e, "graph node count");
+    }
+    g->launches = kernels;
+  }
   e = cudaGraphInstantiate(&g->exec, g->graph, 0);
   if (e != cudaSuccess) {
     graph_release(g);
