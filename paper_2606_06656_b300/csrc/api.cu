@@ -93,13 +93,13 @@ struct cls_problem {
   bool weights_dirty = false;  // device weights changed since the host plan's copy
   int64_t list_epoch = 0;      // bumped whenever the work lists are uploaded again
   // cls_solve_host's recorded step chunk, reused while its workspace, R, lr,
-  // work lists and weight mode stay the same
-  cls_graph* solve_graph = nullptr;
-  const void* sg_ws = nullptr;
-  int sg_R = 0;
-  float sg_lr = 0.f;
-  int64_t sg_epoch = -1;
-  int sg_unit = -1;
+  // work lists and weight mode stay the same (a cache: mutable)
+  mutable cls_graph* solve_graph = nullptr;
+  mutable const void* sg_ws = nullptr;
+  mutable int sg_R = 0;
+  mutable float sg_lr = 0.f;
+  mutable int64_t sg_epoch = -1;
+  mutable int sg_unit = -1;
 };
 
 namespace {
@@ -793,7 +793,7 @@ int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host, float 
   constexpr int kSolveChunk = 10;
   int32_t done_steps = 0;
   if (n_steps >= kSolveChunk && !p->hook) {
-    cls_problem* mp = const_cast<cls_problem*>(p);   // the cache only
+    const cls_problem* mp = p;
     if (!(mp->solve_graph && mp->sg_ws == ws && mp->sg_R == R && mp->sg_lr == lr &&
           mp->sg_epoch == p->list_epoch && mp->sg_unit == p->dev.unit_weights)) {
       if (mp->solve_graph) cls_graph_destroy(mp->solve_graph);
