@@ -233,3 +233,17 @@ def test_readers_feed_problem_check():
             pass
     rc, msg = B.cls_problem_check(read_opb("\n".join(good)))
     assert rc == 0, msg
+
+
+def test_solver_format_detection(tmp_path):
+    """The command-line solver reads a file as DIMACS when its first
+    non-comment line is the problem line, as OPB otherwise."""
+    from paper_2606_06656_b300.solve import read_any
+    f = tmp_path / "a.cnf"
+    f.write_text("c comment\n\np cnf 3 1\n1 -2 3 0\n")
+    inst, kind = read_any(str(f))
+    assert kind == "dimacs" and inst.m == 1
+    g = tmp_path / "b.opb"
+    g.write_text("* #variable= 3 #constraint= 1\n+1 x1 +1 x2 +1 x3 >= 2 ;\n")
+    inst, kind = read_any(str(g))
+    assert kind == "opb" and inst.m == 1 and inst.k.tolist() == [2]
