@@ -20,6 +20,13 @@ independent restarts (Sec. 3.3: all batch elements iterate together).
   "Parallel random numbers: as easy as 1, 2, 3", SC'11), keyed by the seed,
   counter (restart id, v div 4, 0, 0), output word v mod 4; x = (u >> 40) *
   2^-23 - 1.  (Random draws are an input convention, not paper arithmetic.)
+* per-restart tracking, refills, movement and convergence (Sec. 3.3,
+  Sec. 4.3) -- plain definitions, pinned by hand-worked traces and by the
+  projected step's own displacement.
+* adaptive constraint weighting (Sec. 4.1) -- per-constraint gradient-norm
+  sums and violation counts (plain definitions, pinned to the OR/XOR closed
+  forms and direct counts) and the library's update rule (pinned to a
+  hand-worked example).
 """
 import numpy as np
 
