@@ -523,7 +523,7 @@ def run_refill(args):
 
 
 def run_ramsey(args):
-    """Redundant-constraint study on the paper's own structure (Sec. 4.1):
+    """Redundant-constraint study on the paper's own structure (Sec. 3.1):
     balanced 3-colouring of K_16 (EO per edge, CARD_GE 5 per vertex and
     colour), plain and with the decomposed edge encoding added
     (CARD>=2(not x) + OR(x) = EO - 1, doubling the edge gradient).  R
@@ -702,7 +702,7 @@ def run_reweight(args):
 
 
 def run_completion(args):
-    """Partial-assignment completion (Sec. 4.2): planted 3-SAT at clause
+    """Partial-assignment completion (Sec. 3.2): planted 3-SAT at clause
     ratio 4.26 with n = 450, 550 and 650 variables (stand-ins for the
     satisfiable phase-transition instances of the paper's study), a fraction
     of the variables pinned to the plant and folded into the constraints,
@@ -770,7 +770,7 @@ def run_completion(args):
 
 
 def run_profile(args):
-    """Convergence profiles (Sec. 4.3's analysis, on the planted 3-SAT
+    """Convergence profiles (Sec. 3.3's analysis, on the planted 3-SAT
     stand-ins: the Costas encodings are not given): n = 550 at clause ratio
     4.26 with about 10 % and about 66 % of the variables pinned to the plant,
     R = 4096 restarts from uniform points, the paper's 300-step limit.  Per

@@ -190,8 +190,8 @@ int cls_refill(const cls_problem* p, int32_t R, float* x, int32_t* trk, int32_t 
 int cls_unsat_histogram(const cls_problem* p, int32_t R, const int32_t* nsat, int32_t* hist,
                         void* stream);
 
-/* Convergence of projected gradient descent per restart (Sec. 4.3 studies
- * the number of steps restarts take to converge; Sec. 4.1 notes that a
+/* Convergence of projected gradient descent per restart (Sec. 3.3 studies
+ * the number of steps restarts take to converge; Sec. 3.1 notes that a
  * small step can meet a convergence criterion on a plateau):
  *   cls_movement         maxdelta[r] = max over variables v of
  *                        |x[v*R + r] - x_prev[v*R + r]| (device float[R],
@@ -208,7 +208,7 @@ int cls_movement(const cls_problem* p, int32_t R, const float* x_prev, const flo
 int cls_track_converged(const cls_problem* p, int32_t R, const float* maxdelta, float tol,
                         int32_t step, int32_t* conv, void* stream);
 
-/* Adaptive constraint weighting (Sec. 4.1 proposes weights informed by the
+/* Adaptive constraint weighting (Sec. 3.1 proposes weights informed by the
  * constraints' gradient magnitudes, after observing that a doubled edge
  * gradient overwhelms the balancing constraints; the paper gives no rule,
  * so the rule below is this library's).  Weights are per constraint, shared

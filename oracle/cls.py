@@ -21,9 +21,9 @@ independent restarts (Sec. 3.3: all batch elements iterate together).
   counter (restart id, v div 4, 0, 0), output word v mod 4; x = (u >> 40) *
   2^-23 - 1.  (Random draws are an input convention, not paper arithmetic.)
 * per-restart tracking, refills, movement and convergence (Sec. 3.3,
-  Sec. 4.3) -- plain definitions, pinned by hand-worked traces and by the
+  Sec. 3.3) -- plain definitions, pinned by hand-worked traces and by the
   projected step's own displacement.
-* adaptive constraint weighting (Sec. 4.1) -- per-constraint gradient-norm
+* adaptive constraint weighting (Sec. 3.1) -- per-constraint gradient-norm
   sums and violation counts (plain definitions, pinned to the OR/XOR closed
   forms and direct counts) and the library's update rule (pinned to a
   hand-worked example).
@@ -201,8 +201,8 @@ def unsat_histogram(nsat, m):
     return np.bincount(m - np.asarray(nsat, dtype=np.int64), minlength=m + 1)
 
 
-# --- adaptive constraint weighting (Sec. 4.1) -------------------------------
-# Sec. 4.1 finds that a doubled edge-constraint gradient overwhelms the
+# --- adaptive constraint weighting (Sec. 3.1) -------------------------------
+# Sec. 3.1 finds that a doubled edge-constraint gradient overwhelms the
 # balancing constraints and proposes weights informed by the constraints'
 # gradient magnitudes, without a rule.  The statistics are plain
 # definitions; the update is the library's rule (stated in reweight).
@@ -257,7 +257,7 @@ def reweight(w, gnorm, unsat, has_fe, R, eta, kappa, w_max):
     return np.minimum(w_max, w * (1.0 + eta * u * rho)).astype(np.float32)
 
 
-# --- convergence of the descent per restart (Sec. 4.3) ----------------------
+# --- convergence of the descent per restart (Sec. 3.3) ----------------------
 
 def movement(X_prev, X):
     """max over variables of |x - x_prev| per restart, FP32 subtraction."""

@@ -130,7 +130,7 @@ class Problem:
     def refill(self, x, trk, patience, seed, generation, count, r_offset=0):
         B.cls_refill(self.handle, self._x(x), x, trk, patience, seed, r_offset, generation, count)
 
-    # -- adaptive constraint weighting (Sec. 4.1) -------------------------
+    # -- adaptive constraint weighting (Sec. 3.1) -------------------------
     def constraint_stats(self, bits, R):
         """(gnorm float64[m], unsat int32[m]) from the partials of the last
         eval/step with R restarts and the bitset of the rounded points."""

@@ -912,7 +912,7 @@ __device__ __forceinline__ void score_range(int rg, int tile, int lane, int RW,
 }
 
 // ---------------------------------------------------------------------------
-// Adaptive constraint weighting (Sec. 4.1 suggests weights informed by the
+// Adaptive constraint weighting (Sec. 3.1 suggests weights informed by the
 // constraints' gradient magnitudes).  Per constraint c, over the R restarts:
 //   gnorm[c] = sum_r || dFE_c/dy (x_r) ||_2  over the literals entering FE,
 //              from the partials P (= w_c s_e dFE_c/dy_e) of the last

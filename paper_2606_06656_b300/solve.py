@@ -39,7 +39,7 @@ def solve(inst, restarts=1024, steps=1000, lr=0.1, seed=1, patience=50,
     reweight > 0: every refill_every steps the constraint weights are
     updated from the batch's statistics (cls_reweight with eta = reweight,
     kappa 4, w_max 10), raising often-violated constraints with weak
-    gradients (Sec. 4.1)."""
+    gradients (Sec. 3.1)."""
     import torch
     from .api import Problem
     from . import binding as B

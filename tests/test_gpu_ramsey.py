@@ -1,4 +1,4 @@
-"""Ramsey balanced-colouring instances (Sec. 4.1) on the CUDA path: FE and
+"""Ramsey balanced-colouring instances (Sec. 3.1) on the CUDA path: FE and
 gradient against the FP64 oracle (1e-4 per constraint / of the gradient's
 norm), counts bit-exact at the plant and at single-edge changes of it."""
 import numpy as np

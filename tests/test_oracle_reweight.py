@@ -1,4 +1,4 @@
-"""Oracle of the adaptive constraint weighting (Sec. 4.1), pinned on CPU.
+"""Oracle of the adaptive constraint weighting (Sec. 3.1), pinned on CPU.
 
 The statistics are plain definitions, so they are pinned to closed forms
 written out here: the clause (OR) and parity (XOR) expansions of Appendix A,

@@ -1,4 +1,4 @@
-"""Ramsey balanced-colouring instances (Sec. 4.1), CPU pins.
+"""Ramsey balanced-colouring instances (Sec. 3.1), CPU pins.
 
 The generator's structure is checked by direct counting here (edges,
 colour degrees of the plant), independently of the oracle; then the
@@ -89,7 +89,7 @@ def test_single_edge_changes(red):
 
 
 def test_redundant_encoding_doubles_the_edge_gradient():
-    """Sec. 4.1: CARD>=2(not x) + OR(x) = EO(x) - 1 on three literals, so the
+    """Sec. 3.1: CARD>=2(not x) + OR(x) = EO(x) - 1 on three literals, so the
     redundant instance's objective is the plain one's plus sum_e (FE_EO,e - 1)
     and its gradient the plain one's plus the EO part's gradient."""
     plain = W.ramsey_balanced(16, 3)

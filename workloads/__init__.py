@@ -163,7 +163,7 @@ def random_ksat(n=100, m=426, kl=3, seed=1100) -> Instance:
 def planted_ksat(n=550, m=None, kl=3, seed=1600) -> Instance:
     """Random k-SAT with a planted solution at clause ratio 4.26 by default
     (stands in for the satisfiable phase-transition 3-SAT instances of
-    Sec. 4.2, 450-650 variables): kl distinct variables per clause, uniform
+    Sec. 3.2, 450-650 variables): kl distinct variables per clause, uniform
     signs, then each clause the plant violates gets one literal's sign
     flipped (the generator's planting rule)."""
     m = int(round(4.26 * n)) if m is None else m
@@ -210,7 +210,7 @@ def redundant_5sat(n=2000, m=40000, redundancy=0.0, red_len=(50, 200), seed=1300
 
 def ramsey_balanced(V=16, C=3, redundant=False) -> Instance:
     """Balanced edge colouring of the complete graph K_V with C colours
-    (Sec. 4.1).  Variable c(e, i) = e*C + i is True when edge e (pairs u < v
+    (Sec. 3.1).  Variable c(e, i) = e*C + i is True when edge e (pairs u < v
     in lexicographic order) takes colour i.  Constraints, in this order:
       * per edge: EO over c(e, 0..C-1) (each edge takes exactly one colour);
       * per vertex v and colour i: CARD_GE, k = ceil((V-1)/C), over
