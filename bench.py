@@ -38,6 +38,34 @@ SM_MAX_MHZ = 2032.0
 # (2 MUL + 2 FMA), gradient accumulation (2 FMA); FMA = 2 flops.
 
 
+# DRAM traffic of one launch (or one step of a kernel class) as ncu counted
+# it, dram__bytes_read.sum + dram__bytes_write.sum, with the capture's
+# workload, restart count and the SHA-256 (first 16 hex digits) of the
+# kernel sources it was taken on.  A figure is reported, scaled by R (every
+# byte counted grows with the restarts), only while the sources still hash
+# the same; otherwise traffic is null.
+TRAFFIC = {}
+
+
+def _sources_sha(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2606_06656_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload_name, R):
+    rec = TRAFFIC.get(kernel)
+    if rec is None or rec["workload"] != workload_name:
+        return None, "no ncu capture of this kernel on this workload"
+    if _sources_sha(rec["sources"]) != rec["sha"]:
+        return None, "kernel sources changed since the ncu capture"
+    return rec["bytes"] * R / rec["R"], (f"{rec['profile']}: ncu at R={rec['R']}"
+                                         + (f", scaled to R={R}" if R != rec["R"] else ""))
+
+
 def workload(name):
     if name == "mixed":
         return W.mixed_pb(), 4096, 0.1
@@ -138,15 +166,79 @@ def threads_used():
         return 1
 
 
+def _oracle_chunk(a):
+    """One oracle step on a slice of restarts (run in a spawned worker);
+    returns the new points and the seconds it took."""
+    inst, X, lr = a
+    t0 = time.perf_counter()
+    Xn = cpu_oracle_step(inst, X, lr)
+    return Xn, time.perf_counter() - t0
+
+
+def _single_thread_env():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def time_cpu_oracle_all_cores(inst, lr, per_worker=8, steps=1, budget_s=25.0, seed=42):
+    """The oracle, as it stands, on every host core: one spawned process per
+    core, each stepping its own slice of per_worker restarts (restarts are
+    independent, Sec. 3.3).  Wall time per parallel step, after the workers
+    have started and imported the oracle; stops early once budget_s is
+    spent.  Returns (record, steps done)."""
+    import multiprocessing as mp
+    cores = host_cores()
+    X = W.uniform_points(inst.n, cores * per_worker, seed=seed)
+    xs = [np.ascontiguousarray(X[:, i * per_worker:(i + 1) * per_worker]) for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores, initializer=_single_thread_env) as pool:
+        pool.map(_oracle_chunk, [(inst, xs[0][:, :1].copy(), lr)] * cores, chunksize=1)  # warm
+        wall, done = 0.0, 0
+        for _ in range(max(1, steps)):
+            t0 = time.perf_counter()
+            out = pool.map(_oracle_chunk, [(inst, x, lr) for x in xs], chunksize=1)
+            wall += time.perf_counter() - t0
+            xs = [o[0] for o in out]
+            done += 1
+            if wall > budget_s:
+                break
+    per_step = wall / done
+    return ({"value": cores * per_worker * inst.nnz / per_step, "unit": "literal-evals/s",
+             "cores": cores, "restarts": cores * per_worker, "s_per_step": per_step,
+             "cpu_model": cpu_model()}, done)
+
+
 def run_reference(args, rank, world):
+    """The oracle, as it stands, on all host cores (one spawned process per
+    core over slices of restarts), a bounded sample of the workload per
+    step; the single-core figure beside it."""
     inst, R, lr = workload(args.config)
     if rank != 0:
         return
-    R_sample = 8 if inst.nnz > 10000 else min(R, 64)
-    for _ in range(args.warmup if inst.nnz < 10000 else 0):
-        cpu_oracle_step(inst, W.uniform_points(inst.n, R_sample, 1), lr)
-    per_step, done = time_cpu_oracle(inst, R_sample, lr, args.steps)
-    value = R_sample * inst.nnz / per_step
+    big = inst.nnz > 10000
+    per_worker = 8 if big else max(1, min(R, 64) // host_cores())
+    for _ in range(args.warmup if not big else 0):
+        cpu_oracle_step(inst, W.uniform_points(inst.n, per_worker, 1), lr)
+    allc, done = time_cpu_oracle_all_cores(inst, lr, per_worker, steps=args.steps)
+    per_step = allc["s_per_step"]
+    value = allc["value"]
+    t1, d1 = time_cpu_oracle(inst, per_worker, lr, 1 if big else 3, budget_s=10.0)
     line = {
         "impl": "reference", "metric": "constraint-literal FE+grad evals/s",
         "value": value, "unit": "literal-evals/s", "n_gpus": args.gpus, "steps": done,
@@ -154,9 +246,14 @@ def run_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": inst.name, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
                    "R": R, "lr": lr},
-        "cpu_baseline": {"value": value, "unit": "literal-evals/s", "cores": threads_used(),
-                         "kind": "oracle",
-                         "sample": f"{R_sample} of {R} restarts per step, {done} steps"},
+        "cpu_baseline": {"value": value, "unit": "literal-evals/s", "cores": allc["cores"],
+                         "kind": "oracle", "cpu_model": allc["cpu_model"],
+                         "sample": f"{allc['restarts']} of {R} restarts per step "
+                                   f"({per_worker} per core), {done} steps",
+                         "single_core": {"value": per_worker * inst.nnz / t1,
+                                         "unit": "literal-evals/s", "cores": 1,
+                                         "sample": f"{per_worker} of {R} restarts, "
+                                                   f"{d1} step(s)"}},
         "e2e": {"value": value, "unit": "literal-evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -331,10 +428,22 @@ def run_ours(args, rank, world, local_rank):
         flops = dft_flops_dense
         t = kstats_dense[dom]["ms_per_step"] / 1e3
         peak = 2 * SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+        # the dense count of the method's DFT work: 9 L^2 flops per
+        # cardinality constraint and restart (J = L/2 roots, ~18 flops per
+        # literal and root), with no tail cutoff, power sums or corner DPs
+        Lc = inst.lengths()[np.isin(inst.ctype, (W.TYPE_CARD_GE, W.TYPE_CARD_LE))]
+        dense = 9.0 * float((Lc.astype(np.float64) ** 2).sum()) * R
+        tr, tr_src = recorded_traffic("dft_class", inst.name, R)
         roof = {"bound": "alu", "kernel": "k_fe_series / k_fe_group_fr (DFT buckets)",
                 "achieved": flops / t / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak,
-                "traffic": None, "window": f"steps 0-{n_dense - 1} of the run (dense phase)",
+                "traffic": tr, "traffic_source": tr_src,
+                "window": f"steps 0-{n_dense - 1} of the run (dense phase)",
+                "flops_evaluated_per_step": flops,
+                "dense_count": {"flops_per_step": dense, "achieved": dense / t / 1e12,
+                                "frac": dense / t / 1e12 / peak,
+                                "note": "9 L^2 per cardinality constraint and restart; above "
+                                        "1 means the kernels skip work the dense DFT does"},
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flops x 2032 MHz (max SM clock)"}
     # the fused accumulate + step + round kernel: algorithmic bytes = the
     # partial rows read once (4 B per FE literal and restart), x read and
@@ -344,29 +453,32 @@ def run_ours(args, rank, world, local_rank):
     step_bytes = 4 * RT * 32 * info["nnz_fe"] + 8 * inst.n * R + 4 * inst.n * RT
     t_step = kstats_dense["accum_step_round"]["ms_per_step"] / 1e3
     hbm_peak = pk.get("hbm_gbs", 6400.0)
-    # DRAM traffic of one k_accum_step launch as ncu counted it
-    # (dram__bytes_read.sum + dram__bytes_write.sum) on this workload at
-    # R = 4096, step 70: 3,400,302,080 + 81,658,624 bytes; it does not depend
-    # on the step (every partial row is read once)
-    traffic = 3481960704 if (inst.name == "mixedpb_n5000_m22500" and R == 4096) else None
+    traffic, traffic_src = recorded_traffic("k_accum_step", inst.name, R)
     roof_step = {"bound": "hbm", "kernel": "k_accum_step", "bytes": step_bytes,
                  "achieved": step_bytes / t_step / 1e9, "peak": hbm_peak, "unit": "GB/s",
                  "frac": step_bytes / t_step / 1e9 / hbm_peak, "traffic": traffic,
-                 "peak_source": "measured copy bandwidth"}
+                 "traffic_source": traffic_src, "peak_source": "measured copy bandwidth"}
     if dom != "fe_group_dft":
         roof = dict(roof_step)
         if dom != "accum_step_round":
             roof["note"] = (f"the longest kernel class is {dom} "
                             f"({kstats[dom]['ms_per_step']:.4f} ms/step, gather or launch "
                             f"bound); the HBM roofline is given for the fused step kernel")
-    cpu_t, cpu_steps = (None, 0)
     cpu = None
-    if rank == 0 and not args.no_cpu:
-        R_sample = 8 if inst.nnz > 10000 else min(R, 64)
-        cpu_t, cpu_steps = time_cpu_oracle(inst, R_sample, lr, 1 if inst.nnz > 10000 else 3)
-        cpu = {"value": R_sample * inst.nnz / cpu_t, "unit": "literal-evals/s",
-               "cores": threads_used(), "kind": "oracle",
-               "sample": f"{R_sample} of {R} restarts, {cpu_steps} step(s)"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # the oracle as it stands on every host core (spawned workers, one
+        # step on 8 restarts each), and on one core
+        big = inst.nnz > 10000
+        per_worker = 8 if big else max(1, min(R, 64) // host_cores())
+        allc, done = time_cpu_oracle_all_cores(inst, lr, per_worker, steps=1 if big else 3)
+        cpu_t, cpu_steps = time_cpu_oracle(inst, per_worker, lr, 1 if big else 3)
+        cpu = {"value": allc["value"], "unit": "literal-evals/s", "cores": allc["cores"],
+               "kind": "oracle", "cpu_model": allc["cpu_model"],
+               "sample": f"{allc['restarts']} of {R} restarts ({per_worker} per core), "
+                         f"{done} step(s)",
+               "single_core": {"value": per_worker * inst.nnz / cpu_t,
+                               "unit": "literal-evals/s", "cores": 1,
+                               "sample": f"{per_worker} of {R} restarts, {cpu_steps} step(s)"}}
     line = {
         "metric": "constraint-literal FE+grad evals/s", "value": value,
         "unit": "literal-evals/s", "n_gpus": world, "steps": args.steps,
@@ -400,51 +512,123 @@ def run_ours(args, rank, world, local_rank):
         "wall_s": wall,
         "mean_nsat": float(nsat.float().mean().item()),
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     if graph is not None:
         B.cls_graph_destroy(graph)
+    if world == 1 and args.config == "mixed" and not args.no_extras:
+        # the other two targets, on the same GPU in the same run: the fused
+        # step kernel on the 3-SAT instance at scale, and learned vs uniform
+        # initialisation (time to equal satisfaction)
+        del ws, hws, x, x0, xh, flush
+        p._ws.clear()
+        p.close()
+        torch.cuda.empty_cache()
+        line["c1_step_kernel"] = c1_step_kernel()
+        lvu, _, _ = learned_vs_uniform(args.train_instances, args.held_out, args.train_steps)
+        line["learned_vs_uniform"] = lvu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def run_learned(args):
-    """Learned vs uniform initialisation: train the message-passing network
-    on planted mixed-PB instances (n ~ U{1000..4000}, m = 4.5 n) through the
-    CLS objective, then on held-out instances measure the device seconds to
-    reach the median satisfied fraction that uniform starts reach after S
-    steps (1024 restarts each)."""
+def learned_vs_uniform(n_train=512, n_held=64, train_steps=3000, R=1024, S=500):
+    """Learned vs uniform initialisation (time to equal satisfaction): train
+    the message-passing network on n_train planted mixed-PB instances (n ~
+    U{1000..4000}, m = 4.5 n) through the CLS objective; on n_held held-out
+    instances, device seconds until the median satisfied fraction reaches
+    tau = the median that uniform starts reach after S steps (R restarts
+    each), network inference included for the learned side."""
     import torch
     from paper_2606_06656_b300 import learned as Lr
+    workers = max(1, min(32, host_cores()))
     t0 = time.perf_counter()
-    train = W.mixed_instances(args.train_instances, n_range=(1000, 4000), seed=1400)
-    held = W.mixed_instances(args.held_out, n_range=(1000, 4000), seed=91400)
+    train = W.mixed_instances(n_train, n_range=(1000, 4000), seed=1400, workers=workers)
+    held = W.mixed_instances(n_held, n_range=(1000, 4000), seed=91400, workers=workers)
+    t_gen = time.perf_counter() - t0
     tr = Lr.build_entries(train, harvest_R=64, harvest_steps=200)
     te = Lr.build_entries(held, harvest_R=8, harvest_steps=1)
-    t_build = time.perf_counter() - t0
-    params = tr[0][1].init_params(3)
     torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0 - t_gen
+    params = tr[0][1].init_params(3)
     t1 = time.perf_counter()
-    log = Lr.train(tr, params, steps=args.train_steps, R=32, lam=0.5, tau=1.0, lr=2e-3,
-                   log_every=max(1, args.train_steps // 8))
+    log = Lr.train(tr, params, steps=train_steps, R=32, lam=0.5, tau=1.0, lr=2e-3,
+                   log_every=max(1, train_steps // 8))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
-    res = Lr.compare(te, params, R=1024, S=500, tau=1.0)
+    t2 = time.perf_counter()
+    res = Lr.compare(te, params, R=R, S=S, tau=1.0)
+    t_eval = time.perf_counter() - t2
     su = [r["s_uniform"] for r in res]
     sl = [r["s_learned"] if r["s_learned"] is not None else float("inf") for r in res]
+    stu = [r["steps_uniform"] for r in res]
+    stl = [r["steps_learned"] if r["steps_learned"] is not None else float("inf") for r in res]
+    out = {"s_learned_median": float(np.median(sl)), "s_uniform_median": float(np.median(su)),
+           "speedup_median": float(np.median(su) / np.median(sl)),
+           "steps_learned_median": float(np.median(stl)),
+           "steps_uniform_median": float(np.median(stu)),
+           "instances_learned_faster": int(sum(a < b for a, b in zip(sl, su))),
+           "s_inference_median": float(np.median([r["s_inference"] for r in res])),
+           "tau": "per held-out instance, the median over restarts of the satisfied "
+                  "fraction uniform starts reach after S steps",
+           "train_instances": n_train, "held_out": n_held, "train_steps": train_steps,
+           "restarts": R, "S": S, "generate_s": t_gen, "build_s": t_build,
+           "train_s": t_train, "eval_s": t_eval}
+    return out, log, res
+
+
+def run_learned(args):
+    """Learned vs uniform initialisation as its own bench line."""
+    out, log, res = learned_vs_uniform(args.train_instances, args.held_out, args.train_steps)
     line = {
         "metric": "time-to-equal-sat, learned vs uniform init (median device s)",
-        "value": float(np.median(sl)), "unit": "s", "higher_is_better": False,
-        "uniform_s": float(np.median(su)), "speedup": float(np.median(su) / np.median(sl)),
+        "value": out["s_learned_median"], "unit": "s", "higher_is_better": False,
+        "uniform_s": out["s_uniform_median"], "speedup": out["speedup_median"],
         "n_gpus": 1, "dtype": "f32 (network bf16 x bf16 -> f32)", "data": "synthetic",
-        "config": {"workload": "planted mixed PB, n~U{1000..4000}, m=4.5n",
-                   "train_instances": args.train_instances, "held_out": args.held_out,
-                   "train_steps": args.train_steps, "restarts": 1024, "S": 500,
-                   "build_s": t_build, "train_s": t_train},
+        "config": {"workload": "planted mixed PB, n~U{1000..4000}, m=4.5n", **out},
         "train_log": log, "per_instance": res,
     }
     print(json.dumps(line), flush=True)
+
+
+def c1_step_kernel():
+    """The fused accumulate/step/round kernel (k_accum_step) on the random
+    3-SAT instance (n = 100, m = 426) at R = 2^20 restarts, where it is
+    HBM-bound (x is 419 MB, the partial rows 5.4 GB): mean CUDA-event time
+    of the kernel over 5 eager steps after 3 warm-up steps, against its
+    algorithmic bytes (partial rows read once, x read and written, the
+    bitset written)."""
+    import torch
+    from paper_2606_06656_b300 import Problem
+    from paper_2606_06656_b300 import binding as B
+    inst = W.random_ksat()
+    R = 1 << 20
+    p = Problem(inst)
+    x = p.init_uniform(R, seed=42)
+    ws = p.workspace(R)
+    nsat = torch.empty(R, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        B.cls_step(p.handle, R, x, 0.1, 1, None, nsat, None, ws)
+    B.cls_profile_reset(p.handle)
+    B.cls_profile_enable(p.handle, True)
+    for _ in range(5):
+        B.cls_step(p.handle, R, x, 0.1, 1, None, nsat, None, ws)
+    B.cls_profile_enable(p.handle, False)
+    n_l, t_ms = B.cls_profile_read(p.handle, 3)          # accum_step_round
+    torch.cuda.synchronize()
+    RT = (R + 31) // 32
+    nbytes = 4 * RT * 32 * p.info["nnz_fe"] + 8 * inst.n * R + 4 * inst.n * RT
+    t = t_ms / max(n_l, 1) / 1e3
+    peak = peaks().get("hbm_gbs", 6400.0)
+    tr, tr_src = recorded_traffic("k_accum_step", inst.name, R)
+    out = {"kernel": "k_accum_step", "workload": f"{inst.name}, R=2^20", "bytes": nbytes,
+           "us": t * 1e6, "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
+           "frac": nbytes / t / 1e9 / peak, "target_frac": 0.60,
+           "traffic": tr, "traffic_source": tr_src,
+           "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+    del x, ws, p
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_refill(args):
@@ -912,7 +1096,9 @@ def main():
     ap.add_argument("--profile-step", type=int, default=-1,
                     help="run S steps untimed, then one step inside a profiler window")
     ap.add_argument("--train-instances", type=int, default=512)
-    ap.add_argument("--held-out", type=int, default=16)
+    ap.add_argument("--held-out", type=int, default=64)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 3-SAT step-kernel and learned-vs-uniform keys")
     ap.add_argument("--train-steps", type=int, default=3000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -437,7 +437,10 @@ int cls_series_range(int32_t L, int32_t K);
  * CLS_ERR_WORKSPACE (use cls_step with a caller workspace instead).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls on a device share the one array and
+ * before any stream capture.  The current device must be the problem's
+ * device (CLS_ERR_INVALID otherwise).  The looked-up address is kept for the
+ * life of the process: after a cudaDeviceReset it is stale, so do not call
+ * this entry point again in that process.  All calls on a device share the one array and
  * it keeps the previous call's contents (the step writes every scratch byte
  * it reads), so calls that may overlap on the GPU -- on different streams,
  * or from different threads -- race and must be serialised by the caller.

@@ -287,6 +287,7 @@ namespace cls {
 // Helpers for other translation units of the library (noalloc.cu).
 int set_error(int code, const std::string& msg) { return set_err(code, msg); }
 bool profiling_enabled(const cls_problem* p) { return p && p->hook != nullptr; }
+int problem_device(const cls_problem* p) { return p ? p->device : -1; }
 }  // namespace cls
 
 extern "C" {

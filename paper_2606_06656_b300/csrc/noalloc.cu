@@ -18,6 +18,7 @@
 namespace cls {
 int set_error(int code, const std::string& msg);   // api.cu
 bool profiling_enabled(const cls_problem* p);       // api.cu
+int problem_device(const cls_problem* p);           // api.cu
 }  // namespace cls
 
 namespace {
@@ -29,17 +30,26 @@ __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 // Device address of g_static_scratch per device.  In host code the array's
 // name is only a host-side stand-in, so the address is looked up with
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  A
+// cudaDeviceReset (or any teardown of the device's primary context) makes the
+// cached address stale; such a process must not call cls_step_noalloc again.
 void* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-int scratch_for_current_device(void** out) {
+int scratch_for_current_device(int want_dev, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return cls::set_error(CLS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   }
+  // The problem's tables live on the device it was created on; the scratch
+  // must be that device's copy of the array, so the caller's current device
+  // has to match.
+  if (dev != want_dev)
+    return cls::set_error(CLS_ERR_INVALID,
+                          "cls_step_noalloc: current device " + std::to_string(dev) +
+                              " is not the problem's device " + std::to_string(want_dev));
   if (dev < 0 || dev >= kMaxDevices)
     return cls::set_error(CLS_ERR_UNSUPPORTED, "device index beyond the static scratch table");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -76,7 +86,7 @@ extern "C" int cls_step_noalloc(const cls_problem* p, int32_t R, float* x, float
                               ", more than the static limit of " +
                               std::to_string(kStaticScratchBytes) + " bytes (use cls_step)");
   void* scratch = nullptr;
-  rc = scratch_for_current_device(&scratch);
+  rc = scratch_for_current_device(cls::problem_device(p), &scratch);
   if (rc != CLS_OK) return rc;
   // Nothing in the step reads scratch before writing it in the same call, so
   // the array needs no clearing between calls.

@@ -10,7 +10,10 @@ sequences the calls and keeps the tensors.
 Training signal, per instance and step (R restarts, m constraints):
   J = 1/(R m) sum_r F(x0_r) + lam/n_free sum_v softplus(-2 t_v z_v)
 with x0 = tanh(z + tau u) and t the signs of the best assignment the solver
-itself reached from uniform starts (its local minimum).
+itself reached from uniform starts (its local minimum).  The objective
+term's gradient with respect to x0 comes through CLSObjective (the
+torch.autograd.Function whose backward is the hand-written adjoint); the
+head and network backward are the library's own kernels.
 """
 import time
 
@@ -19,6 +22,7 @@ import torch
 
 from . import binding as B
 from .api import Problem
+from .autograd import CLSObjective
 
 
 def _aligned(nbytes, device):
@@ -105,34 +109,56 @@ def train(entries, params, steps, R=32, lam=0.5, tau=1.0, lr=2e-3, seed=11, log_
     for it in range(steps):
         p, net, tgt = entries[int(rng.integers(len(entries)))]
         z = net.forward(params)
-        x0 = net.points(z, R, seed=seed * 100003 + it, tau=tau)
-        obj, grad, _ = p.eval(x0, obj=True, grad=True)
-        gx0 = grad * (1.0 / (R * p.m))           # d(mean objective / m)/dx0
+        x0 = net.points(z, R, seed=seed * 100003 + it, tau=tau).requires_grad_(True)
+        # the objective term through the autograd path: forward = FE and
+        # literal partials, backward = the hand-written adjoint scaled by
+        # d(mean objective / m)/dobj_r = 1/(R m)
+        obj = CLSObjective.apply(p, x0)
+        obj.backward(torch.full_like(obj, 1.0 / (R * p.m)))
+        gx0 = x0.grad
+        x0 = x0.detach()
         dz = net.head_grad(z, x0, gx0, tgt, lam)
         dp = net.backward(params, dz)
         opt.step(params, dp)
         if log_every and it % log_every == 0:
-            log.append((it, float(obj.mean().item()) / p.m))
+            log.append((it, float(obj.detach().mean().item()) / p.m))
     return log
 
 
-def time_to_fraction(problem: Problem, x0, frac, lr=0.1, max_steps=500, chunk=10):
-    """Steps and seconds (device time, CUDA events) until the median over
-    restarts of the satisfied fraction reaches `frac`; None if never."""
+def run_chunks(problem: Problem, x0, lr, steps, chunk=10):
+    """`steps` CLS steps from x0 in chunks of `chunk`, with no host
+    synchronisation inside: each chunk's satisfied counts land in one row of
+    a device buffer and a CUDA event is recorded after it.  Returns (x after
+    the run, median satisfied fraction per chunk, device seconds from the
+    start to the end of each chunk)."""
     x = x0.clone()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R = x.shape[1]
+    K = max(1, steps // chunk)
+    nsat = torch.empty((K, R), dtype=torch.int32, device=x.device)
+    ws = problem.workspace(R)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    evs[0].record()
+    for k in range(K):
+        B.cls_step(problem.handle, R, x, lr, chunk, None, nsat[k], None, ws)
+        evs[k + 1].record()
     torch.cuda.synchronize()
-    start.record()
-    done = 0
-    while done < max_steps:
-        nsat, _, _ = problem.step(x, lr, n_steps=chunk, bits=False)
-        done += chunk
-        med = float(torch.median(nsat.float()).item()) / problem.m
-        if med >= frac:
-            end.record()
-            torch.cuda.synchronize()
-            return done, start.elapsed_time(end) / 1e3
-    return None, None
+    med = (torch.median(nsat.float(), dim=1).values / problem.m).cpu().numpy()
+    secs = np.array([evs[0].elapsed_time(evs[k + 1]) / 1e3 for k in range(K)])
+    return x, med, secs
+
+
+def _first_reach(med, frac):
+    hit = np.nonzero(med >= frac)[0]
+    return int(hit[0]) if len(hit) else None
+
+
+def time_to_fraction(problem: Problem, x0, frac, lr=0.1, max_steps=500, chunk=10):
+    """Steps and device seconds (CUDA events) until the median over restarts
+    of the satisfied fraction reaches `frac`, checked after every chunk;
+    (None, None) if it does not within max_steps."""
+    _, med, secs = run_chunks(problem, x0, lr, max_steps, chunk)
+    k = _first_reach(med, frac)
+    return (None, None) if k is None else ((k + 1) * chunk, float(secs[k]))
 
 
 def median_fraction_after(problem: Problem, x0, steps, lr=0.1):
@@ -145,17 +171,18 @@ def compare(entries, params, R=1024, S=500, tau=1.0, lr=0.1, seed=99, chunk=10):
     """Learned vs uniform initialisation on held-out instances.
 
     tau_i = median over restarts of the satisfied fraction that uniform
-    starts reach after S steps on instance i.  Uniform time = device time of
-    the steps until the median reaches tau_i (at most S); learned time =
-    network forward + points + steps until the median reaches tau_i (at most
-    4 S).  Returns per-instance records."""
+    starts reach after S steps on instance i.  One uniform run of S steps
+    gives both tau_i and the uniform time: the device time until the median,
+    checked every `chunk` steps, first reaches tau_i.  The learned time is
+    the network forward + points (device time) plus the steps from the
+    network's points until the median reaches tau_i (runs of S steps, at
+    most 4 S in all).  Returns per-instance records."""
     out = []
     for i, (p, net, _) in enumerate(entries):
         xu = p.init_uniform(R, seed + i)
-        tau_i = median_fraction_after(p, xu, S, lr)
-        xu = p.init_uniform(R, seed + i)
-        steps_u, t_u = time_to_fraction(p, xu, tau_i, lr, S, chunk)
-        torch.cuda.synchronize()
+        _, med_u, secs_u = run_chunks(p, xu, lr, S, chunk)
+        tau_i = float(med_u[-1])
+        ku = _first_reach(med_u, tau_i)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record()
@@ -164,9 +191,17 @@ def compare(entries, params, R=1024, S=500, tau=1.0, lr=0.1, seed=99, chunk=10):
         t1.record()
         torch.cuda.synchronize()
         t_inf = t0.elapsed_time(t1) / 1e3
-        steps_l, t_l = time_to_fraction(p, xl, tau_i, lr, 4 * S, chunk)
-        out.append(dict(instance=i, n=p.n, m=p.m, tau=tau_i, steps_uniform=steps_u,
-                        s_uniform=t_u, steps_learned=steps_l,
+        steps_l, t_l, done, elapsed = None, None, 0, 0.0
+        while done < 4 * S:
+            xl, med_l, secs_l = run_chunks(p, xl, lr, S, chunk)
+            kl = _first_reach(med_l, tau_i)
+            if kl is not None:
+                steps_l, t_l = done + (kl + 1) * chunk, elapsed + float(secs_l[kl])
+                break
+            done += S
+            elapsed += float(secs_l[-1])
+        out.append(dict(instance=i, n=p.n, m=p.m, tau=tau_i, steps_uniform=(ku + 1) * chunk,
+                        s_uniform=float(secs_u[ku]), steps_learned=steps_l,
                         s_learned=None if t_l is None else t_l + t_inf, s_inference=t_inf))
     return out
 

@@ -146,6 +146,30 @@ def test_training_reduces_loss_and_objective():
     assert after < before - 0.02, (before, after)
 
 
+def test_training_gradient_flows_through_autograd_objective(monkeypatch):
+    """learned.train differentiates the CLS objective through CLSObjective:
+    its backward (the hand-written adjoint) runs once per training step, and
+    the gradient it returns is the oracle-checked objective gradient scaled
+    by 1/(R m)."""
+    from paper_2606_06656_b300 import autograd as AG
+    from paper_2606_06656_b300.learned import build_entries, train
+    calls = []
+    orig = AG.CLSObjective.backward
+
+    def counting(ctx, gout):
+        calls.append(float(gout[0].item()))
+        return orig(ctx, gout)
+
+    monkeypatch.setattr(AG.CLSObjective, "backward", staticmethod(counting))
+    insts = W.mixed_instances(2, n_range=(200, 300), seed=78)
+    entries = build_entries(insts, harvest_R=8, harvest_steps=10)
+    params = entries[0][1].init_params(3)
+    train(entries, params, steps=5, R=16, lam=0.5, tau=1.0, lr=1e-3)
+    assert len(calls) == 5
+    ms = {p.m for p, _, _ in entries}
+    assert all(any(abs(c * 16 * m - 1.0) < 1e-6 for m in ms) for c in calls)
+
+
 def test_learned_initialisation_gains_over_uniform():
     """Trained on planted mixed instances through the CLS objective, the
     network's initial points reach the satisfied fraction that uniform starts
@@ -163,6 +187,8 @@ def test_learned_initialisation_gains_over_uniform():
         assert r["steps_learned"] is not None
         gain += r["steps_learned"] < r["steps_uniform"]
     assert gain >= 2, res
+    # wall-clock on the device, network inference included
+    assert np.median([r["s_learned"] for r in res]) < np.median([r["s_uniform"] for r in res]), res
     f0u = np.median([Lr.median_fraction_after(p, p.init_uniform(256, 5), 1) for p, _, _ in te])
     f0l = np.median([Lr.median_fraction_after(p, n.points(n.forward(params), 256, 5, 1.0), 1)
                      for p, n, _ in te])

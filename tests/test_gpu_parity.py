@@ -5,6 +5,9 @@ constraint; gradient within 1e-4 relative to its norm per restart; rounding,
 bitsets and satisfaction counts bit-exact on a given FP32 assignment; the
 projected step bit-exact given the same FP32 gradient.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -24,24 +27,57 @@ U64 = 2.0 ** -53   # FP64 unit roundoff
 REAL_TYPES = (W.TYPE_OR, W.TYPE_XOR, W.TYPE_NAE)
 
 
-def fp32_floor(inst):
-    """Per-variable absolute error floor of the FP32 gradient, for the
-    isolated single-type stress tests whose exact gradient can be arbitrarily
-    small (far-tail probabilities such as 1e-115, or near-corner points).
-    A DFT literal partial is Re sum_j c'_j T_ij with |c'_j| summing to O(1)
-    and each T_ij a product of L-1 factors of modulus <= 1 carried with two
-    roundings per complex multiply: its absolute error is a few L*u however
-    small the exact value is.  We allow 4*L*u per DFT literal (times the
-    weight); closed-form real products keep relative accuracy and get only
-    the FP32 underflow floor (1e-30).  The FP64 oracle's own floor is added:
-    its partial sum_a P_{i-1}(a) D_i(a) cancels for alternating spectra (XOR:
-    prefix terms of both signs summing to a tiny product), a few L*2^-53."""
-    L = inst.lengths().astype(np.float64)
-    dft = ~np.isin(inst.ctype, REAL_TYPES)
-    w = np.abs(inst.weight.astype(np.float64))
-    per_con = np.where(dft, 4.0 * L * U32 * w, 0.0) + 4.0 * L * U64 * w
-    per_lit = np.repeat(per_con, inst.lengths())
-    out = np.full(inst.n, 1e-30)
+def _root_moduli_sum(sp, Y):
+    """M[i, r] = sum_{j=1..L} |c'_j| |T_ij(y_r)|: the moduli of the terms whose
+    sum is literal i's partial in the root form, c'_j = b_j (1 - w^j)/2 with
+    b_j the spectrum's DFT coefficient and T_ij = prod_{l != i}
+    (alpha_l + beta_l w^j) the leave-one-out product (FP64; a bound input,
+    not a value under test)."""
+    sp = np.asarray(sp, np.float64)
+    L, R = Y.shape
+    j = np.arange(1, L + 1)
+    b = np.fft.fft(sp)[1:] / (L + 1)                      # |b_j| is sign-convention free
+    cmod = np.abs(b) * np.abs(np.sin(np.pi * j / (L + 1)))
+    th = 2 * np.pi * j / (L + 1)
+    out = np.zeros((L, R))
+    for r0 in range(0, R, 8):
+        y = Y[:, r0:r0 + 8]                               # (L, r)
+        ab = (1 - y * y) / 4
+        F = np.sqrt(np.maximum(0.0, 1 - 2 * ab[:, None, :] * (1 - np.cos(th))[None, :, None]))
+        pre = np.cumprod(np.concatenate([np.ones((1,) + F.shape[1:]), F[:-1]]), axis=0)
+        suf = np.cumprod(np.concatenate([F[1:], np.ones((1,) + F.shape[1:])])[::-1], axis=0)[::-1]
+        out[:, r0:r0 + 8] = np.einsum("j,ljr->lr", cmod, pre * suf)
+    return out
+
+
+def fp32_floor(inst, X):
+    """Per-restart FP32 resolution floor of the gradient, for the isolated
+    single-type stress instances, whose exact gradient can be arbitrarily
+    small (far-tail probabilities such as 1e-115, exact zeros at corners).
+
+    A DFT literal partial is Re sum_j c'_j T_ij computed in FP32: each T_ij
+    a product of L-1 factors (two roundings per complex multiply), c'_j a
+    rounded table entry, the J <= L/2 + 1 terms summed, so each term carries
+    about n = 2L + J independent roundings of relative size u = 2^-24.  Its
+    absolute error scales with the terms, M_i = sum_j |c'_j||T_ij|
+    (_root_moduli_sum), not with the (possibly far smaller) result.  We take
+    the probabilistic rounding-error bound lambda sqrt(n) u (Higham and
+    Mary, SIAM J. Sci. Comput. 2019), lambda = 8, per term: 8 sqrt(3L) u M_i.
+    Away from the cube's faces |T_ij| decays quickly with j and M_i is
+    small; at corners |T_ij| = 1 and M_i = sum_j |c'_j|.  Closed-form real products (OR, XOR,
+    NAE) keep relative accuracy and get only the FP32 underflow floor.  The
+    FP64 oracle's own floor is added: its partial sum_a P_{i-1}(a) D_i(a)
+    cancels for alternating spectra, a few L 2^-53.  Returns floor[v, r]."""
+    sps = osp.instance_spectra(inst)
+    Yall = inst.lit_sign.astype(np.float64)[:, None] * np.asarray(X, np.float64)[inst.lit_var]
+    per_lit = np.zeros_like(Yall)
+    for c in range(inst.m):
+        a, b = int(inst.offsets[c]), int(inst.offsets[c + 1])
+        L, w = b - a, abs(float(inst.weight[c]))
+        per_lit[a:b] = 4.0 * L * U64 * w
+        if inst.ctype[c] not in REAL_TYPES:
+            per_lit[a:b] += 8.0 * np.sqrt(3.0 * L) * U32 * w * _root_moduli_sum(sps[c], Yall[a:b])
+    out = np.full((inst.n, Yall.shape[1]), 1e-30)
     np.add.at(out, inst.lit_var, per_lit)
     return out
 
@@ -93,17 +129,44 @@ def gpu_eval(Problem, inst, X, kernel=None):
     return obj.cpu().numpy(), grad.cpu().numpy(), fe.cpu().numpy()
 
 
+def _record(**kw):
+    """Append one line of error statistics to $CLS_PARITY_RECORD, if set
+    (used to tabulate the measured worst errors per path)."""
+    path = os.environ.get("CLS_PARITY_RECORD")
+    if path:
+        kw["test"] = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+        with open(path, "a") as f:
+            f.write(json.dumps(kw) + "\n")
+
+
 def check_against_oracle(inst, X, obj, grad, fe, floored=False):
+    """FE within FE_TOL per constraint; objective within FE_TOL * sum|w|;
+    gradient, per restart r, ||g_r - g64_r|| <= GRAD_RTOL ||g64_r||.
+
+    floored=True (the isolated single-type stress instances only) admits
+    ||g_r - g64_r|| <= ||fp32_floor_r|| for a restart whose strict bound
+    GRAD_RTOL ||g64_r|| lies below its own FP32 resolution floor (a
+    far-tail or exactly zero gradient).  Every restart of the realistic
+    instances (floored=False) meets the strict relative criterion."""
     oobj, ograd, ofe = ocls.objective_grad(inst, X.astype(np.float64))
     err_fe = np.max(np.abs(fe - ofe)) if inst.m else 0.0
     assert err_fe <= FE_TOL, f"FE error {err_fe}"
     num = np.linalg.norm(grad - ograd, axis=0)
     den = np.linalg.norm(ograd, axis=0)
-    floor = np.linalg.norm(fp32_floor(inst)) if floored else 0.0
-    ok = num <= GRAD_RTOL * den + floor + 1e-30
-    r = int(np.argmax(num - GRAD_RTOL * den - floor))
-    assert ok.all(), (f"grad error {num[r]:.3e} vs norm {den[r]:.3e} (rel {num[r]/max(den[r],1e-30):.2e},"
-                      f" floor {floor:.2e})")
+    strict = num <= GRAD_RTOL * den
+    floor = np.linalg.norm(fp32_floor(inst, X), axis=0) if floored else np.zeros_like(den)
+    ok = strict | (num <= floor)
+    used = ~strict & ok
+    rel = num / np.maximum(den, 1e-300)
+    _record(R=int(X.shape[1]), fe_err=float(err_fe),
+            rel_max=float(rel[strict].max()) if strict.any() else None,
+            n_floor=int(used.sum()),
+            floor_use=float((num[used] / floor[used]).max()) if used.any() else None,
+            floor_over_strict=float(np.median(floor / np.maximum(GRAD_RTOL * den, 1e-300)))
+            if floored else None)
+    r = int(np.argmax(np.where(ok, -np.inf, rel)))
+    assert ok.all(), (f"restart {r}: grad error {num[r]:.3e} vs norm {den[r]:.3e} "
+                      f"(rel {rel[r]:.2e}, floor {floor[r]:.2e}, {int((~ok).sum())} restarts fail)")
     wsum = float(np.abs(inst.weight).sum())
     assert np.max(np.abs(obj - oobj)) <= FE_TOL * max(1.0, wsum)
 
@@ -174,9 +237,8 @@ def test_overlapping_mixed_instance(P, kernel):
     for kind in POINTS:
         X = points(kind, inst.n, 70, seed=11)
         # realistic overlapping instance: strict relative criterion at
-        # interior points, FP32 floor only where the gradient is tiny
-        check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel),
-                             floored=kind in ("corner", "near", "mixed"))
+        # every kind of point
+        check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel))
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -612,9 +674,9 @@ def test_corner_dominated_points(P, kernel):
     frac[40:48] = 0.6                       # one 32-restart tile mixes dense restarts in
     frac[64:] = 1.0                         # every literal at a corner
     X = corner_dominated_points(inst.n, R, frac[None, :], seed=5)
-    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel))
     X2 = corner_dominated_points(inst.n, R, 0.97, seed=6)
-    check_against_oracle(inst, X2, *gpu_eval(P, inst, X2, kernel), floored=True)
+    check_against_oracle(inst, X2, *gpu_eval(P, inst, X2, kernel))
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -638,7 +700,7 @@ def test_corner_pass_interior_counts(P, kernel):
     inner = np.abs(X[:, last]) < 1.0
     u = rng.uniform(1e-6, 1e-2, inner.sum()).astype(np.float32)
     X[:, last][inner] = (np.sign(X[:, last][inner]) * (1.0 - u)).astype(np.float32)
-    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel))
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -655,7 +717,43 @@ def test_power_sum_pass_modes(P, kernel):
     R = 32 * len(fr) + 32 + 9
     frac = np.concatenate([np.repeat(np.asarray(fr), 32), rng.uniform(0.0, 0.9, 41)])
     X = corner_dominated_points(inst.n, R, frac[None, :], seed=8)
-    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel), floored=True)
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel))
+
+
+@pytest.fixture(scope="module")
+def trajectory_points():
+    """Points of one CLS run computed by the oracle alone (FP64 gradient,
+    FP32 projected step, lr 0.1) from 16 uniform starts on a reduced instance
+    shaped like the mixed workload (n = 1000; 4000 clauses of 2..8 literals,
+    400 XOR of 3..20, 100 cardinality of 10..300): the restarts at steps 10,
+    20 and 40, where 41 %, 68 % and 94 % of the coordinates sit exactly at
+    +-1.  Such points send tiles through the corner passes, the power-sum
+    pass's low-root handoff and the dense kernel in the proportions of a real
+    run."""
+    inst = W.mixed_pb(n=1000, n_or=4000, n_xor=400, n_card=100, seed=77)
+    X = W.uniform_points(inst.n, 16, 3)
+    snaps = {}
+    for s in range(41):
+        _, g, _ = ocls.objective_grad(inst, X)
+        if s in (10, 20, 40):
+            snaps[s] = X.copy()
+        X = ocls.pgd_step(X, g, 0.1)
+    return inst, snaps
+
+
+@pytest.mark.parametrize("kernel", [None] + KERNELS)
+def test_trajectory_points_strict(P, trajectory_points, kernel):
+    """Late-step points of a real trajectory (not synthetic corner mixes):
+    every restart meets the strict 1e-4 relative gradient criterion, for the
+    default tuning and for every DFT bucket on the direct or factored
+    kernel.  The three steps' restarts share tiles, as restarts at
+    different stages do after refills."""
+    inst, snaps = trajectory_points
+    for s in (10, 20, 40):
+        check_against_oracle(inst, snaps[s], *gpu_eval(P, inst, snaps[s], kernel))
+    X = np.concatenate([snaps[10], snaps[20], snaps[40]], axis=1)
+    X = X[:, np.random.default_rng(2).permutation(X.shape[1])]
+    check_against_oracle(inst, X, *gpu_eval(P, inst, X, kernel))
 
 
 def test_dft_flops_counter_counts_truncated_work(P):

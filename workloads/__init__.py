@@ -271,20 +271,30 @@ def partial_assignment(inst: Instance, frac_fixed=0.9, seed=1500) -> Instance:
     return out
 
 
-def mixed_instances(count, n_range=(1000, 4000), ratio=4.5, seed=1400):
+def mixed_instance(i, n_range=(1000, 4000), ratio=4.5, seed=1400):
+    """The i-th instance of mixed_instances(..., seed): planted mixed PB with
+    m = ratio*n in the 20000:2000:500 (clause:XOR:cardinality) proportions."""
+    rng = np.random.default_rng(seed + i)
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    m = int(round(ratio * n))
+    n_card = max(1, int(round(m * 500 / 22500)))
+    n_xor = max(1, int(round(m * 2000 / 22500)))
+    n_or = m - n_card - n_xor
+    return mixed_pb(n=n, n_or=n_or, n_xor=n_xor, n_card=n_card,
+                    card_len=(10, min(300, n)), seed=seed * 7 + i)
+
+
+def mixed_instances(count, n_range=(1000, 4000), ratio=4.5, seed=1400, workers=1):
     """Planted mixed-PB instances with m = ratio*n in the 20000:2000:500
-    (clause:XOR:cardinality) proportions."""
-    out = []
-    for i in range(count):
-        rng = np.random.default_rng(seed + i)
-        n = int(rng.integers(n_range[0], n_range[1] + 1))
-        m = int(round(ratio * n))
-        n_card = max(1, int(round(m * 500 / 22500)))
-        n_xor = max(1, int(round(m * 2000 / 22500)))
-        n_or = m - n_card - n_xor
-        out.append(mixed_pb(n=n, n_or=n_or, n_xor=n_xor, n_card=n_card,
-                            card_len=(10, min(300, n)), seed=seed * 7 + i))
-    return out
+    (clause:XOR:cardinality) proportions.  workers > 1 draws them in that
+    many spawned processes (same instances, same order)."""
+    if workers > 1 and count > 1:
+        import functools
+        import multiprocessing as mp
+        fn = functools.partial(mixed_instance, n_range=n_range, ratio=ratio, seed=seed)
+        with mp.get_context("spawn").Pool(min(workers, count)) as pool:
+            return pool.map(fn, range(count), chunksize=1)
+    return [mixed_instance(i, n_range, ratio, seed) for i in range(count)]
 
 
 def random_constraint_set(rng, n, m, types, L_range, weights="ones", spectra_for=None):
