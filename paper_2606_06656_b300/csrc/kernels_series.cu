@@ -57,39 +57,62 @@ __device__ __forceinline__ float4 lds4(const float4* p) {
 __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f : 1.0f; }
 
 // Literal values reach the passes as cp.async copies in chunks of kSerChunk
-// literals, double-buffered per warp (stg = the thread's slot of
-// stage[warp][2][kSerChunk][32]); f(i, x_i) is called for i = 0..L-1 in
-// order while the next chunk is in flight.  Each thread reads back only its
-// own copies.  Inactive lanes see x = 1.
+// literals, double-buffered per warp (stw = the warp's stage[2][kSerChunk][32]).
+// With vec (R a multiple of 4 and x 16-byte aligned) lane l copies 16 bytes,
+// restarts 4 (l % 8) .. +3 of chunk literals l / 8, l / 8 + 4, ...: four
+// copies per lane per chunk instead of sixteen; otherwise every lane copies
+// its own 4-byte values.  Each lane reads back its own restart's values
+// after the warp has synchronised.  f2(i, y_i, y_{i+1}) takes two consecutive
+// literals, f1(i, y_i) the last one of an odd chunk, with y = s x when SGN
+// (the signs as a bitmask, sgn bit i = literal i negated) and y = x
+// otherwise.  Inactive lanes see 1.
 constexpr int kSerChunk = 16;
-// f2(i, x_i, x_{i+1}) takes two consecutive literals, f1(i, x_i) the last one
-// of an odd chunk.
-template <typename F2, typename F1>
-__device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const float* xr, int R,
-                                            bool act, float* stg, F2&& f2, F1&& f1) {
+template <bool SGN, typename F2, typename F1>
+__device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const uint32_t* sgn,
+                                            const float* __restrict__ x, int R, int r0, int lane,
+                                            bool vec, float* stw, F2&& f2, F1&& f1) {
+  static_assert(kSerChunk == 16, "one 16-bit half of a sign word per chunk");
   const int nch = (L + kSerChunk - 1) / kSerChunk;
+  const bool act = r0 + lane < R;
   auto issue = [&](int c) {
-    float* dst = stg + (c & 1) * kSerChunk * 32;
+    float* dst = stw + (c & 1) * kSerChunk * 32;
     const int b0 = c * kSerChunk;
-    if (act) {
+    if (vec) {
+      const int q = lane & 7, u0 = lane >> 3;
+      if (r0 + 4 * q < R) {                 // the whole quad: R is a multiple of 4
+#pragma unroll
+        for (int v = 0; v < kSerChunk / 4; ++v) {
+          const int u = u0 + 4 * v;
+          if (b0 + u < L)
+            cp_async16(dst + u * 32 + 4 * q, x + (size_t)recs[b0 + u].var * R + r0 + 4 * q);
+        }
+      }
+    } else if (act) {
 #pragma unroll 8
       for (int u = 0; u < kSerChunk; ++u)
-        if (b0 + u < L) cp_async4(dst + u * 32, xr + (size_t)recs[b0 + u].var * R);
+        if (b0 + u < L) cp_async4(dst + u * 32 + lane, x + (size_t)recs[b0 + u].var * R + r0 + lane);
     }
     cp_async_commit();
   };
+  __syncwarp();                              // the previous scan's reads of buffer 0 are done
   issue(0);
   for (int c = 0; c < nch; ++c) {
+    __syncwarp();                            // every lane is done with the buffer refilled next
     if (c + 1 < nch) issue(c + 1);
     else cp_async_commit();                  // an empty group keeps the count
     cp_async_wait<1>();
-    const float* src = stg + (c & 1) * kSerChunk * 32;
+    __syncwarp();                            // chunk c is in place for every lane
+    const float* src = stw + (c & 1) * kSerChunk * 32 + lane;
     const int b0 = c * kSerChunk, n = min(kSerChunk, L - b0);
+    const uint32_t sb = SGN ? (sgn[b0 >> 5] >> (b0 & 31)) : 0u;
+    auto val = [&](int u) -> float {
+      const float v = act ? src[u * 32] : 1.f;
+      return (SGN && act && ((sb >> u) & 1u)) ? -v : v;
+    };
     int u = 0;
 #pragma unroll 1
-    for (; u + 2 <= n; u += 2)
-      f2(b0 + u, act ? src[u * 32] : 1.f, act ? src[(u + 1) * 32] : 1.f);
-    if (u < n) f1(b0 + u, act ? src[u * 32] : 1.f);
+    for (; u + 2 <= n; u += 2) f2(b0 + u, val(u), val(u + 1));
+    if (u < n) f1(b0 + u, val(u));
   }
   cp_async_wait<0>();
 }
@@ -100,10 +123,13 @@ __device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const flo
 // FE - b0 at sd[k * Rp] instead; the dense factored kernel adds them.
 template <int K>
 __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* recs,
-                                                const float* xr, int R, bool act,
+                                                const uint32_t* sgn, const float* x, int R,
+                                                int r0, int lane, bool vec,
                                                 const float4* tab, const float2* bsm,
-                                                float* __restrict__ P, int Rp, int r, float wgt,
-                                                float* stg, float* sd) {
+                                                float* __restrict__ P, int Rp, float wgt,
+                                                float* stw, float* sd) {
+  const int r = r0 + lane;
+  const bool act = r < R;
   static_assert(K % 2 == 0, "table rows hold pairs of terms");
   // pass B: M[k-1] = sum over interior literals of T_k(y); two literals per
   // packed FP32x2 instruction (float2 sums, folded afterwards)
@@ -111,8 +137,8 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
 #pragma unroll
   for (int k = 0; k < K; ++k) M2[k] = make_float2(0.f, 0.f);
   uint32_t ni = 0, nt = 0;
-  auto cls1 = [&](int i, float xv, float& y, float& m) {
-    y = rec_sgn(recs[i].dst) * xv;
+  auto cls1 = [&](int, float yv, float& y, float& m) {
+    y = yv;
     const bool corner = fabsf(y) == 1.f;
     nt += (y == -1.f) ? 1u : 0u;
     ni += corner ? 0u : 1u;
@@ -130,8 +156,8 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
       M2[k] = __ffma2_rn(m, t, M2[k]);
     }
   };
-  staged_scan(
-      L, recs, xr, R, act, stg,
+  staged_scan<true>(
+      L, recs, sgn, x, R, r0, lane, vec, stw,
       [&](int i, float x0, float x1) {
         float ya, yb, ma, mb;
         cls1(i, x0, ya, ma);
@@ -206,33 +232,33 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
     const int32_t dst = recs[i].dst;
     if (act) st_partial(&P[(size_t)rec_row(dst) * Rp + r], wgt * rec_sgn(dst) * g);
   };
-  staged_scan(
-      L, recs, xr, R, act, stg,
-      [&](int i, float x0, float x1) {
-        const float2 g = clenshaw(make_float2(rec_sgn(recs[i].dst) * x0,
-                                              rec_sgn(recs[i + 1].dst) * x1));
+  staged_scan<true>(
+      L, recs, sgn, x, R, r0, lane, vec, stw,
+      [&](int i, float y0, float y1) {
+        const float2 g = clenshaw(make_float2(y0, y1));
         put(i, g.x);
         put(i + 1, g.y);
       },
-      [&](int i, float x0) { put(i, clenshaw(make_float2(rec_sgn(recs[i].dst) * x0, 0.f)).x); });
+      [&](int i, float y0) { put(i, clenshaw(make_float2(y0, 0.f)).x); });
   return fe;
 }
 
 // Dynamic shared memory: kSeriesMaxRoots * kSerRow float4 (rows), as many
 // float2 (b'_j), the staging buffers (8 warps x 2 x kSerChunk x 32 floats),
-// maxL LitRec.
+// maxL LitRec, the sign bits of maxL literals.
 __global__ void __launch_bounds__(256, 3) k_fe_series(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ coef, const F4* __restrict__ ser_tab,
     const SerInfo* __restrict__ ser_info, const LitRec* __restrict__ lit,
-    const float* __restrict__ x, int R, int Rp, int RT, float* __restrict__ P,
-    float* __restrict__ fe_con, int ldf, uint8_t* __restrict__ done,
+    const float* __restrict__ x, int R, int Rp, int RT, int maxL, int vec,
+    float* __restrict__ P, float* __restrict__ fe_con, int ldf, uint8_t* __restrict__ done,
     float* __restrict__ ser_d, unsigned long long* __restrict__ flops) {
   extern __shared__ float4 ss4[];
   float4* tab = ss4;                                                  // [96][kSerRow]
   float2* bsm = reinterpret_cast<float2*>(tab + kSeriesMaxRoots * kSerRow);  // [96]
   float* stage = reinterpret_cast<float*>(bsm + kSeriesMaxRoots);     // [8][2][chunk][32]
   LitRec* recs = reinterpret_cast<LitRec*>(stage + 8 * 2 * kSerChunk * 32);   // [maxL]
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(recs + maxL);           // [(maxL + 31) / 32]
   __shared__ int jneed_s[8];
   const int ci = list[blockIdx.x];
   const SerInfo si = ser_info[ci];
@@ -245,19 +271,26 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
   const bool mine = live && done[(size_t)ci * RT + tile] != kTileDone;
   if (!__syncthreads_or(mine)) return;
   for (int i = threadIdx.x; i < L; i += 256) recs[i] = lit[it.lit0 + i];
+  for (int w = threadIdx.x; w < (L + 31) / 32; w += 256) {
+    uint32_t bits = 0;
+    for (int b = 0; b < 32 && 32 * w + b < L; ++b)
+      bits |= (lit[it.lit0 + 32 * w + b].dst < 0 ? 1u : 0u) << b;
+    sgn[w] = bits;
+  }
   __syncthreads();
-  const int r = (live ? tile : RT - 1) * 32 + lane;
+  const int r0 = (live ? tile : RT - 1) * 32;
+  const int r = r0 + lane;
   const bool act = r < R;
-  const float* xr = x + (act ? r : R - 1);
-  float* stg = stage + (size_t)warp * 2 * kSerChunk * 32 + lane;
+  float* stw = stage + (size_t)warp * 2 * kSerChunk * 32;
   // pass A: the tail cutoff (as in kernels_fr.cu) and the terms it needs
   int jw = 0, K = 0;
   bool part = false;
   if (mine) {
     float S = 0.f;
     auto acc = [&](float xv) { S = fmaf(-0.25f * xv, xv, S + 0.25f); };
-    staged_scan(L, recs, xr, R, act, stg, [&](int, float x0, float x1) { acc(x0); acc(x1); },
-                [&](int, float x0) { acc(x0); });
+    staged_scan<false>(L, recs, sgn, x, R, r0, lane, vec, stw,
+                       [&](int, float x0, float x1) { acc(x0); acc(x1); },
+                       [&](int, float x0) { acc(x0); });
     int jc = J;
     const float S1 = S - 0.25f;
     if (S1 > 0.f) {
@@ -266,7 +299,15 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
         jc = min(J, (int)ceilf(asinf(sqrtf(q)) * (float)(L + 1) * 0.318309886f) + 1);
     }
     jw = __reduce_max_sync(kFull, act ? jc : 0);
-    K = jw <= si.js0 ? kSeriesK0 : (jw <= si.js1 ? kSeriesK1 : 0);
+    // the fewest terms whose range holds the tile's roots: 12, 14, 16, 18,
+    // 22 or 26
+    K = jw <= si.jsx[0]   ? 12
+        : jw <= si.jsx[1] ? 14
+        : jw <= si.jsx[2] ? 16
+        : jw <= si.js0    ? kSeriesK0
+        : jw <= si.jsx[3] ? 22
+        : jw <= si.js1    ? kSeriesK1
+                          : 0;
     // beyond the range: the low roots 1..js1 here, the others in the dense
     // kernel, when the root products saved (14 flops per literal and root)
     // outweigh the cost of this pass and of the Clenshaw share
@@ -293,10 +334,20 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
   if (K == 0) return;
   float fev;
   float* sd = part ? ser_d + (size_t)si.slot * (kSeriesK1 + 1) * Rp + r : nullptr;
-  if (K == kSeriesK0)
-    fev = series_restart<kSeriesK0>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w, stg, sd);
-  else
-    fev = series_restart<kSeriesK1>(L, jw, recs, xr, R, act, tab, bsm, P, Rp, r, it.w, stg, sd);
+  static_assert(kSeriesK0 == 18 && kSeriesK1 == 26 && kSeriesKx[0] == 12 &&
+                    kSeriesKx[1] == 14 && kSeriesKx[2] == 16 && kSeriesKx[3] == 22,
+                "term counts of the dispatch below");
+#define CLS_SERIES(KK) \
+  series_restart<KK>(L, jw, recs, sgn, x, R, r0, lane, vec, tab, bsm, P, Rp, it.w, stw, sd)
+  switch (K) {
+    case 12: fev = CLS_SERIES(12); break;
+    case 14: fev = CLS_SERIES(14); break;
+    case 16: fev = CLS_SERIES(16); break;
+    case 18: fev = CLS_SERIES(18); break;
+    case 22: fev = CLS_SERIES(22); break;
+    default: fev = CLS_SERIES(26); break;
+  }
+#undef CLS_SERIES
   if (fe_con && act && !part) fe_con[(size_t)it.c * ldf + r] = it.b0 + fev;
   // (K is uniform over the warp, so every lane is here)
   const unsigned nact = (unsigned)__popc(__ballot_sync(kFull, act));
@@ -316,7 +367,8 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 size_t series_smem_bytes(int maxL) {
   return (size_t)kSeriesMaxRoots * kSerRow * sizeof(float4) +
          (size_t)kSeriesMaxRoots * sizeof(float2) +
-         (size_t)8 * 2 * kSerChunk * 32 * sizeof(float) + (size_t)maxL * sizeof(LitRec);
+         (size_t)8 * 2 * kSerChunk * 32 * sizeof(float) + (size_t)maxL * sizeof(LitRec) +
+         (size_t)((maxL + 31) / 32) * sizeof(uint32_t);
 }
 
 }  // namespace
@@ -332,9 +384,12 @@ cudaError_t launch_dft_series(const DevPlan& d, const int32_t* list, int count, 
   if (count == 0 || R == 0 || maxL < kSeriesMinL || !d.ser_info) return cudaSuccess;
   const int RT = ceil_div(R, 32);
   const dim3 grid(count, ceil_div(RT, 8)), block(256);
+  // 16-byte staging copies need every x row and the restart tiles on 16-byte
+  // boundaries
+  const int vec = (R % 4 == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0) ? 1 : 0;
   k_fe_series<<<grid, block, series_smem_bytes(maxL), s>>>(
-      list, d.fe, d.coef_tab, d.ser_tab, d.ser_info, d.fe_lit, x, R, Rp, RT, P, fe_con, ldf,
-      done, ser_terms(d, done, RT), d.dft_flops);
+      list, d.fe, d.coef_tab, d.ser_tab, d.ser_info, d.fe_lit, x, R, Rp, RT, maxL, vec, P,
+      fe_con, ldf, done, ser_terms(d, done, RT), d.dft_flops);
   return cudaGetLastError();
 }
 

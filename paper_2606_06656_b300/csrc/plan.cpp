@@ -155,8 +155,9 @@ static float turn_bits(double turns) {
 
 // Appends the power-sum rows of length L (root j = 1..js1, see kSeriesK0).
 static SerInfo series_table(int L, std::vector<F4>& tab) {
-  SerInfo si{-1, series_roots(L, kSeriesK0), series_roots(L, kSeriesK1), 0};
-  if (si.js1 == 0) return SerInfo{-1, 0, 0, 0};
+  SerInfo si{-1, series_roots(L, kSeriesK0), series_roots(L, kSeriesK1), 0, {0, 0, 0, 0}};
+  if (si.js1 == 0) return SerInfo{-1, 0, 0, 0, {0, 0, 0, 0}};
+  for (int i = 0; i < kNumSeriesKx; ++i) si.jsx[i] = (int16_t)series_roots(L, kSeriesKx[i]);
   si.off = (int32_t)tab.size();
   const int N = L + 1;
   for (int j = 1; j <= si.js1; ++j) {
@@ -262,7 +263,7 @@ int build_plan(int32_t n, int32_t m, const int32_t* offsets, const int32_t* lit_
   P.spec_tab.clear();
   P.spec_off.assign(m, -1);
   P.ser_tab.clear();
-  P.ser_info.assign(m, SerInfo{-1, 0, 0, 0});
+  P.ser_info.assign(m, SerInfo{-1, 0, 0, 0, {0, 0, 0, 0}});
   P.n_ser_slots = 0;
   P.coef_tab = {{2.f, 0.f, 1.f, 0.f},  {1.f, 0.f, 1.f, 0.f},   {2.f, 0.f, 1.f, 0.f},
                 {2.f, 0.f, -1.f, 0.f}, {-1.f, 0.f, -1.f, 0.f}, {-2.f, 0.f, -1.f, 0.f},

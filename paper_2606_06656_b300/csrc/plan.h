@@ -194,11 +194,16 @@ constexpr int kSeriesK0 = 18, kSeriesK1 = 26;
 constexpr int kSeriesMaxRoots = 96;   // rows a block stages
 constexpr int kSeriesMinL = 64;       // shorter constraints keep the root products
 constexpr int kSerRow = 1 + kSeriesK1 / 2;
+// Shorter term counts the pass may take when a tile's roots fit their range
+// (js of 12, 14, 16 and 22 terms, below and between kSeriesK0 and kSeriesK1).
+constexpr int kNumSeriesKx = 4;
+constexpr int kSeriesKx[kNumSeriesKx] = {12, 14, 16, 22};
 struct SerInfo {
   int32_t off;    // first row in ser_tab, -1 if the constraint has none
   int32_t js0;    // roots in range of kSeriesK0 terms
   int32_t js1;    // roots in range of kSeriesK1 terms
   int32_t slot;   // this constraint's rows of saved low-root terms (workspace)
+  int16_t jsx[kNumSeriesKx];   // roots in range of kSeriesKx[i] terms
 };
 
 // roots in range of the power-sum pass with K terms (plan.cpp)
