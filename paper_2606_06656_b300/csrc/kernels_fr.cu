@@ -164,7 +164,9 @@ constexpr size_t fr_smem() {
 template <int G, int Q>
 struct FrcLayout {
   static constexpr int LS = G * Q;                     // staged literal slots
-  static constexpr int QC = Q < 12 ? Q : 12;           // packed slots per lane, at most
+  // packed slots per lane, at most: half of Q rounded down to an even count
+  // (a tabulated slot count), at most 12
+  static constexpr int QC = ((Q / 2) & ~1) < 12 ? ((Q / 2) & ~1) : 12;
   static constexpr int LC = G * QC;                    // packed slots per restart
   static constexpr int JC = FrCap<G, Q>::JC;
   static constexpr int NWD = (LS + 15) / 16;          // 2-bit code words per restart
@@ -185,11 +187,11 @@ struct FrcLayout {
 constexpr int kPackNum = 2, kPackDen = 1;
 
 // Configurations with the packed path: those the corner passes serve (32
-// slots or more) whose full-slot loop already takes about 128 registers
-// (14 <= Q <= 24 and at most 320 slots: two blocks per SM with or without
-// the packed path, no spills; with fewer slots the packed path's registers
-// would halve the occupancy), and where the packed buffers still leave room
-// for two blocks per SM.
+// slots or more) with 14 <= Q <= 24 and at most 320 slots, where the packed
+// buffers leave room for two blocks per SM.  Their full path already takes
+// about 128 registers; with fewer slots the packed path's registers would
+// lower the occupancy, and with the occupancy held (64 or 80 registers) the
+// 8..12-slot configurations measured slower packed than full.
 template <int G, int Q>
 struct FrcFits {
   static constexpr bool value =
@@ -496,8 +498,14 @@ __device__ __forceinline__ void frc_tile(
   if (fe_con && warp == 0 && r < R) fe_con[(size_t)it.c * ldf + r] = fe_s[lane];
 }
 
+// Blocks per SM the packed configurations keep (that of their full path).
+template <int G, int Q>
+struct FrMinBlocks {
+  static constexpr int value = FrcFits<G, Q>::value ? 2 : 0;
+};
+
 template <int G, int Q, bool YS>
-__global__ void __launch_bounds__(256, FrcFits<G, Q>::value ? 2 : 0) k_fe_group_fr(
+__global__ void __launch_bounds__(256, FrMinBlocks<G, Q>::value) k_fe_group_fr(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ root, const F4* __restrict__ zpow, const F4* __restrict__ coef,
     const LitRec* __restrict__ lit,
@@ -647,8 +655,8 @@ __global__ void __launch_bounds__(256, FrcFits<G, Q>::value ? 2 : 0) k_fe_group_
                                                  cs, gs, ws, ys, yc, codes, wbase, q_s, t_s,  \
                                                  fe_s, gF_s, gT_s, R, Rp, r0, P, fe_con, ldf, \
                                                  flops)
-        if (qw <= 4) CLS_FRC_TILE(4);
-        else if (qw <= 6) CLS_FRC_TILE(6);
+        if (qw <= 4 || Lay::QC < 6) CLS_FRC_TILE(4);
+        else if (qw <= 6 || Lay::QC < 8) CLS_FRC_TILE(6);
         else if (qw <= 8) CLS_FRC_TILE(8);
         else if (qw <= 10) CLS_FRC_TILE(10);
         else CLS_FRC_TILE(12);

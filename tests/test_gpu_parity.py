@@ -759,18 +759,19 @@ def test_trajectory_points_strict(P, trajectory_points, kernel):
 @pytest.mark.parametrize("kernel", [None, "factored"])
 def test_packed_interior_kernel_boundaries(P, kernel):
     """The dense factored kernel packs each restart's interior literals and
-    runs its roots over G * qw slots (qw <= 12 per lane); a tile whose
-    largest interior count needs more goes to the full-slot kernel.  Tiles
-    at exactly 12 * 16 = 192 interior literals of a 288-literal cardinality
-    constraint, one past it, and a mix of corner-heavy and interior-heavy
-    restarts; true and false corners in every tile.  A constructed boundary
-    geometry with four constraints, so a few restarts sit in a far tail of
-    every constraint: the floored criterion, as for the other stress
-    instances."""
+    runs its roots over 16 * qw slots when the tile's largest interior
+    count fits in qw <= Q/2 slots per lane (qw <= 8 for the 18-slot
+    configuration of 257..288 literals); other tiles take the full-slot
+    path.  A 288-literal cardinality constraint at exactly 128 interior
+    literals in every restart of the first tile, one restart at 129 in the
+    second, 65..128 in the third (past the 4-lane corner pass's 64), with
+    true and false corners.  A constructed boundary geometry with four
+    constraints, so a few restarts sit in a far tail of every constraint:
+    the floored criterion, as for the other stress instances."""
     rng = np.random.default_rng(61)
     n, L = 700, 288
     rows = []
-    for k in (40, 144, 250):
+    for k in (120, 144, 170):
         rows.append((W.TYPE_CARD_GE, k, rng.choice(n, L, replace=False).astype(np.int32),
                      np.where(rng.random(L) < 0.5, -1, 1).astype(np.int8)))
     rows.append((W.TYPE_EK, 100, rng.choice(n, 200, replace=False).astype(np.int32),
@@ -781,10 +782,8 @@ def test_packed_interior_kernel_boundaries(P, kernel):
     v0 = inst.lit_var[inst.offsets[0]:inst.offsets[1]]
     for r in range(R):
         tile = r // 32
-        # interior literals of the first constraint: tile 0 at most 192,
-        # tile 1 one restart at 193, tile 2 spread from 70 to 192
-        q = 192 if tile == 0 else (193 if (tile == 1 and r == 40) else
-                                    int(rng.integers(70, 193)))
+        q = 128 if tile == 0 else (129 if (tile == 1 and r == 40) else
+                                    (128 if tile == 1 else int(rng.integers(65, 129))))
         corner = np.ones(n, bool)
         corner[rng.choice(v0, q, replace=False)] = False
         X[corner, r] = np.where(rng.random(corner.sum()) < 0.5, -1.0, 1.0)
