@@ -408,7 +408,7 @@ int cls_dft_work(const cls_problem* p, int64_t* out);
 /* Flops of the DFT roots evaluated by the factored path since the last
  * reset (no counterpart in the paper; for roofline accounting): the dense
  * factored kernel skips, per restart, the roots whose terms are provably
- * below 2^-30 in total (see kernels_fr.cu), so its work depends on the
+ * below 2^-24 in total (see kernels_fr.cu), so its work depends on the
  * point; it adds 14 or 16 flops per (literal, evaluated root) of every
  * restart to a per-problem device counter.  The power-sum pass (constraints
  * of 64 literals or more, see cls_series_range) adds L (4 + 6K) + j (16K +

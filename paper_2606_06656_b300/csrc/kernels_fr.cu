@@ -35,9 +35,11 @@ namespace cls {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-// bound on the sum of the skipped tail terms: kTailEps = 2^-30 (the
-// threshold uses ln(1 / kTailEps) = 30 ln 2, rounded up)
-constexpr float kTailLogInvEps = 20.80f;
+// bound on the sum of the skipped tail terms: kTailEps = 2^-24, the FP32
+// unit roundoff, so the skipped terms change FE and each partial by no more
+// than one rounding of a term of modulus 1 (the threshold uses
+// ln(1 / kTailEps) = 24 ln 2, rounded up)
+constexpr float kTailLogInvEps = 16.64f;
 
 __device__ __forceinline__ float4 ldg4(const F4* p) {
   return __ldg(reinterpret_cast<const float4*>(p));

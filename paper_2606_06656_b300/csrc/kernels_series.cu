@@ -40,7 +40,7 @@ namespace cls {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr float kTailLogInvEps = 20.80f;          // as in kernels_fr.cu
+constexpr float kTailLogInvEps = 16.64f;          // as in kernels_fr.cu (2^-24)
 constexpr float kTwoPiOver2p32 = 1.4629180792671596e-9f;
 
 __device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }

@@ -22,6 +22,7 @@ FE_TOL = 1e-4
 GRAD_RTOL = 1e-4
 U32 = 2.0 ** -24   # FP32 unit roundoff
 U64 = 2.0 ** -53   # FP64 unit roundoff
+TAIL_EPS = 2.0 ** -24   # bound of the roots the factored kernels' tail cutoff skips
 
 
 REAL_TYPES = (W.TYPE_OR, W.TYPE_XOR, W.TYPE_NAE)
@@ -64,10 +65,13 @@ def fp32_floor(inst, X):
     the probabilistic rounding-error bound lambda sqrt(n) u (Higham and
     Mary, SIAM J. Sci. Comput. 2019), lambda = 8, per term: 8 sqrt(3L) u M_i.
     Away from the cube's faces |T_ij| decays quickly with j and M_i is
-    small; at corners |T_ij| = 1 and M_i = sum_j |c'_j|.  Closed-form real products (OR, XOR,
-    NAE) keep relative accuracy and get only the FP32 underflow floor.  The
-    FP64 oracle's own floor is added: its partial sum_a P_{i-1}(a) D_i(a)
-    cancels for alternating spectra, a few L 2^-53.  Returns floor[v, r]."""
+    small; at corners |T_ij| = 1 and M_i = sum_j |c'_j|.  The roots the
+    factored kernels' tail cutoff skips add at most 2^-24 to each partial
+    (its proven bound), times the weight.  Closed-form real products (OR,
+    XOR, NAE) keep relative accuracy and get only the FP32 underflow floor.
+    The FP64 oracle's own floor is added: its partial sum_a P_{i-1}(a)
+    D_i(a) cancels for alternating spectra, a few L 2^-53.  Returns
+    floor[v, r]."""
     sps = osp.instance_spectra(inst)
     Yall = inst.lit_sign.astype(np.float64)[:, None] * np.asarray(X, np.float64)[inst.lit_var]
     per_lit = np.zeros_like(Yall)
@@ -76,7 +80,8 @@ def fp32_floor(inst, X):
         L, w = b - a, abs(float(inst.weight[c]))
         per_lit[a:b] = 4.0 * L * U64 * w
         if inst.ctype[c] not in REAL_TYPES:
-            per_lit[a:b] += 8.0 * np.sqrt(3.0 * L) * U32 * w * _root_moduli_sum(sps[c], Yall[a:b])
+            per_lit[a:b] += (8.0 * np.sqrt(3.0 * L) * U32 * _root_moduli_sum(sps[c], Yall[a:b])
+                             + TAIL_EPS) * w
     out = np.full((inst.n, Yall.shape[1]), 1e-30)
     np.add.at(out, inst.lit_var, per_lit)
     return out

@@ -1,21 +1,21 @@
 """The root cutoff of the factored DFT kernel (kernels_fr.cu) drops the
-roots j with 2 sin^2(pi j/(L+1)) (S - 1/4) >= ln(2J / 2^-30), S = sum_i
+roots j with 2 sin^2(pi j/(L+1)) (S - 1/4) >= ln(2J / 2^-24), S = sum_i
 (1 - y_i^2)/4.  The bound behind it: |alpha + beta w^j|^2 = 1 - 2 alpha beta
 (1 - cos theta_j), so every product of all or all-but-one factors has modulus
 at most exp(-(S - 1/4)(1 - cos theta_j)), and the DFT coefficients of a +-1
 spectrum (Sec. 2.3; pairs weighted 2) and their derivative versions have
 modulus at most 2.  This checks the resulting claim directly, in FP64 and
-with a plain DFT written here: the dropped terms add at most 2^-30 to the
+with a plain DFT written here: the dropped terms add at most 2^-24 to the
 expansion and to every partial derivative."""
 import numpy as np
 import pytest
 
-EPS = 2.0 ** -30
+EPS = 2.0 ** -24
 
 
 def cutoff(L, S):
     J = (L + 1) // 2
-    T = np.log(2 * J) + 30 * np.log(2)
+    T = np.log(2 * J) + 24 * np.log(2)
     if S - 0.25 <= 0:
         return J
     q = T / (2 * (S - 0.25))
