@@ -39,12 +39,26 @@ SM_MAX_MHZ = 2032.0
 
 
 # DRAM traffic of one launch (or one step of a kernel class) as ncu counted
-# it, dram__bytes_read.sum + dram__bytes_write.sum, with the capture's
-# workload, restart count and the SHA-256 (first 16 hex digits) of the
-# kernel sources it was taken on.  A figure is reported, scaled by R (every
-# byte counted grows with the restarts), only while the sources still hash
-# the same; otherwise traffic is null.
-TRAFFIC = {}
+# it, dram__bytes_read.sum + dram__bytes_write.sum, keyed by (kernel,
+# workload), with the capture's restart count, the files and the SHA-256
+# (first 16 hex digits) of the kernel sources it was taken on.  A figure is
+# reported, scaled by R (every byte counted grows with the restarts), only
+# while the sources still hash the same; otherwise traffic is null.  The
+# captures and the command are in profiles/traffic_mixedpb_3sat.md.
+_DFT_SOURCES = ("kernels.cu", "kernels_fr.cu", "kernels_series.cu", "kernels_corner.cu",
+                "kernels_p2.cu", "kernels.cuh", "plan.h")
+TRAFFIC = {
+    # the DFT class over one step, mean of steps 0, 3, 6 and 9 of the run
+    ("dft_class", "mixedpb_n5000_m22500"): dict(
+        bytes=257559936, R=1024, sources=_DFT_SOURCES, sha="ef4ad316932c4e69",
+        profile="profiles/traffic_mixedpb_3sat.md"),
+    ("k_accum_step", "mixedpb_n5000_m22500"): dict(
+        bytes=868688256, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="ae9571a0c4f62042",
+        profile="profiles/traffic_mixedpb_3sat.md"),
+    ("k_accum_step", "random3sat_n100_m426"): dict(
+        bytes=381997056, R=65536, sources=("kernels.cu", "kernels.cuh"), sha="ae9571a0c4f62042",
+        profile="profiles/traffic_mixedpb_3sat.md"),
+}
 
 
 def _sources_sha(files):
@@ -57,8 +71,8 @@ def _sources_sha(files):
 
 
 def recorded_traffic(kernel, workload_name, R):
-    rec = TRAFFIC.get(kernel)
-    if rec is None or rec["workload"] != workload_name:
+    rec = TRAFFIC.get((kernel, workload_name))
+    if rec is None:
         return None, "no ncu capture of this kernel on this workload"
     if _sources_sha(rec["sources"]) != rec["sha"]:
         return None, "kernel sources changed since the ncu capture"
