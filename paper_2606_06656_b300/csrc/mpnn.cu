@@ -106,46 +106,141 @@ __global__ void __launch_bounds__(256) k_seg_gather(int N, const int32_t* __rest
 }
 
 // --------------------------------------------------------------------------
-// tensor cores: mma.sync m16n8k16, bf16 x bf16 -> fp32
-//   A fragment (16x16 row): a0 (g, 2t..2t+1), a1 (g+8, 2t..), a2 (g, 2t+8..),
-//   a3 (g+8, 2t+8..);  B fragment (16x8 col): b0 (k 2t..2t+1, n g),
-//   b1 (k 2t+8.., n g);  C: c0,c1 (g, 2t..2t+1), c2,c3 (g+8, 2t..)
-//   with g = lane / 4, t = lane % 4.
+// tensor cores: tcgen05 (5th-generation MMA, accumulator in tensor memory)
+//
+// Each dense product is one 128-row tile per CTA of 128 threads: the bf16
+// operands are staged in shared memory in the canonical K-major layout
+// without swizzle (8 x 16-byte core matrices; core matrices adjacent in K
+// kLBO = 128 bytes apart, 8-row groups KT / 8 * 128 bytes apart), thread 0
+// issues tcgen05.mma (kind::f16, bf16 x bf16 -> fp32) for every 16-wide K
+// step into a tensor-memory accumulator of 128 lanes x N columns and commits
+// them to an mbarrier; every thread waits on it (a bounded wait: past
+// kTcSpin polls the kernel writes NaN instead of a result and sets
+// g_tc_timeout), then warp w reads lanes 32w..32w+31 (rows) with
+// tcgen05.ld for the epilogue.  D = A B^T with A [128 x K] and B [N x K],
+// both K-major.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ void mma16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+constexpr uint32_t kLBO = 128;                // bytes between K-adjacent core matrices
+constexpr int kTcSpin = 1 << 22;              // mbarrier polls before giving up
+__device__ int g_tc_timeout = 0;
+
+// byte offset of element (row, k) of a [rows x KT] K-major operand
+template <int KT>
+__device__ __forceinline__ uint32_t cm_off(int row, int k) {
+  return (uint32_t)((row >> 3) * (KT / 8) * kLBO + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor: start, leading (K) and stride (8-row)
+// byte offsets >> 4, descriptor version 1, no swizzle
+template <int KT>
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr) {
+  constexpr uint32_t sbo = (KT / 8) * kLBO;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+template <int M, int N>
+__device__ __forceinline__ uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void st_bf2(unsigned char* base, uint32_t off, float lo, float hi) {
+  *reinterpret_cast<__nv_bfloat162*>(base + off) = __floats2bfloat162_rn(lo, hi);
+}
+
+// The shared tail of the three products: tensor-memory allocation, the
+// K / 16 MMAs, the bounded wait.  Call with the operands staged (generic
+// stores); returns the tensor-memory address and whether the result is in.
+template <int KT, int N>
+__device__ __forceinline__ bool tc_run(const unsigned char* As, const unsigned char* Bs,
+                                       uint64_t* mbar, uint32_t* tmem_slot, uint32_t& tmem) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  constexpr uint32_t kCols = N < 32 ? 32 : N;
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar)));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 ::"r"(smem_u32(tmem_slot)), "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");     // staged operands
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  tmem = *tmem_slot;
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+    for (int ks = 0; ks < KT / 16; ++ks) {
+      const uint64_t ad = tc_sdesc<KT>(a0 + ks * 2 * kLBO), bd = tc_sdesc<KT>(b0 + ks * 2 * kLBO);
+      const uint32_t acc = ks > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+          ::"r"(tmem), "l"(ad), "l"(bd), "r"(tc_idesc<128, N>()), "r"(acc));
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+        ::"r"(smem_u32(mbar)) : "memory");
+  }
+  uint32_t done = 0;
+  for (int it = 0; it < kTcSpin && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(smem_u32(mbar)), "r"(0u) : "memory");
+  if (!done && (tid & 31) == 0) atomicExch(&g_tc_timeout, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  return done != 0;
+}
+
+// 32 consecutive accumulator columns of this thread's row (lane 32w + lane)
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&f)[32]) {
+  uint32_t v[32];
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 32; ++c) f[c] = __uint_as_float(v[c]);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x = lo (low 16 bits)
-  return *reinterpret_cast<const uint32_t*>(&v);
+template <int N>
+__device__ __forceinline__ void tc_free(uint32_t tmem) {
+  constexpr uint32_t kCols = N < 32 ? 32 : N;
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kCols));
 }
 
-__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) {
-  return *reinterpret_cast<const uint32_t*>(p);
-}
+constexpr int kTcRows = 128;                  // rows of a tile (the MMA's M)
 
 // Y[N,64] = relu([H | A] W^T + b), W: 64 x 128 (fp32 master, rounded to bf16)
-constexpr int kFwdRows = 64;
-constexpr int kLdX = 2 * kHid + 8;          // 136 bf16 per smem row
 __global__ void __launch_bounds__(128) k_dense_fwd(int N, const float* __restrict__ H,
                                                    const float* __restrict__ A,
                                                    const float* __restrict__ W,
                                                    const float* __restrict__ b,
                                                    float* __restrict__ Y) {
-  __shared__ __align__(16) __nv_bfloat16 Xs[kFwdRows * kLdX];
-  __shared__ __align__(16) __nv_bfloat16 Ws[kHid * kLdX];
-  const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * kFwdRows;
-  // stage X tile (64 x 128) and W (64 x 128) as bf16 pairs
-  for (int q = tid; q < kFwdRows * kHid; q += 128) {        // q: (row, pair)
-    const int r = q / kHid, p = q % kHid;                  // pair p covers cols 2p, 2p+1
-    const int col = 2 * p;
+  constexpr int KT = 2 * kHid;
+  __shared__ __align__(1024) unsigned char As[kTcRows * KT * 2];   // X tile, 32 KB
+  __shared__ __align__(1024) unsigned char Bs[kHid * KT * 2];      // W, 16 KB
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row0 = blockIdx.x * kTcRows;
+  for (int q = tid; q < kTcRows * kHid; q += 128) {          // (row, column pair)
+    const int r = q / kHid, col = 2 * (q % kHid);
     float lo = 0.f, hi = 0.f;
     if (row0 + r < N) {
       const float* src = col < kHid ? H + (size_t)(row0 + r) * kHid + col
@@ -153,61 +248,41 @@ __global__ void __launch_bounds__(128) k_dense_fwd(int N, const float* __restric
       lo = src[0];
       hi = src[1];
     }
-    *reinterpret_cast<uint32_t*>(&Xs[r * kLdX + col]) = pack_bf16(lo, hi);
+    st_bf2(As, cm_off<KT>(r, col), lo, hi);
   }
   for (int q = tid; q < kHid * kHid; q += 128) {
     const int r = q / kHid, col = 2 * (q % kHid);
-    *reinterpret_cast<uint32_t*>(&Ws[r * kLdX + col]) =
-        pack_bf16(W[r * 2 * kHid + col], W[r * 2 * kHid + col + 1]);
+    st_bf2(Bs, cm_off<KT>(r, col), W[r * KT + col], W[r * KT + col + 1]);
   }
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  const int r0 = warp * 16;
-  float c[8][4];
+  uint32_t tmem;
+  const bool ok = tc_run<KT, kHid>(As, Bs, &mbar, &tmem_slot, tmem);
+  const int row = row0 + 32 * warp + lane;
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
+  for (int half = 0; half < 2; ++half) {
+    float f[32];
+    if (ok) tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * half, f);
+    if (row < N)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) c[nt][q] = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < 2 * kHid; k0 += 16) {
-    const uint32_t a0 = lds32(&Xs[(r0 + g) * kLdX + k0 + 2 * t]);
-    const uint32_t a1 = lds32(&Xs[(r0 + g + 8) * kLdX + k0 + 2 * t]);
-    const uint32_t a2 = lds32(&Xs[(r0 + g) * kLdX + k0 + 8 + 2 * t]);
-    const uint32_t a3 = lds32(&Xs[(r0 + g + 8) * kLdX + k0 + 8 + 2 * t]);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const uint32_t b0 = lds32(&Ws[(nt * 8 + g) * kLdX + k0 + 2 * t]);
-      const uint32_t b1 = lds32(&Ws[(nt * 8 + g) * kLdX + k0 + 8 + 2 * t]);
-      mma16816(c[nt], a0, a1, a2, a3, b0, b1);
-    }
+      for (int c = 0; c < 32; ++c)
+        Y[(size_t)row * kHid + 32 * half + c] = ok ? fmaxf(f[c] + b[32 * half + c], 0.f) : NAN;
   }
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int col = nt * 8 + 2 * t;
-    const int ra = row0 + r0 + g, rb = ra + 8;
-    if (ra < N) {
-      Y[(size_t)ra * kHid + col] = fmaxf(c[nt][0] + b[col], 0.f);
-      Y[(size_t)ra * kHid + col + 1] = fmaxf(c[nt][1] + b[col + 1], 0.f);
-    }
-    if (rb < N) {
-      Y[(size_t)rb * kHid + col] = fmaxf(c[nt][2] + b[col], 0.f);
-      Y[(size_t)rb * kHid + col + 1] = fmaxf(c[nt][3] + b[col + 1], 0.f);
-    }
-  }
+  tc_free<kHid>(tmem);
 }
 
 // [dH | dA] = (dY * (Y > 0)) W; dH may alias dY (each block reads its rows
-// before writing them).
-constexpr int kLdP = kHid + 8;              // 72 bf16 per smem row
+// before writing them).  A = dpre [128 x 64], B = W^T [128 x 64].
 __global__ void __launch_bounds__(128) k_dense_bwd_dx(int N, const float* dY,
                                                       const float* __restrict__ Y,
                                                       const float* __restrict__ W, float* dH,
                                                       float* __restrict__ dA) {
-  __shared__ __align__(16) __nv_bfloat16 Ps[kFwdRows * kLdP];       // dpre tile 64 x 64
-  __shared__ __align__(16) __nv_bfloat16 Wt[2 * kHid * kLdP];       // W^T: 128 x 64
-  const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * kFwdRows;
-  for (int q = tid; q < kFwdRows * (kHid / 2); q += 128) {
+  constexpr int KT = kHid;
+  __shared__ __align__(1024) unsigned char As[kTcRows * KT * 2];       // dpre, 16 KB
+  __shared__ __align__(1024) unsigned char Bs[2 * kHid * KT * 2];      // W^T, 16 KB
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row0 = blockIdx.x * kTcRows;
+  for (int q = tid; q < kTcRows * (kHid / 2); q += 128) {
     const int r = q / (kHid / 2), col = 2 * (q % (kHid / 2));
     float lo = 0.f, hi = 0.f;
     if (row0 + r < N) {
@@ -215,67 +290,49 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dx(int N, const float* dY,
       lo = Y[o] > 0.f ? dY[o] : 0.f;
       hi = Y[o + 1] > 0.f ? dY[o + 1] : 0.f;
     }
-    *reinterpret_cast<uint32_t*>(&Ps[r * kLdP + col]) = pack_bf16(lo, hi);
+    st_bf2(As, cm_off<KT>(r, col), lo, hi);
   }
-  for (int q = tid; q < 2 * kHid * (kHid / 2); q += 128) {          // Wt[n][k] = W[k][n]
+  for (int q = tid; q < 2 * kHid * (kHid / 2); q += 128) {   // B[n][k] = W[k][n]
     const int n = q / (kHid / 2), k = 2 * (q % (kHid / 2));
-    *reinterpret_cast<uint32_t*>(&Wt[n * kLdP + k]) =
-        pack_bf16(W[k * 2 * kHid + n], W[(k + 1) * 2 * kHid + n]);
+    st_bf2(Bs, cm_off<KT>(n, k), W[k * 2 * kHid + n], W[(k + 1) * 2 * kHid + n]);
   }
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  const int r0 = warp * 16;
-  float c[16][4];
+  uint32_t tmem;
+  // every read of this tile's dY rows is staged before tc_run's barrier, so
+  // the writes below may overwrite them (dH aliasing dY)
+  const bool ok = tc_run<KT, 2 * kHid>(As, Bs, &mbar, &tmem_slot, tmem);
+  const int row = row0 + 32 * warp + lane;
 #pragma unroll
-  for (int nt = 0; nt < 16; ++nt)
+  for (int part = 0; part < 4; ++part) {
+    float f[32];
+    if (ok) tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * part, f);
+    float* dst = part < 2 ? dH : dA;
+    const int c0 = (part & 1) * 32;
+    if (row < N)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) c[nt][q] = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < kHid; k0 += 16) {
-    const uint32_t a0 = lds32(&Ps[(r0 + g) * kLdP + k0 + 2 * t]);
-    const uint32_t a1 = lds32(&Ps[(r0 + g + 8) * kLdP + k0 + 2 * t]);
-    const uint32_t a2 = lds32(&Ps[(r0 + g) * kLdP + k0 + 8 + 2 * t]);
-    const uint32_t a3 = lds32(&Ps[(r0 + g + 8) * kLdP + k0 + 8 + 2 * t]);
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      const uint32_t b0 = lds32(&Wt[(nt * 8 + g) * kLdP + k0 + 2 * t]);
-      const uint32_t b1 = lds32(&Wt[(nt * 8 + g) * kLdP + k0 + 8 + 2 * t]);
-      mma16816(c[nt], a0, a1, a2, a3, b0, b1);
-    }
+      for (int c = 0; c < 32; ++c) dst[(size_t)row * kHid + c0 + c] = ok ? f[c] : NAN;
   }
-  __syncthreads();   // every read of dY rows of this tile is done (dH may alias)
-#pragma unroll
-  for (int nt = 0; nt < 16; ++nt) {
-    const int col = nt * 8 + 2 * t;
-    float* dst = col < kHid ? dH : dA;
-    const int cc = col < kHid ? col : col - kHid;
-    const int ra = row0 + r0 + g, rb = ra + 8;
-    if (ra < N) {
-      dst[(size_t)ra * kHid + cc] = c[nt][0];
-      dst[(size_t)ra * kHid + cc + 1] = c[nt][1];
-    }
-    if (rb < N) {
-      dst[(size_t)rb * kHid + cc] = c[nt][2];
-      dst[(size_t)rb * kHid + cc + 1] = c[nt][3];
-    }
-  }
+  tc_free<2 * kHid>(tmem);
 }
 
 // partial dW[64 x 128] over a chunk of kDwRows node rows, plus db partial:
-// dW = dpre^T [H | A],  dpre = dY * (Y > 0)
+// dW = dpre^T [H | A],  dpre = dY * (Y > 0).  Computed transposed on the
+// tensor cores, dW^T [128 x 64] = [H | A]^T dpre: A = X^T [128 x rows],
+// B = dpre^T [64 x rows], both K-major in the rows.
 constexpr int kDwRows = 64;
-constexpr int kLdT = kDwRows + 8;           // 72 bf16 per smem row (28 KB static smem)
 __global__ void __launch_bounds__(128) k_dense_bwd_dw(int N, const float* __restrict__ dY,
                                                       const float* __restrict__ Y,
                                                       const float* __restrict__ H,
                                                       const float* __restrict__ A,
                                                       float* __restrict__ part) {
-  __shared__ __align__(16) __nv_bfloat16 Pt[kHid * kLdT];            // dpre^T: 64 x rows
-  __shared__ __align__(16) __nv_bfloat16 Xt[2 * kHid * kLdT];        // X^T: 128 x rows
-  __shared__ float dbs[4][kHid];
-  const int tid = threadIdx.x;
+  constexpr int KT = kDwRows;
+  __shared__ __align__(1024) unsigned char As[2 * kHid * KT * 2];      // X^T, 16 KB
+  __shared__ __align__(1024) unsigned char Bs[kHid * KT * 2];          // dpre^T, 8 KB
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float dbs[2][kHid];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kDwRows;
-  // stage transposed; pairs along rows (the K dimension of this product)
+  // pairs along rows (the K dimension of this product)
   for (int q = tid; q < (kDwRows / 2) * kHid; q += 128) {
     const int rp = q / kHid, m = q % kHid;                // rows 2rp, 2rp+1; feature m
     float v[2];
@@ -288,7 +345,7 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dw(int N, const float* __rest
         v[u] = Y[o] > 0.f ? dY[o] : 0.f;
       }
     }
-    *reinterpret_cast<uint32_t*>(&Pt[m * kLdT + 2 * rp]) = pack_bf16(v[0], v[1]);
+    st_bf2(Bs, cm_off<KT>(m, 2 * rp), v[0], v[1]);
   }
   for (int q = tid; q < (kDwRows / 2) * 2 * kHid; q += 128) {
     const int rp = q / (2 * kHid), n = q % (2 * kHid);
@@ -300,7 +357,7 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dw(int N, const float* __rest
       if (r < N)
         v[u] = n < kHid ? H[(size_t)r * kHid + n] : A[(size_t)r * kHid + n - kHid];
     }
-    *reinterpret_cast<uint32_t*>(&Xt[n * kLdT + 2 * rp]) = pack_bf16(v[0], v[1]);
+    st_bf2(As, cm_off<KT>(n, 2 * rp), v[0], v[1]);
   }
   // bias partial in fp32 (fixed order over the chunk's rows)
   {
@@ -315,37 +372,19 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dw(int N, const float* __rest
     }
     dbs[half][m] = s;
   }
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  const int m0 = warp * 16;
-  float c[16][4];
-#pragma unroll
-  for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) c[nt][q] = 0.f;
-#pragma unroll
-  for (int k0 = 0; k0 < kDwRows; k0 += 16) {
-    const uint32_t a0 = lds32(&Pt[(m0 + g) * kLdT + k0 + 2 * t]);
-    const uint32_t a1 = lds32(&Pt[(m0 + g + 8) * kLdT + k0 + 2 * t]);
-    const uint32_t a2 = lds32(&Pt[(m0 + g) * kLdT + k0 + 8 + 2 * t]);
-    const uint32_t a3 = lds32(&Pt[(m0 + g + 8) * kLdT + k0 + 8 + 2 * t]);
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      const uint32_t b0 = lds32(&Xt[(nt * 8 + g) * kLdT + k0 + 2 * t]);
-      const uint32_t b1 = lds32(&Xt[(nt * 8 + g) * kLdT + k0 + 8 + 2 * t]);
-      mma16816(c[nt], a0, a1, a2, a3, b0, b1);
-    }
-  }
+  uint32_t tmem;
+  const bool ok = tc_run<KT, kHid>(As, Bs, &mbar, &tmem_slot, tmem);
   float* o = part + (size_t)blockIdx.x * (kHid * 2 * kHid + kHid);
+  const int n = 32 * warp + lane;                          // input feature = accumulator lane
 #pragma unroll
-  for (int nt = 0; nt < 16; ++nt) {
-    const int col = nt * 8 + 2 * t;
-    o[(m0 + g) * 2 * kHid + col] = c[nt][0];
-    o[(m0 + g) * 2 * kHid + col + 1] = c[nt][1];
-    o[(m0 + g + 8) * 2 * kHid + col] = c[nt][2];
-    o[(m0 + g + 8) * 2 * kHid + col + 1] = c[nt][3];
+  for (int half = 0; half < 2; ++half) {
+    float f[32];
+    if (ok) tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * half, f);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) o[(32 * half + c) * 2 * kHid + n] = ok ? f[c] : NAN;
   }
   if (tid < kHid) o[kHid * 2 * kHid + tid] = dbs[0][tid] + dbs[1][tid];
+  tc_free<kHid>(tmem);
 }
 
 // out[k] = sum_{b < nblk} part[b*stride + k], fixed order
@@ -621,13 +660,13 @@ cudaError_t forward(const Graph& G, const float* P, float* z, float* act, cudaSt
     if (G.m > 0) {
       k_seg_gather<<<ceil_div(G.m, 8), 256, 0, s>>>(G.m, G.con_off, G.con_var, G.con_sgn,
                                                     nullptr, G.isL, hv, ac, 0);
-      k_dense_fwd<<<ceil_div(G.m, kFwdRows), 128, 0, s>>>(G.m, hc, ac, P + L.W_c[l], P + L.b_c[l],
+      k_dense_fwd<<<ceil_div(G.m, kTcRows), 128, 0, s>>>(G.m, hc, ac, P + L.W_c[l], P + L.b_c[l],
                                                           hc_new);
     }
     if (G.n > 0) {
       k_seg_gather<<<ceil_div(G.n, 8), 256, 0, s>>>(G.n, G.var_off, G.var_con, G.var_sgn,
                                                     nullptr, G.isd, hc_new, av, 0);
-      k_dense_fwd<<<ceil_div(G.n, kFwdRows), 128, 0, s>>>(G.n, hv, av, P + L.W_v[l], P + L.b_v[l],
+      k_dense_fwd<<<ceil_div(G.n, kTcRows), 128, 0, s>>>(G.n, hv, av, P + L.W_v[l], P + L.b_v[l],
                                                           hv_new);
     }
     hv = hv_new;
@@ -668,7 +707,7 @@ cudaError_t dense_backward(int N, float* dY_dH, const float* Y, const float* H, 
   k_reduce_parts<<<ceil_div(kHid * 2 * kHid, 256), 256, 0, s>>>(nblk, kHid * 2 * kHid, stride,
                                                                 part, dW);
   k_reduce_parts<<<1, kHid, 0, s>>>(nblk, kHid, stride, part + kHid * 2 * kHid, db);
-  k_dense_bwd_dx<<<ceil_div(N, kFwdRows), 128, 0, s>>>(N, dY_dH, Y, W, dY_dH, dA);
+  k_dense_bwd_dx<<<ceil_div(N, kTcRows), 128, 0, s>>>(N, dY_dH, Y, W, dY_dH, dA);
   return cudaGetLastError();
 }
 
