@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_seg_gather(int N, const int32_t* __rest
 // --------------------------------------------------------------------------
 // tensor cores: tcgen05 (5th-generation MMA, accumulator in tensor memory)
 //
-// Each dense product is one 128-row tile per CTA of 128 threads: the bf16
+// Each dense product is one 128-row tile per CTA of 256 threads: the bf16
 // operands are staged in shared memory in the canonical K-major layout
 // without swizzle (8 x 16-byte core matrices; core matrices adjacent in K
 // kLBO = 128 bytes apart, 8-row groups KT / 8 * 128 bytes apart), thread 0
@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(256) k_seg_gather(int N, const int32_t* __rest
 // step into a tensor-memory accumulator of 128 lanes x N columns and commits
 // them to an mbarrier; every thread waits on it (a bounded wait: past
 // kTcSpin polls the kernel writes NaN instead of a result and sets
-// g_tc_timeout), then warp w reads lanes 32w..32w+31 (rows) with
-// tcgen05.ld for the epilogue.  D = A B^T with A [128 x K] and B [N x K],
+// g_tc_timeout), then warp w reads lanes 32 (w % 4) .. +31 (rows) of its
+// share of the columns with tcgen05.ld for the epilogue.  D = A B^T with A [128 x K] and B [N x K],
 // both K-major.
 // --------------------------------------------------------------------------
 constexpr uint32_t kLBO = 128;                // bytes between K-adjacent core matrices
@@ -227,7 +227,7 @@ __device__ __forceinline__ void tc_free(uint32_t tmem) {
 constexpr int kTcRows = 128;                  // rows of a tile (the MMA's M)
 
 // Y[N,64] = relu([H | A] W^T + b), W: 64 x 128 (fp32 master, rounded to bf16)
-__global__ void __launch_bounds__(128) k_dense_fwd(int N, const float* __restrict__ H,
+__global__ void __launch_bounds__(256) k_dense_fwd(int N, const float* __restrict__ H,
                                                    const float* __restrict__ A,
                                                    const float* __restrict__ W,
                                                    const float* __restrict__ b,
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(128) k_dense_fwd(int N, const float* __restric
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kTcRows;
-  for (int q = tid; q < kTcRows * kHid; q += 128) {          // (row, column pair)
+  for (int q = tid; q < kTcRows * kHid; q += 256) {          // (row, column pair)
     const int r = q / kHid, col = 2 * (q % kHid);
     float lo = 0.f, hi = 0.f;
     if (row0 + r < N) {
@@ -250,17 +250,19 @@ __global__ void __launch_bounds__(128) k_dense_fwd(int N, const float* __restric
     }
     st_bf2(As, cm_off<KT>(r, col), lo, hi);
   }
-  for (int q = tid; q < kHid * kHid; q += 128) {
+  for (int q = tid; q < kHid * kHid; q += 256) {
     const int r = q / kHid, col = 2 * (q % kHid);
     st_bf2(Bs, cm_off<KT>(r, col), W[r * KT + col], W[r * KT + col + 1]);
   }
   uint32_t tmem;
   const bool ok = tc_run<KT, kHid>(As, Bs, &mbar, &tmem_slot, tmem);
-  const int row = row0 + 32 * warp + lane;
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
+  // warp w reads accumulator lanes 32 (w % 4) .. +31 (its rows), columns
+  // 32 (w / 4) .. +31
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = row0 + 32 * quad + lane;
+  {
     float f[32];
-    if (ok) tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * half, f);
+    if (ok) tc_ld32(tmem + ((uint32_t)(32 * quad) << 16) + 32 * half, f);
     if (row < N)
 #pragma unroll
       for (int c = 0; c < 32; ++c)
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(128) k_dense_fwd(int N, const float* __restric
 
 // [dH | dA] = (dY * (Y > 0)) W; dH may alias dY (each block reads its rows
 // before writing them).  A = dpre [128 x 64], B = W^T [128 x 64].
-__global__ void __launch_bounds__(128) k_dense_bwd_dx(int N, const float* dY,
+__global__ void __launch_bounds__(256) k_dense_bwd_dx(int N, const float* dY,
                                                       const float* __restrict__ Y,
                                                       const float* __restrict__ W, float* dH,
                                                       float* __restrict__ dA) {
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dx(int N, const float* dY,
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kTcRows;
-  for (int q = tid; q < kTcRows * (kHid / 2); q += 128) {
+  for (int q = tid; q < kTcRows * (kHid / 2); q += 256) {
     const int r = q / (kHid / 2), col = 2 * (q % (kHid / 2));
     float lo = 0.f, hi = 0.f;
     if (row0 + r < N) {
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dx(int N, const float* dY,
     }
     st_bf2(As, cm_off<KT>(r, col), lo, hi);
   }
-  for (int q = tid; q < 2 * kHid * (kHid / 2); q += 128) {   // B[n][k] = W[k][n]
+  for (int q = tid; q < 2 * kHid * (kHid / 2); q += 256) {   // B[n][k] = W[k][n]
     const int n = q / (kHid / 2), k = 2 * (q % (kHid / 2));
     st_bf2(Bs, cm_off<KT>(n, k), W[k * 2 * kHid + n], W[(k + 1) * 2 * kHid + n]);
   }
@@ -300,11 +302,15 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dx(int N, const float* dY,
   // every read of this tile's dY rows is staged before tc_run's barrier, so
   // the writes below may overwrite them (dH aliasing dY)
   const bool ok = tc_run<KT, 2 * kHid>(As, Bs, &mbar, &tmem_slot, tmem);
-  const int row = row0 + 32 * warp + lane;
+  // warp w: accumulator lanes 32 (w % 4) .. +31, column quarters 2 (w / 4)
+  // and 2 (w / 4) + 1
+  const int quad = warp & 3;
+  const int row = row0 + 32 * quad + lane;
 #pragma unroll
-  for (int part = 0; part < 4; ++part) {
+  for (int pp = 0; pp < 2; ++pp) {
+    const int part = 2 * (warp >> 2) + pp;
     float f[32];
-    if (ok) tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * part, f);
+    if (ok) tc_ld32(tmem + ((uint32_t)(32 * quad) << 16) + 32 * part, f);
     float* dst = part < 2 ? dH : dA;
     const int c0 = (part & 1) * 32;
     if (row < N)
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dx(int N, const float* dY,
 // tensor cores, dW^T [128 x 64] = [H | A]^T dpre: A = X^T [128 x rows],
 // B = dpre^T [64 x rows], both K-major in the rows.
 constexpr int kDwRows = 64;
-__global__ void __launch_bounds__(128) k_dense_bwd_dw(int N, const float* __restrict__ dY,
+__global__ void __launch_bounds__(256) k_dense_bwd_dw(int N, const float* __restrict__ dY,
                                                       const float* __restrict__ Y,
                                                       const float* __restrict__ H,
                                                       const float* __restrict__ A,
@@ -329,11 +335,11 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dw(int N, const float* __rest
   __shared__ __align__(1024) unsigned char Bs[kHid * KT * 2];          // dpre^T, 8 KB
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
-  __shared__ float dbs[2][kHid];
+  __shared__ float dbs[4][kHid];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kDwRows;
   // pairs along rows (the K dimension of this product)
-  for (int q = tid; q < (kDwRows / 2) * kHid; q += 128) {
+  for (int q = tid; q < (kDwRows / 2) * kHid; q += 256) {
     const int rp = q / kHid, m = q % kHid;                // rows 2rp, 2rp+1; feature m
     float v[2];
 #pragma unroll
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dw(int N, const float* __rest
     }
     st_bf2(Bs, cm_off<KT>(m, 2 * rp), v[0], v[1]);
   }
-  for (int q = tid; q < (kDwRows / 2) * 2 * kHid; q += 128) {
+  for (int q = tid; q < (kDwRows / 2) * 2 * kHid; q += 256) {
     const int rp = q / (2 * kHid), n = q % (2 * kHid);
     float v[2];
 #pragma unroll
@@ -361,29 +367,29 @@ __global__ void __launch_bounds__(128) k_dense_bwd_dw(int N, const float* __rest
   }
   // bias partial in fp32 (fixed order over the chunk's rows)
   {
-    const int m = tid & 63, half = tid >> 6;
+    const int m = tid & 63, quarter = tid >> 6;
     float s = 0.f;
-    for (int rr = half; rr < kDwRows; rr += 2) {
+    for (int rr = quarter; rr < kDwRows; rr += 4) {
       const int r = row0 + rr;
       if (r < N) {
         const size_t o = (size_t)r * kHid + m;
         s += Y[o] > 0.f ? dY[o] : 0.f;
       }
     }
-    dbs[half][m] = s;
+    dbs[quarter][m] = s;
   }
   uint32_t tmem;
   const bool ok = tc_run<KT, kHid>(As, Bs, &mbar, &tmem_slot, tmem);
   float* o = part + (size_t)blockIdx.x * (kHid * 2 * kHid + kHid);
-  const int n = 32 * warp + lane;                          // input feature = accumulator lane
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
+  const int quad = warp & 3, half = warp >> 2;
+  const int n = 32 * quad + lane;                          // input feature = accumulator lane
+  {
     float f[32];
-    if (ok) tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + 32 * half, f);
+    if (ok) tc_ld32(tmem + ((uint32_t)(32 * quad) << 16) + 32 * half, f);
 #pragma unroll
     for (int c = 0; c < 32; ++c) o[(32 * half + c) * 2 * kHid + n] = ok ? f[c] : NAN;
   }
-  if (tid < kHid) o[kHid * 2 * kHid + tid] = dbs[0][tid] + dbs[1][tid];
+  if (tid < kHid) o[kHid * 2 * kHid + tid] = (dbs[0][tid] + dbs[1][tid]) + (dbs[2][tid] + dbs[3][tid]);
   tc_free<kHid>(tmem);
 }
 
@@ -660,13 +666,13 @@ cudaError_t forward(const Graph& G, const float* P, float* z, float* act, cudaSt
     if (G.m > 0) {
       k_seg_gather<<<ceil_div(G.m, 8), 256, 0, s>>>(G.m, G.con_off, G.con_var, G.con_sgn,
                                                     nullptr, G.isL, hv, ac, 0);
-      k_dense_fwd<<<ceil_div(G.m, kTcRows), 128, 0, s>>>(G.m, hc, ac, P + L.W_c[l], P + L.b_c[l],
+      k_dense_fwd<<<ceil_div(G.m, kTcRows), 256, 0, s>>>(G.m, hc, ac, P + L.W_c[l], P + L.b_c[l],
                                                           hc_new);
     }
     if (G.n > 0) {
       k_seg_gather<<<ceil_div(G.n, 8), 256, 0, s>>>(G.n, G.var_off, G.var_con, G.var_sgn,
                                                     nullptr, G.isd, hc_new, av, 0);
-      k_dense_fwd<<<ceil_div(G.n, kTcRows), 128, 0, s>>>(G.n, hv, av, P + L.W_v[l], P + L.b_v[l],
+      k_dense_fwd<<<ceil_div(G.n, kTcRows), 256, 0, s>>>(G.n, hv, av, P + L.W_v[l], P + L.b_v[l],
                                                           hv_new);
     }
     hv = hv_new;
@@ -702,12 +708,12 @@ cudaError_t dense_backward(int N, float* dY_dH, const float* Y, const float* H, 
   const int nblk = ceil_div(N, kDwRows);
   if (nblk > nblk_cap) return cudaErrorInvalidValue;
   // dW/db read dY before dH overwrites it (same stream)
-  k_dense_bwd_dw<<<nblk, 128, 0, s>>>(N, dY_dH, Y, H, Aa, part);
+  k_dense_bwd_dw<<<nblk, 256, 0, s>>>(N, dY_dH, Y, H, Aa, part);
   const int stride = kHid * 2 * kHid + kHid;
   k_reduce_parts<<<ceil_div(kHid * 2 * kHid, 256), 256, 0, s>>>(nblk, kHid * 2 * kHid, stride,
                                                                 part, dW);
   k_reduce_parts<<<1, kHid, 0, s>>>(nblk, kHid, stride, part + kHid * 2 * kHid, db);
-  k_dense_bwd_dx<<<ceil_div(N, kTcRows), 128, 0, s>>>(N, dY_dH, Y, W, dY_dH, dA);
+  k_dense_bwd_dx<<<ceil_div(N, kTcRows), 256, 0, s>>>(N, dY_dH, Y, W, dY_dH, dA);
   return cudaGetLastError();
 }
 
