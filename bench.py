@@ -58,6 +58,10 @@ TRAFFIC = {
     ("k_accum_step", "random3sat_n100_m426"): dict(
         bytes=381997056, R=65536, sources=("kernels.cu", "kernels.cuh"), sha="ae9571a0c4f62042",
         profile="profiles/traffic_mixedpb_3sat.md"),
+    # the constraint statistics pass (adaptive weighting), one launch
+    ("k_con_stats_tile", "mixedpb_n5000_m22500"): dict(
+        bytes=848891392, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="ae9571a0c4f62042",
+        profile="profiles/traffic_mixedpb_3sat.md"),
 }
 
 
@@ -884,10 +888,7 @@ def run_reweight(args):
     t_rw = timed(lambda: B.cls_reweight(p.handle, R, gn, un, 0.0, 4.0, 10.0, wv))
     nnz_fe = int(p.info["nnz_fe"])
     byts = nnz_fe * R * 4 + inst.n * ((R + 31) // 32) * 4 + inst.m * 12
-    # DRAM traffic of k_con_stats_tile as ncu counted it on this workload at
-    # R = 1024 (841,977,088 read + 7,235,584 written bytes), scaled by the
-    # restarts: every partial is read once, so the traffic grows with R
-    traffic = 849212672 * R / 1024 if inst.name == "mixedpb_n5000_m22500" else None
+    traffic, traffic_src = recorded_traffic("k_con_stats_tile", inst.name, R)
     peak = float(peaks().get("hbm_gbs", 6400.0))
     ach = byts / (t_stats * 1e-3) / 1e9
     line = {"metric": "constraint statistics pass, fraction of HBM peak",
@@ -897,6 +898,7 @@ def run_reweight(args):
             "overhead_every_10_steps": (t_stats + t_rw) / (10 * t_step),
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": ach / peak, "traffic": traffic,
+                         "traffic_source": traffic_src,
                          "kernel": "k_con_stats", "algorithmic_bytes": byts},
             "config": {"workload": inst.name, "R": R, "inputs": "partials of the last step"}}
     print(json.dumps(line), flush=True)
