@@ -408,18 +408,21 @@ int cls_dft_work(const cls_problem* p, int64_t* out);
 /* Flops of the DFT roots evaluated by the factored path since the last
  * reset (no counterpart in the paper; for roofline accounting): the dense
  * factored kernel skips, per restart, the roots whose terms are provably
- * below 2^-24 in total (see kernels_fr.cu), so its work depends on the
- * point; it adds 14 or 16 flops per (literal, evaluated root) of every
- * restart to a per-problem device counter.  The power-sum pass (constraints
- * of 64 literals or more, see cls_series_range) adds L (4 + 6K) + j (16K +
- * 40) per restart for the j roots it evaluates with K terms.  Synchronises
+ * below 2^-24 in total (a bound on the factors' moduli from the sums of
+ * (1 - y_i^2)^m, m = 1..4), so its work depends on the point; it adds 14 or
+ * 16 flops per (literal, evaluated root) of every restart to a per-problem
+ * device counter.  The power-sum pass (constraints of 64 literals or more,
+ * see cls_series_range) adds L (4 + 8K) + j (8K + 40) per restart for the j
+ * roots it evaluates with K terms (L (4 + 4K) when it hands the remaining
+ * roots to the dense kernel, which counts the other 4K).  Synchronises
  * the device; *flops = the count; reset != 0 zeroes it afterwards.
  * CLS_ERR_INVALID on NULL. */
 int cls_dft_flops_counter(cls_problem* p, int64_t* flops, int32_t reset);
 
 /* Range of the power-sum pass (an evaluation route of the Fourier form of
- * Sec. 2.3 that the paper does not use): with every factor alpha + beta w^j
- * of a constraint of L literals expanded about y = +-1/2, the number of low
+ * Sec. 2.3 that the paper does not use): with the logarithm of every factor
+ * alpha + beta w^j of a constraint of L literals written as a Chebyshev
+ * series in the literal's value on [-1, 1], the number of low
  * roots j = 1..js whose truncation after K terms is at most 2^-24, both for
  * log G_j over the L literals and for each literal's partial, capped at 96.
  * Host-only.  Returns js >= 0, or -1 (CLS_ERR_INVALID) for L < 1 or K < 1. */

@@ -82,6 +82,64 @@ __host__ __device__ inline int fr_roots_form01(int L) {
   const int J = (L + 1) / 2, n = 21 * (L + 1) / 50;
   return n < J ? n : J;
 }
+// Tail cutoff of the DFT root sums (Sec. 2.3's expansion evaluated at the
+// roots w^j, j = 1..J).  With a = 1 - y^2 a literal's factor has
+// |alpha + beta w^j|^2 = 1 - a s_j, s_j = sin^2(pi j / (L + 1)).  Since
+// -ln(1 - x) >= x + x^2/2 + x^3/3 + x^4/4 on [0, 1], a product over all
+// literals, or over all but one, has modulus at most exp(-B(s_j)) with
+//   B(s) = 1/2 sum_{m=1..4} s^m (A_m - a_max^m) / m,   A_m = sum_i a_i^m
+// (leaving out one literal removes at most the terms of the largest a, and
+// literals at +-1 have a = 0).  The DFT coefficients of a +-1 spectrum and
+// their derivative versions are at most 2 in modulus, so the roots with
+// B(s_j) >= T = ln(2J / 2^-24) add at most 2^-24 in total to FE and to
+// every partial; they are skipped.  (The first version used only the m = 1
+// term with a_max <= 1: 1 - x <= e^-x.)
+constexpr float kTailLogInvEps = 16.64f;   // >= 24 ln 2
+struct TailSums {
+  float a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, amax = 0.f;
+  __device__ __forceinline__ void add(float y) {
+    const float a = fmaf(-y, y, 1.f), b = a * a;
+    a1 += a;
+    a2 += b;
+    a3 = fmaf(b, a, a3);
+    a4 = fmaf(b, b, a4);
+    amax = fmaxf(amax, a);
+  }
+  // combine the sums of the lanes of an aligned group of G lanes (xor tree)
+  __device__ __forceinline__ void group_reduce(int G) {
+    for (int d = 1; d < G; d <<= 1) {
+      a1 += __shfl_xor_sync(0xffffffffu, a1, d);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, d);
+      a3 += __shfl_xor_sync(0xffffffffu, a3, d);
+      a4 += __shfl_xor_sync(0xffffffffu, a4, d);
+      amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, d));
+    }
+  }
+};
+// Roots 1..jc to evaluate (jc <= J).  The FP32 sums of up to 1024 terms are
+// within 2^-14 relative, covered by shrinking each A_m by 2^-13.  B is
+// increasing and convex on [0, 1], so Newton's method started right of the
+// root s* of B(s) = T (at the root of the m = 1 term, or at 1) stays right of
+// it; the result is widened by 2^-12 against rounding, and the index by one.
+__device__ __forceinline__ int tail_roots(const TailSums& t, int L, int J, float T) {
+  const float sh = 1.f - 0x1p-13f;
+  const float am = t.amax, am2 = am * am;
+  const float b0 = 0.5f * fmaxf(0.f, fmaf(t.a1, sh, -am));
+  const float b1 = 0.25f * fmaxf(0.f, fmaf(t.a2, sh, -am2));
+  const float b2 = (1.f / 6.f) * fmaxf(0.f, fmaf(t.a3, sh, -am2 * am));
+  const float b3 = 0.125f * fmaxf(0.f, fmaf(t.a4, sh, -am2 * am2));
+  auto B = [&](float s) { return s * fmaf(s, fmaf(s, fmaf(s, b3, b2), b1), b0); };
+  auto dB = [&](float s) {
+    return fmaf(s, fmaf(s, fmaf(s, 4.f * b3, 3.f * b2), 2.f * b1), b0);
+  };
+  if (!(b0 > 0.f) || B(1.f) < T) return J;
+  float s = fminf(1.f, T / b0);
+#pragma unroll
+  for (int it = 0; it < 3; ++it) s -= (B(s) - T) / dB(s);
+  s = fminf(1.f, s * (1.f + 0x1p-12f));
+  return min(J, (int)ceilf(asinf(sqrtf(s)) * (float)(L + 1) * 0.318309886f) + 1);
+}
+
 // A partial row entry: written once per step and read once, by the
 // accumulate kernel; evict-first (st.global.cs) so that the partials do not
 // push the point array x, which the FE kernels gather, out of L2.

@@ -35,11 +35,9 @@ namespace cls {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-// bound on the sum of the skipped tail terms: kTailEps = 2^-24, the FP32
-// unit roundoff, so the skipped terms change FE and each partial by no more
-// than one rounding of a term of modulus 1 (the threshold uses
-// ln(1 / kTailEps) = 24 ln 2, rounded up)
-constexpr float kTailLogInvEps = 16.64f;
+// The root cutoff (kernels.cuh, tail_roots) bounds the skipped tail terms by
+// 2^-24 in total, the FP32 unit roundoff: they change FE and each partial by
+// no more than one rounding of a term of modulus 1.
 
 __device__ __forceinline__ float4 ldg4(const F4* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
@@ -390,19 +388,12 @@ __device__ __forceinline__ void frc_tile(
       y[s] = ycol[s * G * LDR];
       acc[s] = 0.f;
     }
-    // tail cutoff over the interior slots (corners add nothing to S)
-    float S = 0.f;
+    // tail cutoff over the interior slots (corners and padding add nothing)
+    TailSums ts;
 #pragma unroll
-    for (int s = 0; s < QW; ++s) S = fmaf(-0.25f * y[s], y[s], S + 0.25f);
-#pragma unroll
-    for (int d = 1; d < G; d <<= 1) S += __shfl_xor_sync(kFull, S, d);
-    int jc = J;
-    const float S1 = S - 0.25f;
-    if (S1 > 0.f) {
-      const float q = tailT / (2.f * S1);
-      if (q < 1.f)
-        jc = min(J, (int)ceilf(asinf(sqrtf(q)) * (float)(L + 1) * 0.318309886f) + 1);
-    }
+    for (int s = 0; s < QW; ++s) ts.add(y[s]);
+    ts.group_reduce(G);
+    const int jc = tail_roots(ts, L, J, tailT);
     const int jw = __reduce_max_sync(kFull, jc);
     const int qn = q_s[rr], tn = t_s[rr];
     if (flops) {
@@ -695,28 +686,15 @@ __global__ void __launch_bounds__(256, FrMinBlocks<G, Q>::value) k_fe_group_fr(
       if constexpr (!YS) yreg[s] = ycol[s * G * Geo::LDR];
       acc[s] = 0.f;
     }
-    // Tail cutoff.  |alpha + beta w^j|^2 = 1 - 2 alpha beta (1 - cos theta_j),
-    // so with S = sum_i alpha_i beta_i = sum_i (1 - y_i^2)/4 every product
-    // over all or all-but-one factors has modulus <= exp(-(S - 1/4)(1 - cos
-    // theta_j)), and |b'_j|, |c'_j| <= 2.  Roots with 2 sin^2(phi_j)(S - 1/4)
-    // >= T = ln(2J / kTailEps) therefore add at most kTailEps in total to FE
-    // and to every partial; they are skipped.  The warp runs to the largest
-    // cutoff of its groups (extra roots are exact terms).
-    float S = 0.f;
+    // Tail cutoff (kernels.cuh, tail_roots): the roots whose products over
+    // all or all-but-one factors are provably below 2^-24 / (2J) are
+    // skipped.  The warp runs to the largest cutoff of its groups (extra
+    // roots are exact terms).
+    TailSums ts;
 #pragma unroll
-    for (int s = 0; s < Q; ++s) {
-      const float y = YS ? ycol[s * G * Geo::LDR] : yreg[s];
-      S = fmaf(-0.25f * y, y, S + 0.25f);
-    }
-#pragma unroll
-    for (int d = 1; d < G; d <<= 1) S += __shfl_xor_sync(kFull, S, d);
-    int jc = J;
-    const float S1 = S - 0.25f;
-    if (S1 > 0.f) {
-      const float q = tailT / (2.f * S1);
-      if (q < 1.f)
-        jc = min(J, (int)ceilf(asinf(sqrtf(q)) * (float)(L + 1) * 0.318309886f) + 1);
-    }
+    for (int s = 0; s < Q; ++s) ts.add(YS ? ycol[s * G * Geo::LDR] : yreg[s]);
+    ts.group_reduce(G);
+    const int jc = tail_roots(ts, L, J, tailT);
     const int jw = __reduce_max_sync(kFull, jc);
     if (flops) {
       // algorithmic work of the roots each restart needs: 14 / 16 flops per

@@ -20,8 +20,9 @@
 //
 // One thread per (constraint, restart), a warp per tile of 32 restarts, a
 // block per constraint and 8 tiles.  Pass A computes the tail cutoff of
-// kernels_fr.cu (S = sum (1 - y^2) / 4); a tile whose largest cutoff lies in
-// the range of 18 (else 26) terms is finished here (flag done).  A tile that
+// kernels.cuh (tail_roots, from the sums of a^m, a = 1 - y^2, m = 1..4); a
+// tile whose largest cutoff lies in the range of 12..26 terms is finished
+// here with the fewest that suffice (flag done).  A tile that
 // needs more roots gets the terms of the roots 1..js1 (26 terms) here when
 // that saves enough root products (flag low: the dense factored kernel adds
 // the rest); any other is left to the dense kernel.  Pass B forms the
@@ -40,7 +41,6 @@ namespace cls {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr float kTailLogInvEps = 16.64f;          // as in kernels_fr.cu (2^-24)
 constexpr float kTwoPiOver2p32 = 1.4629180792671596e-9f;
 
 __device__ __forceinline__ int rec_row(int32_t dst) { return dst & 0x7fffffff; }
@@ -286,18 +286,11 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
   int jw = 0, K = 0;
   bool part = false;
   if (mine) {
-    float S = 0.f;
-    auto acc = [&](float xv) { S = fmaf(-0.25f * xv, xv, S + 0.25f); };
+    TailSums ts;   // (1 - x^2 does not depend on the literal's sign)
     staged_scan<false>(L, recs, sgn, x, R, r0, lane, vec, stw,
-                       [&](int, float x0, float x1) { acc(x0); acc(x1); },
-                       [&](int, float x0) { acc(x0); });
-    int jc = J;
-    const float S1 = S - 0.25f;
-    if (S1 > 0.f) {
-      const float q = (logf(2.f * (float)J) + kTailLogInvEps) / (2.f * S1);
-      if (q < 1.f)
-        jc = min(J, (int)ceilf(asinf(sqrtf(q)) * (float)(L + 1) * 0.318309886f) + 1);
-    }
+                       [&](int, float x0, float x1) { ts.add(x0); ts.add(x1); },
+                       [&](int, float x0) { ts.add(x0); });
+    const int jc = act ? tail_roots(ts, L, J, logf(2.f * (float)J) + kTailLogInvEps) : 0;
     jw = __reduce_max_sync(kFull, act ? jc : 0);
     // the fewest terms whose range holds the tile's roots: 12, 14, 16, 18,
     // 22 or 26
