@@ -63,10 +63,18 @@ __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f :
 // copies per lane per chunk instead of sixteen; otherwise every lane copies
 // its own 4-byte values.  Each lane reads back its own restart's values
 // after the warp has synchronised.  f2(i, y_i, y_{i+1}) takes two consecutive
-// literals, f1(i, y_i) the last one of an odd chunk, with y = s x when SGN
-// (the signs as a bitmask, sgn bit i = literal i negated) and y = x
-// otherwise.  Inactive lanes see 1.
+// literals, with y = s x when SGN (the signs as a bitmask, sgn bit i =
+// literal i negated; the sign bit is flipped in place) and y = x otherwise;
+// a full chunk runs unrolled, so the sign bits are compile-time positions.
+// f1(i, y_i) takes the last literal of an odd tail.  No copy ever targets an
+// inactive lane's column; the kernel fills those with 1 once
+// (stage_fill_inactive), so every lane reads without a test.
 constexpr int kSerChunk = 16;
+__device__ __forceinline__ void stage_fill_inactive(float* stw, int lane, bool act) {
+  if (!act)
+#pragma unroll
+    for (int u = 0; u < 2 * kSerChunk; ++u) stw[u * 32 + lane] = 1.f;
+}
 template <bool SGN, typename F2, typename F1>
 __device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const uint32_t* sgn,
                                             const float* __restrict__ x, int R, int r0, int lane,
@@ -106,16 +114,46 @@ __device__ __forceinline__ void staged_scan(int L, const LitRec* recs, const uin
     const int b0 = c * kSerChunk, n = min(kSerChunk, L - b0);
     const uint32_t sb = SGN ? (sgn[b0 >> 5] >> (b0 & 31)) : 0u;
     auto val = [&](int u) -> float {
-      const float v = act ? src[u * 32] : 1.f;
-      return (SGN && act && ((sb >> u) & 1u)) ? -v : v;
+      const float v = src[u * 32];
+      return SGN ? __uint_as_float(__float_as_uint(v) ^ ((sb << (31 - u)) & 0x80000000u)) : v;
     };
-    int u = 0;
+    if (n == kSerChunk) {
+#pragma unroll
+      for (int u = 0; u < kSerChunk; u += 2) f2(b0 + u, val(u), val(u + 1));
+    } else {
+      int u = 0;
 #pragma unroll 1
-    for (; u + 2 <= n; u += 2) f2(b0 + u, val(u), val(u + 1));
-    if (u < n) f1(b0 + u, val(u));
+      for (; u + 2 <= n; u += 2) f2(b0 + u, val(u), val(u + 1));
+      if (u < n) f1(b0 + u, val(u));
+    }
   }
   cp_async_wait<0>();
 }
+
+// The tail sums of kernels.cuh for two literals per packed instruction.
+struct TailSums2 {
+  float2 a1 = {0.f, 0.f}, a2 = {0.f, 0.f}, a3 = {0.f, 0.f}, a4 = {0.f, 0.f};
+  float amax = 0.f;
+  __device__ __forceinline__ void add2(float x0, float x1) {
+    const float2 xv = make_float2(x0, x1);
+    const float2 a = __ffma2_rn(make_float2(-x0, -x1), xv, make_float2(1.f, 1.f));
+    const float2 b = __fmul2_rn(a, a);
+    a1 = __fadd2_rn(a1, a);
+    a2 = __fadd2_rn(a2, b);
+    a3 = __ffma2_rn(b, a, a3);
+    a4 = __ffma2_rn(b, b, a4);
+    amax = fmaxf(amax, fmaxf(a.x, a.y));
+  }
+  __device__ __forceinline__ TailSums fold() const {
+    TailSums t;
+    t.a1 = a1.x + a1.y;
+    t.a2 = a2.x + a2.y;
+    t.a3 = a3.x + a3.y;
+    t.a4 = a4.x + a4.y;
+    t.amax = amax;
+    return t;
+  }
+};
 
 // one restart's K-term pass: Chebyshev sums, the root loop over jw roots, the
 // partials of all L literals (written to P) and FE - b0 (returned).  With sd
@@ -282,15 +320,16 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
   const int r = r0 + lane;
   const bool act = r < R;
   float* stw = stage + (size_t)warp * 2 * kSerChunk * 32;
+  stage_fill_inactive(stw, lane, act);
   // pass A: the tail cutoff (as in kernels_fr.cu) and the terms it needs
   int jw = 0, K = 0;
   bool part = false;
   if (mine) {
-    TailSums ts;   // (1 - x^2 does not depend on the literal's sign)
+    TailSums2 ts;   // (1 - x^2 does not depend on the literal's sign)
     staged_scan<false>(L, recs, sgn, x, R, r0, lane, vec, stw,
-                       [&](int, float x0, float x1) { ts.add(x0); ts.add(x1); },
-                       [&](int, float x0) { ts.add(x0); });
-    const int jc = act ? tail_roots(ts, L, J, logf(2.f * (float)J) + kTailLogInvEps) : 0;
+                       [&](int, float x0, float x1) { ts.add2(x0, x1); },
+                       [&](int, float x0) { ts.add2(x0, 1.f); });
+    const int jc = act ? tail_roots(ts.fold(), L, J, logf(2.f * (float)J) + kTailLogInvEps) : 0;
     jw = __reduce_max_sync(kFull, act ? jc : 0);
     // the fewest terms whose range holds the tile's roots: 12, 14, 16, 18,
     // 22 or 26
