@@ -368,10 +368,10 @@ __device__ __forceinline__ void group_low_cheb(int jlo, int nnc, int t, int lam,
     float lr = (float)nnc * h.x, li = 0.f;
 #pragma unroll
     for (int m = 0; m < K / 2; ++m) {
-      const float4 e = __ldg(row + 1 + m);
+      const float4 e = __ldg(row + 1 + m);   // Re E_2m, Re E_2m+1, Im E_2m, Im E_2m+1
       lr = fmaf(e.x, M[2 * m], lr);
-      li = fmaf(e.y, M[2 * m], li);
-      lr = fmaf(e.z, M[2 * m + 1], lr);
+      li = fmaf(e.z, M[2 * m], li);
+      lr = fmaf(e.y, M[2 * m + 1], lr);
       li = fmaf(e.w, M[2 * m + 1], li);
     }
     float sn, cs;
@@ -384,8 +384,8 @@ __device__ __forceinline__ void group_low_cheb(int jlo, int nnc, int t, int lam,
 #pragma unroll
     for (int m = 0; m < K / 2; ++m) {
       const float4 e = __ldg(row + 1 + m);
-      D[2 * m] = fmaf(e.x, wr, fmaf(-e.y, wi, D[2 * m]));
-      D[2 * m + 1] = fmaf(e.z, wr, fmaf(-e.w, wi, D[2 * m + 1]));
+      D[2 * m] = fmaf(e.x, wr, fmaf(-e.z, wi, D[2 * m]));
+      D[2 * m + 1] = fmaf(e.y, wr, fmaf(-e.w, wi, D[2 * m + 1]));
     }
   }
 #pragma unroll

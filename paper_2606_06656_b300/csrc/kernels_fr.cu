@@ -49,6 +49,48 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// The low roots' share of a low tile's partials: acc[s] += sum_k D_k U_k(y_s)
+// by Clenshaw's recurrence, D_k = d[k * 32] (the Chebyshev pass's saved
+// coefficients of this restart).  Slots go four at a time, two per packed
+// FP32x2 instruction, each D_k read once per group of four.  yv(s) = y_s.
+template <int S, typename YF>
+__device__ __forceinline__ void clenshaw_low(const float* d, YF&& yv, float (&acc)[S]) {
+  constexpr int C = 4;
+#pragma unroll
+  for (int s0 = 0; s0 < S; s0 += C) {
+    constexpr int NP = C / 2;
+    float2 y2[NP], b1[NP], b2[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int sa = s0 + 2 * p, sb = sa + 1;
+      const float ya = sa < S ? yv(sa) : 0.f, yb = sb < S ? yv(sb) : 0.f;
+      y2[p] = make_float2(ya + ya, yb + yb);
+      b1[p] = make_float2(0.f, 0.f);
+      b2[p] = b1[p];
+    }
+#pragma unroll
+    for (int k = kSeriesK1 - 1; k >= 0; --k) {
+      const float dk = d[k * 32];
+      const float2 dd = make_float2(dk, dk);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        if (s0 + 2 * p < S) {
+          const float2 b0 =
+              __ffma2_rn(y2[p], b1[p], __fadd2_rn(dd, make_float2(-b2[p].x, -b2[p].y)));
+          b2[p] = b1[p];
+          b1[p] = b0;
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int sa = s0 + 2 * p, sb = sa + 1;
+      if (sa < S) acc[sa] += b1[p].x;
+      if (sb < S) acc[sb] += b1[p].y;
+    }
+  }
+}
+
 // index of Q in kFrQ (compile time)
 template <int Q>
 struct FrQIndex {
@@ -437,18 +479,7 @@ __device__ __forceinline__ void frc_tile(
     if (low) {
       // the low roots' share, sum_k D_k U_k(y) (Clenshaw) for the interior
       // slots; U_k(1) = k + 1 and U_k(-1) = (-1)^k (k + 1) for the corners
-#pragma unroll
-      for (int s = 0; s < QW; ++s) {
-        const float y2 = y[s] + y[s];
-        float b1 = 0.f, b2 = 0.f;
-#pragma unroll
-        for (int k = kSeriesK1 - 1; k >= 0; --k) {
-          const float b0 = fmaf(y2, b1, sD[k * 32 + rr] - b2);
-          b2 = b1;
-          b1 = b0;
-        }
-        acc[s] += b1;
-      }
+      clenshaw_low<QW>(sD + rr, [&](int s) { return y[s]; }, acc);
 #pragma unroll
       for (int k = 0; k < kSeriesK1; ++k) {
         const float dk = sD[k * 32 + rr] * (float)(k + 1);
@@ -720,18 +751,8 @@ __global__ void __launch_bounds__(256, FrMinBlocks<G, Q>::value) k_fe_group_fr(
       val += fr_root<G, Q, YS, 2>(rs[j], cs[j], yreg, ycol, acc);
     if (low) {
       // the low roots' share of each partial, sum_k D_k U_k(y) (Clenshaw)
-#pragma unroll
-      for (int s = 0; s < Q; ++s) {
-        const float y = YS ? ycol[s * G * Geo::LDR] : yreg[s], y2 = y + y;
-        float b1 = 0.f, b2 = 0.f;
-#pragma unroll
-        for (int k = kSeriesK1 - 1; k >= 0; --k) {
-          const float b0 = fmaf(y2, b1, sD[k * 32 + rr] - b2);
-          b2 = b1;
-          b1 = b0;
-        }
-        acc[s] += b1;
-      }
+      clenshaw_low<Q>(sD + rr, [&](int s) { return YS ? ycol[s * G * Geo::LDR] : yreg[s]; },
+                      acc);
       val += sD[kSeriesK1 * 32 + rr];
     }
     // partials back into the staging slots (each slot is owned by one lane)

@@ -207,13 +207,17 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
         cls1(i, x0, ya, ma);
         sums(make_float2(ya, 0.f), make_float2(ma, 0.f));
       });
-  float M[K];
+  // the sums of terms 2m and 2m + 1 side by side (the table's pairs)
+  float2 Mp[K / 2];
 #pragma unroll
-  for (int k = 0; k < K; ++k) M[k] = (M2[k].x + M2[k].y) * (1.0f / (float)(k + 1));
-  // roots: log G_j, G_j, w = b'_j G_j, FE and D_k
-  float D[K];
+  for (int m = 0; m < K / 2; ++m)
+    Mp[m] = make_float2((M2[2 * m].x + M2[2 * m].y) * (1.0f / (float)(2 * m + 1)),
+                        (M2[2 * m + 1].x + M2[2 * m + 1].y) * (1.0f / (float)(2 * m + 2)));
+  // roots: log G_j, G_j, w = b'_j G_j, FE and D_k, two terms per packed
+  // instruction (Dp[m] = {D_2m, D_2m+1})
+  float2 Dp[K / 2];
 #pragma unroll
-  for (int k = 0; k < K; ++k) D[k] = 0.f;
+  for (int m = 0; m < K / 2; ++m) Dp[m] = make_float2(0.f, 0.f);
   float fe = 0.f;
   const float fni = (float)ni;
 #pragma unroll 1
@@ -221,15 +225,14 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
     const float4* row = tab + j * kSerRow;
     const float4 h = row[0];
     const uint32_t turns = ni * __float_as_uint(h.y) + nt * __float_as_uint(h.z);
-    float lr = fni * h.x, li = 0.f;
+    float2 lr2 = make_float2(fni * h.x, 0.f), li2 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int m = 0; m < K / 2; ++m) {
-      const float4 e = lds4(row + 1 + m);     // E_2m, E_2m+1
-      lr = fmaf(e.x, M[2 * m], lr);
-      li = fmaf(e.y, M[2 * m], li);
-      lr = fmaf(e.z, M[2 * m + 1], lr);
-      li = fmaf(e.w, M[2 * m + 1], li);
+      const float4 e = lds4(row + 1 + m);     // Re E_2m, Re E_2m+1, Im E_2m, Im E_2m+1
+      lr2 = __ffma2_rn(make_float2(e.x, e.y), Mp[m], lr2);
+      li2 = __ffma2_rn(make_float2(e.z, e.w), Mp[m], li2);
     }
+    const float lr = lr2.x + lr2.y, li = li2.x + li2.y;
     float sn, cs;
     sincosf(fmaf((float)(int32_t)turns, kTwoPiOver2p32, li), &sn, &cs);
     const float mag = expf(lr);
@@ -237,12 +240,19 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
     const float gr = mag * cs, gi = mag * sn;
     const float wr = fmaf(b.x, gr, -b.y * gi), wi = fmaf(b.x, gi, b.y * gr);
     fe += wr;
+    const float2 wr2 = make_float2(wr, wr), nwi2 = make_float2(-wi, -wi);
 #pragma unroll
     for (int m = 0; m < K / 2; ++m) {
       const float4 e = lds4(row + 1 + m);
-      D[2 * m] = fmaf(e.x, wr, fmaf(-e.y, wi, D[2 * m]));
-      D[2 * m + 1] = fmaf(e.z, wr, fmaf(-e.w, wi, D[2 * m + 1]));
+      Dp[m] = __ffma2_rn(make_float2(e.x, e.y), wr2,
+                         __ffma2_rn(make_float2(e.z, e.w), nwi2, Dp[m]));
     }
+  }
+  float D[K];
+#pragma unroll
+  for (int m = 0; m < K / 2; ++m) {
+    D[2 * m] = Dp[m].x;
+    D[2 * m + 1] = Dp[m].y;
   }
   if (sd) {
     if (act) {

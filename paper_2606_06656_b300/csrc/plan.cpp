@@ -171,7 +171,7 @@ static SerInfo series_table(int L, std::vector<F4>& tab) {
     std::complex<double> e = -2.0 * r;                      // E_0
     for (int k = 0; k < kSeriesK1; k += 2) {
       const std::complex<double> e1 = e * r;
-      tab.push_back({(float)e.real(), (float)e.imag(), (float)e1.real(), (float)e1.imag()});
+      tab.push_back({(float)e.real(), (float)e1.real(), (float)e.imag(), (float)e1.imag()});
       e = e1 * r;
     }
   }

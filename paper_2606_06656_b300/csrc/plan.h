@@ -188,8 +188,9 @@ constexpr int kNumGroupCfg = 99;
 // series over L literals, the derivative series relative to |dlog F/dy| >=
 // sin phi) are at most 2^-24.  Per length L the table holds, for root j =
 // 1..js1, kSerRow float4: {Re C_j, Im C_j and theta_j as uint32 fractions of
-// a turn, 0} with C_j = log h_j - log(1 + r_j^2), then {E_2m, E_2m+1} for
-// m = 0..K1/2 - 1.
+// a turn, 0} with C_j = log h_j - log(1 + r_j^2), then {Re E_2m, Re E_2m+1,
+// Im E_2m, Im E_2m+1} for m = 0..K1/2 - 1 (real and imaginary parts of a
+// pair of terms side by side, for packed FP32x2 products).
 constexpr int kSeriesK0 = 18, kSeriesK1 = 26;
 constexpr int kSeriesMaxRoots = 96;   // rows a block stages
 constexpr int kSeriesMinL = 64;       // shorter constraints keep the root products
