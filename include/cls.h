@@ -413,8 +413,10 @@ int cls_dft_work(const cls_problem* p, int64_t* out);
  * 16 flops per (literal, evaluated root) of every restart to a per-problem
  * device counter.  The power-sum pass (constraints of 64 literals or more,
  * see cls_series_range) adds L (4 + 8K) + j (8K + 40) per restart for the j
- * roots it evaluates with K terms (L (4 + 4K) when it hands the remaining
- * roots to the dense kernel, which counts the other 4K).  Synchronises
+ * roots it evaluates with K terms and the partials by Clenshaw's recurrence,
+ * L (4 + 6K) + K^2 + j (8K + 40) with the partials by Horner's rule, and
+ * L (4 + 4K) + j (8K + 40) when it hands the remaining roots to the dense
+ * kernel (which counts the other 4K per literal).  Synchronises
  * the device; *flops = the count; reset != 0 zeroes it afterwards.
  * CLS_ERR_INVALID on NULL. */
 int cls_dft_flops_counter(cls_problem* p, int64_t* flops, int32_t reset);

@@ -69,6 +69,31 @@ __device__ __forceinline__ float rec_sgn(int32_t dst) { return dst < 0 ? -1.0f :
 // f1(i, y_i) takes the last literal of an odd tail.  No copy ever targets an
 // inactive lane's column; the kernel fills those with 1 once
 // (stage_fill_inactive), so every lane reads without a test.
+// [y^n] U_k: (-1)^m C(k - m, m) 2^(k - 2m) for n = k - 2m, else 0; every
+// value for k < 26 is an integer times a power of 2 with at most 15
+// significant bits, so the float is exact.
+__host__ __device__ constexpr float umono(int k, int n) {
+  if (n > k || ((k - n) & 1)) return 0.f;
+  const int m = (k - n) / 2;
+  double bin = 1.0;
+  for (int i = 0; i < m; ++i) bin = bin * (double)(k - m - i) / (double)(i + 1);
+  double p = 1.0;
+  for (int i = 0; i < k - 2 * m; ++i) p *= 2.0;
+  return (float)((m & 1 ? -1.0 : 1.0) * bin * p);
+}
+// sum of |[y^n] U_k| over n: the Pell number P_(k+1) (P_1 = 1, P_2 = 2,
+// P_n = 2 P_(n-1) + P_(n-2))
+__host__ __device__ constexpr float upell(int k) {
+  double a = 0.0, b = 1.0;   // P_0, P_1
+  for (int i = 0; i < k; ++i) {
+    const double c = 2.0 * b + a;
+    a = b;
+    b = c;
+  }
+  return (float)b;
+}
+static_assert(umono(3, 1) == -4.f && umono(4, 0) == 1.f && upell(3) == 12.f, "U_k tables");
+
 constexpr int kSerChunk = 16;
 __device__ __forceinline__ void stage_fill_inactive(float* stw, int lane, bool act) {
   if (!act)
@@ -165,7 +190,7 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
                                                 int r0, int lane, bool vec,
                                                 const float4* tab, const float2* bsm,
                                                 float* __restrict__ P, int Rp, float wgt,
-                                                float* stw, float* sd) {
+                                                float* stw, float* sd, bool& horner) {
   const int r = r0 + lane;
   const bool act = r < R;
   static_assert(K % 2 == 0, "table rows hold pairs of terms");
@@ -262,8 +287,26 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
     }
     return fe;
   }
-  // pass C: partials, sum_k D_k U_k(y) by Clenshaw's recurrence, two
-  // literals per packed instruction
+  // pass C: partials, p(y) = sum_k D_k U_k(y), two literals per packed
+  // instruction.  Horner's rule on the monomial coefficients c_n takes one
+  // operation per term, Clenshaw's recurrence two.  In FP32 (unit roundoff
+  // u = 2^-24), converting D to c (K products per coefficient) and
+  // evaluating by Horner (|y| <= 1) err by at most about 3K u sum_k |D_k|
+  // P_(k+1), P_(k+1) = sum over n of |[y^n] U_k| (a Pell number, ~2.41^k).
+  // The warp takes Horner's rule only when for every restart that bound is
+  // at most 2^-17 sum_k (k+1) |D_k|, 2^-17 of the largest value |p| can
+  // take on [-1, 1] and below the a-priori bound of the recurrence itself
+  // (of order K^2 u of the same scale).  That holds when D_k decays fast,
+  // as it does while only the first roots matter (points far from the
+  // corners); otherwise the warp keeps Clenshaw's recurrence.
+  float sP = 0.f, sM = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float a = fabsf(D[k]);
+    sP = fmaf(upell(k), a, sP);
+    sM = fmaf((float)(k + 1), a, sM);
+  }
+  horner = __all_sync(0xffffffffu, !act || 3.f * (float)K * sP <= 128.f * sM);
   auto clenshaw = [&](float2 y) -> float2 {
     const float2 y2 = __fadd2_rn(y, y);
     float2 b1 = make_float2(0.f, 0.f), b2 = b1;
@@ -280,14 +323,39 @@ __device__ __forceinline__ float series_restart(int L, int jw, const LitRec* rec
     const int32_t dst = recs[i].dst;
     if (act) st_partial(&P[(size_t)rec_row(dst) * Rp + r], wgt * rec_sgn(dst) * g);
   };
-  staged_scan<true>(
-      L, recs, sgn, x, R, r0, lane, vec, stw,
-      [&](int i, float y0, float y1) {
-        const float2 g = clenshaw(make_float2(y0, y1));
-        put(i, g.x);
-        put(i + 1, g.y);
-      },
-      [&](int i, float y0) { put(i, clenshaw(make_float2(y0, 0.f)).x); });
+  if (horner) {
+    float c[K];                      // c_n = sum_k [y^n] U_k D_k
+#pragma unroll
+    for (int n = 0; n < K; ++n) c[n] = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+      for (int n = k & 1; n <= k; n += 2) c[n] = fmaf(umono(k, n), D[k], c[n]);
+    }
+    auto horner_eval = [&](float2 y) -> float2 {
+      float2 h = make_float2(c[K - 1], c[K - 1]);
+#pragma unroll
+      for (int n = K - 2; n >= 0; --n) h = __ffma2_rn(h, y, make_float2(c[n], c[n]));
+      return h;
+    };
+    staged_scan<true>(
+        L, recs, sgn, x, R, r0, lane, vec, stw,
+        [&](int i, float y0, float y1) {
+          const float2 g = horner_eval(make_float2(y0, y1));
+          put(i, g.x);
+          put(i + 1, g.y);
+        },
+        [&](int i, float y0) { put(i, horner_eval(make_float2(y0, 0.f)).x); });
+  } else {
+    staged_scan<true>(
+        L, recs, sgn, x, R, r0, lane, vec, stw,
+        [&](int i, float y0, float y1) {
+          const float2 g = clenshaw(make_float2(y0, y1));
+          put(i, g.x);
+          put(i + 1, g.y);
+        },
+        [&](int i, float y0) { put(i, clenshaw(make_float2(y0, 0.f)).x); });
+  }
   return fe;
 }
 
@@ -375,12 +443,13 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
   __syncthreads();
   if (K == 0) return;
   float fev;
+  bool horner = false;
   float* sd = part ? ser_d + (size_t)si.slot * (kSeriesK1 + 1) * Rp + r : nullptr;
   static_assert(kSeriesK0 == 18 && kSeriesK1 == 26 && kSeriesKx[0] == 12 &&
                     kSeriesKx[1] == 14 && kSeriesKx[2] == 16 && kSeriesKx[3] == 22,
                 "term counts of the dispatch below");
 #define CLS_SERIES(KK) \
-  series_restart<KK>(L, jw, recs, sgn, x, R, r0, lane, vec, tab, bsm, P, Rp, it.w, stw, sd)
+  series_restart<KK>(L, jw, recs, sgn, x, R, r0, lane, vec, tab, bsm, P, Rp, it.w, stw, sd, horner)
   switch (K) {
     case 12: fev = CLS_SERIES(12); break;
     case 14: fev = CLS_SERIES(14); break;
@@ -394,10 +463,12 @@ __global__ void __launch_bounds__(256, 3) k_fe_series(
   // (K is uniform over the warp, so every lane is here)
   const unsigned nact = (unsigned)__popc(__ballot_sync(kFull, act));
   if (flops && lane == 0) {
-    // per restart: L (4 + 8K) for the passes (L (4 + 4K) on a low tile, whose
+    // per restart: L (4 + 8K) for the passes with Clenshaw's partials,
+    // L (4 + 6K) + K^2 with Horner's (L (4 + 4K) on a low tile, whose
     // Clenshaw pass the dense kernel counts), jw (8K + 40) for the roots
-    const unsigned long long per = (unsigned long long)L * (4 + (part ? 4 : 8) * K) +
-                                   (unsigned long long)jw * (8 * K + 40);
+    const unsigned long long per =
+        (unsigned long long)L * (4 + (part ? 4 : horner ? 6 : 8) * K) +
+        (horner ? (unsigned long long)(K * K) : 0ull) + (unsigned long long)jw * (8 * K + 40);
     atomicAdd(flops, per * (unsigned long long)nact);
   }
   __syncwarp();

@@ -825,3 +825,54 @@ def test_dft_flops_counter_counts_truncated_work(P):
         assert 14 * L * js1 > series                  # the pass takes the low roots
         expect += series - 14 * L * js1
     assert B.cls_dft_flops_counter(p.handle, reset=True) == expect * R
+
+
+def test_power_sum_partials_horner_and_clenshaw(P):
+    """The power-sum pass evaluates a finished tile's partials by Horner's
+    rule on monomial coefficients when its a-priori error bound is small
+    (the coefficients D_k decay fast) and by Clenshaw's recurrence
+    otherwise.  One long constraint, one tile of 32 restarts: the device flop
+    count identifies the route (L (4 + 6K) + K^2 + j (8K + 40) per restart
+    against L (4 + 8K) + j (8K + 40)); both meet the parity criterion."""
+    from paper_2606_06656_b300 import binding as B
+    rng = np.random.default_rng(12)
+    n = 400
+
+    def route(inst, X, floored):
+        p = P(inst)
+        B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle), 3))
+        L = int(inst.offsets[1])
+        B.cls_dft_flops_counter(p.handle, reset=True)
+        x = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        obj, grad, fe = p.eval(x, obj=True, grad=True, fe_con=True)
+        c = B.cls_dft_flops_counter(p.handle, reset=True)
+        check_against_oracle(inst, X, obj.cpu().numpy(), grad.cpu().numpy(), fe.cpu().numpy(),
+                             floored=floored)
+        assert c % 32 == 0
+        per = c // 32
+        kinds = set()
+        for K in (12, 14, 16, 18, 22, 26):
+            for j in range(1, (L + 1) // 2 + 1):
+                if per == L * (4 + 6 * K) + K * K + j * (8 * K + 40):
+                    kinds.add("horner")
+                if per == L * (4 + 8 * K) + j * (8 * K + 40):
+                    kinds.add("clenshaw")
+        return kinds
+
+    # a 300-literal cardinality constraint at uniform points: the first
+    # roots dominate, D_k decays fast, 16 terms
+    L = 300
+    inst = W.build(n, [(W.TYPE_CARD_GE, 150, rng.choice(n, L, replace=False).astype(np.int32),
+                        np.ones(L, np.int8))])
+    assert route(inst, W.uniform_points(n, 32, seed=3), False) == {"horner"}
+    # a 299-literal constraint whose spectrum has period 5 (N = 300), so its
+    # only DFT coefficients below the Nyquist root sit at j = 60 and 120,
+    # at points with |y| in [0.8, 0.9] (the cutoff keeps about 77 roots, 26
+    # terms): D_k ~ tan(60 pi / 600)^(k+1) decays slowly.  A stress set (some
+    # restarts in the far tail), so the FP32 floor applies.
+    L = 299
+    sp = np.array([-1 if t % 5 < 2 else 1 for t in range(L + 1)], np.int8)
+    inst = W.build(n, [(W.TYPE_SPECTRUM, 0, rng.choice(n, L, replace=False).astype(np.int32),
+                        np.ones(L, np.int8))], spectra=sp)
+    X = (rng.choice([-1.0, 1.0], (n, 32)) * rng.uniform(0.8, 0.9, (n, 32))).astype(np.float32)
+    assert route(inst, X, True) == {"clenshaw"}
