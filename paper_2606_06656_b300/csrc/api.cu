@@ -990,8 +990,15 @@ int record_steps(const cls_problem* p, const Layout& L, const Branch& br, int64_
                  void* ws, bool score) {
   const cls::DevPlan& D = p->dev;
   float* P = at<float>(ws, L.P);
+  // capture order: the DFT buckets longest first (the Chebyshev pass and
+  // the dense kernels of the long constraints are the longest branches),
+  // then the short closed forms, then the closed-form lane-group buckets
   std::vector<int> units;
-  for (int u = 0; u < cls::kNumFeUnits; ++u)
+  for (int b = cls::kNumDftBuckets - 1; b >= 0; --b)
+    if (cls::fe_unit_active(D, cls::kNumThreadCls + b)) units.push_back(cls::kNumThreadCls + b);
+  for (int u = 0; u < cls::kNumThreadCls; ++u)
+    if (cls::fe_unit_active(D, u)) units.push_back(u);
+  for (int u = cls::kNumThreadCls + cls::kNumDftBuckets; u < cls::kNumFeUnits; ++u)
     if (cls::fe_unit_active(D, u)) units.push_back(u);
   const int nside = (int)br.side.size();
   cudaEvent_t ev_fork = br.ev[0], ev_score = br.ev[1];
