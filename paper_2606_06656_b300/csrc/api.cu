@@ -1007,14 +1007,14 @@ int record_steps(const cls_problem* p, const Layout& L, const Branch& br, int64_
   for (int st = 0; st < n_steps; ++st) {
     CLS_CUDA_TRY(cudaEventRecord(ev_fork, br.main), "fork");
     for (size_t i = 0; i < units.size(); ++i) {
-      cudaStream_t s = (i == 0) ? br.main : br.side[(i - 1) % (nside - 1)];
-      if (s != br.main) CLS_CUDA_TRY(cudaStreamWaitEvent(s, ev_fork, 0), "fork wait");
+      cudaStream_t s = br.side[i % (nside - 1)];
+      CLS_CUDA_TRY(cudaStreamWaitEvent(s, ev_fork, 0), "fork wait");
       CLS_CUDA_TRY(cls::launch_fe_unit(D, units[i], L.R, L.Rp, x, P, nullptr, 0,
                                        at<uint8_t>(ws, L.done), s, nullptr),
                    "fe unit");
       (*launches)++;
     }
-    for (int k = 0; k + 1 < nside && k + 1 < (int)units.size(); ++k) {
+    for (int k = 0; k + 1 < nside && k < (int)units.size(); ++k) {
       CLS_CUDA_TRY(cudaEventRecord(br.ev[2 + k], br.side[k]), "join");
       CLS_CUDA_TRY(cudaStreamWaitEvent(br.main, br.ev[2 + k], 0), "join wait");
     }
@@ -1038,19 +1038,26 @@ int record_steps(const cls_problem* p, const Layout& L, const Branch& br, int64_
   return CLS_OK;
 }
 
-// One side stream per FE unit beyond the first (which runs on the main
-// stream) and one score stream: every unit of a step is its own branch of
-// the graph, so no unit waits on another that merely shared its stream
-// (against 6 shared side streams: 4.26 -> 4.22 ms per step over the first
-// 60 steps of the mixed workload).
-constexpr int kSideStreams = cls::kNumFeUnits;
+// One side stream per FE unit and one score stream: every unit of a step is
+// its own branch of the graph, so no unit waits on another that merely
+// shared its stream (against 6 shared side streams: 4.26 -> 4.22 ms per
+// step over the first 60 steps of the mixed workload).
+constexpr int kSideStreams = cls::kNumFeUnits + 1;
+// Side streams 0..kHighPrioStreams-1 (the longest units in capture order)
+// carry the device's greatest stream priority; their kernel nodes keep it
+// (the graph is instantiated with node priorities), so when SMs free up the
+// long branches get them first.
+constexpr int kHighPrioStreams = 8;
 
 cudaError_t make_branch(Branch* br, bool own_main) {
   cudaError_t e = cudaSuccess;
   if (own_main) e = cudaStreamCreateWithFlags(&br->main, cudaStreamNonBlocking);
+  int least = 0, greatest = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
   for (int i = 0; i < kSideStreams && e == cudaSuccess; ++i) {
     cudaStream_t s = nullptr;
-    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking,
+                                     i < kHighPrioStreams ? greatest : least);
     if (e == cudaSuccess) br->side.push_back(s);
   }
   for (int i = 0; i < kSideStreams + 2 && e == cudaSuccess; ++i) {
@@ -1179,7 +1186,7 @@ int cls_batch_graph_create(int32_t count, const cls_problem* const* ps, const in
     }
     g->launches = kernels;
   }
-  e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  e = cudaGraphInstantiate(&g->exec, g->graph, cudaGraphInstantiateFlagUseNodePriority);
   if (e != cudaSuccess) {
     graph_release(g);
     (void)cudaGetLastError();
