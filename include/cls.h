@@ -406,7 +406,9 @@ int cls_config_info(int32_t id, int32_t* out);
 int cls_dft_work(const cls_problem* p, int64_t* out);
 
 /* Flops of the DFT roots evaluated by the factored path since the last
- * reset (no counterpart in the paper; for roofline accounting): the dense
+ * reset (no counterpart in the paper; for roofline accounting): the direct
+ * and packed-pair DFT kernels add 20 flops per (literal, root) of every
+ * restart (all J roots); the dense
  * factored kernel skips, per restart, the roots whose terms are provably
  * below 2^-24 in total (a bound on the factors' moduli from the sums of
  * (1 - y_i^2)^m, m = 1..4), so its work depends on the point; it adds 14 or

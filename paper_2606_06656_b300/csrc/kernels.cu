@@ -589,7 +589,8 @@ __global__ void __launch_bounds__(256) k_fe_group(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ root, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
-    float* __restrict__ fe_con, int ldf, const uint8_t* __restrict__ done, int RT) {
+    float* __restrict__ fe_con, int ldf, const uint8_t* __restrict__ done, int RT,
+    unsigned long long* __restrict__ flops) {
   using Geo = GroupGeom<G>;
   constexpr int LS = G * Q;          // staged literal slots
   extern __shared__ float smem[];
@@ -739,6 +740,11 @@ __global__ void __launch_bounds__(256) k_fe_group(
     if (r < R)
       st_partial(&P[(size_t)rec_row(rc.dst) * Rp + r], it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane]);
   }
+  // DFT roots: 20 flops per (literal, root) of every restart (all J roots)
+  if constexpr (CPLX)
+    if (flops && threadIdx.x == 0)
+      atomicAdd(flops, 20ull * (unsigned long long)L * (unsigned long long)it.J *
+                           (unsigned long long)min(32, R - r0));
   if (fe_con && warp == 0 && r0 + lane < R) fe_con[(size_t)it.c * ldf + r0 + lane] = fe_s[lane];
 }
 
@@ -1701,7 +1707,8 @@ cudaError_t launch_group(int cfg, const DevPlan& d, const int32_t* list, int cou
 #define CLS_LAUNCH_CASE(id, G, Q, C, Y)                                                      \
   case id:                                                                                   \
     k_fe_group<G, Q, (C != 0), (Y != 0)><<<grid, block, group_smem<G, Q>(), s>>>(            \
-        list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf, dflags, RTg); \
+        list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf, dflags, RTg,  \
+        d.dft_flops);                                                                        \
     break;
     CLS_GROUP_CONFIGS(CLS_LAUNCH_CASE)
 #undef CLS_LAUNCH_CASE

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) k_fe_group_p2(
     const int32_t* __restrict__ list, const FeItem* __restrict__ fe,
     const F4* __restrict__ root, const F4* __restrict__ coef, const LitRec* __restrict__ lit,
     const float* __restrict__ x, int R, int Rp, float* __restrict__ P,
-    float* __restrict__ fe_con, int ldf) {
+    float* __restrict__ fe_con, int ldf, unsigned long long* __restrict__ flops) {
   using Geo = Geo2<G>;
   constexpr int LS = G * Q;
   extern __shared__ float smem[];
@@ -182,6 +182,10 @@ __global__ void __launch_bounds__(256) k_fe_group_p2(
     if (r < R)
       st_partial(&P[(size_t)rec_row(rc.dst) * Rp + r], it.w * rec_sgn(rc.dst) * ys[i * Geo::LDR + lane]);
   }
+  // 20 flops per (literal, root) of every restart, as the direct form
+  if (flops && threadIdx.x == 0)
+    atomicAdd(flops, 20ull * (unsigned long long)L * (unsigned long long)it.J *
+                         (unsigned long long)min(32, R - r0));
   if (fe_con && warp == 0 && r0 + lane < R) fe_con[(size_t)it.c * ldf + r0 + lane] = fe_s[lane];
 }
 
@@ -214,7 +218,8 @@ cudaError_t launch_group_p2(int cfg, const DevPlan& d, const int32_t* list, int 
 #define CLS_P2_CASE(id, G, Q, C, Y)                                                        \
   case id:                                                                                 \
     k_fe_group_p2<G, Q, (Y != 0)><<<grid, block, p2_smem<G, Q>(), s>>>(                    \
-        list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf);           \
+        list, d.fe, d.root_tab, d.coef_tab, d.fe_lit, x, R, Rp, P, fe_con, ldf,            \
+        d.dft_flops);                                                                      \
     break;
     CLS_P2_CONFIGS(CLS_P2_CASE)
 #undef CLS_P2_CASE

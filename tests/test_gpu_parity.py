@@ -100,8 +100,10 @@ def P():
 
 def kind_tuning(cfg, want):
     """The bucket map with every DFT bucket on its smallest configuration of
-    kind `want` (1 = direct factor alpha + beta w^j, 3 = factored roots)
-    that holds the bucket's longest constraint."""
+    kind `want` (1 = direct factor alpha + beta w^j, 2 = the same with roots
+    in packed pairs, 3 = factored roots) that holds the bucket's longest
+    constraint; a bucket that no configuration of that kind holds keeps its
+    configuration."""
     from paper_2606_06656_b300 import binding as B
     out = list(cfg)
     cands = []
@@ -114,8 +116,9 @@ def kind_tuning(cfg, want):
             cands.append((G * Q, cid))
     for b in range(B.N_BUCKETS):
         dft, bmax, _, _ = B.cls_config_info(1000 + b)
-        if dft:
-            out[b] = min(c for c in cands if c[0] >= bmax)[1]
+        fit = [c for c in cands if c[0] >= bmax]
+        if dft and fit:
+            out[b] = min(fit)[1]
     return out
 
 
@@ -825,6 +828,30 @@ def test_dft_flops_counter_counts_truncated_work(P):
         assert 14 * L * js1 > series                  # the pass takes the low roots
         expect += series - 14 * L * js1
     assert B.cls_dft_flops_counter(p.handle, reset=True) == expect * R
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_dft_flops_counter_direct_and_pair_kernels(P, kind):
+    """The direct-form and packed-pair DFT kernels evaluate every root: they
+    add 20 flops per (literal, root) and restart to the device counter, so
+    the DFT class's evaluated flops cover all its kernels."""
+    from paper_2606_06656_b300 import binding as B
+    rng = np.random.default_rng(6)
+    n = 300
+    Ls = (10, 40, 100)
+    rows = [(W.TYPE_CARD_GE, L // 2, rng.choice(n, L, replace=False).astype(np.int32),
+             np.ones(L, np.int8)) for L in Ls]
+    inst = W.build(n, rows)
+    p = P(inst)
+    B.cls_tuning_set(p.handle, kind_tuning(B.cls_tuning_get(p.handle), kind))
+    R = 40
+    X = W.uniform_points(n, R, seed=2)      # no corners: the corner pass leaves every tile
+    B.cls_dft_flops_counter(p.handle, reset=True)
+    x = torch.from_numpy(X).cuda()
+    obj, grad, fe = p.eval(x, obj=True, grad=True, fe_con=True)
+    c = B.cls_dft_flops_counter(p.handle, reset=True)
+    check_against_oracle(inst, X, obj.cpu().numpy(), grad.cpu().numpy(), fe.cpu().numpy())
+    assert c == sum(20 * L * ((L + 1) // 2) for L in Ls) * R
 
 
 def test_power_sum_partials_horner_and_clenshaw(P):
