@@ -309,7 +309,7 @@ def run_ours(args, rank, world, local_rank):
         if R >= 64 and args.steps >= 20:
             xs, done_steps = x0.clone(), 0
             q = R // 4
-            for blk, at in enumerate((0, 12, 25, 60)):
+            for blk, at in enumerate(tune_points(args)):
                 if at > done_steps:
                     B.cls_step(p.handle, R, xs, lr, at - done_steps, None, None, None, ws)
                     done_steps = at
@@ -509,8 +509,9 @@ def run_ours(args, rank, world, local_rank):
                             f"(after {max(3, args.warmup)} untimed warm-up steps)",
                    "tuning": tuning, "autotune_s": tune_s,
                    "autotune_points": None if (args.tuning or args.no_tune) else
-                   ("four restart blocks of the timed run's own trajectory, at steps 0, 12, "
-                    "25 and 60 (untimed)" if R >= 64 and args.steps >= 20 else "x0")},
+                   ("four restart blocks of the timed run's own trajectory, at steps "
+                    + ", ".join(str(v) for v in tune_points(args)) + " (untimed)"
+                    if R >= 64 and args.steps >= 20 else "x0")},
         "e2e": {"value": units / e2e_s, "unit": "literal-evals/s",
                 "h2d_bytes_per_step": 4 * inst.n * R / K, "d2h_bytes_per_step": 4 * R / K,
                 "call": f"cls_solve_host: x0 from pinned host memory, {K} steps, counts back"},
@@ -607,6 +608,20 @@ def run_learned(args):
         "train_log": log, "per_instance": res,
     }
     print(json.dumps(line), flush=True)
+
+
+def tune_points(args):
+    """Steps of the run whose restart blocks the autotuner times: given
+    (--tune-at), else 0, 12, 25 and 60 (dense, middle and corner-dominated
+    points).  On the driver's 20-step command, points inside its window
+    (0/5/10/15, 0/3/9/15, 0/8/14/19) measured 4.43-4.53 ms per step against
+    4.45, so the default stays."""
+    if args.tune_at:
+        pts = tuple(int(v) for v in args.tune_at.split(","))
+        if len(pts) != 4 or any(v < 0 for v in pts):
+            raise SystemExit("--tune-at takes four steps >= 0")
+        return pts
+    return (0, 12, 25, 60)
 
 
 def c1_step_kernel():
@@ -1108,6 +1123,8 @@ def main():
     ap.add_argument("--persistent", action="store_true",
                     help="time the one-launch persistent step (short closed-form problems)")
     ap.add_argument("--tuning", default="", help="fixed bucket->configuration map (25 ids)")
+    ap.add_argument("--tune-at", default="",
+                    help="four steps of the run to take the autotuner's restart blocks from")
     ap.add_argument("--R", type=int, default=0, help="override restarts (profiling)")
     ap.add_argument("--profile-step", type=int, default=-1,
                     help="run S steps untimed, then one step inside a profiler window")
