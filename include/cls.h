@@ -299,16 +299,26 @@ int cls_step(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_step
              size_t ws_bytes, void* stream);
 
 /* The n-step loop as ONE persistent launch (task: all restarts and all
- * constraints in one persistent launch; Sec. 3.3's lockstep batch): a
- * cooperative kernel whose warps take, in turn, the FE+gradient items, the
- * accumulate/step/round items and the scoring items of every step, separated
- * by grid barriers.  Same arguments and results as cls_step.  Supported when
- * every constraint that needs FE work is a closed-form product of at most
- * 16 literals (e.g. random k-SAT); otherwise CLS_ERR_UNSUPPORTED (use
- * cls_step or a graph), likewise without cooperative launch.  The barriers
- * never spin unboundedly: a barrier that waits too long (~2^22 polls) sets
- * an error flag in the workspace and every block returns; read it with
- * cls_persistent_status (synchronous; 0 = ok, 1 = a barrier timed out). */
+ * constraints in one persistent launch; Sec. 3.3's lockstep batch).  Same
+ * arguments and results as cls_step (x, bits and counts bit for bit).
+ * Supported when every constraint that needs FE work is a closed-form
+ * product of at most 16 literals (e.g. random k-SAT); otherwise
+ * CLS_ERR_UNSUPPORTED (use cls_step or a graph).  Two forms:
+ *   - when one tile of 32 restarts -- x (128 B per variable), every literal
+ *     partial row (128 B per FE literal), the literal records (8 B each),
+ *     the items (32 B per constraint) and the bitset -- fits in 220 KB of
+ *     shared memory (random 3-SAT with n = 100, m = 426 needs 197 KB),
+ *     one CTA per tile runs all n steps with the tile on chip and
+ *     __syncthreads between the phases; the restarts are independent, so
+ *     no CTA waits on another;
+ *   - otherwise a cooperative kernel whose warps take, in turn, the
+ *     FE+gradient items, the accumulate/step/round items and the scoring
+ *     items of every step, separated by grid barriers
+ *     (CLS_ERR_UNSUPPORTED without cooperative launch).  The barriers
+ *     never spin unboundedly: a barrier that waits too long (~2^22 polls)
+ *     sets an error flag in the workspace and every block returns.
+ * cls_persistent_status reads that flag (synchronous; 0 = ok, 1 = a
+ * barrier timed out; the one-CTA-per-tile form always leaves 0). */
 int cls_step_persistent(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
                         uint32_t* bits, int32_t* nsat, double* wsat, void* ws, size_t ws_bytes,
                         void* stream);

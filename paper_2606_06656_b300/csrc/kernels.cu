@@ -1448,6 +1448,204 @@ __global__ void __launch_bounds__(256) k_persistent(DevPlan d, PersistArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// The step loop with one CTA per tile of 32 restarts (A10; the restarts of
+// the lockstep batch are independent, Sec. 3.3).  The CTA keeps its tile of
+// x, every literal partial row of the tile and the tile's bitset in shared
+// memory for the whole n-step loop, with __syncthreads between the phases:
+// no grid barrier, one launch.  For problems whose FE work is all short
+// closed forms (L <= 16) and whose tile fits in shared memory.  Per step:
+// the literal partials of every constraint (the same FP32 operations as
+// thread_body), then per variable the rows summed in row order, the
+// projected step and the ballot (as accum_one); after the last step the
+// bitset and x go back to global memory and the score is taken there (the
+// ranges as score_range, the totals in k_score_final's order), so x, the
+// bitset and the counts equal cls_step's bit for bit.
+// Shared memory: see tile_smem_layout.
+// ---------------------------------------------------------------------------
+struct TileArgs {
+  int R, Rp, RT, n_steps;
+  float lr;
+  float* x;
+  uint32_t* bits;
+  int32_t* rpart_n;     // [range][Rp]
+  double* rpart_w;
+  int32_t* nsat;
+  double* wsat;
+};
+
+constexpr int kTileWarps = 32;          // warps of a k_tile_loop CTA
+constexpr int kTileRoots = 3;           // the real-root table entries (plan.h)
+constexpr int kTileCoefs = 7;           // the closed-form coefficient entries
+
+template <int L>
+__device__ __forceinline__ void tile_fe_body(const FeItem& it, const float4* rt, const float4* cf,
+                                             const int2* rec, const float* xs, float* ps,
+                                             int lane) {
+  const float4 rt0 = rt[it.root_off], cf0 = cf[it.coef_off];
+  const bool two = it.J == 2;
+  const float4 rt1 = two ? rt[it.root_off + 1] : make_float4(1.f, 0.f, 0.f, 0.f);
+  const float4 cf1 = two ? cf[it.coef_off + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float y[L], g[L], pre[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) y[i] = rec_sgn(rec[i].y) * xs[rec[i].x * 32 + lane];
+  float run = 1.f;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    pre[i] = run;
+    run *= fmaf(y[i], rt0.y, rt0.x);
+  }
+  float suf = cf0.z;
+#pragma unroll
+  for (int i = L - 1; i >= 0; --i) {
+    g[i] = pre[i] * suf;
+    suf *= fmaf(y[i], rt0.y, rt0.x);
+  }
+  if (two) {
+    run = 1.f;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      pre[i] = run;
+      run *= fmaf(y[i], rt1.y, rt1.x);
+    }
+    suf = cf1.z;
+#pragma unroll
+    for (int i = L - 1; i >= 0; --i) {
+      g[i] = fmaf(pre[i], suf, g[i]);
+      suf *= fmaf(y[i], rt1.y, rt1.x);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < L; ++i)
+    ps[rec_row(rec[i].y) * 32 + lane] = it.w * rec_sgn(rec[i].y) * g[i];
+}
+
+template <int LO, int HI>
+__device__ __forceinline__ void tile_fe_dispatch(int L, const FeItem& it, const float4* rt,
+                                                 const float4* cf, const int2* rec,
+                                                 const float* xs, float* ps, int lane) {
+  if constexpr (LO <= HI) {
+    if (L == LO)
+      tile_fe_body<LO>(it, rt, cf, rec, xs, ps, lane);
+    else
+      tile_fe_dispatch<LO + 1, HI>(L, it, rt, cf, rec, xs, ps, lane);
+  }
+}
+
+// Shared memory of k_tile_loop (16-byte entries first): the real-root and
+// coefficient tables, the items, then x [n][32], the partial rows
+// [nnz_fe][32], the literal records, the row offsets and the bitset.
+struct TileSmem {
+  size_t items, xs, ps, recs, voff, bs, total;
+};
+
+__host__ __device__ inline TileSmem tile_smem_layout(int n, int64_t nnz_fe, int n_items) {
+  TileSmem t;
+  size_t off = (size_t)(kTileRoots + kTileCoefs) * 16;
+  t.items = off;
+  off += (size_t)n_items * sizeof(FeItem);
+  t.xs = off;
+  off += (size_t)n * 32 * sizeof(float);
+  t.ps = off;
+  off += (size_t)nnz_fe * 32 * sizeof(float);
+  t.recs = off;
+  off += (size_t)nnz_fe * sizeof(int2);
+  t.voff = off;
+  off += (size_t)(n + 1) * sizeof(int32_t);
+  t.bs = off;
+  off += (size_t)n * sizeof(uint32_t);
+  t.total = off;
+  return t;
+}
+
+__global__ void __launch_bounds__(32 * kTileWarps) k_tile_loop(DevPlan d, TileArgs a) {
+  extern __shared__ float4 tl_smem4[];
+  char* base = reinterpret_cast<char*>(tl_smem4);
+  const int n = d.n, n0 = d.thread_count[0], n1 = d.thread_count[1];
+  const TileSmem lay = tile_smem_layout(n, d.nnz_fe, n0 + n1);
+  float4* rt = tl_smem4;                                    // [kTileRoots]
+  float4* cf = tl_smem4 + kTileRoots;                       // [kTileCoefs]
+  FeItem* items = reinterpret_cast<FeItem*>(base + lay.items);
+  float* xs = reinterpret_cast<float*>(base + lay.xs);
+  float* ps = reinterpret_cast<float*>(base + lay.ps);
+  int2* recs = reinterpret_cast<int2*>(base + lay.recs);
+  int32_t* voff = reinterpret_cast<int32_t*>(base + lay.voff);
+  uint32_t* bs = reinterpret_cast<uint32_t*>(base + lay.bs);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tile = blockIdx.x;
+  const int r = tile * 32 + lane;
+  const bool act = r < a.R;
+  // the problem's short-class data, read once for the whole loop
+  for (int i = threadIdx.x; i < kTileRoots; i += blockDim.x) rt[i] = ldg4(&d.root_tab[i]);
+  for (int i = threadIdx.x; i < kTileCoefs; i += blockDim.x) cf[i] = ldg4(&d.coef_tab[i]);
+  for (int i = threadIdx.x; i < n0 + n1; i += blockDim.x)
+    items[i] = i < n0 ? d.thread_items[0][i] : d.thread_items[1][i - n0];
+  for (int64_t e = threadIdx.x; e < d.nnz_fe; e += blockDim.x)
+    recs[e] = make_int2(d.fe_lit[e].var, d.fe_lit[e].dst);
+  for (int v = threadIdx.x; v <= n; v += blockDim.x) voff[v] = d.fe_voff[v];
+  for (int v = warp; v < n; v += kTileWarps)
+    xs[v * 32 + lane] = act ? a.x[(size_t)v * a.R + r] : 0.f;
+  for (int step = 0; step < a.n_steps; ++step) {
+    __syncthreads();                                    // x of the previous step in place
+    for (int ci = warp; ci < n0 + n1; ci += kTileWarps) {
+      const FeItem it = items[ci];
+      if (it.L <= 8)
+        tile_fe_dispatch<1, 8>(it.L, it, rt, cf, recs + it.lit0, xs, ps, lane);
+      else
+        tile_fe_dispatch<9, 16>(it.L, it, rt, cf, recs + it.lit0, xs, ps, lane);
+    }
+    __syncthreads();                                    // every partial row written
+    for (int v = warp; v < n; v += kTileWarps) {
+      float g = 0.f;
+      for (int k = voff[v]; k < voff[v + 1]; ++k) g += ps[k * 32 + lane];
+      float xv = xs[v * 32 + lane];
+      if (act && !(d.fixed && d.fixed[v])) {
+        xv = pgd_project(xv, g, a.lr);
+        xs[v * 32 + lane] = xv;
+      }
+      const uint32_t b = __ballot_sync(kFull, act && xv < 0.0f);
+      if (lane == 0) bs[v] = b;
+    }
+  }
+  __syncthreads();
+  for (int v = warp; v < n; v += kTileWarps) {
+    if (act) a.x[(size_t)v * a.R + r] = xs[v * 32 + lane];
+    if (lane == 0) a.bits[(size_t)v * a.RT + tile] = bs[v];
+  }
+  __syncthreads();                                      // the tile's bitset in global memory
+  // score of the final bitset: ranges over the warps, then the totals per
+  // restart in the order of k_score + k_score_final
+  for (int rg = warp; rg < d.n_ranges; rg += kTileWarps) {
+    int cnt;
+    double ws;
+    score_range<true>(rg, tile, lane, a.RT, d.score_ranges, d.score, d.lit, d.satbits, a.bits,
+                      &cnt, &ws);
+    a.rpart_n[(size_t)rg * a.Rp + tile * 32 + lane] = cnt;
+    a.rpart_w[(size_t)rg * a.Rp + tile * 32 + lane] = ws;
+  }
+  __syncthreads();
+  if (warp == 0 && act) {
+    int cnt = 0;
+    double ws = 0.0;
+    for (int rg0 = 0; rg0 < d.n_ranges; rg0 += kScoreWarps) {
+      int bc = 0;
+      double bw = 0.0;
+      for (int rg = rg0; rg < min(rg0 + kScoreWarps, d.n_ranges); ++rg) {
+        bc += __ldcg(&a.rpart_n[(size_t)rg * a.Rp + r]);
+        bw += __ldcg(&a.rpart_w[(size_t)rg * a.Rp + r]);
+      }
+      cnt += bc;
+      ws += bw;
+    }
+    if (a.nsat) a.nsat[r] = cnt;
+    if (a.wsat) a.wsat[r] = ws;
+  }
+}
+
+size_t tile_loop_smem(const DevPlan& d) {
+  return tile_smem_layout(d.n, d.nnz_fe, d.thread_count[0] + d.thread_count[1]).total;
+}
+
 // Barrier check: `rounds` grid barriers that release after gridDim.x + extra
 // arrivals; with extra > 0 none can release, so every block must time out,
 // raise *err and return.  Block 0 records how many barriers it passed.
@@ -1527,6 +1725,9 @@ cudaError_t set_kernel_attributes() {
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_fe_thread<17, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)thread_xbuf_bytes<24>());
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_tile_loop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTileLoopMaxSmem);
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_fe_thread_ckpt<1, 16>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1846,6 +2047,14 @@ cudaError_t launch_persistent(const DevPlan& d, int R, int Rp, float* x, float l
                               int32_t* nsat, double* wsat, unsigned* bar, int* err,
                               cudaStream_t s) {
   if (n_steps == 0 || R == 0) return cudaSuccess;
+  // a tile that fits in shared memory: one CTA per tile, no grid barrier
+  if (tile_loop_smem(d) <= kTileLoopMaxSmem) {
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    TileArgs ta{R, Rp, ceil_div(R, 32), n_steps, lr, x, bits, rpart_n, rpart_w, nsat, wsat};
+    k_tile_loop<<<ceil_div(R, 32), 32 * kTileWarps, tile_loop_smem(d), s>>>(d, ta);
+    return cudaGetLastError();
+  }
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

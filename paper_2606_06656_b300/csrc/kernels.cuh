@@ -276,9 +276,13 @@ bool fe_unit_active(const DevPlan& d, int unit);
 cudaError_t launch_fe_unit(const DevPlan& d, int unit, int R, int Rp, const float* x, float* P,
                            float* fe_con, int ldf, uint8_t* done, cudaStream_t s, LaunchHook* h);
 
-// The whole step loop as one cooperative persistent launch; only for
-// problems whose FE work is all on the short closed-form path.
+// The whole step loop as one launch; only for problems whose FE work is all
+// on the short closed-form path.  When a restart tile's x, partial rows and
+// bitset fit in kTileLoopMaxSmem bytes of shared memory, one CTA per tile
+// runs the loop with no grid barrier (k_tile_loop); otherwise one
+// cooperative launch over all items with bounded grid barriers.
 bool persistent_eligible(const DevPlan& d);
+constexpr size_t kTileLoopMaxSmem = 220 * 1024;
 cudaError_t launch_persistent(const DevPlan& d, int R, int Rp, float* x, float lr, int n_steps,
                               float* P, uint32_t* bits, int32_t* rpart_n, double* rpart_w,
                               int32_t* nsat, double* wsat, unsigned* bar, int* err,

@@ -44,6 +44,15 @@ CASES = [
     ("or_xor_short", lambda: W.mixed_pb(n=1500, n_or=5000, n_xor=600, xor_len=(3, 16),
                                         n_card=0, seed=7), 200, 4),
     ("one_restart", lambda: W.random_ksat(n=50, m=213, seed=8), 1, 9),
+    # tiles that fit in shared memory (x, every partial row and the bitset of
+    # 32 restarts within 200 KB): one CTA per tile runs the loop
+    ("tile_3sat_c1", lambda: W.random_ksat(n=100, m=426, seed=11), 64, 200),
+    ("tile_3sat_ragged", lambda: W.random_ksat(n=100, m=426, seed=12), 50, 30),
+    ("tile_3sat_many_tiles", lambda: W.random_ksat(n=100, m=426, seed=13), 2000, 12),
+    ("tile_or_xor_nae_weighted",
+     lambda: W.random_constraint_set(np.random.default_rng(14), 150, 150,
+                                     [W.TYPE_OR, W.TYPE_XOR, W.TYPE_NAE], (1, 16),
+                                     weights="random"), 96, 25),
 ]
 
 
@@ -68,6 +77,17 @@ def test_persistent_partial_assignment(P, simplify):
     nsat, _, _ = p.step_persistent(x, 0.2, n_steps=1)
     on, _, _ = ocls.score(inst, x.cpu().numpy())
     assert np.array_equal(nsat.cpu().numpy(), on)
+
+
+@pytest.mark.parametrize("simplify", [False, True])
+def test_tile_loop_partial_assignment(P, simplify):
+    """Pinned variables in the one-CTA-per-tile loop (they never move; with
+    CLS_SIMPLIFY_FIXED their literals leave the FE work)."""
+    inst = W.partial_assignment(W.planted_ksat(n=120, m=400, seed=15), 0.5)
+    p = P(inst, simplify_fixed=simplify)
+    X0 = ocls.init_uniform(inst.n, 70, 5)
+    X0[inst.fixed != 0] = inst.fixed_val[inst.fixed != 0][:, None]
+    _same(*_both(p, X0, 0.2, 15))
 
 
 def test_persistent_rejects_long_constraints(P):
