@@ -1208,6 +1208,9 @@ def main():
         run_completion(args)
     elif args.config == "profile":
         run_profile(args)
+    elif args.config == "c1loop":
+        # the 200-step random 3-SAT loop alone (the default line's c1_loop key)
+        print(json.dumps({"c1_loop": c1_loop(R=args.R or 64)}), flush=True)
     else:
         run_ours(args, rank, world, local_rank)
 
