@@ -50,17 +50,17 @@ _DFT_SOURCES = ("kernels.cu", "kernels_fr.cu", "kernels_series.cu", "kernels_cor
 TRAFFIC = {
     # the DFT class over one step, mean of steps 0, 3, 6 and 9 of the run
     ("dft_class", "mixedpb_n5000_m22500"): dict(
-        bytes=239871488, R=1024, sources=_DFT_SOURCES, sha="265b1c398bffd0c0",
+        bytes=239822912, R=1024, sources=_DFT_SOURCES, sha="8df346d4397e9331",
         profile="profiles/traffic_mixedpb_3sat.md"),
     ("k_accum_step", "mixedpb_n5000_m22500"): dict(
-        bytes=868631360, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="8f59c2710ea6f922",
+        bytes=868627264, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="0586efc5f8aa1002",
         profile="profiles/traffic_mixedpb_3sat.md"),
     ("k_accum_step", "random3sat_n100_m426"): dict(
-        bytes=381965312, R=65536, sources=("kernels.cu", "kernels.cuh"), sha="8f59c2710ea6f922",
+        bytes=381726464, R=65536, sources=("kernels.cu", "kernels.cuh"), sha="0586efc5f8aa1002",
         profile="profiles/traffic_mixedpb_3sat.md"),
     # the constraint statistics pass (adaptive weighting), one launch
     ("k_con_stats_tile", "mixedpb_n5000_m22500"): dict(
-        bytes=848918016, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="8f59c2710ea6f922",
+        bytes=848878592, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="0586efc5f8aa1002",
         profile="profiles/traffic_mixedpb_3sat.md"),
 }
 
