@@ -666,7 +666,7 @@ def c1_step_kernel():
 
 
 def c1_loop(steps=200, R=64, reps=20):
-    """The random 3-SAT configuration as the task states it (n = 100, m =
+    """Random 3-SAT at the phase-transition ratio (n = 100, m =
     426, 64 restarts from U[-1, 1], 200 projected-gradient steps, lr 0.1):
     the whole 200-step loop timed with CUDA events, as one CUDA graph of the
     200 steps and as one cls_step_persistent call (one CTA per tile of 32

@@ -298,8 +298,8 @@ int cls_step(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_step
              uint32_t* bits, int32_t* nsat, double* wsat, void* ws,
              size_t ws_bytes, void* stream);
 
-/* The n-step loop as ONE persistent launch (task: all restarts and all
- * constraints in one persistent launch; Sec. 3.3's lockstep batch).  Same
+/* The n-step loop as ONE persistent launch (all restarts and all
+ * constraints in one launch; Sec. 3.3's lockstep batch).  Same
  * arguments and results as cls_step (x, bits and counts bit for bit).
  * Supported when every constraint that needs FE work is a closed-form
  * product of at most 16 literals (e.g. random k-SAT); otherwise
@@ -352,8 +352,8 @@ int cls_solve_host(const cls_problem* p, int32_t R, const float* x0_host,
                    float lr, int32_t n_steps, int32_t* nsat_host,
                    float* x_host, void* ws, size_t ws_bytes, void* stream);
 
-/* The step loop as one CUDA graph (task: the step loop captured in a CUDA
- * graph; Sec. 3.3: all restarts iterate in lockstep).  cls_graph_create
+/* The step loop as one CUDA graph (Sec. 3.3: all restarts iterate in
+ * lockstep).  cls_graph_create
  * records n_steps steps exactly as cls_step would run them (same kernels,
  * same arguments, same results) on private streams and instantiates the
  * graph.  Inside a step the FE+gradient launches of the different length
@@ -382,8 +382,8 @@ int cls_graph_launch(cls_graph* g, void* stream);
 int cls_graph_kernel_count(const cls_graph* g, int64_t* n);
 int cls_graph_destroy(cls_graph* g);
 
-/* Autotuning of the FE+gradient launch shapes (task: "the segment-to-warp or
- * segment-to-block split and the tile sizes chosen by an autotuner").
+/* Autotuning of the FE+gradient launch shapes: the split of constraints
+ * over lanes and blocks and the tile sizes.
  * Constraints on the lane-group paths are bucketed by length; every bucket
  * is served by one lane-group configuration (lanes per (constraint,
  * restart) G, literal slots per lane Q, DFT or real roots, literal values in
@@ -466,8 +466,8 @@ int cls_series_range(int32_t L, int32_t K);
 int cls_step_noalloc(const cls_problem* p, int32_t R, float* x, float lr, int32_t n_steps,
                      uint32_t* bits, int32_t* nsat, double* wsat, void* stream);
 
-/* Learned initial points (task: a small message-passing network over the
- * constraint-variable incidence graph proposes initial points; the paper
+/* Learned initial points: a small message-passing network over the
+ * constraint-variable incidence graph proposes initial points (the paper
  * has no learned component).  Model, per node, hidden width 64:
  *   embed   h_v = relu(W_vin f_v + b_vin),  h_c = relu(W_cin f_c + b_cin),
  *           f_v = [1, deg/16, pos/deg, neg/deg],

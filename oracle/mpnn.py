@@ -1,6 +1,6 @@
 """Message-passing initialiser -- oracle, test-only.
 
-The paper has no learned component; this model is the task's learned
+The paper has no learned component; this model is this library's learned
 initialiser (a 2-layer message-passing network, hidden width 64, on the
 constraint-variable incidence graph) and is defined here, FP64, as the
 reference the GPU kernels are checked against.

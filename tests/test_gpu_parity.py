@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, through the C ABI.
 
-Tolerances (stated by the task's target): FE within 1e-4 absolute per
+Tolerances: FE within 1e-4 absolute per
 constraint; gradient within 1e-4 relative to its norm per restart; rounding,
 bitsets and satisfaction counts bit-exact on a given FP32 assignment; the
 projected step bit-exact given the same FP32 gradient.
