@@ -50,17 +50,18 @@ _DFT_SOURCES = ("kernels.cu", "kernels_fr.cu", "kernels_series.cu", "kernels_cor
 TRAFFIC = {
     # the DFT class over one step, mean of steps 0, 3, 6 and 9 of the run
     ("dft_class", "mixedpb_n5000_m22500"): dict(
-        bytes=239822912, R=1024, sources=_DFT_SOURCES, sha="8df346d4397e9331",
+        bytes=240030720, R=1024, sources=_DFT_SOURCES, sha="fee6c8bcc731e49d",
         profile="profiles/traffic_mixedpb_3sat.md"),
     ("k_accum_step", "mixedpb_n5000_m22500"): dict(
-        bytes=868627264, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="0586efc5f8aa1002",
+        bytes=868638656, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="93757f47d435cb76",
         profile="profiles/traffic_mixedpb_3sat.md"),
-    ("k_accum_step", "random3sat_n100_m426"): dict(
-        bytes=381726464, R=65536, sources=("kernels.cu", "kernels.cuh"), sha="0586efc5f8aa1002",
+    # few rows per variable and many restarts: four restart tiles per warp
+    ("k_accum_step_nt<4>", "random3sat_n100_m426"): dict(
+        bytes=380754176, R=65536, sources=("kernels.cu", "kernels.cuh"), sha="93757f47d435cb76",
         profile="profiles/traffic_mixedpb_3sat.md"),
     # the constraint statistics pass (adaptive weighting), one launch
     ("k_con_stats_tile", "mixedpb_n5000_m22500"): dict(
-        bytes=848878592, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="0586efc5f8aa1002",
+        bytes=848947712, R=1024, sources=("kernels.cu", "kernels.cuh"), sha="93757f47d435cb76",
         profile="profiles/traffic_mixedpb_3sat.md"),
 }
 
@@ -626,8 +627,9 @@ def tune_points(args):
 
 
 def c1_step_kernel():
-    """The fused accumulate/step/round kernel (k_accum_step) on the random
-    3-SAT instance (n = 100, m = 426) at R = 2^20 restarts, where it is
+    """The fused accumulate/step/round kernel on the random 3-SAT instance
+    (n = 100, m = 426) at R = 2^20 restarts (k_accum_step_nt<4>: about 13
+    partial rows per variable, so each warp takes four restart tiles), where it is
     HBM-bound (x is 419 MB, the partial rows 5.4 GB): mean CUDA-event time
     of the kernel over 5 eager steps after 3 warm-up steps, against its
     algorithmic bytes (partial rows read once, x read and written, the
@@ -654,8 +656,9 @@ def c1_step_kernel():
     nbytes = 4 * RT * 32 * p.info["nnz_fe"] + 8 * inst.n * R + 4 * inst.n * RT
     t = t_ms / max(n_l, 1) / 1e3
     peak = peaks().get("hbm_gbs", 6400.0)
-    tr, tr_src = recorded_traffic("k_accum_step", inst.name, R)
-    out = {"kernel": "k_accum_step", "workload": f"{inst.name}, R=2^20", "bytes": nbytes,
+    tr, tr_src = recorded_traffic("k_accum_step_nt<4>", inst.name, R)
+    out = {"kernel": "k_accum_step_nt<4> (the fused step kernel, four restart tiles per warp)",
+           "workload": f"{inst.name}, R=2^20", "bytes": nbytes,
            "us": t * 1e6, "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
            "frac": nbytes / t / 1e9 / peak, "target_frac": 0.60,
            "traffic": tr, "traffic_source": tr_src,

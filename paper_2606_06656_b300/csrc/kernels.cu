@@ -813,6 +813,80 @@ __global__ void __launch_bounds__(256) k_accum_step(int n, int R, int Rp, int RW
               bits);
 }
 
+// accum_one for NT consecutive restart tiles of one variable per warp: the
+// rows' loads of all NT tiles in flight together (NT x 128 contiguous bytes
+// per row), each tile's sum in row order as in accum_one, so the results are
+// the same bit for bit.  For variables with few rows (short clauses, many
+// restarts), where a warp per (variable, tile) spends more on its fixed
+// work than on its loads.
+template <int NT>
+__global__ void __launch_bounds__(256) k_accum_step_nt(int n, int R, int Rp, int RW,
+                                                       const int32_t* __restrict__ voff,
+                                                       const float* __restrict__ P,
+                                                       float* __restrict__ x, float lr,
+                                                       int do_step,
+                                                       const uint8_t* __restrict__ fixed,
+                                                       float* __restrict__ grad_out,
+                                                       uint32_t* __restrict__ bits) {
+  const int lane = threadIdx.x;
+  const int tile0 = blockIdx.x * NT;
+  for (int v = blockIdx.y * blockDim.y + threadIdx.y; v < n; v += gridDim.y * blockDim.y) {
+    const int k0 = voff[v], k1 = voff[v + 1];
+    float g[NT];
+    bool act[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      g[t] = 0.f;
+      act[t] = tile0 + t < RW && (tile0 + t) * 32 + lane < R;
+    }
+    const float* p = P + (size_t)k0 * Rp + (size_t)tile0 * 32 + lane;
+    int k = k0;
+    for (; k + 2 <= k1; k += 2, p += 2 * (size_t)Rp) {
+      float a[NT], b[NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        a[t] = act[t] ? p[t * 32] : 0.f;
+        b[t] = act[t] ? p[(size_t)Rp + t * 32] : 0.f;
+      }
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        g[t] += a[t];
+        g[t] += b[t];
+      }
+    }
+    for (; k < k1; ++k, p += Rp) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (act[t]) g[t] += p[t * 32];
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int tile = tile0 + t;
+      if (tile >= RW) break;
+      const int r = tile * 32 + lane;
+      if (grad_out && act[t]) grad_out[(size_t)v * R + r] = g[t];
+      if (do_step) {
+        float xv = 0.f;
+        if (act[t]) {
+          xv = x[(size_t)v * R + r];
+          if (!(fixed && fixed[v])) {
+            xv = pgd_project(xv, g[t], lr);
+            x[(size_t)v * R + r] = xv;
+          }
+        }
+        const uint32_t bw = __ballot_sync(kFull, act[t] && xv < 0.0f);
+        if (bits && lane == 0) bits[(size_t)v * RW + tile] = bw;
+      }
+    }
+  }
+}
+
+// tiles per warp of the accumulate kernel: four when the variables have few
+// partial rows on average and there are tiles enough to fill the GPU
+inline int accum_tiles_per_warp(const DevPlan& d, int RT) {
+  return (d.nnz_fe < (int64_t)16 * d.n && RT >= 4 * 148) ? 4 : 1;
+}
+
 __global__ void __launch_bounds__(256) k_pgd(int n, int R, int RW, float* __restrict__ x,
                                              const float* __restrict__ grad, float lr,
                                              int do_step, const uint8_t* __restrict__ fixed,
@@ -1971,8 +2045,14 @@ cudaError_t launch_accum_step(const DevPlan& d, int R, int Rp, const float* P, f
                               cudaStream_t s, LaunchHook* h) {
   if (d.n == 0 || R == 0) return cudaSuccess;
   const int RT = ceil_div(R, 32);
-  dim3 grid(RT, std::min(ceil_div(d.n, 8), 65535)), block(32, 8);
   HookScope hs(h, KC_ACCUM, s);
+  if (accum_tiles_per_warp(d, RT) == 4) {
+    dim3 grid(ceil_div(RT, 4), std::min(ceil_div(d.n, 8), 65535)), block(32, 8);
+    k_accum_step_nt<4><<<grid, block, 0, s>>>(d.n, R, Rp, RT, d.fe_voff, P, x, lr,
+                                              do_step ? 1 : 0, d.fixed, grad_out, bits);
+    return cudaGetLastError();
+  }
+  dim3 grid(RT, std::min(ceil_div(d.n, 8), 65535)), block(32, 8);
   k_accum_step<<<grid, block, 0, s>>>(d.n, R, Rp, RT, d.fe_voff, P, x, lr, do_step ? 1 : 0,
                                       d.fixed, grad_out, bits);
   return cudaGetLastError();

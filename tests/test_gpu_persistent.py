@@ -49,6 +49,9 @@ CASES = [
     ("tile_3sat_c1", lambda: W.random_ksat(n=100, m=426, seed=11), 64, 200),
     ("tile_3sat_ragged", lambda: W.random_ksat(n=100, m=426, seed=12), 50, 30),
     ("tile_3sat_many_tiles", lambda: W.random_ksat(n=100, m=426, seed=13), 2000, 12),
+    # many restarts of few-row variables: cls_step's accumulate takes four
+    # restart tiles per warp (a ragged last group of tiles and restarts)
+    ("tile_3sat_wide", lambda: W.random_ksat(n=100, m=426, seed=16), 20003, 4),
     ("tile_or_xor_nae_weighted",
      lambda: W.random_constraint_set(np.random.default_rng(14), 150, 150,
                                      [W.TYPE_OR, W.TYPE_XOR, W.TYPE_NAE], (1, 16),
